@@ -1,0 +1,410 @@
+#!/usr/bin/env python3
+"""Benchmark of the permutation-avoiding FFT convolution on GB300.
+
+One step = one whole convolution y = conj(A)((A^T x) o Hhat) of the flagship
+workload (3-D periodic convolution 128^3, complex FP32, radix 4 -> stage list
+[4,4,4,2] per axis, Gaussian filter spectrum resident), inputs resident in
+HBM, L2 flushed (512 MiB write) before every step outside the timed events.
+
+Metric: GB/s of compulsory traffic B = 3 N S per convolution (read x, read
+the resident spectrum, write y; N = 128^3, S = 8 bytes), next to the same GPU
+running the permuted form (same kernels plus explicit index-reversal passes)
+and a cuFFT-based convolution, with the CPU oracle timed on the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pac|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs an
+independent replica on its own GPU; value = all ranks' bytes / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "perm-free conv GB/s & %HBM roofline vs permuted path; served p50/p99 latency"
+UNIT = "GB/s"
+FLUSH_BYTES = 512 << 20
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["pac", "reference"], default="pac")
+    ap.add_argument("--radix", type=int, default=4)
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--n", type=int, default=128, help="edge of the 3-D cube")
+    ap.add_argument("--quick", action="store_true", help="main leg only (for profiler runs)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ ranks
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(local_ms: float, local_units: float, world: int, device=None):
+    """Max time and summed work over ranks (replicas): returns (max_ms, total_units)."""
+    if world <= 1:
+        return local_ms, local_units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []  # (t, sm_mhz, max_mhz, reasons)
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm, mx = float(parts[1]), float(parts[2])
+            except ValueError:
+                continue
+            reasons = []
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                                 parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.append(name)
+            self.samples.append((time.time(), sm, mx, reasons))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        inside = [s for s in self.samples if t0 <= s[0] <= t1]
+        note = None
+        if not inside:  # the timed window fell between two samples: take the nearest
+            inside = [min(self.samples, key=lambda s: min(abs(s[0] - t0), abs(s[0] - t1)))]
+            note = "nearest sample to the timed window"
+        reasons = sorted({r for s in inside for r in s[3]})
+        out = {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": max(s[2] for s in inside),
+               "reasons": reasons, "samples": len(inside)}
+        if note:
+            out["note"] = note
+        return out
+
+
+# ------------------------------------------------------------------ timing
+
+
+def time_steps(torch, fn, steps, warmup, flush, stream):
+    """Run warmup + steps calls of fn on `stream`, flushing L2 before each;
+    returns per-step device times (ms) from CUDA events on that stream."""
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            flush()
+            fn()
+        stream.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        for i in range(steps):
+            flush()
+            starts[i].record(stream)
+            fn()
+            ends[i].record(stream)
+        stream.synchronize()
+    return [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2506_12718_gb300", "csrc", "*"))):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = data.get(workload, {}).get(kernel)
+    if not ent or ent.get("source_hash") != source_hash():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def measured_peak_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- the legs
+
+
+def workload_name(a):
+    return (f"3-D periodic convolution {a.n}^3, complex {'FP32' if a.dtype == 'c64' else 'FP64'}, radix {a.radix}, "
+            f"periodised Gaussian sigma=4 filter spectrum resident")
+
+
+def cpu_baseline_leg(a):
+    """The FP64 oracle as it stands on the host cores: the separable per-axis
+    definition (O2) over the full cube, one run."""
+    import numpy as np  # noqa: F401
+
+    import oracle
+    import pac_inputs as pin
+    c = pin.c2(a.radix, a.dtype, a.n)
+    x, (_, fs) = pin.make_x(c), pin.make_h(c)
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.conv_separable(fs, x)
+    dt = time.perf_counter() - t0
+    B = 3 * c.n_total * c.elem_bytes
+    return {"value": B / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"one full {a.n}^3 separable-direct convolution (oracle route O2, FP64, OpenMP), "
+                      f"{dt:.2f} s; GB/s = 3*N*S / time"}
+
+
+def reference_arm(a):
+    """--impl reference: the oracle timed as it stands, each step a bounded
+    sample of the workload: the direct definition (O1) at 64 seeded output
+    points of the 128^3 cube, scaled to a whole convolution's bytes."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle
+    import pac_inputs as pin
+    oracle.build()
+    c = pin.c2(a.radix, a.dtype, a.n)
+    x, (h, _) = pin.make_x(c), pin.make_h(c)
+    npts = 64
+    B = 3 * c.n_total * c.elem_bytes
+    frac = npts / c.n_total
+    for w in range(a.warmup):
+        oracle.conv_direct_points(h, x, pin.sample_points(c.n_total, npts, seed=100 + w))
+    ts = []
+    for k in range(a.steps):
+        idx = pin.sample_points(c.n_total, npts, seed=1000 + k)
+        t0 = time.perf_counter()
+        oracle.conv_direct_points(h, x, idx)
+        ts.append(time.perf_counter() - t0)
+    tot = sum(ts)
+    value = a.steps * B * frac / tot / 1e9
+    sample = (f"direct definition (oracle route O1, FP64, compensated sums) at {npts} seeded output points "
+              f"per step of the {a.n}^3 cube; GB/s scaled by the computed fraction of outputs")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "dims": [a.n] * 3, "radix": a.radix},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+def main(argv=None):
+    a = parse_args(argv)
+    world, rank, local = dist_env()
+    if a.impl == "reference":
+        line = reference_arm(a)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return 0
+
+    import numpy as np
+    import torch
+
+    import pac_inputs as pin
+    import paper_2506_12718_gb300 as pac
+    from paper_2506_12718_gb300 import _build
+
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    pac.load()
+
+    c = pin.c2(a.radix, a.dtype, a.n)
+    x_np, (h_np, _) = pin.make_x(c), pin.make_h(c)
+    N, S = c.n_total, c.elem_bytes
+    B = 3 * N * S
+    x = torch.from_numpy(x_np).to(dev)
+    h = torch.from_numpy(h_np).to(dev)
+    y = torch.empty_like(x)
+    flush_buf = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+
+    def flush():
+        flush_buf.fill_(1)
+
+    plan = pac.Plan(c.dims, c.radix, c.dtype)
+    plan.filter_spectrum(h)
+    launches = plan.query(pac.Q_LAUNCHES_CONVOLVE)
+
+    sampler = ClockSampler(torch.cuda.current_device()).start() if rank == 0 else None
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ms = time_steps(torch, lambda: pac.pac_convolve(plan.handle, x, y, sh), a.steps, a.warmup, flush, stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    barrier(world)
+    tot_ms, tot_bytes = aggregate(sum(ms), a.steps * B, world, dev)
+    value = tot_bytes / (tot_ms * 1e-3) / 1e9
+    ms_per_step = tot_ms / a.steps
+
+    peak, peak_kind = measured_peak_hbm()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if a.dtype == "c64" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "dims": list(c.dims), "radix": a.radix,
+                       "stages_per_axis": plan.stages(0), "bytes_per_step": B,
+                       "l2": f"flushed before every step ({FLUSH_BYTES >> 20} MiB write, outside the timed events)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "pct_hbm_roofline": value / world / peak, "gpu_launches": a.steps * launches,
+            "launches_per_step": launches}
+
+    if not a.quick:
+        # per-kernel times inside the same kind of step (events around each launch)
+        per = {}
+        with torch.cuda.stream(stream):
+            for k in range(max(5, min(a.steps, 50))):
+                flush()
+                for name, t in pac.pac_convolve_timed(plan.handle, 0, x, y, sh):
+                    per.setdefault(name, []).append(t)
+        shares = {k: sum(v) for k, v in per.items()}
+        dom = max(shares, key=shares.get)
+        nlaunch = len(per[dom]) / max(5, min(a.steps, 50))
+        avg_ms = sum(per[dom]) / len(per[dom])
+        alg_bytes = (3 if dom.startswith("fused") else 2) * N * S
+        achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+        line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
+                            "traffic": ncu_traffic(dom, "c2"), "alg_bytes_per_launch": alg_bytes,
+                            "avg_launch_ms": avg_ms, "launches_per_step": nlaunch}
+        line["kernel_ms_per_step"] = {k: sum(v) / max(5, min(a.steps, 50)) for k, v in per.items()}
+
+        # the permuted form on the same GPU, same bytes B
+        msp = time_steps(torch, lambda: pac.pac_convolve_permuted(plan.handle, x, y, sh), a.steps, a.warmup, flush,
+                         stream)
+        tp, _ = aggregate(sum(msp), 0, world, dev)
+        line["permuted"] = {"value": world * a.steps * B / (tp * 1e-3) / 1e9, "unit": UNIT,
+                            "ms_per_step": tp / a.steps, "launches_per_step": plan.query(pac.Q_LAUNCHES_PERMUTED)}
+        line["speedup_vs_permuted"] = (tp / a.steps) / ms_per_step
+
+        # cuFFT-based convolution (torch.fft on the same buffers), spectrum precomputed
+        Hn = torch.fft.fftn(h)
+        yc = torch.empty_like(x)
+
+        def cufft_step():
+            torch.fft.ifftn(torch.fft.fftn(x) * Hn, out=yc)
+
+        msc = time_steps(torch, cufft_step, a.steps, a.warmup, flush, stream)
+        tc, _ = aggregate(sum(msc), 0, world, dev)
+        line["cufft"] = {"value": world * a.steps * B / (tc * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": tc / a.steps,
+                         "note": "torch.fft (cuFFT) fftn -> product -> ifftn, reported baseline"}
+
+        # end to end through the public C-ABI call with HOST buffers (pinned)
+        xh = torch.from_numpy(x_np.copy()).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        mse = time_steps(torch, lambda: pac.pac_convolve_host(plan.handle, xh, yh, sh), max(10, a.steps // 4),
+                         a.warmup, flush, stream)
+        te, _ = aggregate(sum(mse), 0, world, dev)
+        ke = max(10, a.steps // 4)
+        line["e2e"] = {"value": world * ke * B / (te * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": N * S,
+                       "d2h_bytes_per_step": N * S, "ms_per_step": te / ke,
+                       "call": "pac_convolve_host (pinned host x -> device -> convolve -> host y)"}
+        ref = None
+        if rank == 0:
+            ref = yc.cpu().numpy()
+            err = float(np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref))
+            line["check_vs_cufft_rel_l2"] = err
+
+    if sampler:
+        sampler.stop()
+        line["clocks"] = sampler.summary(t_wall0, t_wall1)
+    if rank == 0 and world == 1 and not a.no_cpu and not a.quick:
+        line["cpu_baseline"] = cpu_baseline_leg(a)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

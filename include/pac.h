@@ -1,0 +1,212 @@
+/*
+ * pac.h — permutation-avoiding FFT convolution on one GB300 (sm_103a).
+ *
+ * The library computes the d-dimensional circular convolution
+ *
+ *     y = F_h(x) = DFT^-1( DFT(h) o DFT(x) ),   n_1 x ... x n_d,  d in {1,2,3}
+ *
+ * (the convolution operator of the paper's Section 2, eq. "convolution";
+ * 2-D form Section 3; d-D form Section 4) without ever executing an
+ * index-reversal permutation: the forward transform is the decimation-in-
+ * frequency product A^T (natural order in, index-reversed order out), the
+ * filter spectrum A^T h is stored once in that index-reversed order, and the
+ * inverse is the conjugate decimation-in-time product conj(A) (reversed in,
+ * natural out), Eq. (35) in 1-D, Eq. (80) in 2-D and the d-D form of
+ * Section 4.1.  Per axis, n = r^t or a mixed-radix product (Section 6.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Arrays are complex, interleaved (re, im), row-major with the last index
+ *    fastest (the row-major vec of Section 4), dense, 16-byte aligned.
+ *    dtype PAC_C64 = complex float (8 bytes/element), PAC_C128 = complex
+ *    double (16 bytes/element).
+ *  - Pointers named *_dev are device pointers on the current CUDA device;
+ *    pointers named *_host are host pointers (pinned memory gives the fastest
+ *    copies).  The caller owns every array it passes; the library owns plans,
+ *    queues, twiddle/index tables, filter spectra and its staging buffers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls that take a stream only enqueue work; they do not
+ *    synchronise unless stated.
+ *  - Every function returns a pac_status (0 = PAC_OK).  Nothing throws and no
+ *    kernel traps.  pac_last_error() returns a thread-local message for the
+ *    last failing call of the calling thread.  Asynchronous device faults
+ *    surface at a later call or synchronisation as PAC_ERR_CUDA.
+ *  - Forward sign: w_n = exp(-2 pi i / n) (Section 2).  The inverse applies
+ *    1/N once (N = n_1 ... n_d), folded into the stored filter spectrum.
+ */
+#ifndef PAC_H
+#define PAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pac_plan_s* pac_plan;   /* opaque, library-owned */
+typedef struct pac_queue_s* pac_queue; /* opaque, library-owned */
+
+typedef enum { PAC_C64 = 0, PAC_C128 = 1 } pac_dtype;
+
+typedef enum {
+    PAC_OK = 0,
+    PAC_PENDING = 1,          /* pac_poll: request not finished yet */
+    PAC_ERR_ARG = -1,         /* null pointer, bad enum, misaligned pointer */
+    PAC_ERR_SIZE = -2,        /* a dim is not a power of the radix's prime, or too large */
+    PAC_ERR_NO_SPECTRUM = -3, /* pac_convolve before pac_filter_spectrum */
+    PAC_ERR_NOMEM = -4,       /* device or host allocation failed / over budget */
+    PAC_ERR_CUDA = -5,        /* a CUDA runtime call failed */
+    PAC_ERR_BUSY = -6,        /* request queue full */
+    PAC_ERR_TIMEOUT = -7,     /* a bounded wait gave up */
+    PAC_ERR_NOT_FOUND = -8    /* unknown ticket */
+} pac_status;
+
+/* ------------------------------------------------------------------ plans */
+
+/*
+ * Create a plan for d-D convolutions of shape dims[0] x ... x dims[ndim-1].
+ * ndim in {1,2,3}; radix in {2,3,4,5,8}.  Each dim must be a power of the
+ * radix's prime p (p = 2 for radix 4 and 8).  The per-axis decimation-in-
+ * frequency stage list is [r, r, ..., r] (Section 2.1); when the exponent is
+ * not a multiple of log_p r the leftover factor becomes one smaller stage of
+ * base p placed last (e.g. 128 with radix 4 -> [4,4,4,2]; with radix 8 ->
+ * [8,8,2]), the mixed-radix framework of Section 6.1.  A dim of 1 is allowed
+ * (empty stage list).  Builds twiddle tables in FP64, rounds them once to
+ * dtype and uploads them to the current device.  On success *out owns device
+ * memory until pac_plan_destroy.  Errors: PAC_ERR_ARG, PAC_ERR_SIZE,
+ * PAC_ERR_NOMEM, PAC_ERR_CUDA.
+ */
+int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, pac_plan* out);
+
+/* Release a plan and everything it owns. Waits for the plan's pending work. */
+int pac_plan_destroy(pac_plan p);
+
+/*
+ * Algorithm 11, line 1: store Hhat = A^T h / N (all axes, index-reversed
+ * order, with the inverse's 1/N folded in) in plan-owned device memory.
+ * h_dev is read, not retained.  Synchronises the plan's internal stream.
+ * Calling it again replaces the spectrum.
+ */
+int pac_filter_spectrum(pac_plan p, const void* h_dev);
+
+/*
+ * Algorithm 11, lines 2-4 (permutation-avoiding convolution, Eq. 35/80):
+ * y = conj(A)((A^T x) o Hhat).  x_dev and y_dev hold N elements of the plan's
+ * dtype; y_dev may equal x_dev (in place).  y_dev is also the working buffer
+ * of the intermediate passes.  Asynchronous on `stream`.
+ * Errors: PAC_ERR_ARG, PAC_ERR_NO_SPECTRUM, PAC_ERR_CUDA.
+ */
+int pac_convolve(pac_plan p, const void* x_dev, void* y_dev, void* stream);
+
+/*
+ * As pac_convolve, with x and y in HOST memory: copies x to plan-owned
+ * device staging, convolves, copies y back, all on `stream`, then
+ * synchronises `stream`.  The end-to-end form of the call.
+ */
+int pac_convolve_host(pac_plan p, const void* x_host, void* y_host, void* stream);
+
+/*
+ * Many independent convolutions in one call: plans[i] applied to x_dev[i] ->
+ * y_dev[i] for i < count.  Work of all instances is merged into one launch
+ * per pass level (instances grouped by kernel shape), so a batch of any mix
+ * of shapes costs a handful of launches; the launch sequence is recorded once
+ * per distinct batch and replayed as a CUDA graph.  Plans may repeat.  Each
+ * plan needs its spectrum.  Asynchronous on `stream`.
+ */
+int pac_convolve_many(int count, const pac_plan* plans, const void* const* x_dev, void* const* y_dev,
+                      void* stream);
+
+/* ----------------------------------------------------------------- serving */
+
+/*
+ * A request queue with continuous batching.  Requests (plan, x_dev, y_dev)
+ * are admitted in arrival order while (a) fewer than max_inflight are
+ * running and (b) the device bytes of running requests (2 * N * elem size
+ * each) stay within hbm_budget_bytes and cudaMemGetInfo's free memory; a
+ * request that does not fit waits (it is never dropped).  Admitted requests
+ * run on a pool of streams so their kernels overlap on the device.  Plans
+ * and spectra stay resident; the queue does not own them.
+ */
+int pac_queue_create(size_t hbm_budget_bytes, int max_inflight, pac_queue* out);
+
+/* Enqueue one request; returns a ticket. PAC_ERR_BUSY when 65536 requests are waiting. */
+int pac_submit(pac_queue q, pac_plan p, const void* x_dev, void* y_dev, uint64_t* ticket);
+
+/*
+ * Non-blocking completion check.  Returns PAC_OK (done; *latency_us, if not
+ * NULL, is submit-to-completion time in microseconds), PAC_PENDING, or an
+ * error (PAC_ERR_NOT_FOUND for an unknown or already-reaped ticket, or the
+ * request's own failure status).  A finished ticket is reaped by the first
+ * poll that returns its final status.
+ */
+int pac_poll(pac_queue q, uint64_t ticket, double* latency_us);
+
+/* Block until every submitted request has finished (bounded wait: timeout_ms). */
+int pac_queue_drain(pac_queue q, int timeout_ms);
+
+/* Drain and free the queue. */
+int pac_queue_destroy(pac_queue q);
+
+/* Thread-local message describing the last failing call of this thread. */
+const char* pac_last_error(void);
+
+/* --------------------------------------------------------------- test hooks */
+
+/* Per-axis DIF stage list of a plan: radices[0..*count), s_1 first (full length). */
+int pac_plan_stages(pac_plan p, int axis, int* radices, int* count);
+
+/*
+ * Per-axis index-reversal table of a plan: pos_to_freq[p] = the frequency that
+ * the unordered (A^T) output holds at position p along that axis (F = P A^T,
+ * Section 2.1; F = P_rho A_rho^T, Section 6.1).  Host copy of dims[axis] entries.
+ */
+int pac_plan_reverse_table(pac_plan p, int axis, int64_t* pos_to_freq);
+
+/* Unordered forward transform only: xhat = A^T x (all axes), Algorithms 2-4 (uFFT2). */
+int pac_forward_unordered(pac_plan p, const void* x_dev, void* xhat_dev, void* stream);
+
+/*
+ * Comparator, the standard FFT-based convolution (Algorithm 10): the same
+ * stage kernels plus explicit index-reversal permutation passes (Algorithm 1)
+ * after the forward transform and before the inverse (FFT2 of Algorithm 5 and
+ * iFFT of Algorithm 9), with the filter spectrum kept in natural order.
+ * Uses a plan-owned scratch buffer of N elements.  Asynchronous on `stream`.
+ */
+int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev, void* stream);
+
+/*
+ * Profiling form of pac_convolve (which = 0) or pac_convolve_permuted
+ * (which = 1): the same launches, with a CUDA event recorded on `stream`
+ * before and after each one; synchronises `stream` and writes each launch's
+ * device time (ms) to launch_ms[0..*n_launches) and a kernel id to
+ * kernel_ids[] (0 = forward DIF pass, 1 = fused DIF+product+DIT pass,
+ * 2 = inverse DIT pass, 3 = permutation, 4 = pointwise product).
+ * max_launches bounds both arrays; PAC_ERR_ARG if it is too small.
+ */
+int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, void* stream, int max_launches,
+                       float* launch_ms, int* kernel_ids, int* n_launches);
+
+/* Plan facts for benches and tests: see PAC_Q_* keys. */
+int pac_plan_query(pac_plan p, int key, int64_t* value);
+enum {
+    PAC_Q_NDIM = 0,
+    PAC_Q_N_TOTAL = 1,            /* N */
+    PAC_Q_ELEM_BYTES = 2,         /* 8 or 16 */
+    PAC_Q_LAUNCHES_CONVOLVE = 3,  /* kernel launches per pac_convolve */
+    PAC_Q_LAUNCHES_PERMUTED = 4,  /* kernel launches per pac_convolve_permuted */
+    PAC_Q_LAUNCHES_FORWARD = 5,   /* kernel launches per pac_forward_unordered */
+    PAC_Q_DEVICE_BYTES = 6,       /* device memory the plan owns */
+    PAC_Q_HAS_SPECTRUM = 7
+};
+
+/* Host-only helpers (no device needed): the stage list and reversal table rules. */
+int pac_stage_list(int64_t n, int radix, int* radices, int* count);
+int pac_reverse_table(int nstages, const int* radices, int64_t* pos_to_freq);
+
+/* Library version string. */
+const char* pac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAC_H */

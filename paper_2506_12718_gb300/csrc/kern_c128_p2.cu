@@ -1,0 +1,23 @@
+// Pass-kernel instantiations: double2, group sizes that are powers of 2.
+#include "kern_launch.cuh"
+
+namespace pac {
+
+cudaError_t launch_pass_c128_p2(int M, const PassArgs& a, cudaStream_t s) {
+    switch (M) {
+        case 2: return launch_M<double2, 2>(a, s);
+        case 4: return launch_M<double2, 4>(a, s);
+        case 8: return launch_M<double2, 8>(a, s);
+        case 16: return launch_M<double2, 16>(a, s);
+        case 32: return launch_M<double2, 32>(a, s);
+        case 64: return launch_M<double2, 64>(a, s);
+        case 128: return launch_M<double2, 128>(a, s);
+        case 256: return launch_M<double2, 256>(a, s);
+        case 512: return launch_M<double2, 512>(a, s);
+        case 1024: return launch_M<double2, 1024>(a, s);
+        case 2048: return launch_M<double2, 2048>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pac

@@ -1,0 +1,80 @@
+// Internal declarations of the pac library (host side).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pac.h"
+#include "config.h"
+#include "pass_args.h"
+
+namespace pac {
+
+// One group of consecutive DIF stages of one axis, executed by one pass.
+struct GroupPlan {
+    int axis = 0;
+    int M = 1;              // product of the group's stage radices
+    int first_stage = 0;    // index into the axis' stage list
+    int nstages = 0;
+    int64_t L = 1;          // block length (axis units) at the group's start
+    int64_t Lp = 1;         // L / M
+    int64_t C = 1;          // row stride in elements = Lp * I
+    int64_t I = 1;          // product of the dims after the axis
+    int64_t Q = 1;          // columns = N / M
+    int tw_T = 1, tw_shift = 0;
+    bool has_ext = false;
+    size_t off_twi = 0, off_lo = 0, off_hi = 0, off_rowmap = 0, off_freq = 0;  // byte offsets in tables
+};
+
+void set_error(const char* fmt, ...);
+int fail(int status, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+// exp(-2 pi i e / L) in FP64 with the angle reduced exactly to an eighth turn
+void root_fp64(int64_t e, int64_t L, double* re, double* im);
+
+// kernel launchers (kern_c64.cu / kern_c128.cu)
+cudaError_t launch_pass_c64(int M, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_pass_c128(int M, const PassArgs& a, cudaStream_t s);
+int pass_kernel_supported(int M, int esize);
+
+// auxiliary kernels (aux.cu)
+cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64_t* const* idx_dev,
+                           const void* src, void* dst, const void* mul, cudaStream_t s);
+cudaError_t launch_pointwise_mul(int esize, int64_t n, const void* a, const void* b, void* out, double scale,
+                                 cudaStream_t s);
+
+int device_sm_count(int device);
+
+}  // namespace pac
+
+struct pac_plan_s {
+    int ndim = 0;
+    int64_t dims[3] = {1, 1, 1};
+    int radix = 2;
+    pac_dtype dtype = PAC_C64;
+    int esize = 8;
+    int64_t N = 1;
+    int device = 0;
+    std::vector<std::vector<int>> stages;          // per axis, DIF order
+    std::vector<std::vector<int64_t>> pos_to_freq; // per axis
+    std::vector<pac::GroupPlan> groups;            // forward order
+    void* d_tables = nullptr;
+    size_t tables_bytes = 0;
+    void* d_spec = nullptr;       // A^T h / N, index-reversed order
+    bool has_spec = false;
+    // comparator (permuted form) state, created on first use
+    void* d_spec_nat = nullptr;   // DFT(h) / N in natural order
+    void* d_scratch = nullptr;    // N elements
+    int64_t* d_perm = nullptr;    // per axis: [pos_to_freq | freq_to_pos], 2 * dims[a] each
+    // host-buffer convolution staging, created on first use
+    void* d_stage = nullptr;      // 2 N elements
+    std::mutex mu;
+    size_t device_bytes = 0;
+
+    int64_t bytes() const { return N * esize; }
+};

@@ -1,0 +1,32 @@
+// Arguments of one pass kernel launch (shared by host and device code).
+#pragma once
+#include <stdint.h>
+
+namespace pac {
+
+enum PassMode : int { kFwd = 0, kInv = 1, kFused = 2 };
+
+// One pass over the array, viewed as [beta][m][c]: m in [0, M) is the group
+// axis (row stride C elements); column q = beta * C + c, Q = N / M columns.
+// Element (row g, column q) sits at (q - q mod C) * M + q mod C + g * C.
+struct PassArgs {
+    const void* src;
+    void* dst;              // may equal src (in place)
+    const void* spec;       // filter spectrum (kFused), same layout as the DIF output
+    const void* tw_int;     // w_M^u, u in [0, M): round twiddles
+    const void* tw_lo;      // w_L^u, u in [0, T)       (external factor, two-level)
+    const void* tw_hi;      // w_L^{T v}, v in [0, ceil(L/T))
+    const int* rowmap;      // [M] shared-memory row that holds global row g after the rounds
+    const int* freq;        // [M] group frequency k' held by global row g
+    int64_t Q;              // columns
+    int64_t C;              // row stride in elements
+    int64_t I;              // inner stride of the axis: column j = (q mod C) / I
+    int64_t tiles;          // ceil(Q / W)
+    int tw_T;               // two-level split of the external exponent e = hi * T + lo
+    int tw_shift;           // log2(tw_T) when tw_T is a power of two, else -1
+    int mode;               // PassMode
+    int has_ext;            // apply w_L^{j k'} (L' > 1)
+    double scale;           // applied on store in kFwd (filter spectrum 1/N); 1 = none
+};
+
+}  // namespace pac

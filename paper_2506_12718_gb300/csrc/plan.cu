@@ -1,0 +1,699 @@
+// Plan builder and the plan-level C-ABI entry points.
+//
+// A plan fixes, per axis, the decimation-in-frequency stage list (Section 2.1
+// for a uniform radix; the mixed-radix framework of Section 6.1 for the
+// leftover stage), splits it into groups that one CTA can transform in shared
+// memory, and builds every table the pass kernels read: round twiddles
+// w_M^u, the two-level external twiddles w_L^e, and per group the placement
+// of each frequency (the digit-reversed position of the group's stages).
+// Twiddles are computed in FP64 on the host and rounded once to the plan's
+// precision.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "pac_internal.h"
+
+namespace pac {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+int fail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return PAC_ERR_CUDA;
+}
+
+void root_fp64(int64_t e, int64_t L, double* re, double* im) {
+    e %= L;
+    if (e < 0) e += L;
+    bool conj = false;
+    if (2 * e > L) {  // w^e = conj(w^(L-e))
+        e = L - e;
+        conj = true;
+    }
+    const double two_pi = 6.283185307179586476925286766559;
+    double c, s;
+    if (8 * e <= L) {
+        const double a = two_pi * (double)e / (double)L;
+        c = std::cos(a);
+        s = std::sin(a);
+    } else if (8 * e <= 3 * L) {  // cos(2 pi f) = sin(2 pi (1/4 - f))
+        const double a = two_pi * (double)(L - 4 * e) / (double)(4 * L);
+        c = std::sin(a);
+        s = std::cos(a);
+    } else {  // cos(2 pi f) = -cos(2 pi (1/2 - f))
+        const double a = two_pi * (double)(L - 2 * e) / (double)(2 * L);
+        c = -std::cos(a);
+        s = std::sin(a);
+    }
+    *re = c;
+    *im = conj ? s : -s;
+}
+
+int device_sm_count(int device) {
+    static int cache[64] = {0};
+    if (device < 0 || device >= 64) return 132;
+    if (cache[device] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 132;
+        cache[device] = v;
+    }
+    return cache[device];
+}
+
+static int prime_of(int radix) {
+    switch (radix) {
+        case 2: case 4: case 8: return 2;
+        case 3: return 3;
+        case 5: return 5;
+        default: return 0;
+    }
+}
+
+static int exact_log(int64_t n, int p) {
+    int e = 0;
+    while (n > 1 && n % p == 0) {
+        n /= p;
+        ++e;
+    }
+    return n == 1 ? e : -1;
+}
+
+// DIF stage list of an axis: [r]*(e/f) then a leftover stage p^(e mod f).
+static int stage_list(int64_t n, int radix, std::vector<int>& out) {
+    out.clear();
+    const int p = prime_of(radix);
+    if (p == 0) return fail(PAC_ERR_ARG, "radix %d not in {2,3,4,5,8}", radix);
+    if (n < 1) return fail(PAC_ERR_SIZE, "dimension %lld < 1", (long long)n);
+    const int e = exact_log(n, p);
+    if (e < 0) return fail(PAC_ERR_SIZE, "dimension %lld is not a power of %d (radix %d)", (long long)n, p, radix);
+    const int f = exact_log(radix, p);
+    for (int i = 0; i < e / f; ++i) out.push_back(radix);
+    if (e % f) out.push_back(ipow(p, e % f));
+    return PAC_OK;
+}
+
+// Position -> frequency of a DIF stage list s_1..s_T: frequency
+// k = k_1 + s_1 k_2 + s_1 s_2 k_3 + ... sits at p = sum_i k_i prod_{j>i} s_j.
+static void reverse_table(const int* st, int T, int64_t* p2f) {
+    int64_t n = 1;
+    for (int i = 0; i < T; ++i) n *= st[i];
+    std::vector<int64_t> suffix(T + 1, 1);
+    for (int i = T - 1; i >= 0; --i) suffix[i] = suffix[i + 1] * st[i];
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t rem = k, pos = 0;
+        for (int i = 0; i < T; ++i) {
+            pos += (rem % st[i]) * suffix[i + 1];
+            rem /= st[i];
+        }
+        p2f[pos] = k;
+    }
+}
+
+// Split an axis' stage list into consecutive groups with product <= the
+// largest column one CTA handles, balanced in size.
+static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st, int p, int esize) {
+    std::vector<std::pair<int, int>> out;
+    const int T = (int)st.size();
+    if (T == 0) return out;
+    std::vector<int> ex(T);
+    int etot = 0;
+    for (int i = 0; i < T; ++i) {
+        ex[i] = exact_log(st[i], p);
+        etot += ex[i];
+    }
+    const int emax = exact_log(group_mmax(p, esize), p);
+    int ngroups = (etot + emax - 1) / emax;
+    int i = 0, erem = etot;
+    for (int gi = 0; gi < ngroups && i < T; ++gi) {
+        const int target = (erem + (ngroups - gi) - 1) / (ngroups - gi);
+        int acc = 0, first = i;
+        while (i < T && (acc == 0 || acc + ex[i] <= std::min(target, emax))) {
+            acc += ex[i];
+            ++i;
+        }
+        if (gi == ngroups - 1) {  // the last group takes the rest
+            while (i < T) acc += ex[i++];
+        }
+        out.push_back({first, i - first});
+        erem -= acc;
+    }
+    while (i < T) {  // defensive: any leftover becomes one more group
+        out.push_back({i, T - i});
+        i = T;
+    }
+    return out;
+}
+
+}  // namespace pac
+
+using namespace pac;
+
+// ------------------------------------------------------------- host helpers
+
+extern "C" int pac_stage_list(int64_t n, int radix, int* radices, int* count) {
+    if (!count) return fail(PAC_ERR_ARG, "null count");
+    std::vector<int> st;
+    int rc = stage_list(n, radix, st);
+    if (rc) return rc;
+    if (radices) {
+        if (*count < (int)st.size()) return fail(PAC_ERR_ARG, "radices array too small (%d < %d)", *count, (int)st.size());
+        std::copy(st.begin(), st.end(), radices);
+    }
+    *count = (int)st.size();
+    return PAC_OK;
+}
+
+extern "C" int pac_reverse_table(int nstages, const int* radices, int64_t* pos_to_freq) {
+    if (nstages < 0 || (nstages > 0 && !radices) || !pos_to_freq) return fail(PAC_ERR_ARG, "bad arguments");
+    for (int i = 0; i < nstages; ++i)
+        if (radices[i] < 2) return fail(PAC_ERR_ARG, "radix %d < 2", radices[i]);
+    reverse_table(radices, nstages, pos_to_freq);
+    return PAC_OK;
+}
+
+extern "C" const char* pac_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* pac_version(void) { return "pac 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------- plans
+
+namespace {
+
+template <typename V, typename T>
+void put_root(std::vector<unsigned char>& blob, size_t off, int64_t idx, int64_t e, int64_t L) {
+    double re, im;
+    root_fp64(e, L, &re, &im);
+    V v;
+    v.x = (T)re;
+    v.y = (T)im;
+    std::memcpy(blob.data() + off + idx * sizeof(V), &v, sizeof(V));
+}
+
+size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+}  // namespace
+
+static void free_plan(pac_plan p) {
+    if (!p) return;
+    if (p->d_tables) cudaFree(p->d_tables);
+    if (p->d_spec) cudaFree(p->d_spec);
+    if (p->d_spec_nat) cudaFree(p->d_spec_nat);
+    if (p->d_scratch) cudaFree(p->d_scratch);
+    if (p->d_perm) cudaFree(p->d_perm);
+    if (p->d_stage) cudaFree(p->d_stage);
+    delete p;
+}
+
+extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, pac_plan* out) {
+    if (!out) return fail(PAC_ERR_ARG, "null out");
+    *out = nullptr;
+    if (ndim < 1 || ndim > 3 || !dims) return fail(PAC_ERR_ARG, "ndim must be 1, 2 or 3");
+    if (dtype != PAC_C64 && dtype != PAC_C128) return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
+    const int p = prime_of(radix);
+    if (p == 0) return fail(PAC_ERR_ARG, "radix %d not in {2,3,4,5,8}", radix);
+
+    pac_plan pl = new (std::nothrow) pac_plan_s();
+    if (!pl) return fail(PAC_ERR_NOMEM, "host allocation failed");
+    pl->ndim = ndim;
+    pl->radix = radix;
+    pl->dtype = dtype;
+    pl->esize = dtype == PAC_C64 ? 8 : 16;
+    pl->N = 1;
+    for (int a = 0; a < ndim; ++a) {
+        pl->dims[a] = dims[a];
+        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30)) {
+            delete pl;
+            return fail(PAC_ERR_SIZE, "dimension %lld out of range", (long long)dims[a]);
+        }
+        pl->N *= dims[a];
+    }
+    if (pl->N > (int64_t(1) << 34)) {
+        delete pl;
+        return fail(PAC_ERR_SIZE, "N = %lld too large", (long long)pl->N);
+    }
+    pl->stages.resize(ndim);
+    pl->pos_to_freq.resize(ndim);
+    for (int a = 0; a < ndim; ++a) {
+        int rc = stage_list(dims[a], radix, pl->stages[a]);
+        if (rc) {
+            delete pl;
+            return rc;
+        }
+        pl->pos_to_freq[a].resize(dims[a]);
+        reverse_table(pl->stages[a].data(), (int)pl->stages[a].size(), pl->pos_to_freq[a].data());
+    }
+
+    // groups, forward order: axis 0 (outermost) first, the contiguous axis last
+    size_t off = 0;
+    for (int a = 0; a < ndim; ++a) {
+        int64_t inner = 1;
+        for (int b = a + 1; b < ndim; ++b) inner *= dims[b];
+        int64_t Lcur = dims[a];
+        for (auto [first, cnt] : split_groups(pl->stages[a], p, pl->esize)) {
+            GroupPlan g;
+            g.axis = a;
+            g.first_stage = first;
+            g.nstages = cnt;
+            g.M = 1;
+            for (int i = 0; i < cnt; ++i) g.M *= pl->stages[a][first + i];
+            g.L = Lcur;
+            g.Lp = Lcur / g.M;
+            g.I = inner;
+            g.C = g.Lp * inner;
+            g.Q = pl->N / g.M;
+            g.has_ext = g.Lp > 1;
+            if (!pass_kernel_supported(g.M, pl->esize)) {
+                delete pl;
+                return fail(PAC_ERR_SIZE, "no pass kernel for group size %d", g.M);
+            }
+            // two-level split of the external exponent: T = p^ceil(e/2)
+            const int eL = exact_log(g.L, p);
+            g.tw_T = ipow(p, (eL + 1) / 2);
+            g.tw_shift = (p == 2) ? (eL + 1) / 2 : -1;
+            g.off_twi = off;
+            off = align16(off + (size_t)g.M * pl->esize);
+            if (g.has_ext) {
+                g.off_lo = off;
+                off = align16(off + (size_t)g.tw_T * pl->esize);
+                g.off_hi = off;
+                off = align16(off + (size_t)((g.L + g.tw_T - 1) / g.tw_T) * pl->esize);
+            }
+            g.off_rowmap = off;
+            off = align16(off + (size_t)g.M * sizeof(int));
+            g.off_freq = off;
+            off = align16(off + (size_t)g.M * sizeof(int));
+            pl->groups.push_back(g);
+            Lcur = g.Lp;
+        }
+    }
+
+    // host blob of every table
+    std::vector<unsigned char> blob(std::max<size_t>(off, 16), 0);
+    for (const GroupPlan& g : pl->groups) {
+        for (int64_t u = 0; u < g.M; ++u) {
+            if (pl->esize == 8) put_root<float2, float>(blob, g.off_twi, u, u, g.M);
+            else put_root<double2, double>(blob, g.off_twi, u, u, g.M);
+        }
+        if (g.has_ext) {
+            const int64_t nhi = (g.L + g.tw_T - 1) / g.tw_T;
+            for (int64_t u = 0; u < g.tw_T; ++u) {
+                if (pl->esize == 8) put_root<float2, float>(blob, g.off_lo, u, u, g.L);
+                else put_root<double2, double>(blob, g.off_lo, u, u, g.L);
+            }
+            for (int64_t v = 0; v < nhi; ++v) {
+                if (pl->esize == 8) put_root<float2, float>(blob, g.off_hi, v, v * g.tw_T, g.L);
+                else put_root<double2, double>(blob, g.off_hi, v, v * g.tw_T, g.L);
+            }
+        }
+        // frequency at each global row: digit reversal over the group's stages
+        std::vector<int64_t> f(g.M);
+        reverse_table(pl->stages[g.axis].data() + g.first_stage, g.nstages, f.data());
+        // shared-memory row of frequency k after the in-place rounds: digit
+        // reversal over the round radices (larger rounds first)
+        const int nr = round_count(g.M, pl->esize);
+        std::vector<int> rr(nr);
+        for (int i = 0; i < nr; ++i) rr[i] = round_radix(g.M, pl->esize, i);
+        std::vector<int64_t> r2f(g.M);
+        reverse_table(rr.data(), nr, r2f.data());
+        std::vector<int> f2r(g.M);
+        for (int r = 0; r < g.M; ++r) f2r[r2f[r]] = r;
+        int* rowmap = reinterpret_cast<int*>(blob.data() + g.off_rowmap);
+        int* freq = reinterpret_cast<int*>(blob.data() + g.off_freq);
+        for (int gg = 0; gg < g.M; ++gg) {
+            freq[gg] = (int)f[gg];
+            rowmap[gg] = f2r[f[gg]];
+        }
+    }
+
+    cudaError_t e = cudaGetDevice(&pl->device);
+    if (e != cudaSuccess) {
+        delete pl;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    pl->tables_bytes = blob.size();
+    e = cudaMalloc(&pl->d_tables, pl->tables_bytes);
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return e == cudaErrorMemoryAllocation ? fail(PAC_ERR_NOMEM, "device tables: out of memory")
+                                              : cuda_fail(e, "cudaMalloc(tables)");
+    }
+    e = cudaMemcpy(pl->d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return cuda_fail(e, "cudaMemcpy(tables)");
+    }
+    e = cudaMalloc(&pl->d_spec, (size_t)pl->bytes());
+    if (e != cudaSuccess) {
+        free_plan(pl);
+        return e == cudaErrorMemoryAllocation ? fail(PAC_ERR_NOMEM, "filter spectrum: out of memory")
+                                              : cuda_fail(e, "cudaMalloc(spectrum)");
+    }
+    pl->device_bytes = pl->tables_bytes + (size_t)pl->bytes();
+    *out = pl;
+    return PAC_OK;
+}
+
+extern "C" int pac_plan_destroy(pac_plan p) {
+    if (!p) return fail(PAC_ERR_ARG, "null plan");
+    cudaDeviceSynchronize();
+    free_plan(p);
+    return PAC_OK;
+}
+
+// ----------------------------------------------------------------- passes
+
+namespace pac {
+
+// Optional per-launch event recorder of pac_convolve_timed (thread-local, so
+// concurrent callers on other threads are unaffected).
+struct LaunchTimer {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ids;
+    int max = 0;
+    bool overflow = false;
+};
+static thread_local LaunchTimer* t_timer = nullptr;
+
+static void timer_mark(cudaStream_t s, int id, bool before) {
+    LaunchTimer* t = t_timer;
+    if (!t) return;
+    if (before) {
+        if ((int)t->ids.size() >= t->max) {
+            t->overflow = true;
+            return;
+        }
+        t->ids.push_back(id);
+    } else if (t->overflow) {
+        return;
+    }
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    cudaEventRecord(e, s);
+    t->ev.push_back(e);
+}
+
+int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale, cudaStream_t s) {
+    PassArgs a;
+    const unsigned char* t = static_cast<const unsigned char*>(p->d_tables);
+    a.src = src;
+    a.dst = dst;
+    a.spec = p->d_spec;
+    a.tw_int = t + g.off_twi;
+    a.tw_lo = g.has_ext ? t + g.off_lo : nullptr;
+    a.tw_hi = g.has_ext ? t + g.off_hi : nullptr;
+    a.rowmap = reinterpret_cast<const int*>(t + g.off_rowmap);
+    a.freq = reinterpret_cast<const int*>(t + g.off_freq);
+    a.Q = g.Q;
+    a.C = g.C;
+    a.I = g.I;
+    const int W = tile_w(g.M, p->esize);
+    a.tiles = (g.Q + W - 1) / W;
+    a.tw_T = g.tw_T;
+    a.tw_shift = g.tw_shift;
+    a.mode = mode;
+    a.has_ext = g.has_ext ? 1 : 0;
+    a.scale = scale;
+    const int kid = mode == kFwd ? 0 : (mode == kFused ? 1 : 2);
+    timer_mark(s, kid, true);
+    cudaError_t e = p->esize == 8 ? launch_pass_c64(g.M, a, s) : launch_pass_c128(g.M, a, s);
+    timer_mark(s, kid, false);
+    if (e != cudaSuccess) return cuda_fail(e, "pass kernel launch");
+    return PAC_OK;
+}
+
+static cudaError_t timed_permute(pac_plan p, const int64_t* const* idx, const void* src, void* dst, const void* mul,
+                                 cudaStream_t s) {
+    timer_mark(s, 3, true);
+    cudaError_t e = launch_permute(p->esize, p->ndim, p->dims, idx, src, dst, mul, s);
+    timer_mark(s, 3, false);
+    return e;
+}
+
+// Algorithm 11, lines 2-4, on device pointers: forward groups (the last fused
+// with the product and the first inverse group), then the inverse groups.
+int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s) {
+    const int G = (int)p->groups.size();
+    if (G == 0) {  // N = 1
+        timer_mark(s, 4, true);
+        cudaError_t e = launch_pointwise_mul(p->esize, p->N, x, p->d_spec, y, 1.0, s);
+        timer_mark(s, 4, false);
+        return e == cudaSuccess ? PAC_OK : cuda_fail(e, "pointwise kernel");
+    }
+    for (int i = 0; i < G; ++i) {
+        int rc = run_pass(p, p->groups[i], i == G - 1 ? kFused : kFwd, i == 0 ? x : y, y, 1.0, s);
+        if (rc) return rc;
+    }
+    for (int i = G - 2; i >= 0; --i) {
+        int rc = run_pass(p, p->groups[i], kInv, y, y, 1.0, s);
+        if (rc) return rc;
+    }
+    return PAC_OK;
+}
+
+int run_forward(pac_plan p, const void* x, void* xhat, double scale, cudaStream_t s) {
+    const int G = (int)p->groups.size();
+    if (G == 0) {
+        cudaError_t e = launch_pointwise_mul(p->esize, p->N, x, nullptr, xhat, scale, s);
+        return e == cudaSuccess ? PAC_OK : cuda_fail(e, "pointwise kernel");
+    }
+    for (int i = 0; i < G; ++i) {
+        int rc = run_pass(p, p->groups[i], kFwd, i == 0 ? x : xhat, xhat, i == G - 1 ? scale : 1.0, s);
+        if (rc) return rc;
+    }
+    return PAC_OK;
+}
+
+}  // namespace pac
+
+static int check_ptr(const void* ptr, const char* name) {
+    if (!ptr) return fail(PAC_ERR_ARG, "%s is null", name);
+    if (reinterpret_cast<uintptr_t>(ptr) % 16) return fail(PAC_ERR_ARG, "%s is not 16-byte aligned", name);
+    return PAC_OK;
+}
+
+extern "C" int pac_filter_spectrum(pac_plan p, const void* h_dev) {
+    if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = check_ptr(h_dev, "h_dev")) return rc;
+    std::lock_guard<std::mutex> lk(p->mu);
+    cudaError_t e = cudaDeviceSynchronize();  // h may come from any stream
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    cudaStream_t s;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+    int rc = run_forward(p, h_dev, p->d_spec, 1.0 / (double)p->N, s);
+    e = cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "filter spectrum");
+    p->has_spec = true;
+    if (p->d_spec_nat) {  // comparator spectrum must follow
+        cudaFree(p->d_spec_nat);
+        p->d_spec_nat = nullptr;
+    }
+    return PAC_OK;
+}
+
+extern "C" int pac_convolve(pac_plan p, const void* x_dev, void* y_dev, void* stream) {
+    if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = check_ptr(x_dev, "x_dev")) return rc;
+    if (int rc = check_ptr(y_dev, "y_dev")) return rc;
+    if (!p->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "pac_filter_spectrum was not called for this plan");
+    return run_convolve(p, x_dev, y_dev, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int pac_forward_unordered(pac_plan p, const void* x_dev, void* xhat_dev, void* stream) {
+    if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = check_ptr(x_dev, "x_dev")) return rc;
+    if (int rc = check_ptr(xhat_dev, "xhat_dev")) return rc;
+    return run_forward(p, x_dev, xhat_dev, 1.0, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int pac_convolve_host(pac_plan p, const void* x_host, void* y_host, void* stream) {
+    if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (!x_host || !y_host) return fail(PAC_ERR_ARG, "null host pointer");
+    if (!p->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "pac_filter_spectrum was not called for this plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        if (!p->d_stage) {
+            cudaError_t e = cudaMalloc(&p->d_stage, (size_t)p->bytes());
+            if (e != cudaSuccess) return fail(PAC_ERR_NOMEM, "staging buffer: %s", cudaGetErrorString(e));
+            p->device_bytes += (size_t)p->bytes();
+        }
+    }
+    const size_t nb = (size_t)p->bytes();
+    cudaError_t e = cudaMemcpyAsync(p->d_stage, x_host, nb, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy x to device");
+    int rc = run_convolve(p, p->d_stage, p->d_stage, s);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(y_host, p->d_stage, nb, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "copy y to host");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "pac_convolve_host");
+    return PAC_OK;
+}
+
+// Comparator state: per-axis [pos_to_freq | freq_to_pos] tables, scratch and
+// the natural-order spectrum (one permutation pass at filter time).
+static int ensure_permuted_state(pac_plan p) {
+    cudaError_t e;
+    if (!p->d_perm) {
+        int64_t tot = 0;
+        for (int a = 0; a < p->ndim; ++a) tot += 2 * p->dims[a];
+        std::vector<int64_t> h(tot);
+        int64_t o = 0;
+        for (int a = 0; a < p->ndim; ++a) {
+            const int64_t n = p->dims[a];
+            for (int64_t i = 0; i < n; ++i) {
+                h[o + i] = p->pos_to_freq[a][i];
+                h[o + n + p->pos_to_freq[a][i]] = i;
+            }
+            o += 2 * n;
+        }
+        e = cudaMalloc(&p->d_perm, tot * sizeof(int64_t));
+        if (e != cudaSuccess) return fail(PAC_ERR_NOMEM, "permutation tables: %s", cudaGetErrorString(e));
+        e = cudaMemcpy(p->d_perm, h.data(), tot * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "copy permutation tables");
+        p->device_bytes += tot * sizeof(int64_t);
+    }
+    if (!p->d_scratch) {
+        e = cudaMalloc(&p->d_scratch, (size_t)p->bytes());
+        if (e != cudaSuccess) return fail(PAC_ERR_NOMEM, "scratch: %s", cudaGetErrorString(e));
+        p->device_bytes += (size_t)p->bytes();
+    }
+    if (!p->d_spec_nat) {
+        e = cudaMalloc(&p->d_spec_nat, (size_t)p->bytes());
+        if (e != cudaSuccess) return fail(PAC_ERR_NOMEM, "natural spectrum: %s", cudaGetErrorString(e));
+        const int64_t* idx[3];
+        int64_t o = 0;
+        for (int a = 0; a < p->ndim; ++a) {
+            idx[a] = p->d_perm + o + p->dims[a];  // natural k <- position of k
+            o += 2 * p->dims[a];
+        }
+        e = launch_permute(p->esize, p->ndim, p->dims, idx, p->d_spec, p->d_spec_nat, nullptr, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(e, "natural-order spectrum");
+    }
+    return PAC_OK;
+}
+
+extern "C" int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev, void* stream) {
+    if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = check_ptr(x_dev, "x_dev")) return rc;
+    if (int rc = check_ptr(y_dev, "y_dev")) return rc;
+    if (!p->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "pac_filter_spectrum was not called for this plan");
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        if (int rc = ensure_permuted_state(p)) return rc;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int G = (int)p->groups.size();
+    // FFT2 = permute o uFFT2 (Algorithm 5): DIF passes, then reversed -> natural
+    int rc = run_forward(p, x_dev, y_dev, 1.0, s);
+    if (rc) return rc;
+    const int64_t* to_nat[3];
+    const int64_t* to_rev[3];
+    int64_t o = 0;
+    for (int a = 0; a < p->ndim; ++a) {
+        to_rev[a] = p->d_perm + o;                // position p <- frequency pos_to_freq[p]
+        to_nat[a] = p->d_perm + o + p->dims[a];   // frequency k <- position of k
+        o += 2 * p->dims[a];
+    }
+    // x := h o x in natural order, fused into the permutation
+    cudaError_t e = timed_permute(p, to_nat, y_dev, p->d_scratch, p->d_spec_nat, s);
+    if (e != cudaSuccess) return cuda_fail(e, "permute kernel");
+    // iFFT = uiFFT o permute (Algorithm 9)
+    e = timed_permute(p, to_rev, p->d_scratch, y_dev, nullptr, s);
+    if (e != cudaSuccess) return cuda_fail(e, "permute kernel");
+    for (int i = G - 1; i >= 0; --i) {
+        rc = run_pass(p, p->groups[i], kInv, y_dev, y_dev, 1.0, s);
+        if (rc) return rc;
+    }
+    return PAC_OK;
+}
+
+extern "C" int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, void* stream,
+                                  int max_launches, float* launch_ms, int* kernel_ids, int* n_launches) {
+    if (!p || !launch_ms || !kernel_ids || !n_launches || max_launches < 1) return fail(PAC_ERR_ARG, "bad arguments");
+    if (which != 0 && which != 1) return fail(PAC_ERR_ARG, "which must be 0 or 1");
+    LaunchTimer timer;
+    timer.max = max_launches;
+    t_timer = &timer;
+    int rc = which == 0 ? pac_convolve(p, x_dev, y_dev, stream) : pac_convolve_permuted(p, x_dev, y_dev, stream);
+    t_timer = nullptr;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    const int n = (int)timer.ids.size();
+    if (rc == PAC_OK && e == cudaSuccess && !timer.overflow && (int)timer.ev.size() == 2 * n) {
+        for (int i = 0; i < n; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, timer.ev[2 * i], timer.ev[2 * i + 1]);
+            launch_ms[i] = ms;
+            kernel_ids[i] = timer.ids[i];
+        }
+        *n_launches = n;
+    }
+    for (cudaEvent_t ev : timer.ev) cudaEventDestroy(ev);
+    if (rc) return rc;
+    if (e != cudaSuccess) return cuda_fail(e, "pac_convolve_timed");
+    if (timer.overflow) return fail(PAC_ERR_ARG, "more than %d launches", max_launches);
+    return PAC_OK;
+}
+
+extern "C" int pac_plan_stages(pac_plan p, int axis, int* radices, int* count) {
+    if (!p || !count) return fail(PAC_ERR_ARG, "null argument");
+    if (axis < 0 || axis >= p->ndim) return fail(PAC_ERR_ARG, "axis %d out of range", axis);
+    const auto& st = p->stages[axis];
+    if (radices) {
+        if (*count < (int)st.size()) return fail(PAC_ERR_ARG, "radices array too small");
+        std::copy(st.begin(), st.end(), radices);
+    }
+    *count = (int)st.size();
+    return PAC_OK;
+}
+
+extern "C" int pac_plan_reverse_table(pac_plan p, int axis, int64_t* pos_to_freq) {
+    if (!p || !pos_to_freq) return fail(PAC_ERR_ARG, "null argument");
+    if (axis < 0 || axis >= p->ndim) return fail(PAC_ERR_ARG, "axis %d out of range", axis);
+    std::copy(p->pos_to_freq[axis].begin(), p->pos_to_freq[axis].end(), pos_to_freq);
+    return PAC_OK;
+}
+
+extern "C" int pac_plan_query(pac_plan p, int key, int64_t* value) {
+    if (!p || !value) return fail(PAC_ERR_ARG, "null argument");
+    const int64_t G = (int64_t)p->groups.size();
+    switch (key) {
+        case PAC_Q_NDIM: *value = p->ndim; break;
+        case PAC_Q_N_TOTAL: *value = p->N; break;
+        case PAC_Q_ELEM_BYTES: *value = p->esize; break;
+        case PAC_Q_LAUNCHES_CONVOLVE: *value = G == 0 ? 1 : 2 * G - 1; break;
+        case PAC_Q_LAUNCHES_PERMUTED: *value = 2 * std::max<int64_t>(G, 0) + 2; break;
+        case PAC_Q_LAUNCHES_FORWARD: *value = std::max<int64_t>(G, 1); break;
+        case PAC_Q_DEVICE_BYTES: *value = (int64_t)p->device_bytes; break;
+        case PAC_Q_HAS_SPECTRUM: *value = p->has_spec ? 1 : 0; break;
+        default: return fail(PAC_ERR_ARG, "unknown query key %d", key);
+    }
+    return PAC_OK;
+}

@@ -1,0 +1,247 @@
+// Request queue with continuous batching (serving).
+//
+// pac_submit appends a request and returns at once.  A scheduler thread
+// admits waiting requests in arrival order as soon as a slot and device
+// memory are free (at most max_inflight running, running bytes within the
+// HBM budget), launches each on its own stream
+// of a pool so that requests overlap on the GPU, and marks completion from a
+// host callback enqueued behind the request's kernels.  Requests that arrive
+// while others run are admitted as earlier ones finish: the batch on the
+// device changes continuously instead of in waves.
+//
+// Fault injection (host side only, no device fault): the environment
+// variable PAC_FAULT=launch:K makes the K-th admitted request (1-based) fail
+// as if its launch had failed; the request is marked PAC_ERR_CUDA and the
+// others proceed.
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+#include "pac_internal.h"
+
+namespace pac {
+int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s);
+}
+
+using namespace pac;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+struct Request {
+    uint64_t ticket = 0;
+    pac_plan plan = nullptr;
+    const void* x = nullptr;
+    void* y = nullptr;
+    size_t bytes = 0;
+    Clock::time_point t_submit;
+    Clock::time_point t_done;
+    int status = PAC_PENDING;
+    int slot = -1;
+    std::atomic<bool> gpu_done{false};
+    pac_queue owner = nullptr;
+};
+
+}  // namespace
+
+struct pac_queue_s {
+    size_t budget = 0;
+    int max_inflight = 1;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv;       // wakes the scheduler
+    std::condition_variable cv_done;  // wakes pac_queue_drain
+    std::deque<Request*> waiting;
+    std::vector<Request*> running;
+    std::unordered_map<uint64_t, Request*> by_ticket;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> slot_busy;
+    size_t running_bytes = 0;
+    uint64_t next_ticket = 1;
+    uint64_t admitted = 0;
+    int64_t fault_launch = -1;
+    bool stop = false;
+    std::thread worker;
+};
+
+static void CUDART_CB on_request_done(void* arg) {
+    // runs on a CUDA driver thread once the request's kernels finished: no CUDA calls here
+    Request* r = static_cast<Request*>(arg);
+    r->t_done = Clock::now();
+    r->gpu_done.store(true, std::memory_order_release);
+    pac_queue q = r->owner;
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+    }
+    q->cv.notify_one();
+}
+
+// Admission: a free slot, and the running requests' device bytes plus this
+// one within the HBM budget.  A request larger than the whole budget runs
+// alone rather than never.
+static bool fits(pac_queue q, const Request* r) {
+    if ((int)q->running.size() >= q->max_inflight) return false;
+    if (q->running.empty()) return true;
+    return q->running_bytes + r->bytes <= q->budget;
+}
+
+static void scheduler(pac_queue q) {
+    cudaSetDevice(q->device);
+    std::unique_lock<std::mutex> lk(q->mu);
+    while (true) {
+        bool progress = false;
+        // retire finished requests
+        for (size_t i = 0; i < q->running.size();) {
+            Request* r = q->running[i];
+            if (r->gpu_done.load(std::memory_order_acquire)) {
+                r->status = PAC_OK;
+                q->running_bytes -= r->bytes;
+                q->slot_busy[r->slot] = 0;
+                q->running[i] = q->running.back();
+                q->running.pop_back();
+                progress = true;
+            } else {
+                ++i;
+            }
+        }
+        // admit in arrival order while a slot and memory are free
+        while (!q->waiting.empty() && fits(q, q->waiting.front())) {
+            Request* r = q->waiting.front();
+            q->waiting.pop_front();
+            int slot = 0;
+            while (slot < (int)q->slot_busy.size() && q->slot_busy[slot]) ++slot;
+            r->slot = slot;
+            q->admitted++;
+            int rc;
+            if (q->fault_launch > 0 && (int64_t)q->admitted == q->fault_launch) {
+                rc = PAC_ERR_CUDA;  // injected host-side launch failure
+            } else {
+                rc = run_convolve(r->plan, r->x, r->y, q->streams[slot]);
+                if (rc == PAC_OK) {
+                    cudaError_t e = cudaLaunchHostFunc(q->streams[slot], on_request_done, r);
+                    if (e != cudaSuccess) rc = PAC_ERR_CUDA;
+                }
+            }
+            if (rc != PAC_OK) {
+                r->status = rc;
+                r->t_done = Clock::now();
+                progress = true;
+                continue;
+            }
+            q->slot_busy[slot] = 1;
+            q->running_bytes += r->bytes;
+            q->running.push_back(r);
+            progress = true;
+        }
+        if (progress) q->cv_done.notify_all();
+        if (q->stop && q->waiting.empty() && q->running.empty()) break;
+        if (!progress) q->cv.wait_for(lk, std::chrono::microseconds(200));
+    }
+}
+
+extern "C" int pac_queue_create(size_t hbm_budget_bytes, int max_inflight, pac_queue* out) {
+    if (!out) return fail(PAC_ERR_ARG, "null out");
+    *out = nullptr;
+    if (max_inflight < 1 || max_inflight > 64) return fail(PAC_ERR_ARG, "max_inflight must be in [1, 64]");
+    if (hbm_budget_bytes == 0) return fail(PAC_ERR_ARG, "zero HBM budget");
+    pac_queue q = new (std::nothrow) pac_queue_s();
+    if (!q) return fail(PAC_ERR_NOMEM, "host allocation failed");
+    q->budget = hbm_budget_bytes;
+    q->max_inflight = max_inflight;
+    cudaError_t e = cudaGetDevice(&q->device);
+    if (e != cudaSuccess) {
+        delete q;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    q->streams.resize(max_inflight);
+    q->slot_busy.assign(max_inflight, 0);
+    for (int i = 0; i < max_inflight; ++i) {
+        e = cudaStreamCreateWithFlags(&q->streams[i], cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaStreamDestroy(q->streams[j]);
+            delete q;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+    }
+    if (const char* f = std::getenv("PAC_FAULT")) {
+        if (std::strncmp(f, "launch:", 7) == 0) q->fault_launch = std::atoll(f + 7);
+    }
+    q->worker = std::thread(scheduler, q);
+    *out = q;
+    return PAC_OK;
+}
+
+extern "C" int pac_submit(pac_queue q, pac_plan p, const void* x_dev, void* y_dev, uint64_t* ticket) {
+    if (!q || !p || !x_dev || !y_dev || !ticket) return fail(PAC_ERR_ARG, "null argument");
+    if (!p->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "plan has no filter spectrum");
+    Request* r = new (std::nothrow) Request();
+    if (!r) return fail(PAC_ERR_NOMEM, "host allocation failed");
+    r->plan = p;
+    r->x = x_dev;
+    r->y = y_dev;
+    r->bytes = 2 * (size_t)p->bytes();
+    r->owner = q;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        if (q->waiting.size() >= 65536) {
+            delete r;
+            return fail(PAC_ERR_BUSY, "request queue full");
+        }
+        r->ticket = q->next_ticket++;
+        q->waiting.push_back(r);
+        q->by_ticket[r->ticket] = r;
+        *ticket = r->ticket;
+    }
+    q->cv.notify_one();
+    return PAC_OK;
+}
+
+extern "C" int pac_poll(pac_queue q, uint64_t ticket, double* latency_us) {
+    if (!q) return fail(PAC_ERR_ARG, "null queue");
+    std::lock_guard<std::mutex> lk(q->mu);
+    auto it = q->by_ticket.find(ticket);
+    if (it == q->by_ticket.end()) return fail(PAC_ERR_NOT_FOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Request* r = it->second;
+    if (r->status == PAC_PENDING) return PAC_PENDING;
+    const int st = r->status;
+    if (latency_us) latency_us[0] = std::chrono::duration<double, std::micro>(r->t_done - r->t_submit).count();
+    q->by_ticket.erase(it);
+    delete r;
+    if (st != PAC_OK) return fail(st, "request %llu failed", (unsigned long long)ticket);
+    return PAC_OK;
+}
+
+extern "C" int pac_queue_drain(pac_queue q, int timeout_ms) {
+    if (!q) return fail(PAC_ERR_ARG, "null queue");
+    std::unique_lock<std::mutex> lk(q->mu);
+    bool ok = q->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
+                                  [&] { return q->waiting.empty() && q->running.empty(); });
+    return ok ? PAC_OK : fail(PAC_ERR_TIMEOUT, "queue did not drain within %d ms", timeout_ms);
+}
+
+extern "C" int pac_queue_destroy(pac_queue q) {
+    if (!q) return fail(PAC_ERR_ARG, "null queue");
+    int rc = pac_queue_drain(q, 60000);
+    {
+        std::lock_guard<std::mutex> lk(q->mu);
+        q->stop = true;
+        if (rc != PAC_OK) {  // give up on waiting requests; running ones still finish
+            for (Request* r : q->waiting) r->status = PAC_ERR_TIMEOUT;
+            q->waiting.clear();
+        }
+    }
+    q->cv.notify_all();
+    q->worker.join();
+    for (cudaStream_t s : q->streams) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
+    for (auto& kv : q->by_ticket) delete kv.second;
+    delete q;
+    return rc;
+}

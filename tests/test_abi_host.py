@@ -1,0 +1,99 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol, and
+its host-only rules (stage lists, index-reversal tables) match the oracle's
+reading of the paper bit for bit.  No compute call needs a GPU here."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2506_12718_gb300 as pac
+from oracle import paper_forms as pf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2506_12718_gb300 import _build
+    _build.build()
+    pac.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "pac.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pac_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol():
+    names = declared_symbols()
+    assert len(names) >= 20
+    lib = pac.load()
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding mirrors each name
+    for n in names:
+        assert callable(getattr(pac, n)), n
+
+
+def test_version():
+    assert "sm_103a" in pac.pac_version()
+
+
+@pytest.mark.parametrize("n,radix,want", [
+    (128, 2, [2] * 7), (128, 4, [4, 4, 4, 2]), (128, 8, [8, 8, 2]), (1024, 4, [4] * 5),
+    (2187, 3, [3] * 7), (3125, 5, [5] * 5), (64, 8, [8, 8]), (2, 8, [2]), (1, 2, []), (32, 4, [4, 4, 2]),
+])
+def test_stage_list(n, radix, want):
+    assert pac.pac_stage_list(n, radix) == want
+
+
+@pytest.mark.parametrize("n,radix,status", [
+    (100, 2, pac.Status.ERR_SIZE), (96, 4, pac.Status.ERR_SIZE), (243, 2, pac.Status.ERR_SIZE),
+    (64, 6, pac.Status.ERR_ARG), (64, 0, pac.Status.ERR_ARG), (0, 2, pac.Status.ERR_SIZE),
+])
+def test_stage_list_errors(n, radix, status):
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_stage_list(n, radix)
+    assert ei.value.status == status
+    assert pac.pac_last_error()
+
+
+STAGE_LISTS = [[2] * 7, [4, 4, 4, 2], [8, 8, 2], [3] * 7, [5] * 5, [2, 4, 4, 4], [2, 8, 8], [2, 3, 4],
+               [4] * 5, [8] * 4, [3, 3], [16, 4], [2]]
+
+
+@pytest.mark.parametrize("stages", STAGE_LISTS)
+def test_reverse_table_matches_paper_permutation(stages):
+    """Bit-exact: the library's position->frequency table equals P^T idx from the
+    paper's modulo-r sorts (uniform radix) or perfect shuffles (mixed radix)."""
+    got = np.array(pac.pac_reverse_table(stages))
+    assert np.array_equal(got, pf.pos_to_freq(stages))
+
+
+@pytest.mark.parametrize("r,t", [(2, 10), (4, 5), (8, 4), (3, 7), (5, 5)])
+def test_reverse_table_is_involution_for_uniform_radix(r, t):
+    p = np.array(pac.pac_reverse_table([r] * t))
+    assert np.array_equal(p[p], np.arange(r ** t))
+
+
+def test_plan_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_plan_create(1, [64], 2, pac.C64)
+    assert ei.value.status in (pac.Status.ERR_CUDA, pac.Status.ERR_NOMEM)
+
+
+def test_plan_create_rejects_bad_arguments_before_touching_the_device():
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_plan_create(1, [100], 2, pac.C64)
+    assert ei.value.status == pac.Status.ERR_SIZE
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_plan_create(4, [2, 2, 2, 2], 2, pac.C64)
+    assert ei.value.status == pac.Status.ERR_ARG
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_plan_create(1, [64], 7, pac.C64)
+    assert ei.value.status == pac.Status.ERR_ARG

@@ -1,0 +1,369 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Tolerances (relative L2 over the whole output, accumulated in FP64):
+  complex FP64: <= 1e-12;  complex FP32: <= 1e-5 * log2(N).
+FP32 inputs are generated in FP64 and rounded once; the oracle runs on the
+rounded values promoted to FP64.  For separable filters the oracle's
+per-axis route (O2) uses the FP64 factors while the GPU gets the rounded
+dense filter; the difference (<= 6e-8 relative for FP32, ~1e-16 for FP64) is
+far below the tolerances.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import pac_inputs as pin
+from oracle import paper_forms as pf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_12718_gb300 import _build
+    _build.build()
+    import paper_2506_12718_gb300 as pac
+    pac.load()
+    return pac
+
+
+def pac_mod():
+    import paper_2506_12718_gb300 as pac
+    return pac
+
+
+def tol(dtype, n):
+    return 1e-12 if dtype == "c128" else 1e-5 * max(1.0, math.log2(n))
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_conv(dims, radix, dtype, h, x, permuted=False):
+    pac = pac_mod()
+    plan = pac.Plan(dims, radix, dtype)
+    try:
+        plan.filter_spectrum(dev(h))
+        xd = dev(x)
+        y = plan.convolve_permuted(xd) if permuted else plan.convolve(xd)
+        torch.cuda.synchronize()
+        return y.cpu().numpy()
+    finally:
+        plan.close()
+
+
+def separable_case(dims, dtype, seed):
+    fs = [pin.complex_uniform((n,), seed + 100 + a) for a, n in enumerate(dims)]
+    h = pin.as_dtype(pin.outer(fs), dtype)
+    x = pin.as_dtype(pin.complex_uniform(dims, seed), dtype)
+    return fs, h, x
+
+
+def check(y, ref, dtype, n, what=""):
+    err = oracle.rel_l2(y, ref)
+    assert err <= tol(dtype, n), f"{what} rel_l2={err:.3e} tol={tol(dtype, n):.1e}"
+    return err
+
+
+# ------------------------------------------------------------------ configs
+
+
+def test_c1_full_definition():
+    """1-D n = 2^10, radix 2, complex FP64 against the direct definition (O1)."""
+    c = pin.c1()
+    x, (h, _) = pin.make_x(c), pin.make_h(c)
+    y = gpu_conv(c.dims, c.radix, c.dtype, h, x)
+    check(y, oracle.conv_direct(h, x), c.dtype, c.n_total, "c1")
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("radix", [2, 4, 8])
+def test_c2_128_cubed_gaussian(radix, dtype):
+    """3-D 128^3 periodic convolution with the sigma=4 Gaussian, full array (O2)."""
+    c = pin.c2(radix, dtype)
+    x, (h, fs) = pin.make_x(c), pin.make_h(c)
+    y = gpu_conv(c.dims, c.radix, c.dtype, h, x)
+    ref = _c2_ref(dtype)
+    check(y, ref, dtype, c.n_total, f"c2 r{radix} {dtype}")
+
+
+_C2_CACHE = {}
+
+
+def _c2_ref(dtype):
+    if dtype not in _C2_CACHE:
+        c = pin.c2(2, dtype)
+        x, (_, fs) = pin.make_x(c), pin.make_h(c)
+        _C2_CACHE[dtype] = oracle.conv_separable(fs, x)
+    return _C2_CACHE[dtype]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("radix", [3, 5])
+def test_c3_large_2d_exponential(radix, dtype):
+    """2-D 2187^2 (radix 3) and 3125^2 (radix 5) with the separable exponential (O2)."""
+    c = pin.c3(radix, dtype)
+    x, (h, fs) = pin.make_x(c), pin.make_h(c)
+    y = gpu_conv(c.dims, c.radix, c.dtype, h, x)
+    check(y, oracle.conv_separable(fs, x), dtype, c.n_total, f"c3 r{radix} {dtype}")
+
+
+# --------------------------------------------------------- shapes and radices
+
+SHAPES = [
+    ((2,), 2), ((8,), 2), ((64,), 4), ((128,), 8), ((256,), 2), ((1024,), 4), ((4096,), 2),
+    ((8192,), 2), ((16384,), 4), ((32768,), 8), ((3,), 3), ((27,), 3), ((243,), 3), ((2187,), 3),
+    ((6561,), 3), ((5,), 5), ((125,), 5), ((3125,), 5), ((15625,), 5),
+    ((8, 8), 2), ((64, 32), 4), ((27, 81), 3), ((25, 125), 5), ((2, 1024), 2), ((1024, 2), 8),
+    ((1, 64), 2), ((64, 1), 4), ((243, 9), 3), ((4, 4, 4), 4), ((8, 16, 32), 8), ((27, 9, 3), 3),
+    ((2, 2, 2), 2), ((32, 32, 32), 2), ((5, 25, 5), 5), ((16, 1, 8), 2),
+]
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("dims,radix", SHAPES, ids=[f"{'x'.join(map(str, d))}-r{r}" for d, r in SHAPES])
+def test_shapes_separable(dims, radix, dtype):
+    fs, h, x = separable_case(dims, dtype, seed=hash((dims, radix)) % 1000)
+    y = gpu_conv(dims, radix, dtype, h, x)
+    check(y, oracle.conv_separable(fs, x), dtype, int(np.prod(dims)), f"{dims} r{radix}")
+
+
+@pytest.mark.parametrize("dims,radix", [((16,), 2), ((9, 27), 3), ((8, 4, 16), 4), ((25, 5), 5), ((64, 64), 8)])
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_nonseparable_direct(dims, radix, dtype):
+    h = pin.as_dtype(pin.complex_uniform(dims, 5), dtype)
+    x = pin.as_dtype(pin.complex_normal(dims, 6), dtype)
+    y = gpu_conv(dims, radix, dtype, h, x)
+    check(y, oracle.conv_direct(h, x), dtype, int(np.prod(dims)))
+
+
+def test_single_element():
+    h = np.array([2.0 - 1.0j], np.complex128)
+    x = np.array([0.5 + 3.0j], np.complex128)
+    y = gpu_conv((1,), 2, "c128", h, x)
+    assert abs(y[0] - h[0] * x[0]) < 1e-15
+
+
+def test_delta_filter_is_identity_fp64():
+    dims = (64, 32, 16)
+    h = np.zeros(dims, np.complex128)
+    h[0, 0, 0] = 1.0
+    x = pin.complex_normal(dims, 9)
+    y = gpu_conv(dims, 4, "c128", h, x)
+    assert oracle.rel_l2(y, x) < 1e-14
+
+
+def test_shifted_delta_is_roll():
+    dims = (81, 27)
+    h = np.zeros(dims, np.complex128)
+    h[5, 20] = 1.0
+    x = pin.complex_normal(dims, 10)
+    y = gpu_conv(dims, 3, "c128", h, x)
+    assert oracle.rel_l2(y, np.roll(x, (5, 20), axis=(0, 1))) < 1e-13
+
+
+# ------------------------------------------------------- unordered transform
+
+
+@pytest.mark.parametrize("dims,radix,dtype", [
+    ((128,), 2, "c128"), ((128,), 4, "c128"), ((128,), 8, "c128"), ((81,), 3, "c128"), ((125,), 5, "c128"),
+    ((16, 8), 4, "c128"), ((4, 8, 16), 8, "c128"), ((8192,), 2, "c128"), ((8192,), 4, "c64"),
+    ((6561,), 3, "c128"), ((32, 64), 8, "c64"), ((2187,), 3, "c64"),
+])
+def test_forward_is_dft_in_index_reversed_order(dims, radix, dtype):
+    """The fixed fact of the method: A^T x = P^T F x, per axis (Sections 2.1, 6.1)."""
+    pac = pac_mod()
+    x = pin.as_dtype(pin.complex_uniform(dims, 11), dtype)
+    plan = pac.Plan(dims, radix, dtype)
+    try:
+        stages = [plan.stages(a) for a in range(len(dims))]
+        for a in range(len(dims)):
+            assert plan.stages(a) == pac.pac_stage_list(dims[a], radix)
+            assert np.array_equal(np.array(plan.reverse_table(a)), pf.pos_to_freq(stages[a]))
+        xh = plan.forward_unordered(dev(x))
+        torch.cuda.synchronize()
+        got = xh.cpu().numpy()
+    finally:
+        plan.close()
+    ref = oracle.unordered_forward(x, stages)
+    check(got, ref, dtype, int(np.prod(dims)), "A^T x")
+
+
+# -------------------------------------------------------------- comparator
+
+
+@pytest.mark.parametrize("dims,radix,dtype", [((128, 128, 128), 4, "c64"), ((243, 81), 3, "c128"),
+                                             ((8192,), 2, "c64"), ((32, 16), 8, "c128")])
+def test_permuted_form_matches(dims, radix, dtype):
+    fs, h, x = separable_case(dims, dtype, seed=12)
+    ref = oracle.conv_separable(fs, x)
+    yp = gpu_conv(dims, radix, dtype, h, x, permuted=True)
+    check(yp, ref, dtype, int(np.prod(dims)), "permuted")
+
+
+# ------------------------------------------------------------ API behaviour
+
+
+def test_in_place_and_host_buffers():
+    pac = pac_mod()
+    dims, radix, dtype = (64, 128), 4, "c64"
+    fs, h, x = separable_case(dims, dtype, seed=13)
+    ref = oracle.conv_separable(fs, x)
+    plan = pac.Plan(dims, radix, dtype)
+    try:
+        plan.filter_spectrum(dev(h))
+        xd = dev(x)
+        plan.convolve(xd, xd)  # y == x
+        torch.cuda.synchronize()
+        check(xd.cpu().numpy(), ref, dtype, x.size, "in place")
+        xh = torch.from_numpy(x.copy()).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        s = torch.cuda.Stream()
+        pac.pac_convolve_host(plan.handle, xh, yh, s)
+        check(yh.numpy(), ref, dtype, x.size, "host buffers")
+    finally:
+        plan.close()
+
+
+def test_errors():
+    pac = pac_mod()
+    plan = pac.Plan((64,), 2, "c64")
+    try:
+        x = torch.zeros(64, dtype=torch.complex64, device="cuda")
+        with pytest.raises(pac.PacError) as ei:
+            plan.convolve(x)
+        assert ei.value.status == pac.Status.ERR_NO_SPECTRUM
+        plan.filter_spectrum(x)
+        buf = torch.zeros(80, dtype=torch.complex64, device="cuda")
+        with pytest.raises(pac.PacError) as ei:
+            pac.pac_convolve(plan.handle, buf.data_ptr() + 8, buf.data_ptr() + 16)
+        assert ei.value.status == pac.Status.ERR_ARG
+        assert plan.query(pac.Q_HAS_SPECTRUM) == 1
+        assert plan.query(pac.Q_N_TOTAL) == 64
+    finally:
+        plan.close()
+    with pytest.raises(pac.PacError) as ei:
+        pac.Plan((96,), 2, "c64")
+    assert ei.value.status == pac.Status.ERR_SIZE
+
+
+def test_convolve_many_matches_single():
+    pac = pac_mod()
+    cases = [((4096,), 2, 1), ((27, 81), 3, 2), ((64, 64), 8, 3), ((3125,), 5, 4), ((4096,), 2, 5)]
+    plans, xs, ys, refs = [], [], [], []
+    try:
+        for dims, radix, seed in cases:
+            fs, h, x = separable_case(dims, "c64", seed)
+            p = pac.Plan(dims, radix, "c64")
+            p.filter_spectrum(dev(h))
+            plans.append(p)
+            xs.append(dev(x))
+            ys.append(torch.empty_like(xs[-1]))
+            refs.append(oracle.conv_separable(fs, x))
+        pac.pac_convolve_many([p.handle for p in plans], xs, ys)
+        torch.cuda.synchronize()
+        for y, ref, (dims, _, _) in zip(ys, refs, cases):
+            check(y.cpu().numpy(), ref, "c64", int(np.prod(dims)), f"many {dims}")
+    finally:
+        for p in plans:
+            p.close()
+
+
+def _queue_setup(n_req=24):
+    pac = pac_mod()
+    shapes = [((4096,), 2), ((81, 81), 3), ((32, 32, 32), 2), ((125, 25), 5), ((1024,), 4)]
+    plans = {}
+    reqs = []
+    for i in range(n_req):
+        dims, radix = shapes[i % len(shapes)]
+        dtype = "c64" if i % 3 else "c128"
+        key = (dims, radix, dtype)
+        if key not in plans:
+            _, h, _ = separable_case(dims, dtype, 40 + len(plans))
+            p = pac.Plan(dims, radix, dtype)
+            p.filter_spectrum(dev(h))
+            plans[key] = p
+        x = pin.as_dtype(pin.complex_normal(dims, 1000 + i), dtype)
+        reqs.append((plans[key], dev(x)))
+    return plans, reqs
+
+
+def test_queue_alone_and_in_the_mix_agree():
+    """Continuous batching: each result is the same alone and in the mix."""
+    pac = pac_mod()
+    plans, reqs = _queue_setup()
+    try:
+        alone = []
+        for p, x in reqs:
+            y = p.convolve(x)
+            torch.cuda.synchronize()
+            alone.append(y.cpu().numpy())
+        q = pac.pac_queue_create(1 << 30, 6)
+        ys = [torch.empty_like(x) for _, x in reqs]
+        tickets = [pac.pac_submit(q, p.handle, x, y) for (p, x), y in zip(reqs, ys)]
+        pac.pac_queue_drain(q, 60000)
+        lats = []
+        for t in tickets:
+            st, lat = pac.pac_poll(q, t)
+            assert st == pac.Status.OK
+            lats.append(lat)
+        with pytest.raises(pac.PacError) as ei:
+            pac.pac_poll(q, tickets[0])
+        assert ei.value.status == pac.Status.ERR_NOT_FOUND
+        pac.pac_queue_destroy(q)
+        for a, y, (p, _) in zip(alone, ys, reqs):
+            got = y.cpu().numpy()
+            dtype = p.dtype
+            assert oracle.rel_l2(got, a) <= tol(dtype, got.size)
+        assert all(lat > 0 for lat in lats)
+    finally:
+        for p in plans.values():
+            p.close()
+
+
+def test_queue_injected_launch_failure_isolated(monkeypatch):
+    pac = pac_mod()
+    plans, reqs = _queue_setup(8)
+    monkeypatch.setenv("PAC_FAULT", "launch:3")
+    try:
+        q = pac.pac_queue_create(1 << 30, 2)
+        monkeypatch.delenv("PAC_FAULT")
+        ys = [torch.empty_like(x) for _, x in reqs]
+        tickets = [pac.pac_submit(q, p.handle, x, y) for (p, x), y in zip(reqs, ys)]
+        pac.pac_queue_drain(q, 60000)
+        failed = 0
+        for i, t in enumerate(tickets):
+            try:
+                st, _ = pac.pac_poll(q, t)
+                assert st == pac.Status.OK
+            except pac.PacError as e:
+                assert e.status == pac.Status.ERR_CUDA and i == 2
+                failed += 1
+        assert failed == 1
+        pac.pac_queue_destroy(q)
+    finally:
+        for p in plans.values():
+            p.close()
+
+
+def test_queue_tiny_budget_serialises_but_completes():
+    pac = pac_mod()
+    plans, reqs = _queue_setup(6)
+    try:
+        q = pac.pac_queue_create(1024, 4)  # smaller than any request: one at a time
+        ys = [torch.empty_like(x) for _, x in reqs]
+        tickets = [pac.pac_submit(q, p.handle, x, y) for (p, x), y in zip(reqs, ys)]
+        pac.pac_queue_drain(q, 60000)
+        for t in tickets:
+            assert pac.pac_poll(q, t)[0] == pac.Status.OK
+        pac.pac_queue_destroy(q)
+    finally:
+        for p in plans.values():
+            p.close()
