@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--quick", action="store_true", help="main leg only (for profiler runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--flush-mb", type=int, default=FLUSH_BYTES >> 20,
+                    help="L2 flush buffer written before each step (0: none, for profiler runs only)")
     return ap.parse_args(argv)
 
 
@@ -301,12 +303,13 @@ def main(argv=None):
     x = torch.from_numpy(x_np).to(dev)
     h = torch.from_numpy(h_np).to(dev)
     y = torch.empty_like(x)
-    flush_buf = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    flush_buf = torch.empty(max(1, (a.flush_mb << 20) // 4), dtype=torch.int32, device=dev)
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
 
     def flush():
-        flush_buf.fill_(1)
+        if a.flush_mb > 0:
+            flush_buf.fill_(1)
 
     plan = pac.Plan(c.dims, c.radix, c.dtype)
     plan.filter_spectrum(h)
@@ -331,7 +334,8 @@ def main(argv=None):
             "dtype": "f32" if a.dtype == "c64" else "f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "dims": list(c.dims), "radix": a.radix,
                        "stages_per_axis": plan.stages(0), "bytes_per_step": B,
-                       "l2": f"flushed before every step ({FLUSH_BYTES >> 20} MiB write, outside the timed events)",
+                       "l2": (f"flushed before every step ({a.flush_mb} MiB write, outside the timed events)"
+                              if a.flush_mb > 0 else "not flushed (profiling run)"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "pct_hbm_roofline": value / world / peak, "gpu_launches": a.steps * launches,
             "launches_per_step": launches}

@@ -180,7 +180,8 @@ int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev, void* stre
  * before and after each one; synchronises `stream` and writes each launch's
  * device time (ms) to launch_ms[0..*n_launches) and a kernel id to
  * kernel_ids[] (0 = forward DIF pass, 1 = fused DIF+product+DIT pass,
- * 2 = inverse DIT pass, 3 = permutation, 4 = pointwise product).
+ * 2 = inverse DIT pass, 3 = permutation, 4 = pointwise product, 5 = whole
+ * pass sequence in one cooperative launch).
  * max_launches bounds both arrays; PAC_ERR_ARG if it is too small.
  */
 int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, void* stream, int max_launches,
@@ -196,7 +197,9 @@ enum {
     PAC_Q_LAUNCHES_PERMUTED = 4,  /* kernel launches per pac_convolve_permuted */
     PAC_Q_LAUNCHES_FORWARD = 5,   /* kernel launches per pac_forward_unordered */
     PAC_Q_DEVICE_BYTES = 6,       /* device memory the plan owns */
-    PAC_Q_HAS_SPECTRUM = 7
+    PAC_Q_HAS_SPECTRUM = 7,
+    PAC_Q_DEVICE_ERROR = 8        /* synchronises; returns and clears the device error word
+                                     (1: a bounded grid-barrier wait gave up) */
 };
 
 /* Host-only helpers (no device needed): the stage list and reversal table rules. */

@@ -37,7 +37,7 @@ class Status(enum.IntEnum):
 
 
 Q_NDIM, Q_N_TOTAL, Q_ELEM_BYTES, Q_LAUNCHES_CONVOLVE, Q_LAUNCHES_PERMUTED, Q_LAUNCHES_FORWARD, \
-    Q_DEVICE_BYTES, Q_HAS_SPECTRUM = range(8)
+    Q_DEVICE_BYTES, Q_HAS_SPECTRUM, Q_DEVICE_ERROR = range(9)
 
 # every entry point of include/pac.h: name -> (restype, argtypes)
 _vp, _i64, _i32, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
@@ -202,7 +202,8 @@ def pac_plan_reverse_table(plan: int, axis: int, n: int) -> list[int]:
     return list(out)
 
 
-KERNEL_NAMES = {0: "dif_pass", 1: "fused_dif_mul_dit_pass", 2: "dit_pass", 3: "permute", 4: "pointwise"}
+KERNEL_NAMES = {0: "dif_pass", 1: "fused_dif_mul_dit_pass", 2: "dit_pass", 3: "permute", 4: "pointwise",
+                5: "conv_kernel"}
 
 
 def pac_convolve_timed(plan: int, which: int, x_dev, y_dev, stream=None, max_launches: int = 64):

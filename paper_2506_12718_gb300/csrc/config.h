@@ -7,8 +7,7 @@
 namespace pac {
 
 constexpr int kMaxRounds = 6;
-constexpr int kThreads = 256;           // threads per CTA of a pass kernel
-constexpr int kTileBudget = 48 * 1024;  // target shared-memory bytes of one tile
+constexpr int kTileBudget = 8 * 1024;  // target shared-memory bytes of one tile
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 constexpr int base_of(int m) { return m % 2 == 0 ? 2 : (m % 3 == 0 ? 3 : (m % 5 == 0 ? 5 : 1)); }
@@ -40,12 +39,32 @@ constexpr int round_radix(int m, int esize, int i) {
 constexpr int floor_pow2(int v) { return v >= 2 ? 2 * floor_pow2(v / 2) : 1; }
 constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Columns per tile: enough to fill ~kTileBudget, at least one 32-byte sector per row.
+// Columns per tile: about kTileBudget bytes, at least one 32-byte sector per row.
 constexpr int tile_w(int m, int esize) {
     return clampi(floor_pow2(kTileBudget / (m * esize)), 32 / esize, 256);
 }
-// Row pitch of the tile in elements (odd for conflict-free transposing loads).
+// Row pitch of the tile in elements (odd: conflict-free column walks).
 constexpr int tile_pitch(int m, int esize) { return tile_w(m, esize) + 1; }
-constexpr int tile_smem_bytes(int m, int esize) { return m * tile_pitch(m, esize) * esize; }
+constexpr int tile_elems(int m, int esize) { return m * tile_pitch(m, esize); }
+// Tile buffers per CTA: two (the copy of the next tile overlaps the current
+// one) when they fit in a quarter of the shared memory, else one.
+constexpr int tile_stages(int m, int esize) { return 2 * tile_elems(m, esize) * esize <= 56 * 1024 ? 2 : 1; }
+
+// Threads per CTA: one per task of the first round (a multiple of the warp
+// size and of the tile width), within [64, 256].
+constexpr int pass_threads(int m, int esize) {
+    return clampi(((tile_w(m, esize) * (m / round_radix(m, esize, 0)) + 31) / 32) * 32, 64, 256);
+}
+
+// Register budget per thread the kernel is compiled for: enough for the
+// largest in-register round without spilling, small enough to keep several
+// CTAs resident.  FP64 rounds of 16+ complex values keep the full file.
+constexpr int reg_target(int m, int esize) {
+    return esize == 8 ? (round_radix(m, esize, 0) >= 25 ? 255 : (m >= 2048 ? 104 : 80))
+                      : (round_radix(m, esize, 0) <= 9 ? 128 : 255);
+}
+constexpr int min_blocks(int m, int esize) {
+    return clampi(65536 / (pass_threads(m, esize) * reg_target(m, esize)), 1, 8);
+}
 
 }  // namespace pac

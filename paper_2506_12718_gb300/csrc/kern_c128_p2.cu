@@ -1,4 +1,4 @@
-// Pass-kernel instantiations: double2, group sizes that are powers of 2.
+// Pass-kernel and convolution-kernel instantiations: double2, group sizes that are powers of 2.
 #include "kern_launch.cuh"
 
 namespace pac {
@@ -16,6 +16,40 @@ cudaError_t launch_pass_c128_p2(int M, const PassArgs& a, cudaStream_t s) {
         case 512: return launch_M<double2, 512>(a, s);
         case 1024: return launch_M<double2, 1024>(a, s);
         case 2048: return launch_M<double2, 2048>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int conv_grid_c128_p2(int M, int dev) {
+    switch (M) {
+        case 2: return conv_grid<double2, 2>(dev);
+        case 4: return conv_grid<double2, 4>(dev);
+        case 8: return conv_grid<double2, 8>(dev);
+        case 16: return conv_grid<double2, 16>(dev);
+        case 32: return conv_grid<double2, 32>(dev);
+        case 64: return conv_grid<double2, 64>(dev);
+        case 128: return conv_grid<double2, 128>(dev);
+        case 256: return conv_grid<double2, 256>(dev);
+        case 512: return conv_grid<double2, 512>(dev);
+        case 1024: return conv_grid<double2, 1024>(dev);
+        case 2048: return conv_grid<double2, 2048>(dev);
+        default: return 0;
+    }
+}
+
+cudaError_t launch_conv_c128_p2(int M, ConvArgs& args, int grid, cudaStream_t s) {
+    switch (M) {
+        case 2: return launch_conv_M<double2, 2>(args, grid, s);
+        case 4: return launch_conv_M<double2, 4>(args, grid, s);
+        case 8: return launch_conv_M<double2, 8>(args, grid, s);
+        case 16: return launch_conv_M<double2, 16>(args, grid, s);
+        case 32: return launch_conv_M<double2, 32>(args, grid, s);
+        case 64: return launch_conv_M<double2, 64>(args, grid, s);
+        case 128: return launch_conv_M<double2, 128>(args, grid, s);
+        case 256: return launch_conv_M<double2, 256>(args, grid, s);
+        case 512: return launch_conv_M<double2, 512>(args, grid, s);
+        case 1024: return launch_conv_M<double2, 1024>(args, grid, s);
+        case 2048: return launch_conv_M<double2, 2048>(args, grid, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,4 +1,5 @@
-// Dispatch of a pass to its instantiation by element type and group size.
+// Dispatch of a pass (or a whole single-launch convolution) to its
+// instantiation by element type and group size.
 #include "pac_internal.h"
 
 namespace pac {
@@ -7,13 +8,28 @@ cudaError_t launch_pass_c64_p2(int M, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_pass_c64_p35(int M, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_pass_c128_p2(int M, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_pass_c128_p35(int M, const PassArgs& a, cudaStream_t s);
+int conv_grid_c64_p2(int M, int dev);
+int conv_grid_c64_p35(int M, int dev);
+int conv_grid_c128_p2(int M, int dev);
+int conv_grid_c128_p35(int M, int dev);
+cudaError_t launch_conv_c64_p2(int M, ConvArgs& args, int grid, cudaStream_t s);
+cudaError_t launch_conv_c64_p35(int M, ConvArgs& args, int grid, cudaStream_t s);
+cudaError_t launch_conv_c128_p2(int M, ConvArgs& args, int grid, cudaStream_t s);
+cudaError_t launch_conv_c128_p35(int M, ConvArgs& args, int grid, cudaStream_t s);
 
-cudaError_t launch_pass_c64(int M, const PassArgs& a, cudaStream_t s) {
-    return (M % 2 == 0) ? launch_pass_c64_p2(M, a, s) : launch_pass_c64_p35(M, a, s);
+cudaError_t launch_pass(int esize, int M, const PassArgs& a, cudaStream_t s) {
+    if (esize == 8) return (M % 2 == 0) ? launch_pass_c64_p2(M, a, s) : launch_pass_c64_p35(M, a, s);
+    return (M % 2 == 0) ? launch_pass_c128_p2(M, a, s) : launch_pass_c128_p35(M, a, s);
 }
 
-cudaError_t launch_pass_c128(int M, const PassArgs& a, cudaStream_t s) {
-    return (M % 2 == 0) ? launch_pass_c128_p2(M, a, s) : launch_pass_c128_p35(M, a, s);
+int conv_grid(int esize, int M, int dev) {
+    if (esize == 8) return (M % 2 == 0) ? conv_grid_c64_p2(M, dev) : conv_grid_c64_p35(M, dev);
+    return (M % 2 == 0) ? conv_grid_c128_p2(M, dev) : conv_grid_c128_p35(M, dev);
+}
+
+cudaError_t launch_conv(int esize, int M, ConvArgs& args, int grid, cudaStream_t s) {
+    if (esize == 8) return (M % 2 == 0) ? launch_conv_c64_p2(M, args, grid, s) : launch_conv_c64_p35(M, args, grid, s);
+    return (M % 2 == 0) ? launch_conv_c128_p2(M, args, grid, s) : launch_conv_c128_p35(M, args, grid, s);
 }
 
 int pass_kernel_supported(int M, int esize) {

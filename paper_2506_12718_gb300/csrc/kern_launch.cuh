@@ -9,29 +9,84 @@
 
 namespace pac {
 
-template <typename V, int M>
-cudaError_t launch_M(const PassArgs& a, cudaStream_t s) {
-    constexpr int smem = tile_smem_bytes(M, sizeof(V));
-    static std::atomic<int> resident[64];  // CTAs per SM, per device; 0 = not set up
+template <typename V, int M, bool LINES>
+cudaError_t launch_variant(const PassArgs& a, cudaStream_t s) {
+    using SH = Shape<V, M>;
+    constexpr int smem = pass_smem_bytes<V, M>(LINES);
+    static std::atomic<int> resident[64];  // per device: CTAs per SM; 0 = not set up
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     int per_sm = resident[dev].load(std::memory_order_relaxed);
     if (per_sm == 0) {
-        e = cudaFuncSetAttribute(pass_kernel<V, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(pass_kernel<V, M, LINES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<V, M>, kThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<V, M, LINES>, SH::NT, smem);
         if (e != cudaSuccess) return e;
         per_sm = nb > 0 ? nb : 1;
         resident[dev].store(per_sm, std::memory_order_relaxed);
     }
+    if (a.tiles <= 0) return cudaSuccess;
+    if (a.tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int64_t cap = (int64_t)per_sm * device_sm_count(dev);
     const int64_t grid = a.tiles < cap ? a.tiles : cap;
-    if (grid <= 0) return cudaSuccess;
-    pass_kernel<V, M><<<(unsigned)grid, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(SH::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, pass_kernel<V, M, LINES>, a);
+}
+
+template <typename V, int M>
+cudaError_t launch_M(const PassArgs& a, cudaStream_t s) {
+    return a.C == 1 ? launch_variant<V, M, true>(a, s) : launch_variant<V, M, false>(a, s);
+}
+
+// Co-resident grid size of the cooperative convolution kernel (0 on error).
+template <typename V, int M>
+int conv_grid(int dev) {
+    using SH = Shape<V, M>;
+    constexpr int smem = pass_smem_bytes<V, M>(true) > pass_smem_bytes<V, M>(false) ? pass_smem_bytes<V, M>(true)
+                                                                                      : pass_smem_bytes<V, M>(false);
+    static std::atomic<int> resident[64];
+    if (dev < 0 || dev >= 64) return 0;
+    int per_sm = resident[dev].load(std::memory_order_relaxed);
+    if (per_sm == 0) {
+        if (cudaFuncSetAttribute(conv_kernel<V, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+            return 0;
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, conv_kernel<V, M>, SH::NT, smem) != cudaSuccess || nb < 1)
+            return 0;
+        per_sm = nb;
+        resident[dev].store(per_sm, std::memory_order_relaxed);
+    }
+    return per_sm * device_sm_count(dev);
+}
+
+template <typename V, int M>
+cudaError_t launch_conv_M(ConvArgs& args, int grid, cudaStream_t s) {
+    using SH = Shape<V, M>;
+    constexpr int smem = pass_smem_bytes<V, M>(true) > pass_smem_bytes<V, M>(false) ? pass_smem_bytes<V, M>(true)
+                                                                                      : pass_smem_bytes<V, M>(false);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(SH::NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, conv_kernel<V, M>, args);
 }
 
 }  // namespace pac

@@ -27,7 +27,7 @@ struct GroupPlan {
     int64_t Q = 1;          // columns = N / M
     int tw_T = 1, tw_shift = 0;
     bool has_ext = false;
-    size_t off_twi = 0, off_lo = 0, off_hi = 0, off_rowmap = 0, off_freq = 0;  // byte offsets in tables
+    size_t off_twi = 0, off_lo = 0, off_hi = 0, off_rowmap = 0, off_freq = 0, off_r2g = 0, off_r2f = 0;  // in tables
 };
 
 void set_error(const char* fmt, ...);
@@ -37,10 +37,17 @@ int cuda_fail(cudaError_t e, const char* what);
 // exp(-2 pi i e / L) in FP64 with the angle reduced exactly to an eighth turn
 void root_fp64(int64_t e, int64_t L, double* re, double* im);
 
-// kernel launchers (kern_c64.cu / kern_c128.cu)
-cudaError_t launch_pass_c64(int M, const PassArgs& a, cudaStream_t s);
-cudaError_t launch_pass_c128(int M, const PassArgs& a, cudaStream_t s);
+// kernel launchers (kern_dispatch.cu)
+cudaError_t launch_pass(int esize, int M, const PassArgs& a, cudaStream_t s);
+int conv_grid(int esize, int M, int dev);  // co-resident CTAs of the single-launch kernel (0: unavailable)
+cudaError_t launch_conv(int esize, int M, ConvArgs& args, int grid, cudaStream_t s);
 int pass_kernel_supported(int M, int esize);
+
+// Barrier counters of single-launch convolutions: a device pool of slots,
+// handed out round robin; *base receives the slot's counter value at launch.
+int barrier_slot(int device, unsigned** counter, unsigned* base, unsigned arrivals, unsigned** error);
+// Device error word of the library (barrier timeouts); returns and clears it.
+int take_device_error(int device, unsigned* value);
 
 // auxiliary kernels (aux.cu)
 cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64_t* const* idx_dev,
@@ -59,6 +66,8 @@ struct pac_plan_s {
     pac_dtype dtype = PAC_C64;
     int esize = 8;
     int64_t N = 1;
+    int uniform_m = 0;  // group size shared by every pass (0: sizes differ)
+    bool single_launch = false;  // run a pass sequence as one cooperative launch
     int device = 0;
     std::vector<std::vector<int>> stages;          // per axis, DIF order
     std::vector<std::vector<int64_t>> pos_to_freq; // per axis

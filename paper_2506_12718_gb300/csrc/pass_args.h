@@ -18,6 +18,8 @@ struct PassArgs {
     const void* tw_hi;      // w_L^{T v}, v in [0, ceil(L/T))
     const int* rowmap;      // [M] shared-memory row that holds global row g after the rounds
     const int* freq;        // [M] group frequency k' held by global row g
+    const int* r2g;         // [M] global row of shared-memory row r (inverse of rowmap)
+    const int* r2f;         // [M] group frequency k' of shared-memory row r
     int64_t Q;              // columns
     int64_t C;              // row stride in elements
     int64_t I;              // inner stride of the axis: column j = (q mod C) / I
@@ -27,6 +29,18 @@ struct PassArgs {
     int mode;               // PassMode
     int has_ext;            // apply w_L^{j k'} (L' > 1)
     double scale;           // applied on store in kFwd (filter spectrum 1/N); 1 = none
+};
+
+constexpr int kMaxPasses = 12;
+
+// A whole convolution (or forward transform) as one cooperative launch:
+// passes run as phases separated by grid-wide barriers.
+struct ConvArgs {
+    PassArgs pass[kMaxPasses];
+    int npasses;
+    unsigned* barrier;  // arrival counter (monotonic; never reset)
+    unsigned base;      // its value when this launch starts
+    unsigned* error;    // set to 1 if a barrier wait gave up
 };
 
 }  // namespace pac

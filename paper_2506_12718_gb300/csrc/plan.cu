@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -250,7 +251,7 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
         }
         pl->N *= dims[a];
     }
-    if (pl->N > (int64_t(1) << 34)) {
+    if (pl->N >= (int64_t(1) << 31)) {
         delete pl;
         return fail(PAC_ERR_SIZE, "N = %lld too large", (long long)pl->N);
     }
@@ -305,9 +306,24 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
             off = align16(off + (size_t)g.M * sizeof(int));
             g.off_freq = off;
             off = align16(off + (size_t)g.M * sizeof(int));
+            g.off_r2g = off;
+            off = align16(off + (size_t)g.M * sizeof(int));
+            g.off_r2f = off;
+            off = align16(off + (size_t)g.M * sizeof(int));
             pl->groups.push_back(g);
             Lcur = g.Lp;
         }
+    }
+
+    // single-launch (cooperative) form of the pass sequence: opt-in per plan,
+    // PAC_SINGLE_LAUNCH=1 in the environment when the plan is created
+    const char* sl = std::getenv("PAC_SINGLE_LAUNCH");
+    pl->single_launch = sl && sl[0] == '1';
+    pl->uniform_m = 0;
+    if (!pl->groups.empty()) {
+        pl->uniform_m = pl->groups[0].M;
+        for (const GroupPlan& g : pl->groups)
+            if (g.M != pl->uniform_m) pl->uniform_m = 0;
     }
 
     // host blob of every table
@@ -336,15 +352,19 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
         const int nr = round_count(g.M, pl->esize);
         std::vector<int> rr(nr);
         for (int i = 0; i < nr; ++i) rr[i] = round_radix(g.M, pl->esize, i);
-        std::vector<int64_t> r2f(g.M);
-        reverse_table(rr.data(), nr, r2f.data());
+        std::vector<int64_t> row_freq(g.M);
+        reverse_table(rr.data(), nr, row_freq.data());
         std::vector<int> f2r(g.M);
-        for (int r = 0; r < g.M; ++r) f2r[r2f[r]] = r;
+        for (int r = 0; r < g.M; ++r) f2r[row_freq[r]] = r;
         int* rowmap = reinterpret_cast<int*>(blob.data() + g.off_rowmap);
         int* freq = reinterpret_cast<int*>(blob.data() + g.off_freq);
+        int* r2g = reinterpret_cast<int*>(blob.data() + g.off_r2g);
+        int* r2f = reinterpret_cast<int*>(blob.data() + g.off_r2f);
         for (int gg = 0; gg < g.M; ++gg) {
             freq[gg] = (int)f[gg];
             rowmap[gg] = f2r[f[gg]];
+            r2g[rowmap[gg]] = gg;
+            r2f[rowmap[gg]] = (int)f[gg];
         }
     }
 
@@ -415,7 +435,7 @@ static void timer_mark(cudaStream_t s, int id, bool before) {
     t->ev.push_back(e);
 }
 
-int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale, cudaStream_t s) {
+static PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale) {
     PassArgs a;
     const unsigned char* t = static_cast<const unsigned char*>(p->d_tables);
     a.src = src;
@@ -426,6 +446,8 @@ int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* ds
     a.tw_hi = g.has_ext ? t + g.off_hi : nullptr;
     a.rowmap = reinterpret_cast<const int*>(t + g.off_rowmap);
     a.freq = reinterpret_cast<const int*>(t + g.off_freq);
+    a.r2g = reinterpret_cast<const int*>(t + g.off_r2g);
+    a.r2f = reinterpret_cast<const int*>(t + g.off_r2f);
     a.Q = g.Q;
     a.C = g.C;
     a.I = g.I;
@@ -436,11 +458,56 @@ int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* ds
     a.mode = mode;
     a.has_ext = g.has_ext ? 1 : 0;
     a.scale = scale;
+    return a;
+}
+
+int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale, cudaStream_t s) {
+    const PassArgs a = make_pass(p, g, mode, src, dst, scale);
     const int kid = mode == kFwd ? 0 : (mode == kFused ? 1 : 2);
     timer_mark(s, kid, true);
-    cudaError_t e = p->esize == 8 ? launch_pass_c64(g.M, a, s) : launch_pass_c128(g.M, a, s);
+    cudaError_t e = launch_pass(p->esize, g.M, a, s);
     timer_mark(s, kid, false);
     if (e != cudaSuccess) return cuda_fail(e, "pass kernel launch");
+    return PAC_OK;
+}
+
+// One step of a pass sequence: group index, mode, source, destination, scale.
+struct Step {
+    int group, mode;
+    const void* src;
+    void* dst;
+    double scale;
+};
+
+// Run a pass sequence: as one cooperative launch when every group has the
+// same size M and single launches are allowed, else one launch per pass.
+static int run_steps(pac_plan p, const std::vector<Step>& steps, cudaStream_t s, bool allow_single) {
+    const int n = (int)steps.size();
+    bool single = allow_single && p->single_launch && n > 1 && n <= kMaxPasses && p->uniform_m > 0;
+    int grid = 0;
+    if (single) {
+        grid = conv_grid(p->esize, p->uniform_m, p->device);
+        single = grid > 0;
+    }
+    if (single) {
+        ConvArgs args;
+        args.npasses = n;
+        for (int i = 0; i < n; ++i) {
+            const Step& st = steps[i];
+            args.pass[i] = make_pass(p, p->groups[st.group], st.mode, st.src, st.dst, st.scale);
+        }
+        int rc = barrier_slot(p->device, &args.barrier, &args.base, (unsigned)((n - 1) * grid), &args.error);
+        if (rc) return rc;
+        timer_mark(s, 5, true);
+        cudaError_t e = launch_conv(p->esize, p->uniform_m, args, grid, s);
+        timer_mark(s, 5, false);
+        if (e != cudaSuccess) return cuda_fail(e, "convolution kernel launch");
+        return PAC_OK;
+    }
+    for (const Step& st : steps) {
+        int rc = run_pass(p, p->groups[st.group], st.mode, st.src, st.dst, st.scale, s);
+        if (rc) return rc;
+    }
     return PAC_OK;
 }
 
@@ -454,7 +521,7 @@ static cudaError_t timed_permute(pac_plan p, const int64_t* const* idx, const vo
 
 // Algorithm 11, lines 2-4, on device pointers: forward groups (the last fused
 // with the product and the first inverse group), then the inverse groups.
-int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s) {
+int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s, bool allow_single) {
     const int G = (int)p->groups.size();
     if (G == 0) {  // N = 1
         timer_mark(s, 4, true);
@@ -462,16 +529,13 @@ int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s) {
         timer_mark(s, 4, false);
         return e == cudaSuccess ? PAC_OK : cuda_fail(e, "pointwise kernel");
     }
-    for (int i = 0; i < G; ++i) {
-        int rc = run_pass(p, p->groups[i], i == G - 1 ? kFused : kFwd, i == 0 ? x : y, y, 1.0, s);
-        if (rc) return rc;
-    }
-    for (int i = G - 2; i >= 0; --i) {
-        int rc = run_pass(p, p->groups[i], kInv, y, y, 1.0, s);
-        if (rc) return rc;
-    }
-    return PAC_OK;
+    std::vector<Step> steps;
+    for (int i = 0; i < G; ++i) steps.push_back({i, i == G - 1 ? kFused : kFwd, i == 0 ? x : y, y, 1.0});
+    for (int i = G - 2; i >= 0; --i) steps.push_back({i, kInv, y, y, 1.0});
+    return run_steps(p, steps, s, allow_single);
 }
+
+int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s) { return run_convolve(p, x, y, s, true); }
 
 int run_forward(pac_plan p, const void* x, void* xhat, double scale, cudaStream_t s) {
     const int G = (int)p->groups.size();
@@ -479,11 +543,9 @@ int run_forward(pac_plan p, const void* x, void* xhat, double scale, cudaStream_
         cudaError_t e = launch_pointwise_mul(p->esize, p->N, x, nullptr, xhat, scale, s);
         return e == cudaSuccess ? PAC_OK : cuda_fail(e, "pointwise kernel");
     }
-    for (int i = 0; i < G; ++i) {
-        int rc = run_pass(p, p->groups[i], kFwd, i == 0 ? x : xhat, xhat, i == G - 1 ? scale : 1.0, s);
-        if (rc) return rc;
-    }
-    return PAC_OK;
+    std::vector<Step> steps;
+    for (int i = 0; i < G; ++i) steps.push_back({i, kFwd, i == 0 ? x : xhat, xhat, i == G - 1 ? scale : 1.0});
+    return run_steps(p, steps, s, true);
 }
 
 }  // namespace pac
@@ -628,11 +690,9 @@ extern "C" int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev,
     // iFFT = uiFFT o permute (Algorithm 9)
     e = timed_permute(p, to_rev, p->d_scratch, y_dev, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "permute kernel");
-    for (int i = G - 1; i >= 0; --i) {
-        rc = run_pass(p, p->groups[i], kInv, y_dev, y_dev, 1.0, s);
-        if (rc) return rc;
-    }
-    return PAC_OK;
+    std::vector<Step> steps;
+    for (int i = G - 1; i >= 0; --i) steps.push_back({i, kInv, y_dev, y_dev, 1.0});
+    return run_steps(p, steps, s, true);
 }
 
 extern "C" int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, void* stream,
@@ -681,6 +741,10 @@ extern "C" int pac_plan_reverse_table(pac_plan p, int axis, int64_t* pos_to_freq
     return PAC_OK;
 }
 
+static bool single_ok(pac_plan p, int npasses) {
+    return p->single_launch && npasses > 1 && npasses <= kMaxPasses && p->uniform_m > 0 && conv_grid(p->esize, p->uniform_m, p->device) > 0;
+}
+
 extern "C" int pac_plan_query(pac_plan p, int key, int64_t* value) {
     if (!p || !value) return fail(PAC_ERR_ARG, "null argument");
     const int64_t G = (int64_t)p->groups.size();
@@ -688,9 +752,19 @@ extern "C" int pac_plan_query(pac_plan p, int key, int64_t* value) {
         case PAC_Q_NDIM: *value = p->ndim; break;
         case PAC_Q_N_TOTAL: *value = p->N; break;
         case PAC_Q_ELEM_BYTES: *value = p->esize; break;
-        case PAC_Q_LAUNCHES_CONVOLVE: *value = G == 0 ? 1 : 2 * G - 1; break;
-        case PAC_Q_LAUNCHES_PERMUTED: *value = 2 * std::max<int64_t>(G, 0) + 2; break;
-        case PAC_Q_LAUNCHES_FORWARD: *value = std::max<int64_t>(G, 1); break;
+        case PAC_Q_LAUNCHES_CONVOLVE:
+            *value = G == 0 ? 1 : (single_ok(p, 2 * G - 1) ? 1 : 2 * G - 1);
+            break;
+        case PAC_Q_LAUNCHES_PERMUTED:
+            *value = (G == 0 ? 1 : (single_ok(p, G) ? 1 : G)) * 2 + 2;
+            break;
+        case PAC_Q_LAUNCHES_FORWARD: *value = G == 0 ? 1 : (single_ok(p, G) ? 1 : G); break;
+        case PAC_Q_DEVICE_ERROR: {
+            unsigned v = 0;
+            if (int rc = take_device_error(p->device, &v)) return rc;
+            *value = v;
+            break;
+        }
         case PAC_Q_DEVICE_BYTES: *value = (int64_t)p->device_bytes; break;
         case PAC_Q_HAS_SPECTRUM: *value = p->has_spec ? 1 : 0; break;
         default: return fail(PAC_ERR_ARG, "unknown query key %d", key);

@@ -24,7 +24,7 @@
 #include "pac_internal.h"
 
 namespace pac {
-int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s);
+int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s, bool allow_single);
 }
 
 using namespace pac;
@@ -120,7 +120,8 @@ static void scheduler(pac_queue q) {
             if (q->fault_launch > 0 && (int64_t)q->admitted == q->fault_launch) {
                 rc = PAC_ERR_CUDA;  // injected host-side launch failure
             } else {
-                rc = run_convolve(r->plan, r->x, r->y, q->streams[slot]);
+                // per-pass launches: requests on different streams interleave on the SMs
+                rc = run_convolve(r->plan, r->x, r->y, q->streams[slot], false);
                 if (rc == PAC_OK) {
                     cudaError_t e = cudaLaunchHostFunc(q->streams[slot], on_request_done, r);
                     if (e != cudaSuccess) rc = PAC_ERR_CUDA;
