@@ -187,6 +187,28 @@ int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev, void* stre
 int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, void* stream, int max_launches,
                        float* launch_ms, int* kernel_ids, int* n_launches);
 
+/*
+ * Allocation-free form of pac_convolve_permuted, for callers that cannot
+ * allocate device memory: processes whose GPU memory is owned by another
+ * allocator that reserved nearly all of it up front, services under a hard
+ * device-memory quota that forbids growth after start-up, and latency-critical
+ * paths that cannot afford cudaMalloc's implicit synchronisation.  The paper
+ * has no counterpart; it is an interface convenience of this library.
+ *
+ * Computes the same result as pac_convolve_permuted (same stage kernels and
+ * explicit index-reversal passes) but allocates nothing: its N-element
+ * intermediate lives in one fixed 8 MiB static device buffer inside the
+ * library (held by every GPU that loads the library until exit), and the
+ * index-reversal positions are computed, not read from allocated tables.
+ * Limit: N * elem size <= 8 MiB (1,048,576 complex64 or 524,288 complex128
+ * elements); larger plans return PAC_ERR_SIZE.  All calls share the buffer:
+ * calls whose work overlaps on the GPU race (serialise them on one stream).
+ * The buffer needs no clearing (every element is written before it is read).
+ * The first call on each device looks up the buffer's device address; make it
+ * before any stream capture.  Asynchronous on `stream`; y_dev may equal x_dev.
+ */
+int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void* y_dev, void* stream);
+
 /* Plan facts for benches and tests: see PAC_Q_* keys. */
 int pac_plan_query(pac_plan p, int key, int64_t* value);
 enum {

@@ -58,6 +58,7 @@ _SIGS = {
     "pac_plan_reverse_table": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
     "pac_forward_unordered": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_convolve_permuted": (_i32, [_vp, _vp, _vp, _vp]),
+    "pac_convolve_permuted_noalloc": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_plan_query": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
     "pac_convolve_timed": (_i32, [_vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -187,6 +188,11 @@ def pac_forward_unordered(plan: int, x_dev, xhat_dev, stream=None) -> None:
 
 def pac_convolve_permuted(plan: int, x_dev, y_dev, stream=None) -> None:
     _check(load().pac_convolve_permuted(plan, _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+def pac_convolve_permuted_noalloc(plan: int, x_dev, y_dev, stream=None) -> None:
+    """Allocation-free permuted convolution (fixed 8 MiB static scratch; see include/pac.h)."""
+    _check(load().pac_convolve_permuted_noalloc(plan, _ptr(x_dev), _ptr(y_dev), _stream(stream)))
 
 
 def pac_plan_stages(plan: int, axis: int) -> list[int]:
