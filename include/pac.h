@@ -9,10 +9,14 @@
  * 2-D form Section 3; d-D form Section 4) without ever executing an
  * index-reversal permutation: the forward transform is the decimation-in-
  * frequency product A^T (natural order in, index-reversed order out), the
- * filter spectrum A^T h is stored once in that index-reversed order, and the
+ * filter spectrum A^T h is computed once and kept on the device, and the
  * inverse is the conjugate decimation-in-time product conj(A) (reversed in,
  * natural out), Eq. (35) in 1-D, Eq. (80) in 2-D and the d-D form of
- * Section 4.1.  Per axis, n = r^t or a mixed-radix product (Section 6.1).
+ * Section 4.1.  The spectrum is stored in the order in which the kernel
+ * that multiplies by it reads it (a fixed rearrangement of the
+ * index-reversed order, applied once when the spectrum is made), so the
+ * convolution itself never permutes anything.  Per axis, n = r^t or a
+ * mixed-radix product (Section 6.1).
  *
  * Conventions shared by every entry point:
  *  - Arrays are complex, interleaved (re, im), row-major with the last index
@@ -82,8 +86,9 @@ int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, p
 int pac_plan_destroy(pac_plan p);
 
 /*
- * Algorithm 11, line 1: store Hhat = A^T h / N (all axes, index-reversed
- * order, with the inverse's 1/N folded in) in plan-owned device memory.
+ * Algorithm 11, line 1: store Hhat = A^T h / N (all axes, with the
+ * inverse's 1/N folded in) in plan-owned device memory, in the order the
+ * fused forward/product/inverse pass reads it.
  * h_dev is read, not retained.  Synchronises the plan's internal stream.
  * Calling it again replaces the spectrum.
  */

@@ -1,6 +1,7 @@
 // Auxiliary kernels: the index-reversal permutation of the comparator
 // (Algorithm 1, a gather through per-axis index tables, optionally fused with
-// the Hadamard product) and a pointwise product for the degenerate N = 1 plan.
+// the Hadamard product), the one-time reordering of a filter spectrum into
+// its storage order, and a pointwise product for the degenerate N = 1 plan.
 #include <algorithm>
 
 #include "fft_device.cuh"
@@ -37,6 +38,33 @@ __global__ void pointwise_kernel(int64_t n, const V* a, const V* __restrict__ b,
         if (scale != 1.0) v = cscale(v, (typename Real<V>::T)scale);
         out[i] = v;
     }
+}
+
+// Between the plain index-reversed order of a spectrum and its storage order
+// (see SpecOrder): to_kernel ? dst[slot(e)] = src[e] : dst[e] = src[slot(e)].
+template <typename V>
+__global__ void spec_order_kernel(const SpecOrder o, uint32_t n, const V* __restrict__ src, V* __restrict__ dst,
+                                  int to_kernel) {
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const uint32_t k = spec_slot(o, e);
+        if (to_kernel)
+            dst[k] = src[e];
+        else
+            dst[e] = src[k];
+    }
+}
+
+cudaError_t launch_spec_order(int esize, const SpecOrder& o, int64_t n, const void* src, void* dst, bool to_kernel,
+                              cudaStream_t s) {
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, 8192);
+    if (esize == 8)
+        spec_order_kernel<float2><<<(unsigned)blocks, threads, 0, s>>>(o, (uint32_t)n, (const float2*)src,
+                                                                      (float2*)dst, to_kernel ? 1 : 0);
+    else
+        spec_order_kernel<double2><<<(unsigned)blocks, threads, 0, s>>>(o, (uint32_t)n, (const double2*)src,
+                                                                       (double2*)dst, to_kernel ? 1 : 0);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64_t* const* idx_dev,

@@ -7,7 +7,7 @@
 namespace pac {
 
 constexpr int kMaxRounds = 6;
-constexpr int kTileBudget = 8 * 1024;  // target shared-memory bytes of one tile
+constexpr int kTileBytes = 32 * 1024;  // target data bytes of one tile
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 constexpr int base_of(int m) { return m % 2 == 0 ? 2 : (m % 3 == 0 ? 3 : (m % 5 == 0 ? 5 : 1)); }
@@ -39,29 +39,57 @@ constexpr int round_radix(int m, int esize, int i) {
 constexpr int floor_pow2(int v) { return v >= 2 ? 2 * floor_pow2(v / 2) : 1; }
 constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
-// Columns per tile: about kTileBudget bytes, at least one 32-byte sector per row.
+// Columns per tile: about kTileBytes of data, at least one 32-byte sector and
+// at most 256 bytes per row segment (so a warp's 32 threads cover whole rows).
 constexpr int tile_w(int m, int esize) {
-    return clampi(floor_pow2(kTileBudget / (m * esize)), 32 / esize, 256);
+    return clampi(floor_pow2(kTileBytes / (m * esize)), 32 / esize, 256 / esize);
 }
-// Row pitch of the tile in elements (odd: conflict-free column walks).
-constexpr int tile_pitch(int m, int esize) { return tile_w(m, esize) + 1; }
-constexpr int tile_elems(int m, int esize) { return m * tile_pitch(m, esize); }
-// Tile buffers per CTA: two (the copy of the next tile overlaps the current
-// one) when they fit in a quarter of the shared memory, else one.
-constexpr int tile_stages(int m, int esize) { return 2 * tile_elems(m, esize) * esize <= 56 * 1024 ? 2 : 1; }
 
-// Threads per CTA: one per task of the first round (a multiple of the warp
-// size and of the tile width), within [64, 256].
+// Row padding of the shared-memory exchange buffer, in elements.  Chosen per
+// group size by counting bank wavefronts of every round's access pattern
+// (column-fastest and in-line-fastest task orders) over pads 0..16 and taking
+// the smallest pad with the fewest wavefronts.
+constexpr int tile_pad(int m, int esize) {
+    if (esize == 8) {
+        switch (m) {
+            case 32: return 4;
+            case 64: case 128: case 2187: case 625: case 3125: case 4096: return 2;
+            case 81: case 243: return 9;
+            case 729: return 10;
+            case 125: return 13;
+            case 2: case 4: case 8: case 16: case 3: case 9: case 27: case 5: case 25: return 0;
+            default: return 1;
+        }
+    }
+    switch (m) {
+        case 27: case 243: return 3;
+        case 729: case 125: return 5;
+        case 625: return 7;
+        case 2: case 4: case 8: case 16: case 32: case 3: case 9: case 5: case 25: return 0;
+        default: return 1;
+    }
+}
+// Row pitch of the exchange buffer in elements.
+constexpr int tile_pitch(int m, int esize) { return tile_w(m, esize) + tile_pad(m, esize); }
+constexpr int tile_elems(int m, int esize) { return m * tile_pitch(m, esize); }
+
+// Threads per CTA: one per task of the first (largest) round, rounded up to
+// whole warps, within [64, 512].  A multiple of 32, hence of the tile width,
+// so in the rows case every task of a thread has the same column.
 constexpr int pass_threads(int m, int esize) {
-    return clampi(((tile_w(m, esize) * (m / round_radix(m, esize, 0)) + 31) / 32) * 32, 64, 256);
+    return clampi(((tile_w(m, esize) * (m / round_radix(m, esize, 0)) + 31) / 32) * 32, 64, 512);
 }
 
 // Register budget per thread the kernel is compiled for: enough for the
 // largest in-register round without spilling, small enough to keep several
-// CTAs resident.  FP64 rounds of 16+ complex values keep the full file.
+// CTAs resident.
+constexpr int max_round_radix(int m, int esize) { return round_radix(m, esize, 0); }  // rounds are sorted, largest first
 constexpr int reg_target(int m, int esize) {
-    return esize == 8 ? (round_radix(m, esize, 0) >= 25 ? 255 : (m >= 2048 ? 104 : 80))
-                      : (round_radix(m, esize, 0) <= 9 ? 128 : 255);
+    return esize == 8
+               ? (max_round_radix(m, esize) >= 25 ? 168
+                  : (round_count(m, esize) >= 2 && round_radix(m, esize, 1) >= 16 ? 96 : 64))
+               : (max_round_radix(m, esize) >= 25 ? 255
+                  : (round_count(m, esize) >= 2 && round_radix(m, esize, 1) >= 16 ? 168 : 128));
 }
 constexpr int min_blocks(int m, int esize) {
     return clampi(65536 / (pass_threads(m, esize) * reg_target(m, esize)), 1, 8);

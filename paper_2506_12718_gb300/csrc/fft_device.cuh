@@ -159,6 +159,15 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V* v)
 }
 
 // ------------------------------------------------------------------ passes
+//
+// One tile = W columns of the pass (columns q0 .. q0+W-1) x all M rows of the
+// group.  The first round of a tile reads its R values straight from global
+// memory into registers (coalesced along the tile's columns, or along a line
+// in the lines case), every later round exchanges through a shared-memory
+// buffer of M rows x P (pitch) elements, and the last round writes registers
+// straight to global memory.  So a pass costs one global read and one global
+// write per element, plus one shared-memory write and read per round
+// boundary; there is no separate copy-in or copy-out of the tile.
 
 template <typename V> __device__ __forceinline__ V ld_tw(const void* p, int64_t i) {
     return __ldg(reinterpret_cast<const V*>(p) + i);
@@ -177,19 +186,6 @@ template <typename V> __device__ __forceinline__ V ext_twiddle(const PassArgs& a
     return cmul(ld_tw<V>(a.tw_lo, lo), ld_tw<V>(a.tw_hi, hi));
 }
 
-// asynchronous global -> shared copies (one element per instruction)
-template <int BYTES> __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
 template <int M, int ES, int RI> struct RoundGeom {
     static constexpr int R = round_radix(M, ES, RI);
     // block length before this round: M / (R_0 ... R_{RI-1})
@@ -200,37 +196,6 @@ template <int M, int ES> struct RoundGeom<M, ES, -1> {
     static constexpr int R = 1, S = M * 1, SP = M;
 };
 
-// Per-tile facts shared by the rounds of one tile.  Rows case (C > 1): a
-// thread's column w = tid mod W is fixed within a tile.  Offsets are 32-bit
-// element offsets (plans keep N < 2^31).
-template <typename V> struct TileCtx {
-    const PassArgs* a;
-    V* s;              // tile in shared memory, [m][w], pitch P
-    const V* hs;       // kFused, lines case: the spectrum tile in shared memory (or null)
-    const V* twi;      // w_M^u
-    uint32_t q0;       // first column of the tile
-    uint32_t base;     // rows case: global offset of row 0 of this thread's column
-    uint32_t C;        // row stride
-    uint32_t j;        // rows case: external twiddle column j = (q mod C) / I
-    bool valid;        // rows case: this thread's column exists (q < Q)
-    bool do_scale;     // kFwd: multiply by `scale` on store (decided once, not per element)
-    typename Real<V>::T scale;
-};
-
-// Task decomposition of round RI: task tau -> column w (fastest, so a warp
-// reads consecutive shared-memory words), in-block offset jp, block bp.
-template <int M, int W, int ES, int RI> struct Task {
-    using G = RoundGeom<M, ES, RI>;
-    static constexpr int TASKS = W * (M / G::R);
-    int w, jp, row0;
-    __device__ __forceinline__ explicit Task(int tau) {
-        w = tau % W;
-        const int t2 = tau / W;
-        jp = t2 % G::SP;
-        row0 = (t2 / G::SP) * G::S + jp;
-    }
-};
-
 template <typename V, int M> struct Shape {
     static constexpr int ES = sizeof(V);
     static constexpr int W = tile_w(M, ES);
@@ -238,221 +203,240 @@ template <typename V, int M> struct Shape {
     static constexpr int NR = round_count(M, ES);
     static constexpr int NT = pass_threads(M, ES);
     static constexpr int TILE = M * P;
-    // the fused lines pass stages the spectrum tile in shared memory when it fits
-    static constexpr bool SPEC_SMEM = 2 * TILE * ES <= 200 * 1024;
+    static_assert(NT % W == 0, "a thread's tasks must share one column in the rows case");
 };
 
-// In-place forward round (rounds 0 .. NR-2): DFT_R then twiddles w_S^{jp k}.
-template <typename V, int M, int RI>
-__device__ __forceinline__ void fwd_round(const TileCtx<V>& c) {
-    using SH = Shape<V, M>;
-    using G = RoundGeom<M, SH::ES, RI>;
-    using T = Task<M, SH::W, SH::ES, RI>;
-    constexpr int R = G::R, SP = G::SP, STEP = M / G::S, P = SH::P;
-    for (int tau = threadIdx.x; tau < T::TASKS; tau += SH::NT) {
-        const T t(tau);
-        V v[R];
-#pragma unroll
-        for (int u = 0; u < R; ++u) v[u] = c.s[(t.row0 + SP * u) * P + t.w];
-        dft<R, false>(v);
-        if constexpr (SP > 1) {
-#pragma unroll
-            for (int k = 1; k < R; ++k) v[k] = cmul(v[k], c.twi[STEP * t.jp * k]);
-        }
-#pragma unroll
-        for (int u = 0; u < R; ++u) c.s[(t.row0 + SP * u) * P + t.w] = v[u];
-    }
-}
-
-// In-place inverse round RI (adjoint of forward round RI): conj twiddles,
-// then the conjugate DFT.  FIRST_EXT: the pass' first inverse round in kInv,
-// which also applies conj(w_L^{j k'}) to the rows loaded from the previous
-// pass.  LAST_GLOBAL: round 0 of the rows case, stored straight to global.
-template <typename V, int M, int RI, bool FIRST_EXT, bool LAST_GLOBAL>
-__device__ __forceinline__ void inv_round(const TileCtx<V>& c) {
-    using SH = Shape<V, M>;
-    using G = RoundGeom<M, SH::ES, RI>;
-    using T = Task<M, SH::W, SH::ES, RI>;
-    constexpr int R = G::R, SP = G::SP, STEP = M / G::S, P = SH::P;
-    const PassArgs& a = *c.a;
-    V* dst = reinterpret_cast<V*>(a.dst);
-    for (int tau = threadIdx.x; tau < T::TASKS; tau += SH::NT) {
-        const T t(tau);
-        V v[R];
-#pragma unroll
-        for (int u = 0; u < R; ++u) v[u] = c.s[(t.row0 + SP * u) * P + t.w];
-        if constexpr (FIRST_EXT) {
-            if (a.has_ext && c.j != 0) {
-#pragma unroll
-                for (int u = 0; u < R; ++u)
-                    v[u] = cmulc(v[u], ext_twiddle<V>(a, (int64_t)c.j * __ldg(a.r2f + t.row0 + SP * u)));
-            }
-        }
-        if constexpr (SP > 1) {
-#pragma unroll
-            for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], c.twi[STEP * t.jp * k]);
-        }
-        dft<R, true>(v);
-        if constexpr (LAST_GLOBAL) {
-            if (c.valid) {
-#pragma unroll
-                for (int u = 0; u < R; ++u) dst[c.base + (uint32_t)(t.row0 + SP * u) * c.C] = v[u];
-            }
+// Task tau of round RI: column w of the tile, offset jp inside its block of
+// S rows, first row row0 = block * S + jp; the task transforms rows
+// row0 + SP * u, u < R.  Column-fastest order (a warp covers consecutive
+// columns of the same row: coalesced in the rows case, conflict-free in shared
+// memory) or, for JFAST, offset-fastest order (a warp covers consecutive rows
+// of one line: coalesced in the lines case).
+template <int M, int ES, int W, int RI, bool JFAST> struct Task {
+    using G = RoundGeom<M, ES, RI>;
+    static constexpr int TASKS = W * (M / G::R);
+    int w, jp, row0;
+    __device__ __forceinline__ explicit Task(int tau) {
+        if constexpr (JFAST) {
+            jp = tau % G::SP;
+            const int t2 = tau / G::SP;
+            w = t2 % W;
+            row0 = (t2 / W) * G::S + jp;
         } else {
-#pragma unroll
-            for (int u = 0; u < R; ++u) c.s[(t.row0 + SP * u) * P + t.w] = v[u];
+            w = tau % W;
+            const int t2 = tau / W;
+            jp = t2 % G::SP;
+            row0 = (t2 / G::SP) * G::S + jp;
         }
     }
-}
+};
 
-template <typename V, int M, int RI, bool LINES>
-__device__ __forceinline__ void inv_rounds_from(const TileCtx<V>& c) {
-    // rounds RI, RI-1, ..., 0; round RI is not the pass' first (no external factor)
-    if constexpr (RI >= 0) {
-        inv_round<V, M, RI, false, (!LINES && RI == 0)>(c);
-        if constexpr (RI > 0 || LINES) __syncthreads();
-        inv_rounds_from<V, M, RI - 1, LINES>(c);
+// Storage order of the filter spectrum.  The spectrum is produced once and
+// read only by the last forward round of the fused pass, so it is stored in
+// the order that round reads it: element (tile t, register u, task tau) at
+// t * W * M + u * TASKS + tau, TASKS = W * M / R for the round's radix R
+// (column-fastest tasks, SP = 1: task tau = w + W * b handles rows b R + u).
+// spec_slot maps an element's position in the plain index-reversed (DIF)
+// order of the array to its slot.
+
+__device__ __forceinline__ uint32_t spec_slot(const SpecOrder& o, uint32_t e) {
+    uint32_t q, g;
+    if (o.C == 1) {
+        q = e / o.M;
+        g = e - q * o.M;
+    } else {
+        const uint32_t blk = o.M * o.C;
+        const uint32_t beta = e / blk, rem = e - beta * blk;
+        g = rem / o.C;
+        q = beta * o.C + (rem - g * o.C);
     }
+    const uint32_t t = q / o.W, w = q - t * o.W;
+    const uint32_t r = (uint32_t)__ldg(o.rowmap + g);
+    const uint32_t b = r / o.R, u = r - b * o.R;
+    return t * o.W * o.M + u * o.tasks + w + o.W * b;
 }
 
-template <typename V, int M, int RI>
-__device__ __forceinline__ void fwd_rounds_upto(const TileCtx<V>& c) {
-    // rounds RI .. NR-2 in place
-    if constexpr (RI < Shape<V, M>::NR - 1) {
-        fwd_round<V, M, RI>(c);
-        __syncthreads();
-        fwd_rounds_upto<V, M, RI + 1>(c);
-    }
-}
+// Per-tile facts.  Rows case (C > 1): a thread's column w = tid mod W is
+// fixed, so its global offset and external-twiddle column are computed once
+// per tile.  Offsets are 32-bit element offsets (plans keep N < 2^31).
+template <typename V> struct TileCtx {
+    const PassArgs* a;
+    V* s;              // exchange buffer, [row][w], pitch P
+    const V* twi;      // w_M^u
+    uint32_t t;        // tile index within the pass
+    uint32_t q0;       // first column of the tile
+    uint32_t Q;        // columns of the pass
+    uint32_t C;        // row stride
+    uint32_t base;     // rows case: global offset of row 0 of this thread's column
+    uint32_t j;        // rows case: external twiddle column j = (q mod C) / I
+    bool valid;        // rows case: this thread's column exists (q < Q)
+    bool do_scale;     // kFwd: multiply by `scale` on store (decided once, not per element)
+    typename Real<V>::T scale;
+};
 
-// Last forward round (SP = 1: no internal twiddle).  kFwd, rows case: store
-// to global row r2g[r] with w_L^{j k'} and the scale.  kFwd, lines case:
-// in place (the store loop places rows).  kFused: product with the filter
-// spectrum at the same global position, then the adjoint of this round.
-template <typename V, int M, bool LINES, bool FUSED>
-__device__ __forceinline__ void last_fwd_round(const TileCtx<V>& c) {
+enum : int { kFromSmem = 0, kFromNatural = 1, kFromPlaced = 2 };
+enum : int { kToSmem = 0, kToNatural = 1, kToPlaced = 2 };
+
+// One round of a tile.  SRC: shared memory, natural global rows, or global
+// rows in the pass' output placement (row r of the tile's rounds holds the
+// data of global row r2g[r]).  Forward: DFT_R, then w_S^{jp k} (SP > 1).
+// Inverse (adjoint): conj twiddles, then the conjugate DFT.  MUL (the last
+// forward round of a fused pass): DFT, product with the filter spectrum at
+// the same global position, conjugate DFT.  DST as SRC; a placed store also
+// applies w_L^{j k'} and the scale, a placed load (first inverse round) the
+// conjugate w_L^{j k'}.
+template <typename V, int M, bool LINES, int RI, bool INV, int SRC, int DST, bool MUL>
+__device__ __forceinline__ void round_exec(const TileCtx<V>& c) {
     using SH = Shape<V, M>;
-    constexpr int RI = SH::NR - 1, P = SH::P;
     using G = RoundGeom<M, SH::ES, RI>;
-    using T = Task<M, SH::W, SH::ES, RI>;
-    constexpr int R = G::R;
-    static_assert(G::SP == 1, "the last round acts on whole sub-blocks");
+    constexpr int R = G::R, SP = G::SP, STEP = M / G::S, P = SH::P;
+    constexpr bool JFAST = LINES && !MUL && (SRC == kFromNatural || DST == kToNatural);
+    using T = Task<M, SH::ES, SH::W, RI, JFAST>;
+    static_assert(!MUL || SP == 1, "the product is taken after the last forward round");
     const PassArgs& a = *c.a;
+    const V* src = reinterpret_cast<const V*>(a.src);
     V* dst = reinterpret_cast<V*>(a.dst);
     const V* spec = reinterpret_cast<const V*>(a.spec);
+    const uint32_t stride = LINES ? 1u : c.C;
+#pragma unroll 1
     for (int tau = threadIdx.x; tau < T::TASKS; tau += SH::NT) {
         const T t(tau);
+        uint32_t base = c.base, j = c.j;
+        bool valid = c.valid;
+        if constexpr (LINES) {
+            const uint32_t q = c.q0 + (uint32_t)t.w;
+            valid = q < c.Q;
+            base = q * (uint32_t)M;
+            j = 0;
+        }
         V v[R];
+        if constexpr (SRC == kFromSmem) {
 #pragma unroll
-        for (int u = 0; u < R; ++u) v[u] = c.s[(t.row0 + u) * P + t.w];
-        dft<R, false>(v);
-        if constexpr (FUSED) {
-            if constexpr (LINES && SH::SPEC_SMEM) {
+            for (int u = 0; u < R; ++u) v[u] = c.s[(t.row0 + SP * u) * P + t.w];
+        } else {
 #pragma unroll
-                for (int u = 0; u < R; ++u) v[u] = cmul(v[u], c.hs[__ldg(a.r2g + t.row0 + u) * P + t.w]);
-            } else {
-                bool ok;
-                uint32_t base;
-                if constexpr (LINES) {
-                    const uint32_t q = c.q0 + t.w;
-                    ok = q < (uint32_t)a.Q;
-                    base = q * M;
-                } else {
-                    ok = c.valid;
-                    base = c.base;
+            for (int u = 0; u < R; ++u) {
+                const int row = t.row0 + SP * u;
+                const uint32_t g = SRC == kFromNatural ? (uint32_t)row : (uint32_t)__ldg(a.r2g + row);
+                v[u] = valid ? src[base + g * stride] : V{0, 0};
+            }
+        }
+        if constexpr (INV) {
+            if constexpr (SRC == kFromPlaced && !LINES) {
+                if (a.has_ext && j != 0) {
+#pragma unroll
+                    for (int u = 0; u < R; ++u)
+                        v[u] = cmulc(v[u], ext_twiddle<V>(a, (int64_t)j * __ldg(a.r2f + t.row0 + SP * u)));
                 }
-                if (ok) {
+            }
+            if constexpr (SP > 1) {
 #pragma unroll
-                    for (int u = 0; u < R; ++u) {
-                        const uint32_t g = __ldg(a.r2g + t.row0 + u);
-                        v[u] = cmul(v[u], __ldg(spec + base + g * c.C));
-                    }
-                }
+                for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], c.twi[STEP * t.jp * k]);
             }
             dft<R, true>(v);
-            if constexpr (!LINES && SH::NR == 1) {  // the only round: natural rows straight to global
-                if (c.valid) {
-#pragma unroll
-                    for (int u = 0; u < R; ++u) dst[c.base + (uint32_t)(t.row0 + u) * c.C] = v[u];
-                }
-                continue;
-            }
-#pragma unroll
-            for (int u = 0; u < R; ++u) c.s[(t.row0 + u) * P + t.w] = v[u];
-        } else if constexpr (LINES) {
-#pragma unroll
-            for (int u = 0; u < R; ++u) c.s[(t.row0 + u) * P + t.w] = v[u];
         } else {
-            if (c.valid) {
+            dft<R, false>(v);
+            if constexpr (MUL) {
+                // the spectrum is stored in the order this round consumes it:
+                // slot (tile, u, task), so a warp reads 32 consecutive elements
+                if (valid) {
+                    const V* hs = spec + (size_t)c.t * (SH::W * M) + tau;
+#pragma unroll
+                    for (int u = 0; u < R; ++u) v[u] = cmul(v[u], __ldg(hs + u * T::TASKS));
+                }
+                dft<R, true>(v);
+            } else if constexpr (SP > 1) {
+#pragma unroll
+                for (int k = 1; k < R; ++k) v[k] = cmul(v[k], c.twi[STEP * t.jp * k]);
+            }
+        }
+        if constexpr (DST == kToSmem) {
+#pragma unroll
+            for (int u = 0; u < R; ++u) c.s[(t.row0 + SP * u) * P + t.w] = v[u];
+        } else if constexpr (DST == kToNatural) {
+            if (valid) {
+#pragma unroll
+                for (int u = 0; u < R; ++u) dst[base + (uint32_t)(t.row0 + SP * u) * stride] = v[u];
+            }
+        } else {
+            if (valid) {
 #pragma unroll
                 for (int u = 0; u < R; ++u) {
-                    const int r = t.row0 + u;
+                    const int row = t.row0 + SP * u;
                     V o = v[u];
-                    if (a.has_ext && c.j != 0) o = cmul(o, ext_twiddle<V>(a, (int64_t)c.j * __ldg(a.r2f + r)));
+                    if constexpr (!LINES) {
+                        if (a.has_ext && j != 0) o = cmul(o, ext_twiddle<V>(a, (int64_t)j * __ldg(a.r2f + row)));
+                    }
                     if (c.do_scale) o = cscale(o, c.scale);
-                    dst[c.base + (uint32_t)__ldg(a.r2g + r) * c.C] = o;
+                    dst[base + (uint32_t)__ldg(a.r2g + row) * stride] = o;
                 }
             }
         }
     }
 }
 
-// Issue the asynchronous copy of one tile of `src` (natural rows; with
-// `perm`, rows placed at rowmap[g], the in-CTA position of their frequency).
-// Global order is walked contiguously: along rows of W columns (rows case)
-// or along lines (C = 1).
-template <typename V, int M, bool LINES>
-__device__ __forceinline__ void load_tile(const PassArgs& a, const V* src, V* s, uint32_t q0, bool perm) {
-    using SH = Shape<V, M>;
-    constexpr int W = SH::W, P = SH::P, NT = SH::NT;
-    const uint32_t Q = (uint32_t)a.Q;
-    if constexpr (LINES) {
-        const V* tile = src + q0 * M;
-#pragma unroll 4
-        for (int idx = threadIdx.x; idx < W * M; idx += NT) {
-            const int w = idx / M, g = idx - (idx / M) * M;
-            if (q0 + w >= Q) break;
-            const int r = perm ? __ldg(a.rowmap + g) : g;
-            cp_async<sizeof(V)>(s + r * P + w, tile + idx);
-        }
-    } else {
-        const int w = threadIdx.x % W;
-        const uint32_t q = q0 + w;
-        if (q < Q) {
-            const uint32_t C = (uint32_t)a.C;
-            const uint32_t cq = q % C;
-            const V* col = src + ((q - cq) * M + cq);
-#pragma unroll 4
-            for (int g = threadIdx.x / W; g < M; g += NT / W) {
-                const int r = perm ? __ldg(a.rowmap + g) : g;
-                cp_async<sizeof(V)>(s + r * P + w, col + (uint32_t)g * C);
-            }
-        }
+// forward rounds RI .. NR-2, shared memory in and out
+template <typename V, int M, bool LINES, int RI>
+__device__ __forceinline__ void fwd_middle(const TileCtx<V>& c) {
+    if constexpr (RI < Shape<V, M>::NR - 1) {
+        round_exec<V, M, LINES, RI, false, kFromSmem, kToSmem, false>(c);
+        __syncthreads();
+        fwd_middle<V, M, LINES, RI + 1>(c);
     }
 }
 
-// Lines case: coalesced store of the tile; kFwd reads the row that holds
-// global row g (rowmap) and scales, otherwise natural rows.
-template <typename V, int M>
-__device__ __forceinline__ void store_lines(const TileCtx<V>& c, bool placed) {
-    using SH = Shape<V, M>;
-    constexpr int W = SH::W, P = SH::P, NT = SH::NT;
-    const PassArgs& a = *c.a;
-    const V* s = c.s;
-    const uint32_t q0 = c.q0;
-    V* tile = reinterpret_cast<V*>(a.dst) + q0 * M;
-    const uint32_t Q = (uint32_t)a.Q;
-    for (int idx = threadIdx.x; idx < W * M; idx += NT) {
-        const int w = idx / M, g = idx - (idx / M) * M;
-        if (q0 + w >= Q) break;
-        V v;
-        if (placed) {
-            v = s[__ldg(a.rowmap + g) * P + w];
-            if (c.do_scale) v = cscale(v, c.scale);
-        } else {
-            v = s[g * P + w];
-        }
-        tile[idx] = v;
+// inverse rounds RI, RI-1, ..., 1, shared memory in and out
+template <typename V, int M, bool LINES, int RI>
+__device__ __forceinline__ void inv_middle(const TileCtx<V>& c) {
+    if constexpr (RI >= 1) {
+        round_exec<V, M, LINES, RI, true, kFromSmem, kToSmem, false>(c);
+        __syncthreads();
+        inv_middle<V, M, LINES, RI - 1>(c);
+    }
+}
+
+// kFwd: natural rows in, placed rows out (with w_L^{j k'} and the scale).
+template <typename V, int M, bool LINES>
+__device__ __forceinline__ void tile_forward(const TileCtx<V>& c) {
+    constexpr int NR = Shape<V, M>::NR;
+    if constexpr (NR == 1) {
+        round_exec<V, M, LINES, 0, false, kFromNatural, kToPlaced, false>(c);
+    } else {
+        round_exec<V, M, LINES, 0, false, kFromNatural, kToSmem, false>(c);
+        __syncthreads();
+        fwd_middle<V, M, LINES, 1>(c);
+        round_exec<V, M, LINES, NR - 1, false, kFromSmem, kToPlaced, false>(c);
+    }
+}
+
+// kInv: placed rows in (with conj w_L^{j k'}), natural rows out.
+template <typename V, int M, bool LINES>
+__device__ __forceinline__ void tile_inverse(const TileCtx<V>& c) {
+    constexpr int NR = Shape<V, M>::NR;
+    if constexpr (NR == 1) {
+        round_exec<V, M, LINES, 0, true, kFromPlaced, kToNatural, false>(c);
+    } else {
+        round_exec<V, M, LINES, NR - 1, true, kFromPlaced, kToSmem, false>(c);
+        __syncthreads();
+        inv_middle<V, M, LINES, NR - 2>(c);
+        round_exec<V, M, LINES, 0, true, kFromSmem, kToNatural, false>(c);
+    }
+}
+
+// kFused: natural rows in, forward rounds, product, inverse rounds, natural rows out.
+template <typename V, int M, bool LINES>
+__device__ __forceinline__ void tile_fused(const TileCtx<V>& c) {
+    constexpr int NR = Shape<V, M>::NR;
+    if constexpr (NR == 1) {
+        round_exec<V, M, LINES, 0, false, kFromNatural, kToNatural, true>(c);
+    } else {
+        round_exec<V, M, LINES, 0, false, kFromNatural, kToSmem, false>(c);
+        __syncthreads();
+        fwd_middle<V, M, LINES, 1>(c);
+        round_exec<V, M, LINES, NR - 1, false, kFromSmem, kToSmem, true>(c);
+        __syncthreads();
+        inv_middle<V, M, LINES, NR - 2>(c);
+        round_exec<V, M, LINES, 0, true, kFromSmem, kToNatural, false>(c);
     }
 }
 
@@ -461,112 +445,65 @@ __device__ __forceinline__ void store_lines(const TileCtx<V>& c, bool placed) {
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
-// Transform one tile that is resident in shared memory (all modes).
+// Set up the per-tile facts of tile t.
 template <typename V, int M, bool LINES>
-__device__ __forceinline__ void process_tile(TileCtx<V>& c) {
+__device__ __forceinline__ void tile_setup(TileCtx<V>& c, const PassArgs& a, uint32_t t) {
     using SH = Shape<V, M>;
-    constexpr int NR = SH::NR;
-    const PassArgs& a = *c.a;
-    if (a.mode == kFwd) {
-        fwd_rounds_upto<V, M, 0>(c);
-        last_fwd_round<V, M, LINES, false>(c);
-        if constexpr (LINES) {
-            __syncthreads();
-            store_lines<V, M>(c, true);
+    c.t = t;
+    c.q0 = t * SH::W;
+    c.valid = false;
+    c.base = 0;
+    c.j = 0;
+    if constexpr (!LINES) {
+        const uint32_t q = c.q0 + threadIdx.x % SH::W;
+        if (q < c.Q) {
+            const uint32_t cq = q % c.C;
+            c.valid = true;
+            c.base = (q - cq) * (uint32_t)M + cq;
+            c.j = a.has_ext ? cq / (uint32_t)a.I : 0;
         }
-    } else if (a.mode == kFused) {
-        fwd_rounds_upto<V, M, 0>(c);
-        last_fwd_round<V, M, LINES, true>(c);
-        if constexpr (NR > 1 || LINES) __syncthreads();
-        inv_rounds_from<V, M, NR - 2, LINES>(c);
-        if constexpr (LINES) store_lines<V, M>(c, false);
-    } else {
-        // first inverse round: adjoint of the last forward round, with conj(w_L^{j k'})
-        inv_round<V, M, NR - 1, true, (!LINES && NR == 1)>(c);
-        if constexpr (NR > 1 || LINES) __syncthreads();
-        inv_rounds_from<V, M, NR - 2, LINES>(c);
-        if constexpr (LINES) store_lines<V, M>(c, false);
     }
 }
 
-// One pass over all tiles, CTAs walking tiles blockIdx.x, +gridDim.x, ...;
-// with two buffers the asynchronous copy of the next tile (and, in the fused
-// lines pass, of its spectrum tile) is in flight while the current tile is
-// transformed.
 template <typename V, int M, bool LINES>
-__device__ __forceinline__ void run_phase(const PassArgs& a, V* sbase) {
-    using SH = Shape<V, M>;
-    constexpr int W = SH::W, STAGES = tile_stages(M, sizeof(V));
-    constexpr bool HSMEM = LINES && SH::SPEC_SMEM;
-    // buffer b: data at sbase + b * STRIDE, spectrum (HSMEM) right after it
-    constexpr int STRIDE = (HSMEM ? 2 : 1) * SH::TILE;
+__device__ __forceinline__ void tile_run(const TileCtx<V>& c, int mode) {
+    if (mode == kFwd)
+        tile_forward<V, M, LINES>(c);
+    else if (mode == kFused)
+        tile_fused<V, M, LINES>(c);
+    else
+        tile_inverse<V, M, LINES>(c);
+}
 
-    TileCtx<V> c;
+template <typename V> __device__ __forceinline__ void ctx_init(TileCtx<V>& c, const PassArgs& a, V* s) {
     c.a = &a;
+    c.s = s;
     c.twi = reinterpret_cast<const V*>(a.tw_int);
+    c.Q = (uint32_t)a.Q;
     c.C = (uint32_t)a.C;
     c.do_scale = a.mode == kFwd && a.scale != 1.0;
     c.scale = (typename Real<V>::T)a.scale;
-    const uint32_t Q = (uint32_t)a.Q;
+}
+
+// One pass over all tiles, CTAs walking tiles blockIdx.x, +gridDim.x, ...
+template <typename V, int M, bool LINES>
+__device__ __forceinline__ void run_phase(const PassArgs& a, V* s) {
+    TileCtx<V> c;
+    ctx_init(c, a, s);
     const uint32_t tiles = (uint32_t)a.tiles;
-    const V* src = reinterpret_cast<const V*>(a.src);
-    const V* spec = reinterpret_cast<const V*>(a.spec);
-    const bool perm = a.mode == kInv;
-    const bool with_spec = HSMEM && a.mode == kFused;
-
-    uint32_t t = blockIdx.x;
-    if (STAGES == 2 && t < tiles) {
-        load_tile<V, M, LINES>(a, src, sbase, t * W, perm);
-        if (with_spec) load_tile<V, M, true>(a, spec, sbase + SH::TILE, t * W, false);
+    for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+        tile_setup<V, M, LINES>(c, a, t);
+        tile_run<V, M, LINES>(c, a.mode);
+        __syncthreads();  // the next tile reuses the exchange buffer
     }
-    cp_async_commit();
-    for (int it = 0; t < tiles; t += gridDim.x, ++it) {
-        V* cur = sbase + (STAGES == 2 ? (it & 1) * STRIDE : 0);
-        if constexpr (STAGES == 2) {
-            const uint32_t tn = t + gridDim.x;
-            if (tn < tiles) {
-                V* nxt = sbase + ((it + 1) & 1) * STRIDE;
-                load_tile<V, M, LINES>(a, src, nxt, tn * W, perm);
-                if (with_spec) load_tile<V, M, true>(a, spec, nxt + SH::TILE, tn * W, false);
-            }
-            cp_async_commit();
-            cp_async_wait<1>();
-        } else {
-            load_tile<V, M, LINES>(a, src, cur, t * W, perm);
-            if (with_spec) load_tile<V, M, true>(a, spec, cur + SH::TILE, t * W, false);
-            cp_async_commit();
-            cp_async_wait<0>();
-        }
-        __syncthreads();
-        c.s = cur;
-        c.hs = with_spec ? cur + SH::TILE : nullptr;
-        c.q0 = t * W;
-        c.valid = false;
-        c.base = 0;
-        c.j = 0;
-        if constexpr (!LINES) {
-            const uint32_t q = c.q0 + threadIdx.x % W;
-            if (q < Q) {
-                const uint32_t cq = q % c.C;
-                c.valid = true;
-                c.base = (q - cq) * M + cq;
-                c.j = a.has_ext ? cq / (uint32_t)a.I : 0;
-            }
-        }
-        process_tile<V, M, LINES>(c);
-        __syncthreads();
-    }
-    cp_async_wait<0>();
 }
 
-template <typename V, int M> constexpr int pass_smem_bytes(bool lines) {
-    return tile_stages(M, sizeof(V)) * ((lines && Shape<V, M>::SPEC_SMEM) ? 2 : 1) * Shape<V, M>::TILE *
-           (int)sizeof(V);
-}
+template <typename V, int M> constexpr int pass_smem_bytes(bool) { return Shape<V, M>::TILE * (int)sizeof(V); }
 
 // Generic pass kernel: one pass of a convolution (see run_phase).
 template <typename V, int M, bool LINES>
-__global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, sizeof(V))) pass_kernel(const PassArgs a) {
+__global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, sizeof(V)))
+    pass_kernel(const __grid_constant__ PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_launch_dependents();
     pdl_wait();
@@ -608,7 +545,7 @@ __device__ __forceinline__ void grid_barrier(const ConvArgs& args, unsigned k) {
 // the fused one, inverse groups), all with the same group size M, as phases.
 template <typename V, int M>
 __global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, sizeof(V)))
-    conv_kernel(const ConvArgs args) {
+    conv_kernel(const __grid_constant__ ConvArgs args) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* sbase = reinterpret_cast<V*>(smem_raw);
     for (int p = 0; p < args.npasses; ++p) {

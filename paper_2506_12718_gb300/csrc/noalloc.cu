@@ -14,8 +14,8 @@
 // PAC_NOALLOC_SCRATCH_BYTES (8 MiB) that every GPU which loads this library
 // keeps until the process exits.  The index-reversal positions are computed
 // from the plan's stage lists inside the kernel instead of read from tables,
-// and the natural-order spectrum is gathered from the stored (index-reversed)
-// one on the fly.  Every scratch element is written before it is read, so the
+// and the natural-order spectrum is gathered from the stored one on the fly
+// (through its storage order, spec_slot, and the plan's placement table).  Every scratch element is written before it is read, so the
 // array needs no clearing between calls; it keeps the last call's contents.
 // All calls share the one array: two calls whose kernels overlap on the GPU
 // (on different streams, or on different threads without ordering) race on it.
@@ -74,7 +74,8 @@ __device__ __forceinline__ int64_t freq_of_pos(const int* st, int T, int64_t p) 
 // out[i] = in[src(i)] (* mul[src(i)]), i a row-major multi-index; src maps
 // each axis index through pos_of_freq (to_natural) or freq_of_pos.
 template <typename V>
-__global__ void permute_digits_kernel(const DigitPlan dp, bool to_natural, const V* in, V* out, const V* mul) {
+__global__ void permute_digits_kernel(const DigitPlan dp, bool to_natural, const V* in, V* out, const V* mul,
+                                      const SpecOrder so) {
     const int64_t n = dp.dims[0] * dp.dims[1] * dp.dims[2];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t rem = i, src = 0, stride = 1;
@@ -86,7 +87,7 @@ __global__ void permute_digits_kernel(const DigitPlan dp, bool to_natural, const
             stride *= dp.dims[a];
         }
         V v = in[src];
-        if (mul) v = cmul(v, __ldg(mul + src));
+        if (mul) v = cmul(v, __ldg(mul + spec_slot(so, (uint32_t)src)));  // the stored spectrum's slot
         out[i] = v;
     }
 }
@@ -112,11 +113,11 @@ int scratch_address(int device, void** out) {
 
 template <typename V>
 cudaError_t launch_digits(const DigitPlan& dp, bool to_natural, const void* in, void* out, const void* mul,
-                          int64_t n, cudaStream_t s) {
+                          const SpecOrder& so, int64_t n, cudaStream_t s) {
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, 4096);
     permute_digits_kernel<V><<<(unsigned)blocks, threads, 0, s>>>(dp, to_natural, static_cast<const V*>(in),
-                                                                   static_cast<V*>(out), static_cast<const V*>(mul));
+                                                                   static_cast<V*>(out), static_cast<const V*>(mul), so);
     return cudaGetLastError();
 }
 
@@ -167,12 +168,13 @@ extern "C" int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void
         if (rc) return rc;
     }
     // natural order with the product (spectrum gathered at the same positions), into the static scratch
-    e = p->esize == 8 ? launch_digits<float2>(dp, true, y_dev, scratch, p->d_spec, p->N, s)
-                      : launch_digits<double2>(dp, true, y_dev, scratch, p->d_spec, p->N, s);
+    const SpecOrder so = spec_order_of(p);
+    e = p->esize == 8 ? launch_digits<float2>(dp, true, y_dev, scratch, p->d_spec, so, p->N, s)
+                      : launch_digits<double2>(dp, true, y_dev, scratch, p->d_spec, so, p->N, s);
     if (e != cudaSuccess) return cuda_fail(e, "permute kernel");
     // back to the index-reversed order for the inverse (iFFT = uiFFT o permute, Algorithm 9)
-    e = p->esize == 8 ? launch_digits<float2>(dp, false, scratch, y_dev, nullptr, p->N, s)
-                      : launch_digits<double2>(dp, false, scratch, y_dev, nullptr, p->N, s);
+    e = p->esize == 8 ? launch_digits<float2>(dp, false, scratch, y_dev, nullptr, so, p->N, s)
+                      : launch_digits<double2>(dp, false, scratch, y_dev, nullptr, so, p->N, s);
     if (e != cudaSuccess) return cuda_fail(e, "permute kernel");
     for (int i = G - 1; i >= 0; --i) {
         int rc = run_pass(p, p->groups[i], kInv, y_dev, y_dev, 1.0, s);

@@ -52,10 +52,15 @@ int take_device_error(int device, unsigned* value);
 // auxiliary kernels (aux.cu)
 cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64_t* const* idx_dev,
                            const void* src, void* dst, const void* mul, cudaStream_t s);
+cudaError_t launch_spec_order(int esize, const SpecOrder& o, int64_t n, const void* src, void* dst, bool to_kernel,
+                              cudaStream_t s);
 cudaError_t launch_pointwise_mul(int esize, int64_t n, const void* a, const void* b, void* out, double scale,
                                  cudaStream_t s);
 
 int device_sm_count(int device);
+
+// storage order of a plan's filter spectrum (plan.cu); the plan needs a group
+SpecOrder spec_order_of(pac_plan p);
 
 }  // namespace pac
 
@@ -74,7 +79,8 @@ struct pac_plan_s {
     std::vector<pac::GroupPlan> groups;            // forward order
     void* d_tables = nullptr;
     size_t tables_bytes = 0;
-    void* d_spec = nullptr;       // A^T h / N, index-reversed order
+    void* d_spec = nullptr;       // A^T h / N, in the fused pass' storage order (SpecOrder)
+    int64_t spec_elems = 0;       // slots of d_spec (>= N: whole tiles of the fused pass)
     bool has_spec = false;
     // comparator (permuted form) state, created on first use
     void* d_spec_nat = nullptr;   // DFT(h) / N in natural order

@@ -31,6 +31,16 @@ struct PassArgs {
     double scale;           // applied on store in kFwd (filter spectrum 1/N); 1 = none
 };
 
+// Storage order of a filter spectrum (see spec_slot in fft_device.cuh).
+struct SpecOrder {
+    uint32_t M;       // group size of the fused pass
+    uint32_t W;       // its tile width
+    uint32_t C;       // its row stride
+    uint32_t R;       // radix of its last round
+    uint32_t tasks;   // W * M / R
+    const int* rowmap;  // [M] in-CTA row of global row g
+};
+
 constexpr int kMaxPasses = 12;
 
 // A whole convolution (or forward transform) as one cooperative launch:

@@ -385,13 +385,19 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
         free_plan(pl);
         return cuda_fail(e, "cudaMemcpy(tables)");
     }
-    e = cudaMalloc(&pl->d_spec, (size_t)pl->bytes());
+    pl->spec_elems = pl->N;
+    if (!pl->groups.empty()) {  // whole tiles of the fused pass (see SpecOrder)
+        const GroupPlan& f = pl->groups.back();
+        const int64_t W = tile_w(f.M, pl->esize);
+        pl->spec_elems = (f.Q + W - 1) / W * W * f.M;
+    }
+    e = cudaMalloc(&pl->d_spec, (size_t)pl->spec_elems * pl->esize);
     if (e != cudaSuccess) {
         free_plan(pl);
         return e == cudaErrorMemoryAllocation ? fail(PAC_ERR_NOMEM, "filter spectrum: out of memory")
                                               : cuda_fail(e, "cudaMalloc(spectrum)");
     }
-    pl->device_bytes = pl->tables_bytes + (size_t)pl->bytes();
+    pl->device_bytes = pl->tables_bytes + (size_t)pl->spec_elems * pl->esize;
     *out = pl;
     return PAC_OK;
 }
@@ -433,6 +439,21 @@ static void timer_mark(cudaStream_t s, int id, bool before) {
     if (cudaEventCreate(&e) != cudaSuccess) return;
     cudaEventRecord(e, s);
     t->ev.push_back(e);
+}
+
+// Storage order of the plan's filter spectrum: the read order of the last
+// forward round of its fused pass (the last group).
+SpecOrder spec_order_of(pac_plan p) {
+    const GroupPlan& f = p->groups.back();
+    SpecOrder o;
+    o.M = (uint32_t)f.M;
+    o.W = (uint32_t)tile_w(f.M, p->esize);
+    o.C = (uint32_t)f.C;
+    const int nr = round_count(f.M, p->esize);
+    o.R = (uint32_t)round_radix(f.M, p->esize, nr - 1);
+    o.tasks = o.W * o.M / o.R;
+    o.rowmap = reinterpret_cast<const int*>(static_cast<const unsigned char*>(p->d_tables) + f.off_rowmap);
+    return o;
 }
 
 static PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale) {
@@ -565,9 +586,27 @@ extern "C" int pac_filter_spectrum(pac_plan p, const void* h_dev) {
     cudaStream_t s;
     e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
-    int rc = run_forward(p, h_dev, p->d_spec, 1.0 / (double)p->N, s);
+    int rc;
+    void* tmp = nullptr;
+    if (p->groups.empty()) {  // N = 1
+        rc = run_forward(p, h_dev, p->d_spec, 1.0 / (double)p->N, s);
+    } else {
+        // A^T h / N in the plain index-reversed order, then once into the
+        // order the fused pass reads it
+        e = cudaMalloc(&tmp, (size_t)p->bytes());
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(s);
+            return fail(PAC_ERR_NOMEM, "filter spectrum staging: %s", cudaGetErrorString(e));
+        }
+        rc = run_forward(p, h_dev, tmp, 1.0 / (double)p->N, s);
+        if (rc == PAC_OK) {
+            e = launch_spec_order(p->esize, spec_order_of(p), p->N, tmp, p->d_spec, true, s);
+            if (e != cudaSuccess) rc = cuda_fail(e, "spectrum order kernel");
+        }
+    }
     e = cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
+    if (tmp) cudaFree(tmp);
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "filter spectrum");
     p->has_spec = true;
@@ -655,7 +694,13 @@ static int ensure_permuted_state(pac_plan p) {
             idx[a] = p->d_perm + o + p->dims[a];  // natural k <- position of k
             o += 2 * p->dims[a];
         }
-        e = launch_permute(p->esize, p->ndim, p->dims, idx, p->d_spec, p->d_spec_nat, nullptr, 0);
+        const void* dif = p->d_spec;
+        if (!p->groups.empty()) {  // back to the plain index-reversed order first
+            e = launch_spec_order(p->esize, spec_order_of(p), p->N, p->d_spec, p->d_scratch, false, 0);
+            if (e != cudaSuccess) return cuda_fail(e, "spectrum order kernel");
+            dif = p->d_scratch;
+        }
+        e = launch_permute(p->esize, p->ndim, p->dims, idx, dif, p->d_spec_nat, nullptr, 0);
         if (e == cudaSuccess) e = cudaDeviceSynchronize();
         if (e != cudaSuccess) return cuda_fail(e, "natural-order spectrum");
     }
