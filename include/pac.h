@@ -121,6 +121,13 @@ int pac_convolve_host(pac_plan p, const void* x_host, void* y_host, void* stream
 int pac_convolve_many(int count, const pac_plan* plans, const void* const* x_dev, void* const* y_dev,
                       void* stream);
 
+/*
+ * Kernel launches one pac_convolve_many call over these plans makes (the
+ * merged launches of its captured graph, plus one per N = 1 plan).  Host
+ * only; no device work.
+ */
+int pac_convolve_many_launches(int count, const pac_plan* plans, int* launches);
+
 /* ----------------------------------------------------------------- serving */
 
 /*

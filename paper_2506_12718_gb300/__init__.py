@@ -48,6 +48,7 @@ _SIGS = {
     "pac_convolve": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_convolve_host": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_convolve_many": (_i32, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
+    "pac_convolve_many_launches": (_i32, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_i32)]),
     "pac_queue_create": (_i32, [ctypes.c_size_t, _i32, ctypes.POINTER(_vp)]),
     "pac_submit": (_i32, [_vp, _vp, _vp, _vp, ctypes.POINTER(_u64)]),
     "pac_poll": (_i32, [_vp, _u64, ctypes.POINTER(ctypes.c_double)]),
@@ -180,6 +181,14 @@ def pac_convolve_many(plans, xs, ys, stream=None) -> None:
     X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
     Y = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
     _check(load().pac_convolve_many(n, P, X, Y, _stream(stream)))
+
+
+def pac_convolve_many_launches(plans) -> int:
+    n = len(plans)
+    P = (ctypes.c_void_p * max(1, n))(*plans)
+    out = ctypes.c_int(0)
+    _check(load().pac_convolve_many_launches(n, P, ctypes.byref(out)))
+    return out.value
 
 
 def pac_forward_unordered(plan: int, x_dev, xhat_dev, stream=None) -> None:

@@ -510,6 +510,33 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, size
     run_phase<V, M, LINES>(a, reinterpret_cast<V*>(smem_raw));
 }
 
+// Many passes of one kernel shape in one launch (batched convolutions): the
+// tiles of passes list[0..n) are numbered consecutively, pass i owning global
+// tiles [tile_start[i], tile_start[i+1]); CTAs walk the global tiles.
+template <typename V, int M, bool LINES>
+__global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, sizeof(V)))
+    pass_multi_kernel(const PassArgs* __restrict__ list, const uint32_t* __restrict__ tile_start, int n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* s = reinterpret_cast<V*>(smem_raw);
+    const uint32_t total = __ldg(tile_start + n);
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = n - 1;  // the last pass whose first tile is <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(tile_start + mid) <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const PassArgs& a = list[lo];
+        TileCtx<V> c;
+        ctx_init(c, a, s);
+        tile_setup<V, M, LINES>(c, a, t - __ldg(tile_start + lo));
+        tile_run<V, M, LINES>(c, a.mode);
+        __syncthreads();
+    }
+}
+
 // Grid-wide barrier for the cooperative convolution kernel (all CTAs are
 // co-resident).  The arrival counter only grows; barrier k of a launch waits
 // for base + (k+1) * gridDim.x arrivals.  The wait is bounded: after the

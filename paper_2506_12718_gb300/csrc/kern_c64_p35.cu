@@ -1,4 +1,4 @@
-// Pass-kernel and convolution-kernel instantiations: float2, group sizes that are powers of 35.
+// Pass-kernel and convolution-kernel instantiations: float2, group sizes that are powers of 3 or 5.
 #include "kern_launch.cuh"
 
 namespace pac {

@@ -1,5 +1,5 @@
-// Dispatch of a pass (or a whole single-launch convolution) to its
-// instantiation by element type and group size.
+// Dispatch of a pass (a whole single-launch convolution, or a batch of
+// passes of one shape) to its instantiation by element type and group size.
 #include "pac_internal.h"
 
 namespace pac {
@@ -30,6 +30,24 @@ int conv_grid(int esize, int M, int dev) {
 cudaError_t launch_conv(int esize, int M, ConvArgs& args, int grid, cudaStream_t s) {
     if (esize == 8) return (M % 2 == 0) ? launch_conv_c64_p2(M, args, grid, s) : launch_conv_c64_p35(M, args, grid, s);
     return (M % 2 == 0) ? launch_conv_c128_p2(M, args, grid, s) : launch_conv_c128_p35(M, args, grid, s);
+}
+
+cudaError_t launch_multi_c64_p2(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
+                               cudaStream_t s);
+cudaError_t launch_multi_c64_p35(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
+                                cudaStream_t s);
+cudaError_t launch_multi_c128_p2(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
+                                cudaStream_t s);
+cudaError_t launch_multi_c128_p35(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+                                 int64_t total, cudaStream_t s);
+
+cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+                         int64_t total, cudaStream_t s) {
+    if (esize == 8)
+        return (M % 2 == 0) ? launch_multi_c64_p2(M, lines, list, starts, n, total, s)
+                            : launch_multi_c64_p35(M, lines, list, starts, n, total, s);
+    return (M % 2 == 0) ? launch_multi_c128_p2(M, lines, list, starts, n, total, s)
+                        : launch_multi_c128_p35(M, lines, list, starts, n, total, s);
 }
 
 int pass_kernel_supported(int M, int esize) {

@@ -1,0 +1,25 @@
+// Batched pass-kernel instantiations: float2, group sizes that are powers of 2.
+#include "kern_launch.cuh"
+
+namespace pac {
+
+cudaError_t launch_multi_c64_p2(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+                                 int64_t total, cudaStream_t s) {
+    switch (M) {
+        case 2: return launch_multi_M<float2, 2>(lines, list, starts, n, total, s);
+        case 4: return launch_multi_M<float2, 4>(lines, list, starts, n, total, s);
+        case 8: return launch_multi_M<float2, 8>(lines, list, starts, n, total, s);
+        case 16: return launch_multi_M<float2, 16>(lines, list, starts, n, total, s);
+        case 32: return launch_multi_M<float2, 32>(lines, list, starts, n, total, s);
+        case 64: return launch_multi_M<float2, 64>(lines, list, starts, n, total, s);
+        case 128: return launch_multi_M<float2, 128>(lines, list, starts, n, total, s);
+        case 256: return launch_multi_M<float2, 256>(lines, list, starts, n, total, s);
+        case 512: return launch_multi_M<float2, 512>(lines, list, starts, n, total, s);
+        case 1024: return launch_multi_M<float2, 1024>(lines, list, starts, n, total, s);
+        case 2048: return launch_multi_M<float2, 2048>(lines, list, starts, n, total, s);
+        case 4096: return launch_multi_M<float2, 4096>(lines, list, starts, n, total, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pac

@@ -42,6 +42,21 @@ cudaError_t launch_pass(int esize, int M, const PassArgs& a, cudaStream_t s);
 int conv_grid(int esize, int M, int dev);  // co-resident CTAs of the single-launch kernel (0: unavailable)
 cudaError_t launch_conv(int esize, int M, ConvArgs& args, int grid, cudaStream_t s);
 int pass_kernel_supported(int M, int esize);
+// n passes of one shape in one launch; list and starts in device memory (starts has n + 1 entries)
+cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+                         int64_t total, cudaStream_t s);
+
+// pass sequence of a convolution (plan.cu): group, mode, source, destination, scale
+struct Step {
+    int group, mode;
+    const void* src;
+    void* dst;
+    double scale;
+};
+void convolve_steps(pac_plan p, const void* x, void* y, std::vector<Step>& out);
+PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale);
+// forget every cached batch that uses plan p (batch.cu); called by pac_plan_destroy
+void batch_forget_plan(pac_plan p);
 
 // Barrier counters of single-launch convolutions: a device pool of slots,
 // handed out round robin; *base receives the slot's counter value at launch.

@@ -405,6 +405,7 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
 extern "C" int pac_plan_destroy(pac_plan p) {
     if (!p) return fail(PAC_ERR_ARG, "null plan");
     cudaDeviceSynchronize();
+    batch_forget_plan(p);
     free_plan(p);
     return PAC_OK;
 }
@@ -456,7 +457,7 @@ SpecOrder spec_order_of(pac_plan p) {
     return o;
 }
 
-static PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale) {
+PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale) {
     PassArgs a;
     const unsigned char* t = static_cast<const unsigned char*>(p->d_tables);
     a.src = src;
@@ -492,13 +493,6 @@ int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* ds
     return PAC_OK;
 }
 
-// One step of a pass sequence: group index, mode, source, destination, scale.
-struct Step {
-    int group, mode;
-    const void* src;
-    void* dst;
-    double scale;
-};
 
 // Run a pass sequence: as one cooperative launch when every group has the
 // same size M and single launches are allowed, else one launch per pass.
@@ -551,9 +545,17 @@ int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s, bool allow_
         return e == cudaSuccess ? PAC_OK : cuda_fail(e, "pointwise kernel");
     }
     std::vector<Step> steps;
+    convolve_steps(p, x, y, steps);
+    return run_steps(p, steps, s, allow_single);
+}
+
+// Algorithm 11, lines 2-4, as a pass sequence: forward groups (the last fused
+// with the product and the first inverse group), then the inverse groups.
+void convolve_steps(pac_plan p, const void* x, void* y, std::vector<Step>& steps) {
+    const int G = (int)p->groups.size();
+    steps.clear();
     for (int i = 0; i < G; ++i) steps.push_back({i, i == G - 1 ? kFused : kFwd, i == 0 ? x : y, y, 1.0});
     for (int i = G - 2; i >= 0; --i) steps.push_back({i, kInv, y, y, 1.0});
-    return run_steps(p, steps, s, allow_single);
 }
 
 int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s) { return run_convolve(p, x, y, s, true); }

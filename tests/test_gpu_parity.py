@@ -276,6 +276,80 @@ def test_convolve_many_matches_single():
             p.close()
 
 
+def test_convolve_many_graph_replay_and_plan_reuse():
+    """A batch replays its captured graph on the second call (same result),
+    a changed batch (new y pointers) is captured anew, and destroying a plan
+    drops the cached batches that used it."""
+    pac = pac_mod()
+    cases = [((256,), 2, 7), ((81, 27), 3, 8), ((32, 32, 32), 4, 9), ((16384,), 8, 10), ((125,), 5, 11)]
+    plans, xs, refs = [], [], []
+    try:
+        for dims, radix, seed in cases:
+            fs, h, x = separable_case(dims, "c64", seed)
+            p = pac.Plan(dims, radix, "c64")
+            p.filter_spectrum(dev(h))
+            plans.append(p)
+            xs.append(dev(x))
+            refs.append(oracle.conv_separable(fs, x))
+        handles = [p.handle for p in plans] * 3  # plans repeat across instances
+        xs3 = xs * 3
+        for attempt in range(2):
+            ys = [torch.full_like(x, float("nan")) for x in xs3]
+            for _ in range(2):
+                pac.pac_convolve_many(handles, xs3, ys)
+            torch.cuda.synchronize()
+            for k, y in enumerate(ys):
+                dims = cases[k % len(cases)][0]
+                check(y.cpu().numpy(), refs[k % len(cases)], "c64", int(np.prod(dims)), f"many[{k}] {dims}")
+        plans[1].close()
+        rest = [p.handle for i, p in enumerate(plans) if i != 1]
+        xr = [x for i, x in enumerate(xs) if i != 1]
+        yr = [torch.empty_like(x) for x in xr]
+        pac.pac_convolve_many(rest, xr, yr)
+        torch.cuda.synchronize()
+        for y, ref, (dims, _, _) in zip(yr, [r for i, r in enumerate(refs) if i != 1],
+                                        [c for i, c in enumerate(cases) if i != 1]):
+            check(y.cpu().numpy(), ref, "c64", int(np.prod(dims)), f"after destroy {dims}")
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_convolve_many_batched_workload_sample():
+    """96 instances drawn from the batched workload's 20 size classes (FP32,
+    64 filter ids), checked at 48 seeded output points each against the
+    direct definition (O1)."""
+    pac = pac_mod()
+    insts = pin.c4_instances(96)
+    plans, xs, ys, hs = {}, [], [], []
+    try:
+        handles = []
+        for c in insts:
+            key = (c.dims, c.radix, c.h_seed)
+            h, _ = pin.make_h(c)
+            if key not in plans:
+                p = pac.Plan(c.dims, c.radix, c.dtype)
+                p.filter_spectrum(dev(h))
+                plans[key] = p
+            handles.append(plans[key].handle)
+            x = pin.make_x(c)
+            xs.append(x)
+            hs.append(h)
+        xd = [dev(x) for x in xs]
+        yd = [torch.empty_like(x) for x in xd]
+        pac.pac_convolve_many(handles, xd, yd)
+        torch.cuda.synchronize()
+        for i, (c, h, x, y) in enumerate(zip(insts, hs, xs, yd)):
+            idx = pin.sample_points(c.n_total, 48, seed=500 + i)
+            ref = oracle.conv_direct_points(h, x, idx)
+            got = y.cpu().numpy().reshape(-1)[idx]
+            err = oracle.rel_l2(got, ref)
+            assert err <= tol("c64", c.n_total), f"instance {i} {c.dims}: rel_l2 {err:.3e}"
+    finally:
+        for p in plans.values():
+            p.close()
+
+
 def _queue_setup(n_req=24):
     pac = pac_mod()
     shapes = [((4096,), 2), ((81, 81), 3), ((32, 32, 32), 2), ((125, 25), 5), ((1024,), 4)]
