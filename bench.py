@@ -481,7 +481,8 @@ def main(argv=None):
         # pass of the contiguous axis another (lines case)
         vname = "float2" if a.dtype == "c64" else "double2"
         kern = {"dif_pass": f"pass_kernel<{vname},128,rows>", "dit_pass": f"pass_kernel<{vname},128,rows>",
-                "fused_dif_mul_dit_pass": f"pass_kernel<{vname},128,lines>"}
+                "fused_dif_mul_dit_pass": f"pass_kernel<{vname},128,lines>",
+                "plane_pass": f"plane_kernel<{vname},128,128>"}
         byk = {}
         for name, v in per.items():
             byk.setdefault(kern.get(name, name), []).extend(v)
@@ -489,12 +490,13 @@ def main(argv=None):
         dom = max(byk, key=lambda k: sum(byk[k]))
         nlaunch = len(byk[dom]) / reps
         avg_ms = sum(byk[dom]) / len(byk[dom])
-        alg_bytes = (3 if dom.endswith("lines>") else 2) * N * S
+        alg_bytes = (3 if dom.endswith("lines>") or dom.startswith("plane") else 2) * N * S
         achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
         line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                             "traffic": ncu_traffic(dom, "conv3d"), "alg_bytes_per_launch": alg_bytes,
-                            "alg_bytes_rule": "2*N*S per rows pass (read+write the array); 3*N*S per fused pass",
+                            "alg_bytes_rule": "2*N*S per rows pass (read+write the array); 3*N*S per fused or "
+                                              "plane pass (read x, read the spectrum, write y)",
                             "avg_launch_ms": avg_ms, "launches_per_step": nlaunch,
                             "time_share": sum(byk[dom]) / sum(sum(v) for v in byk.values())}
         line["kernel_ms_per_step"] = {k: sum(v) / reps for k, v in per.items()}

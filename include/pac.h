@@ -193,7 +193,8 @@ int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev, void* stre
  * device time (ms) to launch_ms[0..*n_launches) and a kernel id to
  * kernel_ids[] (0 = forward DIF pass, 1 = fused DIF+product+DIT pass,
  * 2 = inverse DIT pass, 3 = permutation, 4 = pointwise product, 5 = whole
- * pass sequence in one cooperative launch).
+ * pass sequence in one cooperative launch, 6 = plane pass: the last two
+ * axes forward, product and inverse with whole planes in one CTA).
  * max_launches bounds both arrays; PAC_ERR_ARG if it is too small.
  */
 int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, void* stream, int max_launches,

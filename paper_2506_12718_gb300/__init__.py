@@ -218,7 +218,7 @@ def pac_plan_reverse_table(plan: int, axis: int, n: int) -> list[int]:
 
 
 KERNEL_NAMES = {0: "dif_pass", 1: "fused_dif_mul_dit_pass", 2: "dit_pass", 3: "permute", 4: "pointwise",
-                5: "conv_kernel"}
+                5: "conv_kernel", 6: "plane_pass"}
 
 
 def pac_convolve_timed(plan: int, which: int, x_dev, y_dev, stream=None, max_launches: int = 64):

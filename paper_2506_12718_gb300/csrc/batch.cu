@@ -4,8 +4,9 @@
 // fused group, inverse groups: 2 G_i - 1 passes).  Passes are aligned by
 // level: level l holds pass l of every instance that has one.  Within a
 // level, the passes that share a kernel shape (element type, group size M,
-// rows or lines) run as ONE launch of pass_multi_kernel, which numbers the
-// tiles of all its passes consecutively; launches of one level are
+// rows or lines; for plane passes both group sizes) run as ONE launch of
+// pass_multi_kernel (plane_multi_kernel), which numbers the tiles (planes)
+// of all its passes consecutively; launches of one level are
 // independent and run as parallel branches, and each level waits for the one
 // before.  A batch of any mix of shapes therefore costs a handful of
 // launches.  The launch sequence of a distinct batch (same plans, same x and
@@ -32,6 +33,7 @@ namespace {
 struct MultiLaunch {
     int esize, M;
     bool lines;
+    int M2;              // > 0: a plane launch (groups M x M2), arguments are PlaneArgs
     int n;               // passes in the launch
     size_t off_args;     // byte offset of its PassArgs[n] in the buffer
     size_t off_starts;   // byte offset of its uint32 tile starts [n + 1]
@@ -59,6 +61,43 @@ void free_entry(BatchEntry* e) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Kernel shape of a step: element size, group size, rows/lines, and for a
+// plane step the second group size.
+using ShapeKey = std::tuple<int, int, int, int>;
+
+ShapeKey shape_key(pac_plan p, const Step& st) {
+    if (st.mode == kPlane)
+        return ShapeKey(p->esize, p->groups[p->plane_g1].M, 0, p->groups[p->plane_g1 + 1].M);
+    const GroupPlan& g = p->groups[st.group];
+    return ShapeKey(p->esize, g.M, g.C == 1 ? 1 : 0, 0);
+}
+
+// Append one merged launch (arguments, then tile starts) to the host image.
+int add_launch(std::vector<unsigned char>& blob, const ShapeKey& key, const void* args, size_t arg_size,
+               const std::vector<int64_t>& tiles, std::vector<MultiLaunch>& out) {
+    MultiLaunch m;
+    int lines;
+    std::tie(m.esize, m.M, lines, m.M2) = key;
+    m.lines = lines != 0;
+    m.n = (int)tiles.size();
+    m.off_args = align_up(blob.size(), 64);
+    blob.resize(m.off_args + tiles.size() * arg_size);
+    std::memcpy(blob.data() + m.off_args, args, tiles.size() * arg_size);
+    m.off_starts = align_up(blob.size(), 16);
+    blob.resize(m.off_starts + (tiles.size() + 1) * sizeof(uint32_t));
+    uint32_t* st = reinterpret_cast<uint32_t*>(blob.data() + m.off_starts);
+    int64_t acc = 0;
+    for (size_t k = 0; k < tiles.size(); ++k) {
+        st[k] = (uint32_t)acc;
+        acc += tiles[k];
+    }
+    st[tiles.size()] = (uint32_t)acc;
+    if (acc > 0x7fffffffLL) return fail(PAC_ERR_SIZE, "batch launch has too many tiles");
+    m.tiles = acc;
+    out.push_back(m);
+    return PAC_OK;
+}
+
 // Build the merged launches of a batch and upload their arguments.
 int build_entry(int count, const pac_plan* plans, const void* const* x, void* const* y, BatchEntry* e) {
     std::vector<std::vector<Step>> seq(count);
@@ -71,15 +110,18 @@ int build_entry(int count, const pac_plan* plans, const void* const* x, void* co
         convolve_steps(plans[i], x[i], y[i], seq[i]);
         levels = std::max(levels, seq[i].size());
     }
-    // level -> shape -> passes
-    using Shape = std::tuple<int, int, bool>;
-    std::vector<std::map<Shape, std::vector<PassArgs>>> by_level(levels);
+    // level -> shape -> passes (plane steps keyed by both group sizes)
+    std::vector<std::map<ShapeKey, std::vector<PassArgs>>> by_level(levels);
+    std::vector<std::map<ShapeKey, std::vector<PlaneArgs>>> planes_by_level(levels);
     for (int i = 0; i < count; ++i) {
         for (size_t l = 0; l < seq[i].size(); ++l) {
             const Step& st = seq[i][l];
-            const GroupPlan& g = plans[i]->groups[st.group];
-            by_level[l][Shape(plans[i]->esize, g.M, g.C == 1)].push_back(
-                make_pass(plans[i], g, st.mode, st.src, st.dst, st.scale));
+            const ShapeKey k = shape_key(plans[i], st);
+            if (st.mode == kPlane)
+                planes_by_level[l][k].push_back(make_plane(plans[i], st.src, st.dst));
+            else
+                by_level[l][k].push_back(make_pass(plans[i], plans[i]->groups[st.group], st.mode, st.src, st.dst,
+                                                   st.scale));
         }
     }
     // one host image of every launch's arguments and tile starts
@@ -87,25 +129,16 @@ int build_entry(int count, const pac_plan* plans, const void* const* x, void* co
     e->levels.assign(levels, {});
     for (size_t l = 0; l < levels; ++l) {
         for (auto& kv : by_level[l]) {
-            const std::vector<PassArgs>& passes = kv.second;
-            MultiLaunch m;
-            std::tie(m.esize, m.M, m.lines) = kv.first;
-            m.n = (int)passes.size();
-            m.off_args = align_up(blob.size(), 64);
-            blob.resize(m.off_args + passes.size() * sizeof(PassArgs));
-            std::memcpy(blob.data() + m.off_args, passes.data(), passes.size() * sizeof(PassArgs));
-            m.off_starts = align_up(blob.size(), 16);
-            blob.resize(m.off_starts + (passes.size() + 1) * sizeof(uint32_t));
-            uint32_t* st = reinterpret_cast<uint32_t*>(blob.data() + m.off_starts);
-            int64_t acc = 0;
-            for (size_t k = 0; k < passes.size(); ++k) {
-                st[k] = (uint32_t)acc;
-                acc += passes[k].tiles;
-            }
-            st[passes.size()] = (uint32_t)acc;
-            if (acc > 0x7fffffffLL) return fail(PAC_ERR_SIZE, "batch level %zu has too many tiles", l);
-            m.tiles = acc;
-            e->levels[l].push_back(m);
+            std::vector<int64_t> tiles;
+            for (const PassArgs& a : kv.second) tiles.push_back(a.tiles);
+            int rc = add_launch(blob, kv.first, kv.second.data(), sizeof(PassArgs), tiles, e->levels[l]);
+            if (rc) return rc;
+        }
+        for (auto& kv : planes_by_level[l]) {
+            std::vector<int64_t> tiles;
+            for (const PlaneArgs& a : kv.second) tiles.push_back(a.planes);
+            int rc = add_launch(blob, kv.first, kv.second.data(), sizeof(PlaneArgs), tiles, e->levels[l]);
+            if (rc) return rc;
         }
     }
     if (!blob.empty()) {
@@ -119,8 +152,18 @@ int build_entry(int count, const pac_plan* plans, const void* const* x, void* co
 
 cudaError_t enqueue_launch(const BatchEntry* e, const MultiLaunch& m, cudaStream_t s) {
     const unsigned char* b = static_cast<const unsigned char*>(e->d_buf);
-    return launch_multi(m.esize, m.M, m.lines, reinterpret_cast<const PassArgs*>(b + m.off_args),
-                        reinterpret_cast<const uint32_t*>(b + m.off_starts), m.n, m.tiles, s);
+    const uint32_t* starts = reinterpret_cast<const uint32_t*>(b + m.off_starts);
+    if (m.M2 > 0)
+        return launch_plane_multi(m.esize, m.M, m.M2, reinterpret_cast<const PlaneArgs*>(b + m.off_args), starts,
+                                  m.n, m.tiles, s);
+    return launch_multi(m.esize, m.M, m.lines, reinterpret_cast<const PassArgs*>(b + m.off_args), starts, m.n,
+                        m.tiles, s);
+}
+
+// per-kernel set-up (shared-memory attribute, occupancy): a launch with no work
+cudaError_t prepare_launch(const MultiLaunch& m, cudaStream_t s) {
+    if (m.M2 > 0) return launch_plane_multi(m.esize, m.M, m.M2, nullptr, nullptr, 0, 0, s);
+    return launch_multi(m.esize, m.M, m.lines, nullptr, nullptr, 0, 0, s);
 }
 
 // Capture the batch's launches into a graph: per level a fork over the
@@ -137,7 +180,7 @@ int capture(BatchEntry* e) {
     // per-kernel set-up (shared-memory attribute, occupancy) happens outside the capture
     for (const auto& lv : e->levels)
         for (const MultiLaunch& m : lv)
-            if (ce == cudaSuccess) ce = launch_multi(m.esize, m.M, m.lines, nullptr, nullptr, 0, 0, st[0]);
+            if (ce == cudaSuccess) ce = prepare_launch(m, st[0]);
     cudaGraph_t graph = nullptr;
     if (ce == cudaSuccess) ce = cudaStreamBeginCapture(st[0], cudaStreamCaptureModeThreadLocal);
     if (ce == cudaSuccess) {
@@ -247,8 +290,7 @@ extern "C" int pac_convolve_many(int count, const pac_plan* plans, const void* c
 
 extern "C" int pac_convolve_many_launches(int count, const pac_plan* plans, int* launches) {
     if (count < 0 || !launches || (count > 0 && !plans)) return fail(PAC_ERR_ARG, "bad arguments");
-    using Shape = std::tuple<int, int, bool>;
-    std::vector<std::map<Shape, int>> by_level;
+    std::vector<std::map<ShapeKey, int>> by_level;
     int pointwise = 0;
     for (int i = 0; i < count; ++i) {
         if (!plans[i]) return fail(PAC_ERR_ARG, "null plan %d", i);
@@ -259,10 +301,7 @@ extern "C" int pac_convolve_many_launches(int count, const pac_plan* plans, int*
         std::vector<Step> seq;
         convolve_steps(plans[i], nullptr, nullptr, seq);
         if (by_level.size() < seq.size()) by_level.resize(seq.size());
-        for (size_t l = 0; l < seq.size(); ++l) {
-            const GroupPlan& g = plans[i]->groups[seq[l].group];
-            by_level[l][Shape(plans[i]->esize, g.M, g.C == 1)] += 1;
-        }
+        for (size_t l = 0; l < seq.size(); ++l) by_level[l][shape_key(plans[i], seq[l])] += 1;
     }
     int n = pointwise;
     for (const auto& lv : by_level) n += (int)lv.size();

@@ -95,4 +95,23 @@ constexpr int min_blocks(int m, int esize) {
     return clampi(65536 / (pass_threads(m, esize) * reg_target(m, esize)), 1, 8);
 }
 
+// ------------------------------------------------------------------ planes
+// A plane pass holds whole n1 x n2 planes (the last two axes) in one CTA's
+// shared memory, element (i1, i2) at i1 * plane_pitch + i2.  Padding chosen
+// like tile_pad, over both axes' round patterns.
+constexpr int plane_pad(int m1, int m2, int esize) {
+    return esize == 8 ? (base_of(m2) == 2 ? (m2 >= 32 ? 3 : 1) : (m2 == 81 ? 8 : 0))
+                      : (base_of(m2) == 2 ? 1 : 0);
+}
+constexpr int plane_pitch(int m1, int m2, int esize) { return m2 + plane_pad(m1, m2, esize); }
+constexpr int plane_smem_bytes(int m1, int m2, int esize) { return m1 * plane_pitch(m1, m2, esize) * esize; }
+constexpr int plane_threads(int m1, int m2, int esize) {
+    return clampi((((m1 * (m2 / round_radix(m2, esize, 0)) > m2 * (m1 / round_radix(m1, esize, 0))
+                         ? m1 * (m2 / round_radix(m2, esize, 0))
+                         : m2 * (m1 / round_radix(m1, esize, 0))) + 31) / 32) * 32,
+                  64, 512);
+}
+// largest plane the plane pass takes (bytes of shared memory)
+constexpr int kPlaneSmemMax = 200 * 1024;
+
 }  // namespace pac

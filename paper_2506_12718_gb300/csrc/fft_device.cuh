@@ -206,6 +206,22 @@ template <typename V, int M> struct Shape {
     static_assert(NT % W == 0, "a thread's tasks must share one column in the rows case");
 };
 
+// Geometry of one group's rounds inside a CTA: M rows (the transformed
+// axis), W independent columns, NT threads, element (row, w) of the exchange
+// buffer at row * RS + w * WS.
+// PF: a thread with several tasks in a round that reads global memory
+// issues all their loads first (needs registers for all of them).
+template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_> struct Geo {
+    using V = V_;
+    static constexpr int M = M_, W = W_, NT = NT_, RS = RS_, WS = WS_, ES = (int)sizeof(V_);
+    static constexpr int NR = round_count(M_, ES);
+    static constexpr bool PF = PF_;
+};
+// the pass kernels' geometry: a tile of W columns, buffer [row][w] of pitch
+// P; several CTAs per SM hide latency, so registers are not spent on prefetch
+template <typename V, int M>
+using PassGeo = Geo<V, M, Shape<V, M>::W, Shape<V, M>::NT, Shape<V, M>::P, 1, false>;
+
 // Task tau of round RI: column w of the tile, offset jp inside its block of
 // S rows, first row row0 = block * S + jp; the task transforms rows
 // row0 + SP * u, u < R.  Column-fastest order (a warp covers consecutive
@@ -237,9 +253,19 @@ template <int M, int ES, int W, int RI, bool JFAST> struct Task {
 // t * W * M + u * TASKS + tau, TASKS = W * M / R for the round's radix R
 // (column-fastest tasks, SP = 1: task tau = w + W * b handles rows b R + u).
 // spec_slot maps an element's position in the plain index-reversed (DIF)
-// order of the array to its slot.
+// order of the array to its slot.  For a plane pass the product is taken in
+// the last forward round of axis d-2 over columns w = the in-CTA row of axis
+// d-1, so (plane, u, task) with task = w + n2 * b.
 
 __device__ __forceinline__ uint32_t spec_slot(const SpecOrder& o, uint32_t e) {
+    if (o.M2) {  // plane pass: (plane, axis d-2 position g1, axis d-1 position g2)
+        const uint32_t ps = o.M * o.M2;
+        const uint32_t pl = e / ps, rem = e - pl * ps;
+        const uint32_t g1 = rem / o.M2, g2 = rem - g1 * o.M2;
+        const uint32_t r1 = (uint32_t)__ldg(o.rowmap + g1), r2 = (uint32_t)__ldg(o.rowmap2 + g2);
+        const uint32_t b = r1 / o.R, u = r1 - b * o.R;
+        return pl * ps + u * o.tasks + r2 + o.M2 * b;
+    }
     uint32_t q, g;
     if (o.C == 1) {
         q = e / o.M;
@@ -285,158 +311,256 @@ enum : int { kToSmem = 0, kToNatural = 1, kToPlaced = 2 };
 // the same global position, conjugate DFT.  DST as SRC; a placed store also
 // applies w_L^{j k'} and the scale, a placed load (first inverse round) the
 // conjugate w_L^{j k'}.
-template <typename V, int M, bool LINES, int RI, bool INV, int SRC, int DST, bool MUL>
-__device__ __forceinline__ void round_exec(const TileCtx<V>& c) {
-    using SH = Shape<V, M>;
-    using G = RoundGeom<M, SH::ES, RI>;
-    constexpr int R = G::R, SP = G::SP, STEP = M / G::S, P = SH::P;
-    constexpr bool JFAST = LINES && !MUL && (SRC == kFromNatural || DST == kToNatural);
-    using T = Task<M, SH::ES, SH::W, RI, JFAST>;
-    static_assert(!MUL || SP == 1, "the product is taken after the last forward round");
+// Global position of a task's column: offset of its row 0, external-twiddle
+// column, and whether the column exists.
+struct TaskCol {
+    uint32_t base, j;
+    bool valid;
+};
+
+template <bool LINES, int M, typename V>
+__device__ __forceinline__ TaskCol task_col(const TileCtx<V>& c, int w) {
+    if constexpr (LINES) {
+        const uint32_t q = c.q0 + (uint32_t)w;
+        return TaskCol{q * (uint32_t)M, 0u, q < c.Q};
+    } else {
+        return TaskCol{c.base, c.j, c.valid};
+    }
+}
+
+// Everything of a task after its R values are in registers: twiddles and
+// DFTs, the product with the spectrum values hs (MUL), and the store.
+template <typename GEO, bool LINES, int RI, bool INV, int SRC, int DST, bool MUL, typename TT>
+__device__ __forceinline__ void task_body(const TileCtx<typename GEO::V>& c, const TT& t, const TaskCol& col,
+                                          typename GEO::V* v, const typename GEO::V* hs) {
+    using V = typename GEO::V;
+    constexpr int M = GEO::M, RS = GEO::RS, WS = GEO::WS;
+    using G = RoundGeom<M, GEO::ES, RI>;
+    constexpr int R = G::R, SP = G::SP, STEP = M / G::S;
     const PassArgs& a = *c.a;
-    const V* src = reinterpret_cast<const V*>(a.src);
     V* dst = reinterpret_cast<V*>(a.dst);
-    const V* spec = reinterpret_cast<const V*>(a.spec);
     const uint32_t stride = LINES ? 1u : c.C;
-#pragma unroll 1
-    for (int tau = threadIdx.x; tau < T::TASKS; tau += SH::NT) {
-        const T t(tau);
-        uint32_t base = c.base, j = c.j;
-        bool valid = c.valid;
-        if constexpr (LINES) {
-            const uint32_t q = c.q0 + (uint32_t)t.w;
-            valid = q < c.Q;
-            base = q * (uint32_t)M;
-            j = 0;
-        }
-        V v[R];
-        if constexpr (SRC == kFromSmem) {
+    if constexpr (INV) {
+        if constexpr (SRC == kFromPlaced && !LINES) {
+            if (a.has_ext && col.j != 0) {
 #pragma unroll
-            for (int u = 0; u < R; ++u) v[u] = c.s[(t.row0 + SP * u) * P + t.w];
-        } else {
+                for (int u = 0; u < R; ++u)
+                    v[u] = cmulc(v[u], ext_twiddle<V>(a, (int64_t)col.j * __ldg(a.r2f + t.row0 + SP * u)));
+            }
+        }
+        if constexpr (SP > 1) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], c.twi[STEP * t.jp * k]);
+        }
+        dft<R, true>(v);
+    } else {
+        dft<R, false>(v);
+        if constexpr (MUL) {
+            if (col.valid) {
+#pragma unroll
+                for (int u = 0; u < R; ++u) v[u] = cmul(v[u], hs[u]);
+            }
+            dft<R, true>(v);
+        } else if constexpr (SP > 1) {
+#pragma unroll
+            for (int k = 1; k < R; ++k) v[k] = cmul(v[k], c.twi[STEP * t.jp * k]);
+        }
+    }
+    if constexpr (DST == kToSmem) {
+#pragma unroll
+        for (int u = 0; u < R; ++u) c.s[(t.row0 + SP * u) * RS + t.w * WS] = v[u];
+    } else if constexpr (DST == kToNatural) {
+        if (col.valid) {
+#pragma unroll
+            for (int u = 0; u < R; ++u) dst[col.base + (uint32_t)(t.row0 + SP * u) * stride] = v[u];
+        }
+    } else {
+        if (col.valid) {
 #pragma unroll
             for (int u = 0; u < R; ++u) {
                 const int row = t.row0 + SP * u;
-                const uint32_t g = SRC == kFromNatural ? (uint32_t)row : (uint32_t)__ldg(a.r2g + row);
-                v[u] = valid ? src[base + g * stride] : V{0, 0};
+                V o = v[u];
+                if constexpr (!LINES) {
+                    if (a.has_ext && col.j != 0) o = cmul(o, ext_twiddle<V>(a, (int64_t)col.j * __ldg(a.r2f + row)));
+                }
+                if (c.do_scale) o = cscale(o, c.scale);
+                dst[col.base + (uint32_t)__ldg(a.r2g + row) * stride] = o;
             }
         }
-        if constexpr (INV) {
-            if constexpr (SRC == kFromPlaced && !LINES) {
-                if (a.has_ext && j != 0) {
+    }
+}
+
+// a task's R input values from global memory (natural or placed rows)
+template <typename GEO, bool LINES, int RI, int SRC, typename TT>
+__device__ __forceinline__ void load_src(const TileCtx<typename GEO::V>& c, const TT& t, const TaskCol& col,
+                                         typename GEO::V* v) {
+    using V = typename GEO::V;
+    using G = RoundGeom<GEO::M, GEO::ES, RI>;
+    const PassArgs& a = *c.a;
+    const V* src = reinterpret_cast<const V*>(a.src);
+    const uint32_t stride = LINES ? 1u : c.C;
 #pragma unroll
-                    for (int u = 0; u < R; ++u)
-                        v[u] = cmulc(v[u], ext_twiddle<V>(a, (int64_t)j * __ldg(a.r2f + t.row0 + SP * u)));
-                }
-            }
-            if constexpr (SP > 1) {
+    for (int u = 0; u < G::R; ++u) {
+        const int row = t.row0 + G::SP * u;
+        const uint32_t g = SRC == kFromNatural ? (uint32_t)row : (uint32_t)__ldg(a.r2g + row);
+        v[u] = col.valid ? src[col.base + g * stride] : V{0, 0};
+    }
+}
+
+// the spectrum values of task tau's R outputs: the spectrum is stored in the
+// order this round consumes it, slot (tile, u, task), so a warp reads 32
+// consecutive elements
+template <typename GEO, int RI, typename TT>
+__device__ __forceinline__ void load_spec(const TileCtx<typename GEO::V>& c, int tau, const TaskCol& col,
+                                          typename GEO::V* hs) {
+    using V = typename GEO::V;
+    using G = RoundGeom<GEO::M, GEO::ES, RI>;
+    constexpr int TASKS = TT::TASKS;
+    const V* spec = reinterpret_cast<const V*>(c.a->spec) + (size_t)c.t * (GEO::W * GEO::M) + tau;
 #pragma unroll
-                for (int k = 1; k < R; ++k) v[k] = cmulc(v[k], c.twi[STEP * t.jp * k]);
-            }
-            dft<R, true>(v);
-        } else {
-            dft<R, false>(v);
-            if constexpr (MUL) {
-                // the spectrum is stored in the order this round consumes it:
-                // slot (tile, u, task), so a warp reads 32 consecutive elements
-                if (valid) {
-                    const V* hs = spec + (size_t)c.t * (SH::W * M) + tau;
+    for (int u = 0; u < G::R; ++u) hs[u] = col.valid ? __ldg(spec + u * TASKS) : V{0, 0};
+}
+
+// One round of a tile.  SRC: shared memory, natural global rows, or global
+// rows in the pass' output placement (row r of the tile's rounds holds the
+// data of global row r2g[r]).  Forward: DFT_R, then w_S^{jp k} (SP > 1).
+// Inverse (adjoint): conj twiddles, then the conjugate DFT.  MUL (the last
+// forward round of a fused pass): DFT, product with the filter spectrum at
+// the same global position, conjugate DFT.  DST as SRC; a placed store also
+// applies w_L^{j k'} and the scale, a placed load (first inverse round) the
+// conjugate w_L^{j k'}.  When a thread has a few tasks in the round and the
+// round reads global memory, every global load of all its tasks is issued
+// before the first task is computed, so their latencies overlap.
+template <typename GEO, bool LINES, int RI, bool INV, int SRC, int DST, bool MUL>
+__device__ __forceinline__ void round_exec(const TileCtx<typename GEO::V>& c) {
+    using V = typename GEO::V;
+    constexpr int M = GEO::M, RS = GEO::RS, WS = GEO::WS;
+    using G = RoundGeom<M, GEO::ES, RI>;
+    constexpr int R = G::R, SP = G::SP;
+    constexpr bool JFAST = LINES && !MUL && (SRC == kFromNatural || DST == kToNatural);
+    using T = Task<M, GEO::ES, GEO::W, RI, JFAST>;
+    static_assert(!MUL || SP == 1, "the product is taken after the last forward round");
+    constexpr bool GSRC = SRC != kFromSmem;
+    constexpr int ITER = (T::TASKS + GEO::NT - 1) / GEO::NT;
+    constexpr bool PREFETCH = GEO::PF && ITER > 1 && ITER * R * GEO::ES <= 256 && (GSRC || MUL);
+    if constexpr (PREFETCH) {
+        V pre[ITER][R];
 #pragma unroll
-                    for (int u = 0; u < R; ++u) v[u] = cmul(v[u], __ldg(hs + u * T::TASKS));
-                }
-                dft<R, true>(v);
-            } else if constexpr (SP > 1) {
-#pragma unroll
-                for (int k = 1; k < R; ++k) v[k] = cmul(v[k], c.twi[STEP * t.jp * k]);
+        for (int it = 0; it < ITER; ++it) {
+            const int tau = (int)threadIdx.x + it * GEO::NT;
+            if (tau < T::TASKS) {
+                const T t(tau);
+                const TaskCol col = task_col<LINES, M>(c, t.w);
+                if constexpr (GSRC)
+                    load_src<GEO, LINES, RI, SRC>(c, t, col, pre[it]);
+                else
+                    load_spec<GEO, RI, T>(c, tau, col, pre[it]);
             }
         }
-        if constexpr (DST == kToSmem) {
 #pragma unroll
-            for (int u = 0; u < R; ++u) c.s[(t.row0 + SP * u) * P + t.w] = v[u];
-        } else if constexpr (DST == kToNatural) {
-            if (valid) {
+        for (int it = 0; it < ITER; ++it) {
+            const int tau = (int)threadIdx.x + it * GEO::NT;
+            if (tau < T::TASKS) {
+                const T t(tau);
+                const TaskCol col = task_col<LINES, M>(c, t.w);
+                V v[R];
+                V hs[MUL ? R : 1];
+                if constexpr (GSRC) {
 #pragma unroll
-                for (int u = 0; u < R; ++u) dst[base + (uint32_t)(t.row0 + SP * u) * stride] = v[u];
-            }
-        } else {
-            if (valid) {
+                    for (int u = 0; u < R; ++u) v[u] = pre[it][u];
+                    if constexpr (MUL) load_spec<GEO, RI, T>(c, tau, col, hs);
+                } else {
 #pragma unroll
-                for (int u = 0; u < R; ++u) {
-                    const int row = t.row0 + SP * u;
-                    V o = v[u];
-                    if constexpr (!LINES) {
-                        if (a.has_ext && j != 0) o = cmul(o, ext_twiddle<V>(a, (int64_t)j * __ldg(a.r2f + row)));
+                    for (int u = 0; u < R; ++u) v[u] = c.s[(t.row0 + SP * u) * RS + t.w * WS];
+                    if constexpr (MUL) {
+#pragma unroll
+                        for (int u = 0; u < R; ++u) hs[u] = pre[it][u];
                     }
-                    if (c.do_scale) o = cscale(o, c.scale);
-                    dst[base + (uint32_t)__ldg(a.r2g + row) * stride] = o;
                 }
+                task_body<GEO, LINES, RI, INV, SRC, DST, MUL>(c, t, col, v, hs);
             }
+        }
+    } else {
+#pragma unroll 1
+        for (int tau = threadIdx.x; tau < T::TASKS; tau += GEO::NT) {
+            const T t(tau);
+            const TaskCol col = task_col<LINES, M>(c, t.w);
+            V v[R];
+            V hs[MUL ? R : 1];
+            if constexpr (GSRC) {
+                load_src<GEO, LINES, RI, SRC>(c, t, col, v);
+            } else {
+#pragma unroll
+                for (int u = 0; u < R; ++u) v[u] = c.s[(t.row0 + SP * u) * RS + t.w * WS];
+            }
+            if constexpr (MUL) load_spec<GEO, RI, T>(c, tau, col, hs);
+            task_body<GEO, LINES, RI, INV, SRC, DST, MUL>(c, t, col, v, hs);
         }
     }
 }
 
 // forward rounds RI .. NR-2, shared memory in and out
-template <typename V, int M, bool LINES, int RI>
-__device__ __forceinline__ void fwd_middle(const TileCtx<V>& c) {
-    if constexpr (RI < Shape<V, M>::NR - 1) {
-        round_exec<V, M, LINES, RI, false, kFromSmem, kToSmem, false>(c);
+template <typename GEO, bool LINES, int RI>
+__device__ __forceinline__ void fwd_middle(const TileCtx<typename GEO::V>& c) {
+    if constexpr (RI < GEO::NR - 1) {
+        round_exec<GEO, LINES, RI, false, kFromSmem, kToSmem, false>(c);
         __syncthreads();
-        fwd_middle<V, M, LINES, RI + 1>(c);
+        fwd_middle<GEO, LINES, RI + 1>(c);
     }
 }
 
 // inverse rounds RI, RI-1, ..., 1, shared memory in and out
-template <typename V, int M, bool LINES, int RI>
-__device__ __forceinline__ void inv_middle(const TileCtx<V>& c) {
+template <typename GEO, bool LINES, int RI>
+__device__ __forceinline__ void inv_middle(const TileCtx<typename GEO::V>& c) {
     if constexpr (RI >= 1) {
-        round_exec<V, M, LINES, RI, true, kFromSmem, kToSmem, false>(c);
+        round_exec<GEO, LINES, RI, true, kFromSmem, kToSmem, false>(c);
         __syncthreads();
-        inv_middle<V, M, LINES, RI - 1>(c);
+        inv_middle<GEO, LINES, RI - 1>(c);
     }
 }
 
 // kFwd: natural rows in, placed rows out (with w_L^{j k'} and the scale).
-template <typename V, int M, bool LINES>
-__device__ __forceinline__ void tile_forward(const TileCtx<V>& c) {
-    constexpr int NR = Shape<V, M>::NR;
+template <typename GEO, bool LINES>
+__device__ __forceinline__ void tile_forward(const TileCtx<typename GEO::V>& c) {
+    constexpr int NR = GEO::NR;
     if constexpr (NR == 1) {
-        round_exec<V, M, LINES, 0, false, kFromNatural, kToPlaced, false>(c);
+        round_exec<GEO, LINES, 0, false, kFromNatural, kToPlaced, false>(c);
     } else {
-        round_exec<V, M, LINES, 0, false, kFromNatural, kToSmem, false>(c);
+        round_exec<GEO, LINES, 0, false, kFromNatural, kToSmem, false>(c);
         __syncthreads();
-        fwd_middle<V, M, LINES, 1>(c);
-        round_exec<V, M, LINES, NR - 1, false, kFromSmem, kToPlaced, false>(c);
+        fwd_middle<GEO, LINES, 1>(c);
+        round_exec<GEO, LINES, NR - 1, false, kFromSmem, kToPlaced, false>(c);
     }
 }
 
 // kInv: placed rows in (with conj w_L^{j k'}), natural rows out.
-template <typename V, int M, bool LINES>
-__device__ __forceinline__ void tile_inverse(const TileCtx<V>& c) {
-    constexpr int NR = Shape<V, M>::NR;
+template <typename GEO, bool LINES>
+__device__ __forceinline__ void tile_inverse(const TileCtx<typename GEO::V>& c) {
+    constexpr int NR = GEO::NR;
     if constexpr (NR == 1) {
-        round_exec<V, M, LINES, 0, true, kFromPlaced, kToNatural, false>(c);
+        round_exec<GEO, LINES, 0, true, kFromPlaced, kToNatural, false>(c);
     } else {
-        round_exec<V, M, LINES, NR - 1, true, kFromPlaced, kToSmem, false>(c);
+        round_exec<GEO, LINES, NR - 1, true, kFromPlaced, kToSmem, false>(c);
         __syncthreads();
-        inv_middle<V, M, LINES, NR - 2>(c);
-        round_exec<V, M, LINES, 0, true, kFromSmem, kToNatural, false>(c);
+        inv_middle<GEO, LINES, NR - 2>(c);
+        round_exec<GEO, LINES, 0, true, kFromSmem, kToNatural, false>(c);
     }
 }
 
 // kFused: natural rows in, forward rounds, product, inverse rounds, natural rows out.
-template <typename V, int M, bool LINES>
-__device__ __forceinline__ void tile_fused(const TileCtx<V>& c) {
-    constexpr int NR = Shape<V, M>::NR;
+template <typename GEO, bool LINES>
+__device__ __forceinline__ void tile_fused(const TileCtx<typename GEO::V>& c) {
+    constexpr int NR = GEO::NR;
     if constexpr (NR == 1) {
-        round_exec<V, M, LINES, 0, false, kFromNatural, kToNatural, true>(c);
+        round_exec<GEO, LINES, 0, false, kFromNatural, kToNatural, true>(c);
     } else {
-        round_exec<V, M, LINES, 0, false, kFromNatural, kToSmem, false>(c);
+        round_exec<GEO, LINES, 0, false, kFromNatural, kToSmem, false>(c);
         __syncthreads();
-        fwd_middle<V, M, LINES, 1>(c);
-        round_exec<V, M, LINES, NR - 1, false, kFromSmem, kToSmem, true>(c);
+        fwd_middle<GEO, LINES, 1>(c);
+        round_exec<GEO, LINES, NR - 1, false, kFromSmem, kToSmem, true>(c);
         __syncthreads();
-        inv_middle<V, M, LINES, NR - 2>(c);
-        round_exec<V, M, LINES, 0, true, kFromSmem, kToNatural, false>(c);
+        inv_middle<GEO, LINES, NR - 2>(c);
+        round_exec<GEO, LINES, 0, true, kFromSmem, kToNatural, false>(c);
     }
 }
 
@@ -467,12 +591,13 @@ __device__ __forceinline__ void tile_setup(TileCtx<V>& c, const PassArgs& a, uin
 
 template <typename V, int M, bool LINES>
 __device__ __forceinline__ void tile_run(const TileCtx<V>& c, int mode) {
+    using GEO = PassGeo<V, M>;
     if (mode == kFwd)
-        tile_forward<V, M, LINES>(c);
+        tile_forward<GEO, LINES>(c);
     else if (mode == kFused)
-        tile_fused<V, M, LINES>(c);
+        tile_fused<GEO, LINES>(c);
     else
-        tile_inverse<V, M, LINES>(c);
+        tile_inverse<GEO, LINES>(c);
 }
 
 template <typename V> __device__ __forceinline__ void ctx_init(TileCtx<V>& c, const PassArgs& a, V* s) {
@@ -533,6 +658,124 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, size
         ctx_init(c, a, s);
         tile_setup<V, M, LINES>(c, a, t - __ldg(tile_start + lo));
         tile_run<V, M, LINES>(c, a.mode);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ planes
+//
+// Plane pass: the last two axes (n1 x n2, one group each) of whole planes in
+// one CTA's shared memory.  Axis d-1 forward (first round from global, lines
+// coalesced), axis d-2 forward with the product in its last round, axis d-2
+// inverse, axis d-1 inverse (last round to global): the convolution of the
+// two innermost axes in one pass, so a 3-D convolution takes 3 passes and a
+// 2-D one a single launch.
+
+template <typename V, int M1, int M2> struct PlaneShape {
+    static constexpr int ES = sizeof(V);
+    static constexpr int P2 = plane_pitch(M1, M2, ES);
+    static constexpr int NT = plane_threads(M1, M2, ES);
+    static constexpr int SMEM = plane_smem_bytes(M1, M2, ES);
+    using G2 = Geo<V, M2, M1, NT, 1, P2, true>;  // axis d-1: rows i2, columns i1
+    using G1 = Geo<V, M1, M2, NT, P2, 1, true>;  // axis d-2: rows i1, columns i2
+    static_assert(SMEM <= kPlaneSmemMax, "plane too large for one CTA");
+};
+
+// forward rounds 0..NR-1, the first from global (natural rows), all results in shared memory
+template <typename GEO, bool LINES>
+__device__ __forceinline__ void fwd_all_to_smem(const TileCtx<typename GEO::V>& c) {
+    constexpr int NR = GEO::NR;
+    round_exec<GEO, LINES, 0, false, kFromNatural, kToSmem, false>(c);
+    if constexpr (NR > 1) {
+        __syncthreads();
+        fwd_middle<GEO, LINES, 1>(c);
+        round_exec<GEO, LINES, NR - 1, false, kFromSmem, kToSmem, false>(c);
+    }
+}
+
+// forward rounds, product, inverse rounds, all in shared memory
+template <typename GEO>
+__device__ __forceinline__ void fused_in_smem(const TileCtx<typename GEO::V>& c) {
+    constexpr int NR = GEO::NR;
+    if constexpr (NR == 1) {
+        round_exec<GEO, false, 0, false, kFromSmem, kToSmem, true>(c);
+    } else {
+        round_exec<GEO, false, 0, false, kFromSmem, kToSmem, false>(c);
+        __syncthreads();
+        fwd_middle<GEO, false, 1>(c);
+        round_exec<GEO, false, NR - 1, false, kFromSmem, kToSmem, true>(c);
+        __syncthreads();
+        inv_middle<GEO, false, NR - 2>(c);
+        round_exec<GEO, false, 0, true, kFromSmem, kToSmem, false>(c);
+    }
+}
+
+// inverse rounds NR-1..0 from shared memory, the last to global (natural rows)
+template <typename GEO, bool LINES>
+__device__ __forceinline__ void inv_all_from_smem(const TileCtx<typename GEO::V>& c) {
+    constexpr int NR = GEO::NR;
+    if constexpr (NR == 1) {
+        round_exec<GEO, LINES, 0, true, kFromSmem, kToNatural, false>(c);
+    } else {
+        round_exec<GEO, LINES, NR - 1, true, kFromSmem, kToSmem, false>(c);
+        __syncthreads();
+        inv_middle<GEO, LINES, NR - 2>(c);
+        round_exec<GEO, LINES, 0, true, kFromSmem, kToNatural, false>(c);
+    }
+}
+
+template <typename V, int M1, int M2>
+__device__ __forceinline__ void plane_run(const PlaneArgs& pa, uint32_t plane, V* s) {
+    using PS = PlaneShape<V, M1, M2>;
+    TileCtx<V> c2, c1;
+    ctx_init(c2, pa.a2, s);
+    c2.t = plane;
+    c2.q0 = plane * (uint32_t)M1;  // lines of this plane
+    c2.valid = true;
+    c2.base = 0;
+    c2.j = 0;
+    ctx_init(c1, pa.a1, s);
+    c1.t = plane;
+    c1.q0 = 0;
+    c1.valid = true;
+    c1.base = 0;
+    c1.j = 0;
+    fwd_all_to_smem<typename PS::G2, true>(c2);
+    __syncthreads();
+    fused_in_smem<typename PS::G1>(c1);
+    __syncthreads();
+    inv_all_from_smem<typename PS::G2, true>(c2);
+}
+
+template <typename V, int M1, int M2>
+__global__ void __launch_bounds__(PlaneShape<V, M1, M2>::NT, 1) plane_kernel(const __grid_constant__ PlaneArgs pa) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_launch_dependents();
+    pdl_wait();
+    V* s = reinterpret_cast<V*>(smem_raw);
+    for (uint32_t p = blockIdx.x; p < (uint32_t)pa.planes; p += gridDim.x) {
+        plane_run<V, M1, M2>(pa, p, s);
+        __syncthreads();
+    }
+}
+
+// batched form: planes of list[0..n) numbered consecutively (tile_start as in pass_multi_kernel)
+template <typename V, int M1, int M2>
+__global__ void __launch_bounds__(PlaneShape<V, M1, M2>::NT, 1)
+    plane_multi_kernel(const PlaneArgs* __restrict__ list, const uint32_t* __restrict__ start, int n) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V* s = reinterpret_cast<V*>(smem_raw);
+    const uint32_t total = __ldg(start + n);
+    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(start + mid) <= t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        plane_run<V, M1, M2>(list[lo], t - __ldg(start + lo), s);
         __syncthreads();
     }
 }

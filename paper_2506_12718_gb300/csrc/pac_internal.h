@@ -42,6 +42,13 @@ cudaError_t launch_pass(int esize, int M, const PassArgs& a, cudaStream_t s);
 int conv_grid(int esize, int M, int dev);  // co-resident CTAs of the single-launch kernel (0: unavailable)
 cudaError_t launch_conv(int esize, int M, ConvArgs& args, int grid, cudaStream_t s);
 int pass_kernel_supported(int M, int esize);
+// plane pass (kern_plane.cu): whole planes of the last two axes in one CTA
+int plane_supported(int M1, int M2, int esize);
+cudaError_t launch_plane(int esize, int M1, int M2, const PlaneArgs& pa, cudaStream_t s);
+cudaError_t launch_plane_multi(int esize, int M1, int M2, const PlaneArgs* list, const uint32_t* starts, int n,
+                               int64_t total, cudaStream_t s);
+PlaneArgs make_plane(pac_plan p, const void* src, void* dst);
+
 // n passes of one shape in one launch; list and starts in device memory (starts has n + 1 entries)
 cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
                          int64_t total, cudaStream_t s);
@@ -87,6 +94,8 @@ struct pac_plan_s {
     int esize = 8;
     int64_t N = 1;
     int uniform_m = 0;  // group size shared by every pass (0: sizes differ)
+    bool plane = false;  // the last two axes run as one plane pass (groups plane_g1, plane_g1 + 1)
+    int plane_g1 = -1;
     bool single_launch = false;  // run a pass sequence as one cooperative launch
     int device = 0;
     std::vector<std::vector<int>> stages;          // per axis, DIF order

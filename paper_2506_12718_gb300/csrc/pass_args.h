@@ -4,7 +4,7 @@
 
 namespace pac {
 
-enum PassMode : int { kFwd = 0, kInv = 1, kFused = 2 };
+enum PassMode : int { kFwd = 0, kInv = 1, kFused = 2, kPlane = 3 };
 
 // One pass over the array, viewed as [beta][m][c]: m in [0, M) is the group
 // axis (row stride C elements); column q = beta * C + c, Q = N / M columns.
@@ -31,14 +31,25 @@ struct PassArgs {
     double scale;           // applied on store in kFwd (filter spectrum 1/N); 1 = none
 };
 
+// A plane pass (the last two axes, one group each, whole planes in one CTA):
+// a1 = the group of axis d-2 (rows of the plane), a2 = the group of axis d-1
+// (lines of the plane); planes = N / (n1 n2).  a2.src / a2.dst are the
+// pass' input and output, a1.spec the spectrum.
+struct PlaneArgs {
+    PassArgs a1, a2;
+    int64_t planes;
+};
+
 // Storage order of a filter spectrum (see spec_slot in fft_device.cuh).
 struct SpecOrder {
-    uint32_t M;       // group size of the fused pass
-    uint32_t W;       // its tile width
+    uint32_t M;       // group size of the fused pass (plane: n1)
+    uint32_t W;       // its tile width (plane: n2)
     uint32_t C;       // its row stride
-    uint32_t R;       // radix of its last round
+    uint32_t R;       // radix of its last round (plane: of axis d-2's last round)
     uint32_t tasks;   // W * M / R
-    const int* rowmap;  // [M] in-CTA row of global row g
+    const int* rowmap;  // [M] in-CTA row of global row g (plane: of axis d-2)
+    uint32_t M2;        // plane order when > 0: n2
+    const int* rowmap2; // plane: [n2] in-CTA row of axis d-1
 };
 
 constexpr int kMaxPasses = 12;

@@ -319,6 +319,22 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
     // PAC_SINGLE_LAUNCH=1 in the environment when the plan is created
     const char* sl = std::getenv("PAC_SINGLE_LAUNCH");
     pl->single_launch = sl && sl[0] == '1';
+    // plane pass: the last two axes each one group, a supported plane shape;
+    // PAC_PLANE=0 in the environment keeps per-axis passes instead
+    const char* pe = std::getenv("PAC_PLANE");
+    if (ndim >= 2 && !(pe && pe[0] == '0')) {
+        int g_last = 0, g_prev = 0;
+        for (const GroupPlan& g : pl->groups) {
+            if (g.axis == ndim - 1) ++g_last;
+            if (g.axis == ndim - 2) ++g_prev;
+        }
+        const int G = (int)pl->groups.size();
+        if (g_last == 1 && g_prev == 1 && G >= 2 &&
+            plane_supported(pl->groups[G - 2].M, pl->groups[G - 1].M, pl->esize)) {
+            pl->plane = true;
+            pl->plane_g1 = G - 2;
+        }
+    }
     pl->uniform_m = 0;
     if (!pl->groups.empty()) {
         pl->uniform_m = pl->groups[0].M;
@@ -386,7 +402,7 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
         return cuda_fail(e, "cudaMemcpy(tables)");
     }
     pl->spec_elems = pl->N;
-    if (!pl->groups.empty()) {  // whole tiles of the fused pass (see SpecOrder)
+    if (!pl->groups.empty() && !pl->plane) {  // whole tiles of the fused pass (see SpecOrder)
         const GroupPlan& f = pl->groups.back();
         const int64_t W = tile_w(f.M, pl->esize);
         pl->spec_elems = (f.Q + W - 1) / W * W * f.M;
@@ -447,6 +463,21 @@ static void timer_mark(cudaStream_t s, int id, bool before) {
 SpecOrder spec_order_of(pac_plan p) {
     const GroupPlan& f = p->groups.back();
     SpecOrder o;
+    o.M2 = 0;
+    o.rowmap2 = nullptr;
+    if (p->plane) {  // the plane pass: product in the last forward round of axis d-2
+        const GroupPlan& g1 = p->groups[p->plane_g1];
+        const unsigned char* t = static_cast<const unsigned char*>(p->d_tables);
+        o.M = (uint32_t)g1.M;
+        o.W = (uint32_t)f.M;
+        o.C = (uint32_t)g1.C;
+        o.R = (uint32_t)round_radix(g1.M, p->esize, round_count(g1.M, p->esize) - 1);
+        o.tasks = o.W * o.M / o.R;
+        o.rowmap = reinterpret_cast<const int*>(t + g1.off_rowmap);
+        o.M2 = (uint32_t)f.M;
+        o.rowmap2 = reinterpret_cast<const int*>(t + f.off_rowmap);
+        return o;
+    }
     o.M = (uint32_t)f.M;
     o.W = (uint32_t)tile_w(f.M, p->esize);
     o.C = (uint32_t)f.C;
@@ -483,6 +514,23 @@ PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, vo
     return a;
 }
 
+PlaneArgs make_plane(pac_plan p, const void* src, void* dst) {
+    PlaneArgs pa;
+    pa.a1 = make_pass(p, p->groups[p->plane_g1], kPlane, src, dst, 1.0);
+    pa.a2 = make_pass(p, p->groups[p->plane_g1 + 1], kPlane, src, dst, 1.0);
+    pa.planes = p->N / ((int64_t)p->groups[p->plane_g1].M * p->groups[p->plane_g1 + 1].M);
+    return pa;
+}
+
+static int run_plane(pac_plan p, const void* src, void* dst, cudaStream_t s) {
+    const PlaneArgs pa = make_plane(p, src, dst);
+    timer_mark(s, 6, true);
+    cudaError_t e = launch_plane(p->esize, p->groups[p->plane_g1].M, p->groups[p->plane_g1 + 1].M, pa, s);
+    timer_mark(s, 6, false);
+    if (e != cudaSuccess) return cuda_fail(e, "plane kernel launch");
+    return PAC_OK;
+}
+
 int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale, cudaStream_t s) {
     const PassArgs a = make_pass(p, g, mode, src, dst, scale);
     const int kid = mode == kFwd ? 0 : (mode == kFused ? 1 : 2);
@@ -498,7 +546,7 @@ int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* ds
 // same size M and single launches are allowed, else one launch per pass.
 static int run_steps(pac_plan p, const std::vector<Step>& steps, cudaStream_t s, bool allow_single) {
     const int n = (int)steps.size();
-    bool single = allow_single && p->single_launch && n > 1 && n <= kMaxPasses && p->uniform_m > 0;
+    bool single = allow_single && p->single_launch && !p->plane && n > 1 && n <= kMaxPasses && p->uniform_m > 0;
     int grid = 0;
     if (single) {
         grid = conv_grid(p->esize, p->uniform_m, p->device);
@@ -520,7 +568,8 @@ static int run_steps(pac_plan p, const std::vector<Step>& steps, cudaStream_t s,
         return PAC_OK;
     }
     for (const Step& st : steps) {
-        int rc = run_pass(p, p->groups[st.group], st.mode, st.src, st.dst, st.scale, s);
+        int rc = st.mode == kPlane ? run_plane(p, st.src, st.dst, s)
+                                   : run_pass(p, p->groups[st.group], st.mode, st.src, st.dst, st.scale, s);
         if (rc) return rc;
     }
     return PAC_OK;
@@ -551,9 +600,17 @@ int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s, bool allow_
 
 // Algorithm 11, lines 2-4, as a pass sequence: forward groups (the last fused
 // with the product and the first inverse group), then the inverse groups.
+// With a plane pass, the groups of the last two axes are one step.
 void convolve_steps(pac_plan p, const void* x, void* y, std::vector<Step>& steps) {
     const int G = (int)p->groups.size();
     steps.clear();
+    if (p->plane) {
+        const int g1 = p->plane_g1;
+        for (int i = 0; i < g1; ++i) steps.push_back({i, kFwd, i == 0 ? x : y, y, 1.0});
+        steps.push_back({g1, kPlane, g1 == 0 ? x : y, y, 1.0});
+        for (int i = g1 - 1; i >= 0; --i) steps.push_back({i, kInv, y, y, 1.0});
+        return;
+    }
     for (int i = 0; i < G; ++i) steps.push_back({i, i == G - 1 ? kFused : kFwd, i == 0 ? x : y, y, 1.0});
     for (int i = G - 2; i >= 0; --i) steps.push_back({i, kInv, y, y, 1.0});
 }
@@ -799,9 +856,12 @@ extern "C" int pac_plan_query(pac_plan p, int key, int64_t* value) {
         case PAC_Q_NDIM: *value = p->ndim; break;
         case PAC_Q_N_TOTAL: *value = p->N; break;
         case PAC_Q_ELEM_BYTES: *value = p->esize; break;
-        case PAC_Q_LAUNCHES_CONVOLVE:
-            *value = G == 0 ? 1 : (single_ok(p, 2 * G - 1) ? 1 : 2 * G - 1);
+        case PAC_Q_LAUNCHES_CONVOLVE: {
+            std::vector<Step> st;
+            convolve_steps(p, nullptr, nullptr, st);
+            *value = G == 0 ? 1 : (!p->plane && single_ok(p, (int)st.size()) ? 1 : (int64_t)st.size());
             break;
+        }
         case PAC_Q_LAUNCHES_PERMUTED:
             *value = (G == 0 ? 1 : (single_ok(p, G) ? 1 : G)) * 2 + 2;
             break;

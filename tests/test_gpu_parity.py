@@ -135,6 +135,33 @@ def test_shapes_separable(dims, radix, dtype):
     check(y, oracle.conv_separable(fs, x), dtype, int(np.prod(dims)), f"{dims} r{radix}")
 
 
+PLANE_SHAPES = [((128, 128), 4, "c64"), ((64, 64), 2, "c64"), ((2, 32, 32), 8, "c64"), ((16, 16), 2, "c64"),
+                ((4, 64, 128), 2, "c64"), ((2, 128, 64), 4, "c64"), ((81, 81), 3, "c64"), ((27, 27), 3, "c64"),
+                ((25, 25), 5, "c64"), ((125, 125), 5, "c64"), ((9, 9), 3, "c64"), ((64, 64), 4, "c128"),
+                ((4, 32, 32), 2, "c128"), ((81, 81), 3, "c128"), ((25, 25), 5, "c128"), ((16, 16), 8, "c128"),
+                ((3, 27, 27), 3, "c128")]
+
+
+@pytest.mark.parametrize("dims,radix,dtype", PLANE_SHAPES,
+                         ids=[f"{'x'.join(map(str, d))}-r{r}-{t}" for d, r, t in PLANE_SHAPES])
+def test_plane_pass_shapes(dims, radix, dtype, monkeypatch):
+    """Shapes whose last two axes run as one plane pass (whole planes in one
+    CTA): against the oracle, and equal to the per-axis passes (PAC_PLANE=0)."""
+    pac = pac_mod()
+    fs, h, x = separable_case(dims, dtype, seed=len(dims) * 100 + dims[-1])
+    ref = oracle.conv_separable(fs, x)
+    y = gpu_conv(dims, radix, dtype, h, x)
+    check(y, ref, dtype, int(np.prod(dims)), f"plane {dims}")
+    plan = pac.Plan(dims, radix, dtype)
+    try:
+        assert plan.query(pac.Q_LAUNCHES_CONVOLVE) == 2 * (len(dims) - 2) + 1
+    finally:
+        plan.close()
+    monkeypatch.setenv("PAC_PLANE", "0")
+    y2 = gpu_conv(dims, radix, dtype, h, x)
+    check(y2, ref, dtype, int(np.prod(dims)), f"per-axis {dims}")
+
+
 @pytest.mark.parametrize("dims,radix", [((16,), 2), ((9, 27), 3), ((8, 4, 16), 4), ((25, 5), 5), ((64, 64), 8)])
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 def test_nonseparable_direct(dims, radix, dtype):
@@ -452,8 +479,10 @@ def test_single_launch_repeatable_and_barrier_clean(dims, radix, dtype, monkeypa
     pac = pac_mod()
     fs, h, x = separable_case(dims, dtype, seed=21)
     monkeypatch.setenv("PAC_SINGLE_LAUNCH", "1")
+    monkeypatch.setenv("PAC_PLANE", "0")  # the single launch runs the per-axis pass sequence
     plan = pac.Plan(dims, radix, dtype)
     monkeypatch.delenv("PAC_SINGLE_LAUNCH")
+    monkeypatch.delenv("PAC_PLANE")
     try:
         plan.filter_spectrum(dev(h))
         xd = dev(x)
