@@ -178,18 +178,22 @@ def time_steps(torch, fn, steps, warmup, flush, stream):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
+# sources that define the pass and plane kernels and their launch shapes
+KERNEL_SOURCES = ("fft_device.cuh", "config.h", "pass_args.h", "roots.h", "kern_launch.cuh", "kern_c64_p2.cu",
+                  "kern_c128_p2.cu", "kern_plane.cu")
+
+
 def source_hash():
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2506_12718_gb300", "csrc", "*"))):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(f, "rb").read())
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2506_12718_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.txt")  # JSON text
     try:
         data = json.load(open(path))
     except (OSError, ValueError):

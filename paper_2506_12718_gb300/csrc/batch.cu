@@ -34,6 +34,7 @@ struct MultiLaunch {
     int esize, M;
     bool lines;
     int M2;              // > 0: a plane launch (groups M x M2), arguments are PlaneArgs
+    int K;               // plane launch: CTAs per plane
     int n;               // passes in the launch
     size_t off_args;     // byte offset of its PassArgs[n] in the buffer
     size_t off_starts;   // byte offset of its uint32 tile starts [n + 1]
@@ -61,13 +62,13 @@ void free_entry(BatchEntry* e) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Kernel shape of a step: element size, group size, rows/lines, and for a
-// plane step the second group size.
+// Kernel shape of a step: element size, group size, rows/lines (for a plane
+// step: CTAs per plane), and for a plane step the second group size.
 using ShapeKey = std::tuple<int, int, int, int>;
 
 ShapeKey shape_key(pac_plan p, const Step& st) {
     if (st.mode == kPlane)
-        return ShapeKey(p->esize, p->groups[p->plane_g1].M, 0, p->groups[p->plane_g1 + 1].M);
+        return ShapeKey(p->esize, p->groups[p->plane_g1].M, p->plane_k, p->groups[p->plane_g1 + 1].M);
     const GroupPlan& g = p->groups[st.group];
     return ShapeKey(p->esize, g.M, g.C == 1 ? 1 : 0, 0);
 }
@@ -78,7 +79,8 @@ int add_launch(std::vector<unsigned char>& blob, const ShapeKey& key, const void
     MultiLaunch m;
     int lines;
     std::tie(m.esize, m.M, lines, m.M2) = key;
-    m.lines = lines != 0;
+    m.lines = m.M2 == 0 && lines != 0;
+    m.K = m.M2 > 0 ? lines : 1;
     m.n = (int)tiles.size();
     m.off_args = align_up(blob.size(), 64);
     blob.resize(m.off_args + tiles.size() * arg_size);
@@ -154,15 +156,15 @@ cudaError_t enqueue_launch(const BatchEntry* e, const MultiLaunch& m, cudaStream
     const unsigned char* b = static_cast<const unsigned char*>(e->d_buf);
     const uint32_t* starts = reinterpret_cast<const uint32_t*>(b + m.off_starts);
     if (m.M2 > 0)
-        return launch_plane_multi(m.esize, m.M, m.M2, reinterpret_cast<const PlaneArgs*>(b + m.off_args), starts,
-                                  m.n, m.tiles, s);
+        return launch_plane_multi(m.esize, m.M, m.M2, m.K, reinterpret_cast<const PlaneArgs*>(b + m.off_args),
+                                  starts, m.n, m.tiles, s);
     return launch_multi(m.esize, m.M, m.lines, reinterpret_cast<const PassArgs*>(b + m.off_args), starts, m.n,
                         m.tiles, s);
 }
 
 // per-kernel set-up (shared-memory attribute, occupancy): a launch with no work
 cudaError_t prepare_launch(const MultiLaunch& m, cudaStream_t s) {
-    if (m.M2 > 0) return launch_plane_multi(m.esize, m.M, m.M2, nullptr, nullptr, 0, 0, s);
+    if (m.M2 > 0) return launch_plane_multi(m.esize, m.M, m.M2, m.K, nullptr, nullptr, 0, 0, s);
     return launch_multi(m.esize, m.M, m.lines, nullptr, nullptr, 0, 0, s);
 }
 

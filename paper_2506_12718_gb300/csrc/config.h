@@ -105,12 +105,16 @@ constexpr int plane_pad(int m1, int m2, int esize) {
 }
 constexpr int plane_pitch(int m1, int m2, int esize) { return m2 + plane_pad(m1, m2, esize); }
 constexpr int plane_smem_bytes(int m1, int m2, int esize) { return m1 * plane_pitch(m1, m2, esize) * esize; }
-constexpr int plane_threads(int m1, int m2, int esize) {
-    return clampi((((m1 * (m2 / round_radix(m2, esize, 0)) > m2 * (m1 / round_radix(m1, esize, 0))
-                         ? m1 * (m2 / round_radix(m2, esize, 0))
-                         : m2 * (m1 / round_radix(m1, esize, 0))) + 31) / 32) * 32,
-                  64, 512);
+// threads of a plane CTA (K CTAs per plane): the larger first-round task count
+constexpr int plane_threads(int m1, int m2, int esize, int k) {
+    return clampi((((m1 / k * (m2 / round_radix(m2, esize, 0)) > m2 / k * (m1 / round_radix(m1, esize, 0))
+                         ? m1 / k * (m2 / round_radix(m2, esize, 0))
+                         : m2 / k * (m1 / round_radix(m1, esize, 0))) + 31) / 32) * 32,
+                  64, k > 1 ? 256 : 512);
 }
+// resident CTAs per SM a plane kernel is compiled for: split planes (K > 1)
+// keep two per SM so that one cluster's barriers overlap another's work
+constexpr int plane_min_blocks(int k) { return k > 1 ? 2 : 1; }
 // largest plane the plane pass takes (bytes of shared memory)
 constexpr int kPlaneSmemMax = 200 * 1024;
 

@@ -211,9 +211,12 @@ template <typename V, int M> struct Shape {
 // buffer at row * RS + w * WS.
 // PF: a thread with several tasks in a round that reads global memory
 // issues all their loads first (needs registers for all of them).
-template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_> struct Geo {
+// KS > 1: the M rows are split over the KS CTAs of a thread-block cluster
+// (rows [k M/KS, (k+1) M/KS) in CTA k's buffer, reached through distributed
+// shared memory), and rounds synchronise the whole cluster.
+template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int KS_ = 1> struct Geo {
     using V = V_;
-    static constexpr int M = M_, W = W_, NT = NT_, RS = RS_, WS = WS_, ES = (int)sizeof(V_);
+    static constexpr int M = M_, W = W_, NT = NT_, RS = RS_, WS = WS_, ES = (int)sizeof(V_), KS = KS_;
     static constexpr int NR = round_count(M_, ES);
     static constexpr bool PF = PF_;
 };
@@ -255,16 +258,18 @@ template <int M, int ES, int W, int RI, bool JFAST> struct Task {
 // spec_slot maps an element's position in the plain index-reversed (DIF)
 // order of the array to its slot.  For a plane pass the product is taken in
 // the last forward round of axis d-2 over columns w = the in-CTA row of axis
-// d-1, so (plane, u, task) with task = w + n2 * b.
+// d-1; with a plane split over a K-CTA cluster, CTA k owns columns
+// [k n2/K, (k+1) n2/K), so (plane, k, u, task) with task = w - k n2/K + (n2/K) b.
 
 __device__ __forceinline__ uint32_t spec_slot(const SpecOrder& o, uint32_t e) {
     if (o.M2) {  // plane pass: (plane, axis d-2 position g1, axis d-1 position g2)
-        const uint32_t ps = o.M * o.M2;
+        const uint32_t ps = o.M * o.M2, wk = o.M2 / o.K;
         const uint32_t pl = e / ps, rem = e - pl * ps;
         const uint32_t g1 = rem / o.M2, g2 = rem - g1 * o.M2;
         const uint32_t r1 = (uint32_t)__ldg(o.rowmap + g1), r2 = (uint32_t)__ldg(o.rowmap2 + g2);
         const uint32_t b = r1 / o.R, u = r1 - b * o.R;
-        return pl * ps + u * o.tasks + r2 + o.M2 * b;
+        const uint32_t rank = r2 / wk, wl = r2 - rank * wk;  // the cluster CTA that owns column r2
+        return pl * ps + rank * (ps / o.K) + u * o.tasks + wl + wk * b;
     }
     uint32_t q, g;
     if (o.C == 1) {
@@ -298,7 +303,72 @@ template <typename V> struct TileCtx {
     bool valid;        // rows case: this thread's column exists (q < Q)
     bool do_scale;     // kFwd: multiply by `scale` on store (decided once, not per element)
     typename Real<V>::T scale;
+    int wofs;          // column offset of this CTA's columns in the buffer (split rows)
+    uint32_t sk[4];    // split rows: the buffer of each CTA of the cluster (shared::cluster addresses)
 };
+
+// Loads and stores of distributed shared memory (a CTA of the cluster,
+// 32-bit shared::cluster address).
+__device__ __forceinline__ float2 ld_dsmem(uint32_t a, float2*) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ double2 ld_dsmem(uint32_t a, double2*) {
+    double2 v;
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];\n" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_dsmem(uint32_t a, float2 v) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};\n" ::"r"(a), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void st_dsmem(uint32_t a, double2 v) {
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};\n" ::"r"(a), "d"(v.x), "d"(v.y) : "memory");
+}
+
+// shared::cluster address of element (row, w) of a split buffer: rows of CTA
+// `part` at sk[part] (selected without run-time array indexing, which would
+// put the array in local memory)
+template <typename GEO>
+__device__ __forceinline__ uint32_t dsmem_addr(const TileCtx<typename GEO::V>& c, int row, int w) {
+    constexpr int H = GEO::M / GEO::KS;
+    const int part = row / H;
+    uint32_t b = c.sk[0];
+#pragma unroll
+    for (int k = 1; k < GEO::KS; ++k) b = part == k ? c.sk[k] : b;
+    return b + (uint32_t)(((row - part * H) * GEO::RS + (w + c.wofs) * GEO::WS) * GEO::ES);
+}
+
+// Element (row, w) of a round's exchange buffer.
+template <typename GEO>
+__device__ __forceinline__ typename GEO::V sld(const TileCtx<typename GEO::V>& c, int row, int w) {
+    if constexpr (GEO::KS == 1)
+        return c.s[row * GEO::RS + w * GEO::WS];
+    else
+        return ld_dsmem(dsmem_addr<GEO>(c, row, w), static_cast<typename GEO::V*>(nullptr));
+}
+template <typename GEO>
+__device__ __forceinline__ void sst(const TileCtx<typename GEO::V>& c, int row, int w, typename GEO::V v) {
+    if constexpr (GEO::KS == 1)
+        c.s[row * GEO::RS + w * GEO::WS] = v;
+    else
+        st_dsmem(dsmem_addr<GEO>(c, row, w), v);
+}
+
+// barrier of every thread of a cluster, with release/acquire ordering of
+// shared-memory accesses (distributed shared memory included)
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n"
+                 "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// synchronisation between two rounds of a geometry
+template <typename GEO> __device__ __forceinline__ void round_sync() {
+    if constexpr (GEO::KS > 1)
+        cluster_sync_all();
+    else
+        __syncthreads();
+}
 
 enum : int { kFromSmem = 0, kFromNatural = 1, kFromPlaced = 2 };
 enum : int { kToSmem = 0, kToNatural = 1, kToPlaced = 2 };
@@ -334,7 +404,7 @@ template <typename GEO, bool LINES, int RI, bool INV, int SRC, int DST, bool MUL
 __device__ __forceinline__ void task_body(const TileCtx<typename GEO::V>& c, const TT& t, const TaskCol& col,
                                           typename GEO::V* v, const typename GEO::V* hs) {
     using V = typename GEO::V;
-    constexpr int M = GEO::M, RS = GEO::RS, WS = GEO::WS;
+    constexpr int M = GEO::M;
     using G = RoundGeom<M, GEO::ES, RI>;
     constexpr int R = G::R, SP = G::SP, STEP = M / G::S;
     const PassArgs& a = *c.a;
@@ -368,7 +438,7 @@ __device__ __forceinline__ void task_body(const TileCtx<typename GEO::V>& c, con
     }
     if constexpr (DST == kToSmem) {
 #pragma unroll
-        for (int u = 0; u < R; ++u) c.s[(t.row0 + SP * u) * RS + t.w * WS] = v[u];
+        for (int u = 0; u < R; ++u) sst<GEO>(c, t.row0 + SP * u, t.w, v[u]);
     } else if constexpr (DST == kToNatural) {
         if (col.valid) {
 #pragma unroll
@@ -434,7 +504,7 @@ __device__ __forceinline__ void load_spec(const TileCtx<typename GEO::V>& c, int
 template <typename GEO, bool LINES, int RI, bool INV, int SRC, int DST, bool MUL>
 __device__ __forceinline__ void round_exec(const TileCtx<typename GEO::V>& c) {
     using V = typename GEO::V;
-    constexpr int M = GEO::M, RS = GEO::RS, WS = GEO::WS;
+    constexpr int M = GEO::M;
     using G = RoundGeom<M, GEO::ES, RI>;
     constexpr int R = G::R, SP = G::SP;
     constexpr bool JFAST = LINES && !MUL && (SRC == kFromNatural || DST == kToNatural);
@@ -471,7 +541,7 @@ __device__ __forceinline__ void round_exec(const TileCtx<typename GEO::V>& c) {
                     if constexpr (MUL) load_spec<GEO, RI, T>(c, tau, col, hs);
                 } else {
 #pragma unroll
-                    for (int u = 0; u < R; ++u) v[u] = c.s[(t.row0 + SP * u) * RS + t.w * WS];
+                    for (int u = 0; u < R; ++u) v[u] = sld<GEO>(c, t.row0 + SP * u, t.w);
                     if constexpr (MUL) {
 #pragma unroll
                         for (int u = 0; u < R; ++u) hs[u] = pre[it][u];
@@ -491,7 +561,7 @@ __device__ __forceinline__ void round_exec(const TileCtx<typename GEO::V>& c) {
                 load_src<GEO, LINES, RI, SRC>(c, t, col, v);
             } else {
 #pragma unroll
-                for (int u = 0; u < R; ++u) v[u] = c.s[(t.row0 + SP * u) * RS + t.w * WS];
+                for (int u = 0; u < R; ++u) v[u] = sld<GEO>(c, t.row0 + SP * u, t.w);
             }
             if constexpr (MUL) load_spec<GEO, RI, T>(c, tau, col, hs);
             task_body<GEO, LINES, RI, INV, SRC, DST, MUL>(c, t, col, v, hs);
@@ -504,7 +574,7 @@ template <typename GEO, bool LINES, int RI>
 __device__ __forceinline__ void fwd_middle(const TileCtx<typename GEO::V>& c) {
     if constexpr (RI < GEO::NR - 1) {
         round_exec<GEO, LINES, RI, false, kFromSmem, kToSmem, false>(c);
-        __syncthreads();
+        round_sync<GEO>();
         fwd_middle<GEO, LINES, RI + 1>(c);
     }
 }
@@ -514,7 +584,7 @@ template <typename GEO, bool LINES, int RI>
 __device__ __forceinline__ void inv_middle(const TileCtx<typename GEO::V>& c) {
     if constexpr (RI >= 1) {
         round_exec<GEO, LINES, RI, true, kFromSmem, kToSmem, false>(c);
-        __syncthreads();
+        round_sync<GEO>();
         inv_middle<GEO, LINES, RI - 1>(c);
     }
 }
@@ -527,7 +597,7 @@ __device__ __forceinline__ void tile_forward(const TileCtx<typename GEO::V>& c) 
         round_exec<GEO, LINES, 0, false, kFromNatural, kToPlaced, false>(c);
     } else {
         round_exec<GEO, LINES, 0, false, kFromNatural, kToSmem, false>(c);
-        __syncthreads();
+        round_sync<GEO>();
         fwd_middle<GEO, LINES, 1>(c);
         round_exec<GEO, LINES, NR - 1, false, kFromSmem, kToPlaced, false>(c);
     }
@@ -541,7 +611,7 @@ __device__ __forceinline__ void tile_inverse(const TileCtx<typename GEO::V>& c) 
         round_exec<GEO, LINES, 0, true, kFromPlaced, kToNatural, false>(c);
     } else {
         round_exec<GEO, LINES, NR - 1, true, kFromPlaced, kToSmem, false>(c);
-        __syncthreads();
+        round_sync<GEO>();
         inv_middle<GEO, LINES, NR - 2>(c);
         round_exec<GEO, LINES, 0, true, kFromSmem, kToNatural, false>(c);
     }
@@ -555,10 +625,10 @@ __device__ __forceinline__ void tile_fused(const TileCtx<typename GEO::V>& c) {
         round_exec<GEO, LINES, 0, false, kFromNatural, kToNatural, true>(c);
     } else {
         round_exec<GEO, LINES, 0, false, kFromNatural, kToSmem, false>(c);
-        __syncthreads();
+        round_sync<GEO>();
         fwd_middle<GEO, LINES, 1>(c);
         round_exec<GEO, LINES, NR - 1, false, kFromSmem, kToSmem, true>(c);
-        __syncthreads();
+        round_sync<GEO>();
         inv_middle<GEO, LINES, NR - 2>(c);
         round_exec<GEO, LINES, 0, true, kFromSmem, kToNatural, false>(c);
     }
@@ -608,6 +678,8 @@ template <typename V> __device__ __forceinline__ void ctx_init(TileCtx<V>& c, co
     c.C = (uint32_t)a.C;
     c.do_scale = a.mode == kFwd && a.scale != 1.0;
     c.scale = (typename Real<V>::T)a.scale;
+    c.wofs = 0;
+    for (int k = 0; k < 4; ++k) c.sk[k] = 0;
 }
 
 // One pass over all tiles, CTAs walking tiles blockIdx.x, +gridDim.x, ...
@@ -671,14 +743,18 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, size
 // two innermost axes in one pass, so a 3-D convolution takes 3 passes and a
 // 2-D one a single launch.
 
-template <typename V, int M1, int M2> struct PlaneShape {
+// K = 1: one CTA per plane.  K > 1: a cluster of K CTAs per plane, CTA k
+// holding plane rows [k n1/K, (k+1) n1/K) (its own lines of axis d-1) and,
+// for axis d-2, transforming columns [k n2/K, (k+1) n2/K) over all rows.
+template <typename V, int M1, int M2, int K> struct PlaneShape {
     static constexpr int ES = sizeof(V);
     static constexpr int P2 = plane_pitch(M1, M2, ES);
-    static constexpr int NT = plane_threads(M1, M2, ES);
-    static constexpr int SMEM = plane_smem_bytes(M1, M2, ES);
-    using G2 = Geo<V, M2, M1, NT, 1, P2, true>;  // axis d-1: rows i2, columns i1
-    using G1 = Geo<V, M1, M2, NT, P2, 1, true>;  // axis d-2: rows i1, columns i2
+    static constexpr int NT = plane_threads(M1, M2, ES, K);
+    static constexpr int SMEM = plane_smem_bytes(M1 / K, M2, ES);
+    using G2 = Geo<V, M2, M1 / K, NT, 1, P2, true, 1>;  // axis d-1: rows i2, columns = local lines
+    using G1 = Geo<V, M1, M2 / K, NT, P2, 1, true, K>;  // axis d-2: rows i1 (split), columns i2
     static_assert(SMEM <= kPlaneSmemMax, "plane too large for one CTA");
+    static_assert(M1 % K == 0 && M2 % K == 0, "the plane must split evenly");
 };
 
 // forward rounds 0..NR-1, the first from global (natural rows), all results in shared memory
@@ -687,7 +763,7 @@ __device__ __forceinline__ void fwd_all_to_smem(const TileCtx<typename GEO::V>& 
     constexpr int NR = GEO::NR;
     round_exec<GEO, LINES, 0, false, kFromNatural, kToSmem, false>(c);
     if constexpr (NR > 1) {
-        __syncthreads();
+        round_sync<GEO>();
         fwd_middle<GEO, LINES, 1>(c);
         round_exec<GEO, LINES, NR - 1, false, kFromSmem, kToSmem, false>(c);
     }
@@ -701,10 +777,10 @@ __device__ __forceinline__ void fused_in_smem(const TileCtx<typename GEO::V>& c)
         round_exec<GEO, false, 0, false, kFromSmem, kToSmem, true>(c);
     } else {
         round_exec<GEO, false, 0, false, kFromSmem, kToSmem, false>(c);
-        __syncthreads();
+        round_sync<GEO>();
         fwd_middle<GEO, false, 1>(c);
         round_exec<GEO, false, NR - 1, false, kFromSmem, kToSmem, true>(c);
-        __syncthreads();
+        round_sync<GEO>();
         inv_middle<GEO, false, NR - 2>(c);
         round_exec<GEO, false, 0, true, kFromSmem, kToSmem, false>(c);
     }
@@ -718,55 +794,78 @@ __device__ __forceinline__ void inv_all_from_smem(const TileCtx<typename GEO::V>
         round_exec<GEO, LINES, 0, true, kFromSmem, kToNatural, false>(c);
     } else {
         round_exec<GEO, LINES, NR - 1, true, kFromSmem, kToSmem, false>(c);
-        __syncthreads();
+        round_sync<GEO>();
         inv_middle<GEO, LINES, NR - 2>(c);
         round_exec<GEO, LINES, 0, true, kFromSmem, kToNatural, false>(c);
     }
 }
 
-template <typename V, int M1, int M2>
-__device__ __forceinline__ void plane_run(const PlaneArgs& pa, uint32_t plane, V* s) {
-    using PS = PlaneShape<V, M1, M2>;
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;\n" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of the same shared-memory location in CTA `rank` of the cluster
+template <typename V> __device__ __forceinline__ uint32_t map_cluster(V* p, unsigned rank) {
+    const uint32_t local = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;\n" : "=r"(out) : "r"(local), "r"(rank));
+    return out;
+}
+
+template <typename V, int M1, int M2, int K>
+__device__ __forceinline__ void plane_run(const PlaneArgs& pa, uint32_t plane, unsigned rank, V* s) {
+    using PS = PlaneShape<V, M1, M2, K>;
     TileCtx<V> c2, c1;
     ctx_init(c2, pa.a2, s);
     c2.t = plane;
-    c2.q0 = plane * (uint32_t)M1;  // lines of this plane
+    c2.q0 = plane * (uint32_t)M1 + rank * (uint32_t)(M1 / K);  // this CTA's lines
     c2.valid = true;
     c2.base = 0;
     c2.j = 0;
     ctx_init(c1, pa.a1, s);
-    c1.t = plane;
+    c1.t = plane * K + rank;  // spectrum slots of this CTA's columns
     c1.q0 = 0;
     c1.valid = true;
     c1.base = 0;
     c1.j = 0;
+    c1.wofs = (int)rank * (M2 / K);
+    if constexpr (K > 1) {
+        for (int k = 0; k < K; ++k) c1.sk[k] = map_cluster(s, (unsigned)k);
+    }
     fwd_all_to_smem<typename PS::G2, true>(c2);
-    __syncthreads();
+    round_sync<typename PS::G1>();
     fused_in_smem<typename PS::G1>(c1);
-    __syncthreads();
+    round_sync<typename PS::G1>();
     inv_all_from_smem<typename PS::G2, true>(c2);
 }
 
-template <typename V, int M1, int M2>
-__global__ void __launch_bounds__(PlaneShape<V, M1, M2>::NT, 1) plane_kernel(const __grid_constant__ PlaneArgs pa) {
+template <typename V, int M1, int M2, int K>
+__global__ void __launch_bounds__(PlaneShape<V, M1, M2, K>::NT, plane_min_blocks(K))
+    plane_kernel(const __grid_constant__ PlaneArgs pa) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_launch_dependents();
     pdl_wait();
     V* s = reinterpret_cast<V*>(smem_raw);
-    for (uint32_t p = blockIdx.x; p < (uint32_t)pa.planes; p += gridDim.x) {
-        plane_run<V, M1, M2>(pa, p, s);
+    const unsigned rank = K > 1 ? cluster_ctarank() : 0u;
+    if constexpr (K > 1) cluster_sync_all();  // every CTA of the cluster is running
+    for (uint32_t p = blockIdx.x / K; p < (uint32_t)pa.planes; p += gridDim.x / K) {
+        plane_run<V, M1, M2, K>(pa, p, rank, s);
         __syncthreads();
     }
 }
 
 // batched form: planes of list[0..n) numbered consecutively (tile_start as in pass_multi_kernel)
-template <typename V, int M1, int M2>
-__global__ void __launch_bounds__(PlaneShape<V, M1, M2>::NT, 1)
+template <typename V, int M1, int M2, int K>
+__global__ void __launch_bounds__(PlaneShape<V, M1, M2, K>::NT, plane_min_blocks(K))
     plane_multi_kernel(const PlaneArgs* __restrict__ list, const uint32_t* __restrict__ start, int n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* s = reinterpret_cast<V*>(smem_raw);
+    const unsigned rank = K > 1 ? cluster_ctarank() : 0u;
+    if constexpr (K > 1) cluster_sync_all();
     const uint32_t total = __ldg(start + n);
-    for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+    for (uint32_t t = blockIdx.x / K; t < total; t += gridDim.x / K) {
         int lo = 0, hi = n - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -775,7 +874,7 @@ __global__ void __launch_bounds__(PlaneShape<V, M1, M2>::NT, 1)
             else
                 hi = mid - 1;
         }
-        plane_run<V, M1, M2>(list[lo], t - __ldg(start + lo), s);
+        plane_run<V, M1, M2, K>(list[lo], t - __ldg(start + lo), rank, s);
         __syncthreads();
     }
 }

@@ -44,8 +44,10 @@ cudaError_t launch_conv(int esize, int M, ConvArgs& args, int grid, cudaStream_t
 int pass_kernel_supported(int M, int esize);
 // plane pass (kern_plane.cu): whole planes of the last two axes in one CTA
 int plane_supported(int M1, int M2, int esize);
-cudaError_t launch_plane(int esize, int M1, int M2, const PlaneArgs& pa, cudaStream_t s);
-cudaError_t launch_plane_multi(int esize, int M1, int M2, const PlaneArgs* list, const uint32_t* starts, int n,
+int plane_supported_k(int M1, int M2, int esize, int K);
+int plane_cluster(int M1, int M2, int esize, int64_t planes, int device);  // CTAs per plane (0: none)
+cudaError_t launch_plane(int esize, int M1, int M2, int K, const PlaneArgs& pa, cudaStream_t s);
+cudaError_t launch_plane_multi(int esize, int M1, int M2, int K, const PlaneArgs* list, const uint32_t* starts, int n,
                                int64_t total, cudaStream_t s);
 PlaneArgs make_plane(pac_plan p, const void* src, void* dst);
 
@@ -96,6 +98,7 @@ struct pac_plan_s {
     int uniform_m = 0;  // group size shared by every pass (0: sizes differ)
     bool plane = false;  // the last two axes run as one plane pass (groups plane_g1, plane_g1 + 1)
     int plane_g1 = -1;
+    int plane_k = 1;     // CTAs (a thread-block cluster) per plane
     bool single_launch = false;  // run a pass sequence as one cooperative launch
     int device = 0;
     std::vector<std::vector<int>> stages;          // per axis, DIF order

@@ -50,6 +50,7 @@ struct SpecOrder {
     const int* rowmap;  // [M] in-CTA row of global row g (plane: of axis d-2)
     uint32_t M2;        // plane order when > 0: n2
     const int* rowmap2; // plane: [n2] in-CTA row of axis d-1
+    uint32_t K;         // plane: CTAs per plane (columns of axis d-1 split K ways)
 };
 
 constexpr int kMaxPasses = 12;

@@ -333,6 +333,10 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
             plane_supported(pl->groups[G - 2].M, pl->groups[G - 1].M, pl->esize)) {
             pl->plane = true;
             pl->plane_g1 = G - 2;
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+            pl->plane_k = plane_cluster(pl->groups[G - 2].M, pl->groups[G - 1].M, pl->esize,
+                                        pl->N / ((int64_t)pl->groups[G - 2].M * pl->groups[G - 1].M), dev);
         }
     }
     pl->uniform_m = 0;
@@ -472,12 +476,14 @@ SpecOrder spec_order_of(pac_plan p) {
         o.W = (uint32_t)f.M;
         o.C = (uint32_t)g1.C;
         o.R = (uint32_t)round_radix(g1.M, p->esize, round_count(g1.M, p->esize) - 1);
-        o.tasks = o.W * o.M / o.R;
+        o.K = (uint32_t)p->plane_k;
+        o.tasks = o.W / o.K * o.M / o.R;
         o.rowmap = reinterpret_cast<const int*>(t + g1.off_rowmap);
         o.M2 = (uint32_t)f.M;
         o.rowmap2 = reinterpret_cast<const int*>(t + f.off_rowmap);
         return o;
     }
+    o.K = 1;
     o.M = (uint32_t)f.M;
     o.W = (uint32_t)tile_w(f.M, p->esize);
     o.C = (uint32_t)f.C;
@@ -525,7 +531,7 @@ PlaneArgs make_plane(pac_plan p, const void* src, void* dst) {
 static int run_plane(pac_plan p, const void* src, void* dst, cudaStream_t s) {
     const PlaneArgs pa = make_plane(p, src, dst);
     timer_mark(s, 6, true);
-    cudaError_t e = launch_plane(p->esize, p->groups[p->plane_g1].M, p->groups[p->plane_g1 + 1].M, pa, s);
+    cudaError_t e = launch_plane(p->esize, p->groups[p->plane_g1].M, p->groups[p->plane_g1 + 1].M, p->plane_k, pa, s);
     timer_mark(s, 6, false);
     if (e != cudaSuccess) return cuda_fail(e, "plane kernel launch");
     return PAC_OK;
