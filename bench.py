@@ -50,10 +50,12 @@ def parse_args(argv=None):
     ap.add_argument("--quick", action="store_true", help="main leg only (for profiler runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
-    ap.add_argument("--legs", default="batched,served",
-                    help="extra legs after the main one: batched (4096 mixed convolutions in one call), "
+    ap.add_argument("--legs", default="configs,batched,served",
+                    help="extra legs after the main one: configs (every workload shape, dtype and radix, "
+                         "with its permuted form and cuFFT), batched (4096 mixed convolutions in one call), "
                          "served (Poisson request stream through the queue)")
     ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default pass schedules)")
     ap.add_argument("--flush-mb", type=int, default=FLUSH_BYTES >> 20,
                     help="L2 flush buffer written before each step (0: none, for profiler runs only)")
     return ap.parse_args(argv)
@@ -276,6 +278,75 @@ def reference_arm(a):
     return line
 
 
+def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
+    """Every single-convolution workload: 1-D 2^10 FP64 radix 2; 3-D 128^3
+    radix 2/4/8 FP32 and FP64; 2-D 2187^2 radix 3 and 3125^2 radix 5, FP32
+    and FP64.  Each: GB/s of 3 N S, the permuted form and cuFFT on the same
+    GPU, launches per convolution and the pass schedule (autotuned unless
+    --no-tune).  Inputs of each workload's recipe, generated on the device
+    from a seed (x: re, im N(0,1) or U[-1,1]; the workload's filter)."""
+    out = []
+    cases = [(pin.c1(), "1-D n=2^10, radix 2, complex FP64")]
+    for dt in ("c64", "c128"):
+        for r in (2, 4, 8):
+            cases.append((pin.c2(r, dt), f"3-D 128^3, radix {r}, complex {'FP32' if dt == 'c64' else 'FP64'}"))
+    for dt in ("c64", "c128"):
+        for r in (3, 5):
+            c = pin.c3(r, dt)
+            cases.append((c, f"2-D {c.dims[0]}^2, radix {r}, complex {'FP32' if dt == 'c64' else 'FP64'}"))
+    sh = stream.cuda_stream
+    for c, name in cases:
+        N, S = c.n_total, c.elem_bytes
+        B = 3 * N * S
+        real = torch.float32 if c.dtype == "c64" else torch.float64
+        g = torch.Generator(device=dev)
+        g.manual_seed(c.seed)
+        if c.x_kind == "normal":
+            x = torch.view_as_complex(torch.randn(*c.dims, 2, generator=g, device=dev, dtype=real))
+        else:
+            x = torch.view_as_complex(torch.rand(*c.dims, 2, generator=g, device=dev, dtype=real) * 2 - 1)
+        if c.h_kind == "uniform":
+            h = torch.view_as_complex(torch.rand(*c.dims, 2, generator=g, device=dev, dtype=real) * 2 - 1)
+        else:
+            fs = pin.gaussian_factors(c.dims, c.h_param) if c.h_kind == "gauss" else \
+                pin.exponential_factors(c.dims, c.h_param)
+            h = torch.from_numpy(fs[0]).to(dev)
+            for f in fs[1:]:
+                h = torch.outer(h.reshape(-1), torch.from_numpy(f).to(dev)).reshape(*h.shape, f.shape[0])
+            h = h.to(x.dtype).contiguous()
+        y = torch.empty_like(x)
+        tuned_us = None
+        if not a.no_tune:
+            tuned_us = pac.pac_tune(c.dims, c.radix, c.dtype, 5)
+        plan = pac.Plan(c.dims, c.radix, c.dtype)
+        plan.filter_spectrum(h)
+        steps = 30 if N * S < (64 << 20) else 10
+        ms = time_steps(torch, lambda: pac.pac_convolve(plan.handle, x, y, sh), steps, 3, flush, stream)
+        msp = time_steps(torch, lambda: pac.pac_convolve_permuted(plan.handle, x, y, sh), steps, 3, flush, stream)
+        Hn = torch.fft.fftn(h)
+        yc = torch.empty_like(x)
+
+        def cufft_step():
+            torch.fft.ifftn(torch.fft.fftn(x) * Hn, out=yc)
+
+        msc = time_steps(torch, cufft_step, steps, 3, flush, stream)
+        pac.pac_convolve(plan.handle, x, y, sh)
+        stream.synchronize()
+        diff = float(torch.linalg.vector_norm(y - yc) / torch.linalg.vector_norm(yc))
+        t, tp, tc = (statistics.median(v) for v in (ms, msp, msc))
+        out.append({"workload": name, "dims": list(c.dims), "radix": c.radix, "dtype": c.dtype,
+                    "ms": t, "GBps": B / (t * 1e-3) / 1e9, "pct_hbm_roofline": B / (t * 1e-3) / 1e9 / peak,
+                    "permuted_GBps": B / (tp * 1e-3) / 1e9, "speedup_vs_permuted": tp / t,
+                    "cufft_GBps": B / (tc * 1e-3) / 1e9, "speedup_vs_cufft": tc / t,
+                    "launches": plan.query(pac.Q_LAUNCHES_CONVOLVE), "groups": plan.query(pac.Q_GROUPS),
+                    "plane_ctas": plan.query(pac.Q_PLANE), "group_cap": plan.query(pac.Q_GROUP_CAP),
+                    "tuned_us": tuned_us, "rel_l2_vs_cufft": diff})
+        plan.close()
+        del x, y, h, yc, Hn
+        torch.cuda.empty_cache()
+    return out
+
+
 def batched_leg(a, torch, pac, pin, dev, stream, flush):
     """4096 independent complex FP32 convolutions, sizes from 20 classes
     (1-D 2^8..2^16 and 3^5..3^10, 2-D (2^6..2^10)^2), 64 filter ids, in one
@@ -288,6 +359,9 @@ def batched_leg(a, torch, pac, pin, dev, stream, flush):
     plans, handles, xs, ys = {}, [], [], []
     total = 0
     t_setup = time.perf_counter()
+    if not a.no_tune:  # one schedule per size class (20 classes)
+        for dims, radix in pin.C4_CLASSES:
+            pac.pac_tune(dims, radix, "c64", 3)
     for c in insts:
         key = (c.dims, c.radix, c.h_seed)
         if key not in plans:
@@ -317,7 +391,8 @@ def batched_leg(a, torch, pac, pin, dev, stream, flush):
            "value": total / (t * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": t, "bytes_per_step": total,
            "launches_per_step": launches, "plans": len(plans),
            "one_call_each": {"value": total / (t1 * 1e-3) / 1e9, "ms_per_step": t1},
-           "setup_s": setup_s, "inputs": "device-generated, seeded (torch Philox)"}
+           "setup_s": setup_s, "inputs": "device-generated, seeded (torch Philox)",
+           "schedules": "autotuned per size class" if not a.no_tune else "default"}
     for p in plans.values():
         p.close()
     del xs, ys
@@ -443,6 +518,9 @@ def main(argv=None):
         if a.flush_mb > 0:
             flush_buf.fill_(1)
 
+    tuned_us = None
+    if not a.quick and not a.no_tune:  # pass schedule picked by the autotuner (setup, not timed)
+        tuned_us = pac.pac_tune(c.dims, c.radix, c.dtype, 5)
     plan = pac.Plan(c.dims, c.radix, c.dtype)
     plan.filter_spectrum(h)
     launches = plan.query(pac.Q_LAUNCHES_CONVOLVE)
@@ -466,6 +544,9 @@ def main(argv=None):
             "dtype": "f32" if a.dtype == "c64" else "f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "dims": list(c.dims), "radix": a.radix,
                        "stages_per_axis": plan.stages(0), "bytes_per_step": B,
+                       "schedule": {"passes": launches, "groups": plan.query(pac.Q_GROUPS),
+                                    "plane_ctas": plan.query(pac.Q_PLANE), "group_cap": plan.query(pac.Q_GROUP_CAP),
+                                    "autotuned": tuned_us is not None},
                        "l2": (f"flushed before every step ({a.flush_mb} MiB write, outside the timed events)"
                               if a.flush_mb > 0 else "not flushed (profiling run)"),
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -544,6 +625,8 @@ def main(argv=None):
     if sampler:
         sampler.stop()
         line["clocks"] = sampler.summary(t_wall0, t_wall1)
+    if not a.quick and "configs" in a.legs:
+        line["configs"] = configs_leg(a, torch, pac, pin, dev, stream, flush, peak)
     if not a.quick and "batched" in a.legs:
         line["batched"] = batched_leg(a, torch, pac, pin, dev, stream, flush)
     if not a.quick and "served" in a.legs:

@@ -222,6 +222,19 @@ int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, vo
  */
 int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void* y_dev, void* stream);
 
+/*
+ * Autotuner: time the candidate pass schedules of this problem on the current
+ * device (the largest group per pass, i.e. how many DIF stages one pass fuses,
+ * from the largest a CTA holds down to small groups; and, in 2-D/3-D, the
+ * plane pass on or off), `reps` convolutions each after a warm-up, and keep
+ * the fastest.  Plans created afterwards with the same (dims, radix, dtype)
+ * use it.  With PAC_TUNE_FILE set in the environment, tuned schedules are
+ * read from that file on first use and appended to it.  Allocates and frees
+ * device memory (twice the problem) and synchronises the device.
+ * best_us (may be NULL) receives the winner's median time per convolution.
+ */
+int pac_tune(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int reps, double* best_us);
+
 /* Plan facts for benches and tests: see PAC_Q_* keys. */
 int pac_plan_query(pac_plan p, int key, int64_t* value);
 enum {
@@ -233,8 +246,11 @@ enum {
     PAC_Q_LAUNCHES_FORWARD = 5,   /* kernel launches per pac_forward_unordered */
     PAC_Q_DEVICE_BYTES = 6,       /* device memory the plan owns */
     PAC_Q_HAS_SPECTRUM = 7,
-    PAC_Q_DEVICE_ERROR = 8        /* synchronises; returns and clears the device error word
+    PAC_Q_DEVICE_ERROR = 8,       /* synchronises; returns and clears the device error word
                                      (1: a bounded grid-barrier wait gave up) */
+    PAC_Q_GROUPS = 9,             /* stage groups (one pass each) over all axes */
+    PAC_Q_PLANE = 10,             /* CTAs per plane of the plane pass, 0 when the plan has none */
+    PAC_Q_GROUP_CAP = 11          /* the schedule's group-exponent cap (0: none) */
 };
 
 /* Host-only helpers (no device needed): the stage list and reversal table rules. */

@@ -37,7 +37,7 @@ class Status(enum.IntEnum):
 
 
 Q_NDIM, Q_N_TOTAL, Q_ELEM_BYTES, Q_LAUNCHES_CONVOLVE, Q_LAUNCHES_PERMUTED, Q_LAUNCHES_FORWARD, \
-    Q_DEVICE_BYTES, Q_HAS_SPECTRUM, Q_DEVICE_ERROR = range(9)
+    Q_DEVICE_BYTES, Q_HAS_SPECTRUM, Q_DEVICE_ERROR, Q_GROUPS, Q_PLANE, Q_GROUP_CAP = range(12)
 
 # every entry point of include/pac.h: name -> (restype, argtypes)
 _vp, _i64, _i32, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
@@ -61,6 +61,7 @@ _SIGS = {
     "pac_convolve_permuted": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_convolve_permuted_noalloc": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_plan_query": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
+    "pac_tune": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, ctypes.POINTER(ctypes.c_double)]),
     "pac_convolve_timed": (_i32, [_vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "pac_stage_list": (_i32, [_i64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -229,6 +230,15 @@ def pac_convolve_timed(plan: int, which: int, x_dev, y_dev, stream=None, max_lau
     _check(load().pac_convolve_timed(plan, int(which), _ptr(x_dev), _ptr(y_dev), _stream(stream), max_launches,
                                      ms, ids, ctypes.byref(n)))
     return [(KERNEL_NAMES.get(ids[i], str(ids[i])), float(ms[i])) for i in range(n.value)]
+
+
+def pac_tune(dims, radix: int, dtype: str = "c64", reps: int = 5) -> float:
+    """Autotune the pass schedule of this problem; returns the winner's time per convolution (us)."""
+    vals = [int(v) for v in dims]
+    d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
+    us = ctypes.c_double(0.0)
+    _check(load().pac_tune(len(vals), d, int(radix), C64 if dtype == "c64" else C128, int(reps), ctypes.byref(us)))
+    return us.value
 
 
 def pac_plan_query(plan: int, key: int) -> int:

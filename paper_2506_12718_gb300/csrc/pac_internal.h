@@ -30,6 +30,16 @@ struct GroupPlan {
     size_t off_twi = 0, off_lo = 0, off_hi = 0, off_rowmap = 0, off_freq = 0, off_r2g = 0, off_r2f = 0;  // in tables
 };
 
+// A pass schedule: the largest group exponent per pass (0: the largest a CTA
+// takes) and whether the last two axes may run as a plane pass.
+struct Schedule {
+    int cap = 0;
+    bool plane = true;
+};
+int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out);
+// the tuned schedule for a problem, if pac_tune (or the tuning file) has one (tune.cu)
+void tuned_schedule(int ndim, const int64_t* dims, int radix, pac_dtype dtype, Schedule* out);
+
 void set_error(const char* fmt, ...);
 int fail(int status, const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
@@ -99,6 +109,7 @@ struct pac_plan_s {
     bool plane = false;  // the last two axes run as one plane pass (groups plane_g1, plane_g1 + 1)
     int plane_g1 = -1;
     int plane_k = 1;     // CTAs (a thread-block cluster) per plane
+    pac::Schedule schedule;
     bool single_launch = false;  // run a pass sequence as one cooperative launch
     int device = 0;
     std::vector<std::vector<int>> stages;          // per axis, DIF order

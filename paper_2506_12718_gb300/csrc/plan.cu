@@ -134,8 +134,8 @@ static void reverse_table(const int* st, int T, int64_t* p2f) {
 }
 
 // Split an axis' stage list into consecutive groups with product <= the
-// largest column one CTA handles, balanced in size.
-static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st, int p, int esize) {
+// largest column one CTA handles (or p^cap, a schedule's cap), balanced in size.
+static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st, int p, int esize, int cap) {
     std::vector<std::pair<int, int>> out;
     const int T = (int)st.size();
     if (T == 0) return out;
@@ -145,7 +145,9 @@ static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st,
         ex[i] = exact_log(st[i], p);
         etot += ex[i];
     }
-    const int emax = exact_log(group_mmax(p, esize), p);
+    int emax = exact_log(group_mmax(p, esize), p);
+    if (cap > 0 && cap < emax) emax = cap;  // a schedule's smaller group cap (more, smaller passes)
+    for (int i = 0; i < T; ++i) emax = std::max(emax, ex[i]);  // a single stage is never split
     int ngroups = (etot + emax - 1) / emax;
     int i = 0, erem = etot;
     for (int gi = 0; gi < ngroups && i < T; ++gi) {
@@ -229,6 +231,14 @@ static void free_plan(pac_plan p) {
 }
 
 extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, pac_plan* out) {
+    Schedule sch;
+    tuned_schedule(ndim, dims, radix, dtype, &sch);
+    return plan_build(ndim, dims, radix, dtype, sch, out);
+}
+
+namespace pac {
+
+int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out) {
     if (!out) return fail(PAC_ERR_ARG, "null out");
     *out = nullptr;
     if (ndim < 1 || ndim > 3 || !dims) return fail(PAC_ERR_ARG, "ndim must be 1, 2 or 3");
@@ -273,7 +283,7 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
         int64_t inner = 1;
         for (int b = a + 1; b < ndim; ++b) inner *= dims[b];
         int64_t Lcur = dims[a];
-        for (auto [first, cnt] : split_groups(pl->stages[a], p, pl->esize)) {
+        for (auto [first, cnt] : split_groups(pl->stages[a], p, pl->esize, sch.cap)) {
             GroupPlan g;
             g.axis = a;
             g.first_stage = first;
@@ -322,7 +332,7 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
     // plane pass: the last two axes each one group, a supported plane shape;
     // PAC_PLANE=0 in the environment keeps per-axis passes instead
     const char* pe = std::getenv("PAC_PLANE");
-    if (ndim >= 2 && !(pe && pe[0] == '0')) {
+    if (ndim >= 2 && sch.plane && !(pe && pe[0] == '0')) {
         int g_last = 0, g_prev = 0;
         for (const GroupPlan& g : pl->groups) {
             if (g.axis == ndim - 1) ++g_last;
@@ -418,9 +428,12 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
                                               : cuda_fail(e, "cudaMalloc(spectrum)");
     }
     pl->device_bytes = pl->tables_bytes + (size_t)pl->spec_elems * pl->esize;
+    pl->schedule = sch;
     *out = pl;
     return PAC_OK;
 }
+
+}  // namespace pac
 
 extern "C" int pac_plan_destroy(pac_plan p) {
     if (!p) return fail(PAC_ERR_ARG, "null plan");
@@ -880,6 +893,9 @@ extern "C" int pac_plan_query(pac_plan p, int key, int64_t* value) {
         }
         case PAC_Q_DEVICE_BYTES: *value = (int64_t)p->device_bytes; break;
         case PAC_Q_HAS_SPECTRUM: *value = p->has_spec ? 1 : 0; break;
+        case PAC_Q_GROUPS: *value = G; break;
+        case PAC_Q_PLANE: *value = p->plane ? p->plane_k : 0; break;
+        case PAC_Q_GROUP_CAP: *value = p->schedule.cap; break;
         default: return fail(PAC_ERR_ARG, "unknown query key %d", key);
     }
     return PAC_OK;

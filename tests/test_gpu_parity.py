@@ -377,6 +377,45 @@ def test_convolve_many_batched_workload_sample():
             p.close()
 
 
+@pytest.mark.parametrize("dims,radix,dtype", [((4096,), 2, "c64"), ((243, 243), 3, "c64"), ((32, 64, 64), 4, "c128"),
+                                             ((65536,), 4, "c64")])
+def test_autotuned_schedule_matches_oracle(dims, radix, dtype):
+    """pac_tune times the candidate pass schedules and keeps the fastest; a
+    plan created afterwards uses it and still matches the oracle."""
+    pac = pac_mod()
+    us = pac.pac_tune(dims, radix, dtype, reps=3)
+    assert us > 0
+    fs, h, x = separable_case(dims, dtype, seed=77)
+    plan = pac.Plan(dims, radix, dtype)
+    try:
+        cap = plan.query(pac.Q_GROUP_CAP)
+        assert cap >= 1  # a tuned schedule always carries its cap
+        assert plan.query(pac.Q_GROUPS) >= len(dims)
+    finally:
+        plan.close()
+    y = gpu_conv(dims, radix, dtype, h, x)
+    check(y, oracle.conv_separable(fs, x), dtype, int(np.prod(dims)), f"tuned {dims}")
+
+
+def test_tune_file_round_trip(tmp_path):
+    """With PAC_TUNE_FILE set, a schedule tuned in one process is used by
+    plans of a later process."""
+    import subprocess
+    import sys
+    path = tmp_path / "tune.txt"
+    env = dict(os.environ, PAC_TUNE_FILE=str(path))
+    code1 = ("import paper_2506_12718_gb300 as pac; pac.load(); import torch; torch.cuda.init(); "
+             "print(pac.pac_tune((2187, 2187), 3, 'c64', 2))")
+    subprocess.run([sys.executable, "-c", code1], env=env, check=True, cwd=os.path.dirname(os.path.dirname(__file__)))
+    line = path.read_text().split()
+    assert len(line) == 9 and line[0] == "2" and line[1] == "2187"
+    code2 = ("import paper_2506_12718_gb300 as pac; pac.load(); import torch; torch.cuda.init(); "
+             "p = pac.Plan((2187, 2187), 3, 'c64'); print(p.query(pac.Q_GROUP_CAP)); p.close()")
+    out = subprocess.run([sys.executable, "-c", code2], env=env, check=True, capture_output=True, text=True,
+                         cwd=os.path.dirname(os.path.dirname(__file__)))
+    assert int(out.stdout.strip().splitlines()[-1]) == int(line[6])
+
+
 def _queue_setup(n_req=24):
     pac = pac_mod()
     shapes = [((4096,), 2), ((81, 81), 3), ((32, 32, 32), 2), ((125, 25), 5), ((1024,), 4)]
