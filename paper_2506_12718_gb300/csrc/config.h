@@ -46,38 +46,49 @@ constexpr int tile_w(int m, int esize) {
 }
 
 // Row padding of the shared-memory exchange buffer, in elements.  Chosen per
-// group size by counting bank wavefronts of every round's access pattern
-// (column-fastest and in-line-fastest task orders) over pads 0..16 and taking
-// the smallest pad with the fewest wavefronts.
-constexpr int tile_pad(int m, int esize) {
+// group size and layout by counting the bank wavefronts of every round's
+// access pattern (8-byte accesses served per half-warp, 16-byte per quarter
+// warp) over pads 0..32 and taking the smallest pad with the fewest.  Rows
+// case (column-fastest tasks): no padding.  Lines case: the tasks that touch
+// global memory run in-line-fastest order when the tile is at least 8 lines
+// wide, which wants the padding below; narrower tiles keep column-fastest
+// order and no padding.
+constexpr int tile_pad(int m, int esize, bool lines) {
+    if (!lines || tile_w(m, esize) < 8) return 0;
     if (esize == 8) {
         switch (m) {
             case 32: return 4;
-            case 64: case 128: case 2187: case 625: case 3125: case 4096: return 2;
+            case 64: case 128: return 2;
             case 81: case 243: return 9;
-            case 729: return 10;
             case 125: return 13;
-            case 2: case 4: case 8: case 16: case 3: case 9: case 27: case 5: case 25: return 0;
-            default: return 1;
+            case 256: case 512: return 1;
+            default: return 0;
         }
     }
     switch (m) {
+        case 32: return 2;
         case 27: case 243: return 3;
-        case 729: case 125: return 5;
-        case 625: return 7;
-        case 2: case 4: case 8: case 16: case 32: case 3: case 9: case 5: case 25: return 0;
-        default: return 1;
+        case 125: return 5;
+        case 64: case 128: case 256: case 81: return 1;
+        default: return 0;
     }
 }
 // Row pitch of the exchange buffer in elements.
-constexpr int tile_pitch(int m, int esize) { return tile_w(m, esize) + tile_pad(m, esize); }
-constexpr int tile_elems(int m, int esize) { return m * tile_pitch(m, esize); }
+constexpr int tile_pitch(int m, int esize, bool lines) { return tile_w(m, esize) + tile_pad(m, esize, lines); }
+constexpr int tile_elems(int m, int esize, bool lines) { return m * tile_pitch(m, esize, lines); }
+// tasks of a lines-case round that reads or writes global memory run in-line-fastest order
+constexpr bool lines_jfast(int m, int esize) { return tile_w(m, esize) >= 8; }
 
 // Threads per CTA: one per task of the first (largest) round, rounded up to
 // whole warps, within [64, 512].  A multiple of 32, hence of the tile width,
 // so in the rows case every task of a thread has the same column.
+// Large base-3 FP32 groups (27-point rounds) run 256 threads at 128
+// registers so that two CTAs share an SM (measured 2187^2: 121 -> 108 us);
+// for base 2 and 5 the 512-thread form measured faster.
+constexpr bool two_ctas_per_sm(int m, int esize) { return esize == 8 && base_of(m) == 3 && m >= 729; }
 constexpr int pass_threads(int m, int esize) {
-    return clampi(((tile_w(m, esize) * (m / round_radix(m, esize, 0)) + 31) / 32) * 32, 64, 512);
+    return clampi(((tile_w(m, esize) * (m / round_radix(m, esize, 0)) + 31) / 32) * 32, 64,
+                  two_ctas_per_sm(m, esize) ? 256 : 512);
 }
 
 // Register budget per thread the kernel is compiled for: enough for the
@@ -86,7 +97,7 @@ constexpr int pass_threads(int m, int esize) {
 constexpr int max_round_radix(int m, int esize) { return round_radix(m, esize, 0); }  // rounds are sorted, largest first
 constexpr int reg_target(int m, int esize) {
     return esize == 8
-               ? (max_round_radix(m, esize) >= 25 ? 168
+               ? (max_round_radix(m, esize) >= 25 ? (two_ctas_per_sm(m, esize) ? 128 : 168)
                   : (round_count(m, esize) >= 2 && round_radix(m, esize, 1) >= 16 ? 96 : 64))
                : (max_round_radix(m, esize) >= 25 ? 255
                   : (round_count(m, esize) >= 2 && round_radix(m, esize, 1) >= 16 ? 168 : 128));

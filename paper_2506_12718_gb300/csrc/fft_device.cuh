@@ -196,10 +196,10 @@ template <int M, int ES> struct RoundGeom<M, ES, -1> {
     static constexpr int R = 1, S = M * 1, SP = M;
 };
 
-template <typename V, int M> struct Shape {
+template <typename V, int M, bool LINES = false> struct Shape {
     static constexpr int ES = sizeof(V);
     static constexpr int W = tile_w(M, ES);
-    static constexpr int P = tile_pitch(M, ES);
+    static constexpr int P = tile_pitch(M, ES, LINES);
     static constexpr int NR = round_count(M, ES);
     static constexpr int NT = pass_threads(M, ES);
     static constexpr int TILE = M * P;
@@ -222,8 +222,8 @@ template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int 
 };
 // the pass kernels' geometry: a tile of W columns, buffer [row][w] of pitch
 // P; several CTAs per SM hide latency, so registers are not spent on prefetch
-template <typename V, int M>
-using PassGeo = Geo<V, M, Shape<V, M>::W, Shape<V, M>::NT, Shape<V, M>::P, 1, false>;
+template <typename V, int M, bool LINES>
+using PassGeo = Geo<V, M, Shape<V, M, LINES>::W, Shape<V, M, LINES>::NT, Shape<V, M, LINES>::P, 1, false>;
 
 // Task tau of round RI: column w of the tile, offset jp inside its block of
 // S rows, first row row0 = block * S + jp; the task transforms rows
@@ -507,7 +507,7 @@ __device__ __forceinline__ void round_exec(const TileCtx<typename GEO::V>& c) {
     constexpr int M = GEO::M;
     using G = RoundGeom<M, GEO::ES, RI>;
     constexpr int R = G::R, SP = G::SP;
-    constexpr bool JFAST = LINES && !MUL && (SRC == kFromNatural || DST == kToNatural);
+    constexpr bool JFAST = LINES && !MUL && (SRC == kFromNatural || DST == kToNatural) && GEO::W >= 8;
     using T = Task<M, GEO::ES, GEO::W, RI, JFAST>;
     static_assert(!MUL || SP == 1, "the product is taken after the last forward round");
     constexpr bool GSRC = SRC != kFromSmem;
@@ -661,7 +661,7 @@ __device__ __forceinline__ void tile_setup(TileCtx<V>& c, const PassArgs& a, uin
 
 template <typename V, int M, bool LINES>
 __device__ __forceinline__ void tile_run(const TileCtx<V>& c, int mode) {
-    using GEO = PassGeo<V, M>;
+    using GEO = PassGeo<V, M, LINES>;
     if (mode == kFwd)
         tile_forward<GEO, LINES>(c);
     else if (mode == kFused)
@@ -695,7 +695,9 @@ __device__ __forceinline__ void run_phase(const PassArgs& a, V* s) {
     }
 }
 
-template <typename V, int M> constexpr int pass_smem_bytes(bool) { return Shape<V, M>::TILE * (int)sizeof(V); }
+template <typename V, int M> constexpr int pass_smem_bytes(bool lines) {
+    return (lines ? Shape<V, M, true>::TILE : Shape<V, M, false>::TILE) * (int)sizeof(V);
+}
 
 // Generic pass kernel: one pass of a convolution (see run_phase).
 template <typename V, int M, bool LINES>
