@@ -286,6 +286,10 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
     --no-tune).  Inputs of each workload's recipe, generated on the device
     from a seed (x: re, im N(0,1) or U[-1,1]; the workload's filter)."""
     out = []
+    fma_peak = {dt: pac.pac_measure_fma_peak(dt) for dt in ("c64", "c128")}
+    # algorithmic flops per convolution: 2 c_r N log2 N + 6 N, c_r = 5, 4.25, 4.08 for
+    # radix 2, 4, 8 (the paper's per-transform counts); 5.9 for radix 3 and 5 (estimates)
+    c_r = {2: 5.0, 4: 4.25, 8: 4.08, 3: 5.9, 5: 5.9}
     cases = [(pin.c1(), "1-D n=2^10, radix 2, complex FP64")]
     for dt in ("c64", "c128"):
         for r in (2, 4, 8):
@@ -341,6 +345,11 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
                     "launches": plan.query(pac.Q_LAUNCHES_CONVOLVE), "groups": plan.query(pac.Q_GROUPS),
                     "plane_ctas": plan.query(pac.Q_PLANE), "group_cap": plan.query(pac.Q_GROUP_CAP),
                     "tuned_us": tuned_us, "rel_l2_vs_cufft": diff})
+        flops = 2 * c_r[c.radix] * N * math.log2(N) + 6 * N
+        out[-1]["alu"] = {"flops_per_conv": flops, "achieved_gflops": flops / (t * 1e-3) / 1e9,
+                          "peak_gflops": fma_peak[c.dtype],
+                          "frac": flops / (t * 1e-3) / 1e9 / fma_peak[c.dtype],
+                          "peak_kind": "measured FMA probe (pac_measure_fma_peak)"}
         plan.close()
         del x, y, h, yc, Hn
         torch.cuda.empty_cache()
@@ -436,6 +445,10 @@ def served_leg(a, torch, pac, pin, dev):
             xbuf[sk] = torch.view_as_complex(torch.randn(*c.dims, 2, generator=g, device=dev, dtype=real))
             ybuf[sk] = [torch.empty_like(xbuf[sk]) for _ in range(K)]
             rr[sk] = 0
+    # warm-up: every plan once, outside the timed stream (first-use costs of
+    # its kernels and streams are not part of a served request's latency)
+    for (dims, radix, dtype, fid), p in plans.items():
+        pac.pac_convolve(p.handle, xbuf[(dims, dtype)], ybuf[(dims, dtype)][0])
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
     q = pac.pac_queue_create(budget, max_inflight)
@@ -452,10 +465,13 @@ def served_leg(a, torch, pac, pin, dev):
         nbytes += 3 * c.n_total * c.elem_bytes
     pac.pac_queue_drain(q, 600000)
     t_end = time.perf_counter()
-    lats = []
-    for tk in tickets:
+    lats, by_class = [], {}
+    for tk, r in zip(tickets, reqs):
         st, lat = pac.pac_poll(q, tk)
         lats.append(lat)
+        small = 2 * r.conv.n_total * r.conv.elem_bytes <= (8 << 20)  # the queue's small-request class
+        by_class.setdefault(f"{'small' if small else 'large'} {'FP32' if r.conv.dtype == 'c64' else 'FP64'}",
+                            []).append(lat)
     pac.pac_queue_destroy(q)
     for p in plans.values():
         p.close()
@@ -465,11 +481,18 @@ def served_leg(a, torch, pac, pin, dev):
         return lats[min(len(lats) - 1, int(math.ceil(p / 100 * len(lats))) - 1)]
 
     span = t_end - t0
+
+    def pcts(v):
+        v = sorted(v)
+        return {"n": len(v), "p50_us": v[min(len(v) - 1, max(0, math.ceil(0.5 * len(v)) - 1))],
+                "p99_us": v[min(len(v) - 1, max(0, math.ceil(0.99 * len(v)) - 1))]}
     out = {"workload": f"Poisson {len(reqs) / a.serve_seconds:.0f} req/s for {a.serve_seconds:g} s: 1-D/2-D/3-D, "
                        "radix 2/3, 70% FP32 / 30% FP64, 32 resident filters",
            "requests": len(reqs), "p50_us": pct(50), "p99_us": pct(99), "mean_us": sum(lats) / len(lats),
            "value": nbytes / span / 1e9, "unit": "GB/s", "offered_GBps": nbytes / a.serve_seconds / 1e9,
            "span_s": span, "max_inflight": max_inflight, "hbm_budget_bytes": budget, "plans": len(plans),
+           "by_class": {k: pcts(v) for k, v in sorted(by_class.items())},
+           "by_class_note": "small = at most 8 MiB of device bytes (2 N S): high-priority streams, reserved slots",
            "setup_s": setup_s}
     torch.cuda.empty_cache()
     return out

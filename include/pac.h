@@ -137,7 +137,10 @@ int pac_convolve_many_launches(int count, const pac_plan* plans, int* launches);
  * each) stay within hbm_budget_bytes and cudaMemGetInfo's free memory; a
  * request that does not fit waits (it is never dropped).  Admitted requests
  * run on a pool of streams so their kernels overlap on the device.  Plans
- * and spectra stay resident; the queue does not own them.
+ * and spectra stay resident; the queue does not own them.  Requests of at
+ * most 8 MiB of device bytes are "small": they run on high-priority streams
+ * and a quarter of the slots is kept for them, so large requests cannot hold
+ * every slot; within each class admission is in arrival order.
  */
 int pac_queue_create(size_t hbm_budget_bytes, int max_inflight, pac_queue* out);
 
@@ -252,6 +255,14 @@ enum {
     PAC_Q_PLANE = 10,             /* CTAs per plane of the plane pass, 0 when the plan has none */
     PAC_Q_GROUP_CAP = 11          /* the schedule's group-exponent cap (0: none) */
 };
+
+/*
+ * Measured peak fused multiply-add rate of the current device in GFLOP/s
+ * (2 flops per FMA) for the real type of dtype (FP32 for PAC_C64, FP64 for
+ * PAC_C128): the ALU roofline of passes that the FP64 pipe bounds.  Runs a
+ * short probe kernel and synchronises.
+ */
+int pac_measure_fma_peak(int dtype, double* gflops);
 
 /* Host-only helpers (no device needed): the stage list and reversal table rules. */
 int pac_stage_list(int64_t n, int radix, int* radices, int* count);

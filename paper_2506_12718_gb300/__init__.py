@@ -61,6 +61,7 @@ _SIGS = {
     "pac_convolve_permuted": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_convolve_permuted_noalloc": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_plan_query": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
+    "pac_measure_fma_peak": (_i32, [_i32, ctypes.POINTER(ctypes.c_double)]),
     "pac_tune": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, ctypes.POINTER(ctypes.c_double)]),
     "pac_convolve_timed": (_i32, [_vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
@@ -230,6 +231,13 @@ def pac_convolve_timed(plan: int, which: int, x_dev, y_dev, stream=None, max_lau
     _check(load().pac_convolve_timed(plan, int(which), _ptr(x_dev), _ptr(y_dev), _stream(stream), max_launches,
                                      ms, ids, ctypes.byref(n)))
     return [(KERNEL_NAMES.get(ids[i], str(ids[i])), float(ms[i])) for i in range(n.value)]
+
+
+def pac_measure_fma_peak(dtype: str = "c128") -> float:
+    """Measured peak FMA rate (GFLOP/s) of the device for FP32 ("c64") or FP64 ("c128")."""
+    g = ctypes.c_double(0.0)
+    _check(load().pac_measure_fma_peak(C64 if dtype == "c64" else C128, ctypes.byref(g)))
+    return g.value
 
 
 def pac_tune(dims, radix: int, dtype: str = "c64", reps: int = 5) -> float:

@@ -103,3 +103,58 @@ cudaError_t launch_pointwise_mul(int esize, int64_t n, const void* a, const void
 }
 
 }  // namespace pac
+
+// ---------------------------------------------------------------- FMA probe
+//
+// Peak fused multiply-add throughput of the device for one precision: every
+// thread runs 8 independent chains of dependent FMAs, enough warps per SM to
+// cover the pipe latency.  Used as the ALU roofline of FP64 passes, which
+// on this GPU are bound by the FP64 pipe rather than by HBM.
+namespace pac {
+
+template <typename T>
+__global__ void fma_probe_kernel(T* out, int iters, T a, T b) {
+    T x0 = (T)threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+    for (int i = 0; i < iters; ++i) {
+        x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+        x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+    }
+    const T s = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+    if (s == (T)-1.2345) out[blockIdx.x] = s;  // never true in practice; keeps the chains live
+}
+
+}  // namespace pac
+
+extern "C" int pac_measure_fma_peak(int dtype, double* gflops) {
+    using namespace pac;
+    if (!gflops || (dtype != PAC_C64 && dtype != PAC_C128)) return fail(PAC_ERR_ARG, "bad arguments");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    const int blocks = device_sm_count(dev) * 8, threads = 256, iters = 4096;
+    void* out = nullptr;
+    e = cudaMalloc(&out, (size_t)blocks * 16);
+    if (e != cudaSuccess) return fail(PAC_ERR_NOMEM, "probe buffer: %s", cudaGetErrorString(e));
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        cudaEventRecord(a, 0);
+        if (dtype == PAC_C64)
+            fma_probe_kernel<float><<<blocks, threads>>>((float*)out, iters, 0.999f, 0.001f);
+        else
+            fma_probe_kernel<double><<<blocks, threads>>>((double*)out, iters, 0.999, 0.001);
+        cudaEventRecord(b, 0);
+        e = cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < best) best = ms;  // the first run warms up
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    if (e != cudaSuccess) return cuda_fail(e, "FMA probe");
+    *gflops = 2.0 * 8.0 * (double)iters * blocks * threads / (best * 1e-3) / 1e9;
+    return PAC_OK;
+}

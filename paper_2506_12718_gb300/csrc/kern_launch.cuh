@@ -1,6 +1,6 @@
 // Launch helper for the pass kernels: one instantiation per (element type,
-// group size M).  Grid = resident CTAs of the whole GPU (persistent loop over
-// tiles), capped by the tile count.
+// group size M).  Grid = one CTA per tile for single passes; the batched and
+// single-launch forms use resident CTAs walking the tiles.
 #pragma once
 #include <atomic>
 
@@ -30,8 +30,10 @@ cudaError_t launch_variant(const PassArgs& a, cudaStream_t s) {
     }
     if (a.tiles <= 0) return cudaSuccess;
     if (a.tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const int64_t cap = (int64_t)per_sm * device_sm_count(dev);
-    const int64_t grid = a.tiles < cap ? a.tiles : cap;
+    // one CTA per tile: the hardware fills the SMs wave after wave, and CTAs
+    // end every few microseconds, so kernels of other streams (higher
+    // priority requests of a serving queue) get SMs between them
+    const int64_t grid = a.tiles;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3(SH::NT);

@@ -43,7 +43,7 @@ cudaError_t launch_one(const PlaneArgs& pa, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (pa.planes <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(K * cluster_grid(dev, pa.planes, K)));
+    cfg.gridDim = dim3((unsigned)(K * pa.planes));  // one cluster per plane (CTAs end often; see kern_launch.cuh)
     cfg.blockDim = dim3(PS::NT);
     cfg.dynamicSmemBytes = PS::SMEM;
     cfg.stream = s;

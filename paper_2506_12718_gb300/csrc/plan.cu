@@ -655,6 +655,29 @@ static int check_ptr(const void* ptr, const char* name) {
     return PAC_OK;
 }
 
+// Load and set up (module load, shared-memory attribute, occupancy) every
+// kernel the plan's convolution launches, with launches of no work, so that
+// the first convolution (a served request, a captured graph) does not pay
+// for it.
+static int prepare_convolve(pac_plan p) {
+    std::vector<Step> steps;
+    convolve_steps(p, nullptr, nullptr, steps);
+    for (const Step& st : steps) {
+        cudaError_t e;
+        if (st.mode == kPlane) {
+            PlaneArgs pa = make_plane(p, nullptr, nullptr);
+            pa.planes = 0;
+            e = launch_plane(p->esize, p->groups[p->plane_g1].M, p->groups[p->plane_g1 + 1].M, p->plane_k, pa, 0);
+        } else {
+            PassArgs a = make_pass(p, p->groups[st.group], st.mode, nullptr, nullptr, 1.0);
+            a.tiles = 0;
+            e = launch_pass(p->esize, p->groups[st.group].M, a, 0);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "kernel set-up");
+    }
+    return PAC_OK;
+}
+
 extern "C" int pac_filter_spectrum(pac_plan p, const void* h_dev) {
     if (!p) return fail(PAC_ERR_ARG, "null plan");
     if (int rc = check_ptr(h_dev, "h_dev")) return rc;
@@ -687,6 +710,7 @@ extern "C" int pac_filter_spectrum(pac_plan p, const void* h_dev) {
     if (tmp) cudaFree(tmp);
     if (rc) return rc;
     if (e != cudaSuccess) return cuda_fail(e, "filter spectrum");
+    if (int prc = prepare_convolve(p)) return prc;
     p->has_spec = true;
     if (p->d_spec_nat) {  // comparator spectrum must follow
         cudaFree(p->d_spec_nat);

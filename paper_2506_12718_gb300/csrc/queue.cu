@@ -9,6 +9,13 @@
 // while others run are admitted as earlier ones finish: the batch on the
 // device changes continuously instead of in waves.
 //
+// Quality of service: a request is "small" when its device bytes (2 N S) are
+// at most 8 MiB.  Small requests run on high-priority streams (the GPU's
+// block scheduler starts their CTAs before those of large requests as SMs
+// free up) and a quarter of the slots is kept for them, so a burst of large
+// requests cannot hold every slot while small ones wait; within each class
+// admission stays in arrival order.
+//
 // Fault injection (host side only, no device fault): the environment
 // variable PAC_FAULT=launch:K makes the K-th admitted request (1-based) fail
 // as if its launch had failed; the request is marked PAC_ERR_CUDA and the
@@ -30,6 +37,8 @@ int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s, bool allow_
 using namespace pac;
 using Clock = std::chrono::steady_clock;
 
+constexpr size_t kSmallBytes = size_t(8) << 20;  // requests up to this many device bytes are "small"
+
 namespace {
 
 struct Request {
@@ -42,6 +51,7 @@ struct Request {
     Clock::time_point t_done;
     int status = PAC_PENDING;
     int slot = -1;
+    bool small = false;
     std::atomic<bool> gpu_done{false};
     pac_queue owner = nullptr;
 };
@@ -55,8 +65,12 @@ struct pac_queue_s {
     std::mutex mu;
     std::condition_variable cv;       // wakes the scheduler
     std::condition_variable cv_done;  // wakes pac_queue_drain
-    std::deque<Request*> waiting;
+    std::deque<Request*> waiting;        // large requests, arrival order
+    std::deque<Request*> waiting_small;  // small requests, arrival order
     std::vector<Request*> running;
+    int running_large = 0;
+    int reserve_small = 1;               // slots large requests may not take
+    std::vector<int> slot_small;         // slot's stream has high priority
     std::unordered_map<uint64_t, Request*> by_ticket;
     std::vector<cudaStream_t> streams;
     std::vector<int> slot_busy;
@@ -85,8 +99,20 @@ static void CUDART_CB on_request_done(void* arg) {
 // alone rather than never.
 static bool fits(pac_queue q, const Request* r) {
     if ((int)q->running.size() >= q->max_inflight) return false;
+    if (!r->small && q->running_large >= q->max_inflight - q->reserve_small) return false;
     if (q->running.empty()) return true;
     return q->running_bytes + r->bytes <= q->budget;
+}
+
+// a free slot of the request's class (high-priority streams for small requests), else any free slot
+static int pick_slot(pac_queue q, const Request* r) {
+    int any = -1;
+    for (int s = 0; s < (int)q->slot_busy.size(); ++s) {
+        if (q->slot_busy[s]) continue;
+        if ((q->slot_small[s] != 0) == r->small) return s;
+        if (any < 0) any = s;
+    }
+    return any;
 }
 
 static void scheduler(pac_queue q) {
@@ -100,6 +126,7 @@ static void scheduler(pac_queue q) {
             if (r->gpu_done.load(std::memory_order_acquire)) {
                 r->status = PAC_OK;
                 q->running_bytes -= r->bytes;
+                if (!r->small) --q->running_large;
                 q->slot_busy[r->slot] = 0;
                 q->running[i] = q->running.back();
                 q->running.pop_back();
@@ -108,12 +135,17 @@ static void scheduler(pac_queue q) {
                 ++i;
             }
         }
-        // admit in arrival order while a slot and memory are free
-        while (!q->waiting.empty() && fits(q, q->waiting.front())) {
-            Request* r = q->waiting.front();
-            q->waiting.pop_front();
-            int slot = 0;
-            while (slot < (int)q->slot_busy.size() && q->slot_busy[slot]) ++slot;
+        // admit in arrival order within each class (small first) while a slot and memory are free
+        while (true) {
+            std::deque<Request*>* from = nullptr;
+            if (!q->waiting_small.empty() && fits(q, q->waiting_small.front()))
+                from = &q->waiting_small;
+            else if (!q->waiting.empty() && fits(q, q->waiting.front()))
+                from = &q->waiting;
+            if (!from) break;
+            Request* r = from->front();
+            from->pop_front();
+            const int slot = pick_slot(q, r);
             r->slot = slot;
             q->admitted++;
             int rc;
@@ -135,11 +167,12 @@ static void scheduler(pac_queue q) {
             }
             q->slot_busy[slot] = 1;
             q->running_bytes += r->bytes;
+            if (!r->small) ++q->running_large;
             q->running.push_back(r);
             progress = true;
         }
         if (progress) q->cv_done.notify_all();
-        if (q->stop && q->waiting.empty() && q->running.empty()) break;
+        if (q->stop && q->waiting.empty() && q->waiting_small.empty() && q->running.empty()) break;
         if (!progress) q->cv.wait_for(lk, std::chrono::microseconds(200));
     }
 }
@@ -160,8 +193,13 @@ extern "C" int pac_queue_create(size_t hbm_budget_bytes, int max_inflight, pac_q
     }
     q->streams.resize(max_inflight);
     q->slot_busy.assign(max_inflight, 0);
+    q->reserve_small = max_inflight >= 4 ? max_inflight / 4 : (max_inflight > 1 ? 1 : 0);
+    q->slot_small.assign(max_inflight, 0);
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);  // numerically lower = higher priority
     for (int i = 0; i < max_inflight; ++i) {
-        e = cudaStreamCreateWithFlags(&q->streams[i], cudaStreamNonBlocking);
+        q->slot_small[i] = i < q->reserve_small ? 1 : (i % 2);  // the reserved slots, then every other one
+        e = cudaStreamCreateWithPriority(&q->streams[i], cudaStreamNonBlocking, q->slot_small[i] ? prio_hi : prio_lo);
         if (e != cudaSuccess) {
             for (int j = 0; j < i; ++j) cudaStreamDestroy(q->streams[j]);
             delete q;
@@ -185,16 +223,17 @@ extern "C" int pac_submit(pac_queue q, pac_plan p, const void* x_dev, void* y_de
     r->x = x_dev;
     r->y = y_dev;
     r->bytes = 2 * (size_t)p->bytes();
+    r->small = r->bytes <= kSmallBytes;
     r->owner = q;
     r->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(q->mu);
-        if (q->waiting.size() >= 65536) {
+        if (q->waiting.size() + q->waiting_small.size() >= 65536) {
             delete r;
             return fail(PAC_ERR_BUSY, "request queue full");
         }
         r->ticket = q->next_ticket++;
-        q->waiting.push_back(r);
+        (r->small ? q->waiting_small : q->waiting).push_back(r);
         q->by_ticket[r->ticket] = r;
         *ticket = r->ticket;
     }
@@ -221,7 +260,7 @@ extern "C" int pac_queue_drain(pac_queue q, int timeout_ms) {
     if (!q) return fail(PAC_ERR_ARG, "null queue");
     std::unique_lock<std::mutex> lk(q->mu);
     bool ok = q->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms),
-                                  [&] { return q->waiting.empty() && q->running.empty(); });
+                                  [&] { return q->waiting.empty() && q->waiting_small.empty() && q->running.empty(); });
     return ok ? PAC_OK : fail(PAC_ERR_TIMEOUT, "queue did not drain within %d ms", timeout_ms);
 }
 
@@ -233,7 +272,9 @@ extern "C" int pac_queue_destroy(pac_queue q) {
         q->stop = true;
         if (rc != PAC_OK) {  // give up on waiting requests; running ones still finish
             for (Request* r : q->waiting) r->status = PAC_ERR_TIMEOUT;
+            for (Request* r : q->waiting_small) r->status = PAC_ERR_TIMEOUT;
             q->waiting.clear();
+            q->waiting_small.clear();
         }
     }
     q->cv.notify_all();
