@@ -648,11 +648,13 @@ def main(argv=None):
     if sampler:
         sampler.stop()
         line["clocks"] = sampler.summary(t_wall0, t_wall1)
-    if not a.quick and "configs" in a.legs:
+    # the extra legs describe one GPU; a multi-GPU (replicas) run reports the main leg only
+    extra = not a.quick and world == 1
+    if extra and "configs" in a.legs:
         line["configs"] = configs_leg(a, torch, pac, pin, dev, stream, flush, peak)
-    if not a.quick and "batched" in a.legs:
+    if extra and "batched" in a.legs:
         line["batched"] = batched_leg(a, torch, pac, pin, dev, stream, flush)
-    if not a.quick and "served" in a.legs:
+    if extra and "served" in a.legs:
         line["served"] = served_leg(a, torch, pac, pin, dev)
     if rank == 0 and world == 1 and not a.no_cpu and not a.quick:
         line["cpu_baseline"] = cpu_baseline_leg(a)
