@@ -47,6 +47,8 @@ def parse_args(argv=None):
     ap.add_argument("--radix", type=int, default=4)
     ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
     ap.add_argument("--n", type=int, default=128, help="edge of the 3-D cube")
+    ap.add_argument("--workload", choices=["conv3d", "conv2d-r3", "conv2d-r5", "conv1d"], default="conv3d",
+                    help="the main leg's problem (default: the 3-D n^3 workload)")
     ap.add_argument("--quick", action="store_true", help="main leg only (for profiler runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
@@ -217,8 +219,27 @@ def measured_peak_hbm():
 # --------------------------------------------------------------- the legs
 
 
-def workload_name(a):
-    return (f"3-D periodic convolution {a.n}^3, complex {'FP32' if a.dtype == 'c64' else 'FP64'}, radix {a.radix}, "
+def workload_conv(a, pin):
+    """The main leg's problem: --workload conv3d (default: n^3, --radix, --dtype), conv2d-r3 (2187^2),
+    conv2d-r5 (3125^2) or conv1d (n = 2^10, radix 2, FP64)."""
+    if a.workload == "conv2d-r3":
+        return pin.c3(3, a.dtype)
+    if a.workload == "conv2d-r5":
+        return pin.c3(5, a.dtype)
+    if a.workload == "conv1d":
+        return pin.c1()
+    return pin.c2(a.radix, a.dtype, a.n)
+
+
+def workload_name(a, c=None):
+    prec = f"complex {'FP32' if a.dtype == 'c64' else 'FP64'}"
+    if a.workload == "conv2d-r3":
+        return f"2-D periodic convolution 2187^2, {prec}, radix 3, periodised exponential filter spectrum resident"
+    if a.workload == "conv2d-r5":
+        return f"2-D periodic convolution 3125^2, {prec}, radix 5, periodised exponential filter spectrum resident"
+    if a.workload == "conv1d":
+        return "1-D circular convolution n=2^10, complex FP64, radix 2, uniform filter spectrum resident"
+    return (f"3-D periodic convolution {a.n}^3, {prec}, radix {a.radix}, "
             f"periodised Gaussian sigma=4 filter spectrum resident")
 
 
@@ -229,7 +250,7 @@ def cpu_baseline_leg(a):
 
     import oracle
     import pac_inputs as pin
-    c = pin.c2(a.radix, a.dtype, a.n)
+    c = workload_conv(a, pin)
     x, (_, fs) = pin.make_x(c), pin.make_h(c)
     oracle.build()
     t0 = time.perf_counter()
@@ -251,7 +272,7 @@ def reference_arm(a):
     import oracle
     import pac_inputs as pin
     oracle.build()
-    c = pin.c2(a.radix, a.dtype, a.n)
+    c = workload_conv(a, pin)
     x, (h, _) = pin.make_x(c), pin.make_h(c)
     npts = 64
     B = 3 * c.n_total * c.elem_bytes
@@ -271,7 +292,7 @@ def reference_arm(a):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot / a.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "dims": [a.n] * 3, "radix": a.radix},
+            "config": {"workload": workload_name(a), "dims": list(c.dims), "radix": c.radix},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -526,7 +547,7 @@ def main(argv=None):
     barrier(world)
     pac.load()
 
-    c = pin.c2(a.radix, a.dtype, a.n)
+    c = workload_conv(a, pin)
     x_np, (h_np, _) = pin.make_x(c), pin.make_h(c)
     N, S = c.n_total, c.elem_bytes
     B = 3 * N * S
@@ -564,8 +585,8 @@ def main(argv=None):
     peak, peak_kind = measured_peak_hbm()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if a.dtype == "c64" else "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "dims": list(c.dims), "radix": a.radix,
+            "dtype": "f32" if c.dtype == "c64" else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "dims": list(c.dims), "radix": c.radix,
                        "stages_per_axis": plan.stages(0), "bytes_per_step": B,
                        "schedule": {"passes": launches, "groups": plan.query(pac.Q_GROUPS),
                                     "plane_ctas": plan.query(pac.Q_PLANE), "group_cap": plan.query(pac.Q_GROUP_CAP),
@@ -587,10 +608,12 @@ def main(argv=None):
         # group launches by kernel instantiation (what ncu lists): the DIF and
         # DIT passes of the outer axes are one kernel (rows case), the fused
         # pass of the contiguous axis another (lines case)
-        vname = "float2" if a.dtype == "c64" else "double2"
-        kern = {"dif_pass": f"pass_kernel<{vname},128,rows>", "dit_pass": f"pass_kernel<{vname},128,rows>",
-                "fused_dif_mul_dit_pass": f"pass_kernel<{vname},128,lines>",
-                "plane_pass": f"plane_kernel<{vname},128,128>"}
+        vname = "float2" if c.dtype == "c64" else "double2"
+        m0 = math.prod(plan.stages(0))  # axis-0 group size (one group per axis in these workloads)
+        ml = math.prod(plan.stages(len(c.dims) - 1))
+        kern = {"dif_pass": f"pass_kernel<{vname},{m0},rows>", "dit_pass": f"pass_kernel<{vname},{m0},rows>",
+                "fused_dif_mul_dit_pass": f"pass_kernel<{vname},{ml},lines>",
+                "plane_pass": f"plane_kernel<{vname},{m0 if len(c.dims) == 2 else math.prod(plan.stages(1))},{ml}>"}
         byk = {}
         for name, v in per.items():
             byk.setdefault(kern.get(name, name), []).extend(v)
@@ -602,7 +625,8 @@ def main(argv=None):
         achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
         line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                            "traffic": ncu_traffic(dom, "conv3d"), "alg_bytes_per_launch": alg_bytes,
+                            "traffic": ncu_traffic(dom, {"conv2d-r5": "conv2d_3125"}.get(a.workload, a.workload)),
+                            "alg_bytes_per_launch": alg_bytes,
                             "alg_bytes_rule": "2*N*S per rows pass (read+write the array); 3*N*S per fused or "
                                               "plane pass (read x, read the spectrum, write y)",
                             "avg_launch_ms": avg_ms, "launches_per_step": nlaunch,

@@ -87,20 +87,21 @@ cudaError_t launch_many(const PlaneArgs* list, const uint32_t* starts, int n, in
 // CTAs per plane for a plane shape and plane count (0: no plane kernel).
 // Enough planes to give every SM one (planes >= SMs / 2): one CTA per plane
 // (a cluster's barriers and remote accesses only cost time then); fewer
-// planes: the split form, so that more SMs share the work.  PAC_PLANE_K in
-// the environment forces a cluster size where that form exists.
+// planes: the split form where one exists (measured faster for 81^2 and
+// 125^2; a 128^2 FP64 plane exists only split).  PAC_PLANE_K in the
+// environment forces a cluster size where that form exists.
 int plane_cluster(int M1, int M2, int esize, int64_t planes, int device) {
     const char* f = std::getenv("PAC_PLANE_K");
     const int want = f ? std::atoi(f) : 0;
     if (want > 0 && plane_supported_k(M1, M2, esize, want)) return want;
     if (2 * planes >= device_sm_count(device) && plane_supported_k(M1, M2, esize, 1)) return 1;
     if (esize == 8) {
-        if (M1 == 128 && M2 == 128) return 2;
+        if (M1 == 128 && M2 == 128) return 1;
         if (M1 == 64 && M2 == 64) return 1;
         if (M1 == 32 && M2 == 32) return 1;
         if (M1 == 16 && M2 == 16) return 1;
-        if (M1 == 64 && M2 == 128) return 2;
-        if (M1 == 128 && M2 == 64) return 2;
+        if (M1 == 64 && M2 == 128) return 1;
+        if (M1 == 128 && M2 == 64) return 1;
         if (M1 == 81 && M2 == 81) return 3;
         if (M1 == 27 && M2 == 27) return 1;
         if (M1 == 9 && M2 == 9) return 1;
@@ -108,7 +109,7 @@ int plane_cluster(int M1, int M2, int esize, int64_t planes, int device) {
         if (M1 == 125 && M2 == 125) return 5;
         return 0;
     }
-    if (M1 == 64 && M2 == 64) return 2;
+    if (M1 == 64 && M2 == 64) return 1;
     if (M1 == 32 && M2 == 32) return 1;
     if (M1 == 16 && M2 == 16) return 1;
     if (M1 == 27 && M2 == 27) return 1;
@@ -122,14 +123,11 @@ int plane_cluster(int M1, int M2, int esize, int64_t planes, int device) {
 int plane_supported_k(int M1, int M2, int esize, int K) {
     if (esize == 8) {
         if (M1 == 128 && M2 == 128 && K == 1) return 1;
-        if (M1 == 128 && M2 == 128 && K == 2) return 1;
         if (M1 == 64 && M2 == 64 && K == 1) return 1;
         if (M1 == 32 && M2 == 32 && K == 1) return 1;
         if (M1 == 16 && M2 == 16 && K == 1) return 1;
         if (M1 == 64 && M2 == 128 && K == 1) return 1;
         if (M1 == 128 && M2 == 64 && K == 1) return 1;
-        if (M1 == 64 && M2 == 128 && K == 2) return 1;
-        if (M1 == 128 && M2 == 64 && K == 2) return 1;
         if (M1 == 81 && M2 == 81 && K == 1) return 1;
         if (M1 == 81 && M2 == 81 && K == 3) return 1;
         if (M1 == 27 && M2 == 27 && K == 1) return 1;
@@ -140,7 +138,6 @@ int plane_supported_k(int M1, int M2, int esize, int K) {
         return 0;
     }
     if (M1 == 64 && M2 == 64 && K == 1) return 1;
-    if (M1 == 64 && M2 == 64 && K == 2) return 1;
     if (M1 == 32 && M2 == 32 && K == 1) return 1;
     if (M1 == 16 && M2 == 16 && K == 1) return 1;
     if (M1 == 27 && M2 == 27 && K == 1) return 1;
@@ -156,14 +153,11 @@ int plane_supported(int M1, int M2, int esize) { return plane_cluster(M1, M2, es
 cudaError_t launch_plane(int esize, int M1, int M2, int K, const PlaneArgs& pa, cudaStream_t s) {
     if (esize == 8) {
         if (M1 == 128 && M2 == 128 && K == 1) return launch_one<float2, 128, 128, 1>(pa, s);
-        if (M1 == 128 && M2 == 128 && K == 2) return launch_one<float2, 128, 128, 2>(pa, s);
         if (M1 == 64 && M2 == 64 && K == 1) return launch_one<float2, 64, 64, 1>(pa, s);
         if (M1 == 32 && M2 == 32 && K == 1) return launch_one<float2, 32, 32, 1>(pa, s);
         if (M1 == 16 && M2 == 16 && K == 1) return launch_one<float2, 16, 16, 1>(pa, s);
         if (M1 == 64 && M2 == 128 && K == 1) return launch_one<float2, 64, 128, 1>(pa, s);
         if (M1 == 128 && M2 == 64 && K == 1) return launch_one<float2, 128, 64, 1>(pa, s);
-        if (M1 == 64 && M2 == 128 && K == 2) return launch_one<float2, 64, 128, 2>(pa, s);
-        if (M1 == 128 && M2 == 64 && K == 2) return launch_one<float2, 128, 64, 2>(pa, s);
         if (M1 == 81 && M2 == 81 && K == 1) return launch_one<float2, 81, 81, 1>(pa, s);
         if (M1 == 81 && M2 == 81 && K == 3) return launch_one<float2, 81, 81, 3>(pa, s);
         if (M1 == 27 && M2 == 27 && K == 1) return launch_one<float2, 27, 27, 1>(pa, s);
@@ -173,7 +167,6 @@ cudaError_t launch_plane(int esize, int M1, int M2, int K, const PlaneArgs& pa, 
         if (M1 == 125 && M2 == 125 && K == 5) return launch_one<float2, 125, 125, 5>(pa, s);
     } else {
         if (M1 == 64 && M2 == 64 && K == 1) return launch_one<double2, 64, 64, 1>(pa, s);
-        if (M1 == 64 && M2 == 64 && K == 2) return launch_one<double2, 64, 64, 2>(pa, s);
         if (M1 == 32 && M2 == 32 && K == 1) return launch_one<double2, 32, 32, 1>(pa, s);
         if (M1 == 16 && M2 == 16 && K == 1) return launch_one<double2, 16, 16, 1>(pa, s);
         if (M1 == 27 && M2 == 27 && K == 1) return launch_one<double2, 27, 27, 1>(pa, s);
@@ -189,14 +182,11 @@ cudaError_t launch_plane_multi(int esize, int M1, int M2, int K, const PlaneArgs
                                int64_t total, cudaStream_t s) {
     if (esize == 8) {
         if (M1 == 128 && M2 == 128 && K == 1) return launch_many<float2, 128, 128, 1>(list, starts, n, total, s);
-        if (M1 == 128 && M2 == 128 && K == 2) return launch_many<float2, 128, 128, 2>(list, starts, n, total, s);
         if (M1 == 64 && M2 == 64 && K == 1) return launch_many<float2, 64, 64, 1>(list, starts, n, total, s);
         if (M1 == 32 && M2 == 32 && K == 1) return launch_many<float2, 32, 32, 1>(list, starts, n, total, s);
         if (M1 == 16 && M2 == 16 && K == 1) return launch_many<float2, 16, 16, 1>(list, starts, n, total, s);
         if (M1 == 64 && M2 == 128 && K == 1) return launch_many<float2, 64, 128, 1>(list, starts, n, total, s);
         if (M1 == 128 && M2 == 64 && K == 1) return launch_many<float2, 128, 64, 1>(list, starts, n, total, s);
-        if (M1 == 64 && M2 == 128 && K == 2) return launch_many<float2, 64, 128, 2>(list, starts, n, total, s);
-        if (M1 == 128 && M2 == 64 && K == 2) return launch_many<float2, 128, 64, 2>(list, starts, n, total, s);
         if (M1 == 81 && M2 == 81 && K == 1) return launch_many<float2, 81, 81, 1>(list, starts, n, total, s);
         if (M1 == 81 && M2 == 81 && K == 3) return launch_many<float2, 81, 81, 3>(list, starts, n, total, s);
         if (M1 == 27 && M2 == 27 && K == 1) return launch_many<float2, 27, 27, 1>(list, starts, n, total, s);
@@ -206,7 +196,6 @@ cudaError_t launch_plane_multi(int esize, int M1, int M2, int K, const PlaneArgs
         if (M1 == 125 && M2 == 125 && K == 5) return launch_many<float2, 125, 125, 5>(list, starts, n, total, s);
     } else {
         if (M1 == 64 && M2 == 64 && K == 1) return launch_many<double2, 64, 64, 1>(list, starts, n, total, s);
-        if (M1 == 64 && M2 == 64 && K == 2) return launch_many<double2, 64, 64, 2>(list, starts, n, total, s);
         if (M1 == 32 && M2 == 32 && K == 1) return launch_many<double2, 32, 32, 1>(list, starts, n, total, s);
         if (M1 == 16 && M2 == 16 && K == 1) return launch_many<double2, 16, 16, 1>(list, starts, n, total, s);
         if (M1 == 27 && M2 == 27 && K == 1) return launch_many<double2, 27, 27, 1>(list, starts, n, total, s);
