@@ -111,7 +111,7 @@ constexpr int min_blocks(int m, int esize) {
 // shared memory, element (i1, i2) at i1 * plane_pitch + i2.  Padding chosen
 // like tile_pad, over both axes' round patterns.
 constexpr int plane_pad(int m1, int m2, int esize) {
-    return esize == 8 ? (base_of(m2) == 2 ? (m2 >= 32 ? 3 : 1) : (m2 == 81 ? 8 : 0))
+    return esize == 8 ? (base_of(m2) == 2 ? (m2 >= 32 ? 3 : 1) : (m2 == 81 || m2 == 125 ? 8 : 0))
                       : (base_of(m2) == 2 ? 1 : 0);
 }
 constexpr int plane_pitch(int m1, int m2, int esize) { return m2 + plane_pad(m1, m2, esize); }
