@@ -355,6 +355,16 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
             torch.fft.ifftn(torch.fft.fftn(x) * Hn, out=yc)
 
         msc = time_steps(torch, cufft_step, steps, 3, flush, stream)
+        # the paper's transform-level comparison: unordered DIF output (uFFT2) against the ordered
+        # DFT with its index-reversal pass (FFT2), and the permutation's share of the latter
+        msu = time_steps(torch, lambda: pac.pac_forward_unordered(plan.handle, x, y, sh), steps, 3, flush, stream)
+        mso = time_steps(torch, lambda: pac.pac_fft(plan.handle, x, y, False, sh), steps, 3, flush, stream)
+        per = {}
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                flush()
+                for kname, tt in pac.pac_convolve_timed(plan.handle, 2, x, y, sh):
+                    per[kname] = per.get(kname, 0.0) + tt
         pac.pac_convolve(plan.handle, x, y, sh)
         stream.synchronize()
         diff = float(torch.linalg.vector_norm(y - yc) / torch.linalg.vector_norm(yc))
@@ -365,7 +375,10 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
                     "cufft_GBps": B / (tc * 1e-3) / 1e9, "speedup_vs_cufft": tc / t,
                     "launches": plan.query(pac.Q_LAUNCHES_CONVOLVE), "groups": plan.query(pac.Q_GROUPS),
                     "plane_ctas": plan.query(pac.Q_PLANE), "group_cap": plan.query(pac.Q_GROUP_CAP),
-                    "tuned_us": tuned_us, "rel_l2_vs_cufft": diff})
+                    "tuned_us": tuned_us, "rel_l2_vs_cufft": diff,
+                    "transform": {"unordered_us": statistics.median(msu) * 1e3,
+                                  "ordered_us": statistics.median(mso) * 1e3,
+                                  "permutation_share_of_ordered": per.get("permute", 0.0) / sum(per.values())}})
         flops = 2 * c_r[c.radix] * N * math.log2(N) + 6 * N
         out[-1]["alu"] = {"flops_per_conv": flops, "achieved_gflops": flops / (t * 1e-3) / 1e9,
                           "peak_gflops": fma_peak[c.dtype],

@@ -190,8 +190,21 @@ int pac_forward_unordered(pac_plan p, const void* x_dev, void* xhat_dev, void* s
 int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev, void* stream);
 
 /*
- * Profiling form of pac_convolve (which = 0) or pac_convolve_permuted
- * (which = 1): the same launches, with a CUDA event recorded on `stream`
+ * Ordered DFT with an explicit index-reversal pass, the standard FFT of the
+ * paper's comparison: inverse = 0 gives out = F in in natural frequency
+ * order (FFT2 of Algorithm 5: the DIF passes A^T, then the permutation P of
+ * Algorithm 1); inverse = 1 gives out = F^-1 in = conj(A) P in / N (iFFT of
+ * Algorithm 9).  Forward sign w_n = exp(-2 pi i / n).  Uses plan-owned
+ * scratch (N elements) and index tables made on first use; in_dev may equal
+ * out_dev.  pac_convolve_timed-style timing of its launches: kernel ids 0
+ * (DIF pass), 2 (DIT pass), 3 (permutation).  Asynchronous on `stream`.
+ */
+int pac_fft(pac_plan p, const void* in_dev, void* out_dev, int inverse, void* stream);
+
+/*
+ * Profiling form of pac_convolve (which = 0), pac_convolve_permuted
+ * (which = 1), pac_fft forward (which = 2) or pac_fft inverse (which = 3):
+ * the same launches, with a CUDA event recorded on `stream`
  * before and after each one; synchronises `stream` and writes each launch's
  * device time (ms) to launch_ms[0..*n_launches) and a kernel id to
  * kernel_ids[] (0 = forward DIF pass, 1 = fused DIF+product+DIT pass,

@@ -59,6 +59,7 @@ _SIGS = {
     "pac_plan_reverse_table": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
     "pac_forward_unordered": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_convolve_permuted": (_i32, [_vp, _vp, _vp, _vp]),
+    "pac_fft": (_i32, [_vp, _vp, _vp, _i32, _vp]),
     "pac_convolve_permuted_noalloc": (_i32, [_vp, _vp, _vp, _vp]),
     "pac_plan_query": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
     "pac_measure_fma_peak": (_i32, [_i32, ctypes.POINTER(ctypes.c_double)]),
@@ -195,6 +196,11 @@ def pac_convolve_many_launches(plans) -> int:
 
 def pac_forward_unordered(plan: int, x_dev, xhat_dev, stream=None) -> None:
     _check(load().pac_forward_unordered(plan, _ptr(x_dev), _ptr(xhat_dev), _stream(stream)))
+
+
+def pac_fft(plan: int, in_dev, out_dev, inverse: bool = False, stream=None) -> None:
+    """Ordered DFT (DIF passes + index-reversal permutation) or its inverse (with 1/N)."""
+    _check(load().pac_fft(plan, _ptr(in_dev), _ptr(out_dev), 1 if inverse else 0, _stream(stream)))
 
 
 def pac_convolve_permuted(plan: int, x_dev, y_dev, stream=None) -> None:

@@ -9,11 +9,11 @@
 
 namespace pac {
 
-// out[i0,i1,i2] = in[t0[i0], t1[i1], t2[i2]] (* mul[i0,i1,i2]); a null table is the identity
+// out[i0,i1,i2] = in[t0[i0], t1[i1], t2[i2]] (* mul[i0,i1,i2]) (* scale); a null table is the identity
 template <typename V>
 __global__ void permute_kernel(int64_t d0, int64_t d1, int64_t d2, const int64_t* __restrict__ t0,
                                const int64_t* __restrict__ t1, const int64_t* __restrict__ t2, const V* src,
-                               V* dst, const V* __restrict__ mul) {
+                               V* dst, const V* __restrict__ mul, double scale) {
     const int64_t rows = d0 * d1;
     for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
         const int64_t i0 = row / d1, i1 = row - (row / d1) * d1;
@@ -25,6 +25,7 @@ __global__ void permute_kernel(int64_t d0, int64_t d1, int64_t d2, const int64_t
              i2 += (int64_t)gridDim.x * blockDim.x) {
             V v = srow[t2 ? __ldg(t2 + i2) : i2];
             if (mul) v = cmul(v, __ldg(mul + row * d2 + i2));
+            if (scale != 1.0) v = cscale(v, (typename Real<V>::T)scale);
             drow[i2] = v;
         }
     }
@@ -68,7 +69,7 @@ cudaError_t launch_spec_order(int esize, const SpecOrder& o, int64_t n, const vo
 }
 
 cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64_t* const* idx_dev,
-                           const void* src, void* dst, const void* mul, cudaStream_t s) {
+                           const void* src, void* dst, const void* mul, cudaStream_t s, double scale) {
     int64_t d[3] = {1, 1, 1};
     const int64_t* t[3] = {nullptr, nullptr, nullptr};
     for (int a = 0; a < ndim; ++a) {
@@ -82,10 +83,10 @@ cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64
     dim3 grid((unsigned)gx, (unsigned)gy);
     if (esize == 8)
         permute_kernel<float2><<<grid, threads, 0, s>>>(d[0], d[1], d[2], t[0], t[1], t[2], (const float2*)src,
-                                                         (float2*)dst, (const float2*)mul);
+                                                         (float2*)dst, (const float2*)mul, scale);
     else
         permute_kernel<double2><<<grid, threads, 0, s>>>(d[0], d[1], d[2], t[0], t[1], t[2], (const double2*)src,
-                                                          (double2*)dst, (const double2*)mul);
+                                                          (double2*)dst, (const double2*)mul, scale);
     return cudaGetLastError();
 }
 

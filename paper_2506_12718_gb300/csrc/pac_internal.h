@@ -85,7 +85,7 @@ int take_device_error(int device, unsigned* value);
 
 // auxiliary kernels (aux.cu)
 cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64_t* const* idx_dev,
-                           const void* src, void* dst, const void* mul, cudaStream_t s);
+                           const void* src, void* dst, const void* mul, cudaStream_t s, double scale = 1.0);
 cudaError_t launch_spec_order(int esize, const SpecOrder& o, int64_t n, const void* src, void* dst, bool to_kernel,
                               cudaStream_t s);
 cudaError_t launch_pointwise_mul(int esize, int64_t n, const void* a, const void* b, void* out, double scale,

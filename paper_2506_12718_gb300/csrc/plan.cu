@@ -759,9 +759,8 @@ extern "C" int pac_convolve_host(pac_plan p, const void* x_host, void* y_host, v
     return PAC_OK;
 }
 
-// Comparator state: per-axis [pos_to_freq | freq_to_pos] tables, scratch and
-// the natural-order spectrum (one permutation pass at filter time).
-static int ensure_permuted_state(pac_plan p) {
+// Per-axis [pos_to_freq | freq_to_pos] tables and an N-element scratch.
+static int ensure_perm_tables(pac_plan p) {
     cudaError_t e;
     if (!p->d_perm) {
         int64_t tot = 0;
@@ -787,6 +786,14 @@ static int ensure_permuted_state(pac_plan p) {
         if (e != cudaSuccess) return fail(PAC_ERR_NOMEM, "scratch: %s", cudaGetErrorString(e));
         p->device_bytes += (size_t)p->bytes();
     }
+    return PAC_OK;
+}
+
+// Comparator state: the tables and scratch above, and the natural-order
+// spectrum (one permutation pass at filter time).
+static int ensure_permuted_state(pac_plan p) {
+    cudaError_t e;
+    if (int rc = ensure_perm_tables(p)) return rc;
     if (!p->d_spec_nat) {
         e = cudaMalloc(&p->d_spec_nat, (size_t)p->bytes());
         if (e != cudaSuccess) return fail(PAC_ERR_NOMEM, "natural spectrum: %s", cudaGetErrorString(e));
@@ -842,14 +849,60 @@ extern "C" int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev,
     return run_steps(p, steps, s, true);
 }
 
+// Ordered transforms (Algorithm 5 FFT2 and Algorithm 9 iFFT): the DIF passes
+// then the index-reversal permutation into natural frequency order, or the
+// permutation (with 1/N) then the conjugate DIT passes.
+static int ensure_perm_tables(pac_plan p);
+
+extern "C" int pac_fft(pac_plan p, const void* in_dev, void* out_dev, int inverse, void* stream) {
+    if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = check_ptr(in_dev, "in_dev")) return rc;
+    if (int rc = check_ptr(out_dev, "out_dev")) return rc;
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        if (int rc = ensure_perm_tables(p)) return rc;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t* to_nat[3];
+    const int64_t* to_rev[3];
+    int64_t o = 0;
+    for (int a = 0; a < p->ndim; ++a) {
+        to_rev[a] = p->d_perm + o;
+        to_nat[a] = p->d_perm + o + p->dims[a];
+        o += 2 * p->dims[a];
+    }
+    const int G = (int)p->groups.size();
+    if (!inverse) {
+        int rc = run_forward(p, in_dev, p->d_scratch, 1.0, s);  // A^T x, index-reversed
+        if (rc) return rc;
+        cudaError_t e = timed_permute(p, to_nat, p->d_scratch, out_dev, nullptr, s);
+        return e == cudaSuccess ? PAC_OK : cuda_fail(e, "permute kernel");
+    }
+    // x = conj(A) P X / N
+    timer_mark(s, 3, true);
+    cudaError_t e = launch_permute(p->esize, p->ndim, p->dims, to_rev, in_dev, p->d_scratch, nullptr, s,
+                                   1.0 / (double)p->N);
+    timer_mark(s, 3, false);
+    if (e != cudaSuccess) return cuda_fail(e, "permute kernel");
+    if (G == 0) {
+        e = cudaMemcpyAsync(out_dev, p->d_scratch, (size_t)p->bytes(), cudaMemcpyDeviceToDevice, s);
+        return e == cudaSuccess ? PAC_OK : cuda_fail(e, "copy");
+    }
+    std::vector<Step> steps;
+    for (int i = G - 1; i >= 0; --i) steps.push_back({i, kInv, i == G - 1 ? (const void*)p->d_scratch : out_dev, out_dev, 1.0});
+    return run_steps(p, steps, s, false);
+}
+
 extern "C" int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, void* stream,
                                   int max_launches, float* launch_ms, int* kernel_ids, int* n_launches) {
     if (!p || !launch_ms || !kernel_ids || !n_launches || max_launches < 1) return fail(PAC_ERR_ARG, "bad arguments");
-    if (which != 0 && which != 1) return fail(PAC_ERR_ARG, "which must be 0 or 1");
+    if (which < 0 || which > 3) return fail(PAC_ERR_ARG, "which must be 0, 1, 2 or 3");
     LaunchTimer timer;
     timer.max = max_launches;
     t_timer = &timer;
-    int rc = which == 0 ? pac_convolve(p, x_dev, y_dev, stream) : pac_convolve_permuted(p, x_dev, y_dev, stream);
+    int rc = which == 0   ? pac_convolve(p, x_dev, y_dev, stream)
+             : which == 1 ? pac_convolve_permuted(p, x_dev, y_dev, stream)
+                          : pac_fft(p, x_dev, y_dev, which == 3 ? 1 : 0, stream);
     t_timer = nullptr;
     cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     const int n = (int)timer.ids.size();

@@ -223,6 +223,34 @@ def test_forward_is_dft_in_index_reversed_order(dims, radix, dtype):
     check(got, ref, dtype, int(np.prod(dims)), "A^T x")
 
 
+# -------------------------------------------------------- ordered transforms
+
+
+@pytest.mark.parametrize("dims,radix,dtype", [((128,), 4, "c128"), ((81,), 3, "c128"), ((16, 32), 8, "c128"),
+                                             ((8, 4, 16), 2, "c64"), ((125, 25), 5, "c64"), ((4096,), 2, "c64")])
+def test_ordered_fft_is_the_dft(dims, radix, dtype):
+    """pac_fft: forward = the naive DFT (O3) in natural order; inverse(forward(x)) = x; inverse = O3's inverse."""
+    pac = pac_mod()
+    x = pin.as_dtype(pin.complex_uniform(dims, 15), dtype)
+    plan = pac.Plan(dims, radix, dtype)
+    try:
+        xd = dev(x)
+        X = torch.empty_like(xd)
+        pac.pac_fft(plan.handle, xd, X)
+        back = torch.empty_like(xd)
+        pac.pac_fft(plan.handle, X, back, inverse=True)
+        torch.cuda.synchronize()
+        Xn = X.cpu().numpy()
+        check(Xn, oracle.dft(x), dtype, x.size, "F x")
+        check(back.cpu().numpy(), x, dtype, x.size, "F^-1 F x")
+        y = torch.empty_like(xd)
+        pac.pac_fft(plan.handle, dev(Xn), y, inverse=True)
+        torch.cuda.synchronize()
+        check(y.cpu().numpy(), oracle.idft(Xn), dtype, x.size, "F^-1 X")
+    finally:
+        plan.close()
+
+
 # -------------------------------------------------------------- comparator
 
 
