@@ -738,8 +738,9 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, size
 
 // ------------------------------------------------------------------ planes
 //
-// Plane pass: the last two axes (n1 x n2, one group each) of whole planes in
-// one CTA's shared memory.  Axis d-1 forward (first round from global, lines
+// Plane pass: the last group of axis d-2 (n1 = its size M1; it never carries
+// an external twiddle) and the single group of axis d-1 (M2) for whole
+// M1 x M2 planes in one CTA's shared memory.  Axis d-1 forward (first round from global, lines
 // coalesced), axis d-2 forward with the product in its last round, axis d-2
 // inverse, axis d-1 inverse (last round to global): the convolution of the
 // two innermost axes in one pass, so a 3-D convolution takes 3 passes and a

@@ -107,6 +107,14 @@ int plane_cluster(int M1, int M2, int esize, int64_t planes, int device) {
         if (M1 == 9 && M2 == 9) return 1;
         if (M1 == 25 && M2 == 25) return 1;
         if (M1 == 125 && M2 == 125) return 5;
+        if (M1 == 128 && M2 == 2) return 1;
+        if (M1 == 256 && M2 == 2) return 1;
+        if (M1 == 512 && M2 == 2) return 1;
+        if (M1 == 1024 && M2 == 2) return 1;
+        if (M1 == 2048 && M2 == 2) return 1;
+        if (M1 == 4096 && M2 == 2) return 1;
+        if (M1 == 256 && M2 == 4) return 1;
+        if (M1 == 1024 && M2 == 4) return 1;
         return 0;
     }
     if (M1 == 64 && M2 == 64) return 1;
@@ -117,6 +125,11 @@ int plane_cluster(int M1, int M2, int esize, int64_t planes, int device) {
     if (M1 == 25 && M2 == 25) return 1;
     if (M1 == 9 && M2 == 9) return 1;
     if (M1 == 128 && M2 == 128) return 2;
+    if (M1 == 128 && M2 == 2) return 1;
+    if (M1 == 256 && M2 == 2) return 1;
+    if (M1 == 512 && M2 == 2) return 1;
+    if (M1 == 1024 && M2 == 2) return 1;
+    if (M1 == 2048 && M2 == 2) return 1;
     return 0;
 }
 
@@ -135,6 +148,14 @@ int plane_supported_k(int M1, int M2, int esize, int K) {
         if (M1 == 25 && M2 == 25 && K == 1) return 1;
         if (M1 == 125 && M2 == 125 && K == 1) return 1;
         if (M1 == 125 && M2 == 125 && K == 5) return 1;
+        if (M1 == 128 && M2 == 2 && K == 1) return 1;
+        if (M1 == 256 && M2 == 2 && K == 1) return 1;
+        if (M1 == 512 && M2 == 2 && K == 1) return 1;
+        if (M1 == 1024 && M2 == 2 && K == 1) return 1;
+        if (M1 == 2048 && M2 == 2 && K == 1) return 1;
+        if (M1 == 4096 && M2 == 2 && K == 1) return 1;
+        if (M1 == 256 && M2 == 4 && K == 1) return 1;
+        if (M1 == 1024 && M2 == 4 && K == 1) return 1;
         return 0;
     }
     if (M1 == 64 && M2 == 64 && K == 1) return 1;
@@ -145,6 +166,11 @@ int plane_supported_k(int M1, int M2, int esize, int K) {
     if (M1 == 25 && M2 == 25 && K == 1) return 1;
     if (M1 == 9 && M2 == 9 && K == 1) return 1;
     if (M1 == 128 && M2 == 128 && K == 2) return 1;
+    if (M1 == 128 && M2 == 2 && K == 1) return 1;
+    if (M1 == 256 && M2 == 2 && K == 1) return 1;
+    if (M1 == 512 && M2 == 2 && K == 1) return 1;
+    if (M1 == 1024 && M2 == 2 && K == 1) return 1;
+    if (M1 == 2048 && M2 == 2 && K == 1) return 1;
     return 0;
 }
 
@@ -165,6 +191,14 @@ cudaError_t launch_plane(int esize, int M1, int M2, int K, const PlaneArgs& pa, 
         if (M1 == 25 && M2 == 25 && K == 1) return launch_one<float2, 25, 25, 1>(pa, s);
         if (M1 == 125 && M2 == 125 && K == 1) return launch_one<float2, 125, 125, 1>(pa, s);
         if (M1 == 125 && M2 == 125 && K == 5) return launch_one<float2, 125, 125, 5>(pa, s);
+        if (M1 == 128 && M2 == 2 && K == 1) return launch_one<float2, 128, 2, 1>(pa, s);
+        if (M1 == 256 && M2 == 2 && K == 1) return launch_one<float2, 256, 2, 1>(pa, s);
+        if (M1 == 512 && M2 == 2 && K == 1) return launch_one<float2, 512, 2, 1>(pa, s);
+        if (M1 == 1024 && M2 == 2 && K == 1) return launch_one<float2, 1024, 2, 1>(pa, s);
+        if (M1 == 2048 && M2 == 2 && K == 1) return launch_one<float2, 2048, 2, 1>(pa, s);
+        if (M1 == 4096 && M2 == 2 && K == 1) return launch_one<float2, 4096, 2, 1>(pa, s);
+        if (M1 == 256 && M2 == 4 && K == 1) return launch_one<float2, 256, 4, 1>(pa, s);
+        if (M1 == 1024 && M2 == 4 && K == 1) return launch_one<float2, 1024, 4, 1>(pa, s);
     } else {
         if (M1 == 64 && M2 == 64 && K == 1) return launch_one<double2, 64, 64, 1>(pa, s);
         if (M1 == 32 && M2 == 32 && K == 1) return launch_one<double2, 32, 32, 1>(pa, s);
@@ -174,6 +208,11 @@ cudaError_t launch_plane(int esize, int M1, int M2, int K, const PlaneArgs& pa, 
         if (M1 == 25 && M2 == 25 && K == 1) return launch_one<double2, 25, 25, 1>(pa, s);
         if (M1 == 9 && M2 == 9 && K == 1) return launch_one<double2, 9, 9, 1>(pa, s);
         if (M1 == 128 && M2 == 128 && K == 2) return launch_one<double2, 128, 128, 2>(pa, s);
+        if (M1 == 128 && M2 == 2 && K == 1) return launch_one<double2, 128, 2, 1>(pa, s);
+        if (M1 == 256 && M2 == 2 && K == 1) return launch_one<double2, 256, 2, 1>(pa, s);
+        if (M1 == 512 && M2 == 2 && K == 1) return launch_one<double2, 512, 2, 1>(pa, s);
+        if (M1 == 1024 && M2 == 2 && K == 1) return launch_one<double2, 1024, 2, 1>(pa, s);
+        if (M1 == 2048 && M2 == 2 && K == 1) return launch_one<double2, 2048, 2, 1>(pa, s);
     }
     return cudaErrorInvalidValue;
 }
@@ -194,6 +233,14 @@ cudaError_t launch_plane_multi(int esize, int M1, int M2, int K, const PlaneArgs
         if (M1 == 25 && M2 == 25 && K == 1) return launch_many<float2, 25, 25, 1>(list, starts, n, total, s);
         if (M1 == 125 && M2 == 125 && K == 1) return launch_many<float2, 125, 125, 1>(list, starts, n, total, s);
         if (M1 == 125 && M2 == 125 && K == 5) return launch_many<float2, 125, 125, 5>(list, starts, n, total, s);
+        if (M1 == 128 && M2 == 2 && K == 1) return launch_many<float2, 128, 2, 1>(list, starts, n, total, s);
+        if (M1 == 256 && M2 == 2 && K == 1) return launch_many<float2, 256, 2, 1>(list, starts, n, total, s);
+        if (M1 == 512 && M2 == 2 && K == 1) return launch_many<float2, 512, 2, 1>(list, starts, n, total, s);
+        if (M1 == 1024 && M2 == 2 && K == 1) return launch_many<float2, 1024, 2, 1>(list, starts, n, total, s);
+        if (M1 == 2048 && M2 == 2 && K == 1) return launch_many<float2, 2048, 2, 1>(list, starts, n, total, s);
+        if (M1 == 4096 && M2 == 2 && K == 1) return launch_many<float2, 4096, 2, 1>(list, starts, n, total, s);
+        if (M1 == 256 && M2 == 4 && K == 1) return launch_many<float2, 256, 4, 1>(list, starts, n, total, s);
+        if (M1 == 1024 && M2 == 4 && K == 1) return launch_many<float2, 1024, 4, 1>(list, starts, n, total, s);
     } else {
         if (M1 == 64 && M2 == 64 && K == 1) return launch_many<double2, 64, 64, 1>(list, starts, n, total, s);
         if (M1 == 32 && M2 == 32 && K == 1) return launch_many<double2, 32, 32, 1>(list, starts, n, total, s);
@@ -203,6 +250,11 @@ cudaError_t launch_plane_multi(int esize, int M1, int M2, int K, const PlaneArgs
         if (M1 == 25 && M2 == 25 && K == 1) return launch_many<double2, 25, 25, 1>(list, starts, n, total, s);
         if (M1 == 9 && M2 == 9 && K == 1) return launch_many<double2, 9, 9, 1>(list, starts, n, total, s);
         if (M1 == 128 && M2 == 128 && K == 2) return launch_many<double2, 128, 128, 2>(list, starts, n, total, s);
+        if (M1 == 128 && M2 == 2 && K == 1) return launch_many<double2, 128, 2, 1>(list, starts, n, total, s);
+        if (M1 == 256 && M2 == 2 && K == 1) return launch_many<double2, 256, 2, 1>(list, starts, n, total, s);
+        if (M1 == 512 && M2 == 2 && K == 1) return launch_many<double2, 512, 2, 1>(list, starts, n, total, s);
+        if (M1 == 1024 && M2 == 2 && K == 1) return launch_many<double2, 1024, 2, 1>(list, starts, n, total, s);
+        if (M1 == 2048 && M2 == 2 && K == 1) return launch_many<double2, 2048, 2, 1>(list, starts, n, total, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -329,7 +329,7 @@ int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const 
     // PAC_SINGLE_LAUNCH=1 in the environment when the plan is created
     const char* sl = std::getenv("PAC_SINGLE_LAUNCH");
     pl->single_launch = sl && sl[0] == '1';
-    // plane pass: the last two axes each one group, a supported plane shape;
+    // plane pass: axis d-1 one group, a supported shape of (last group of axis d-2) x (axis d-1);
     // PAC_PLANE=0 in the environment keeps per-axis passes instead
     const char* pe = std::getenv("PAC_PLANE");
     if (ndim >= 2 && sch.plane && !(pe && pe[0] == '0')) {
@@ -339,7 +339,8 @@ int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const 
             if (g.axis == ndim - 2) ++g_prev;
         }
         const int G = (int)pl->groups.size();
-        if (g_last == 1 && g_prev == 1 && G >= 2 &&
+        // groups[G-2] is the last group of axis d-2 (no external twiddle), groups[G-1] all of axis d-1
+        if (g_last == 1 && g_prev >= 1 && G >= 2 &&
             plane_supported(pl->groups[G - 2].M, pl->groups[G - 1].M, pl->esize)) {
             pl->plane = true;
             pl->plane_g1 = G - 2;

@@ -124,6 +124,8 @@ SHAPES = [
     ((8, 8), 2), ((64, 32), 4), ((27, 81), 3), ((25, 125), 5), ((2, 1024), 2), ((1024, 2), 8),
     ((1, 64), 2), ((64, 1), 4), ((243, 9), 3), ((4, 4, 4), 4), ((8, 16, 32), 8), ((27, 9, 3), 3),
     ((2, 2, 2), 2), ((32, 32, 32), 2), ((5, 25, 5), 5), ((16, 1, 8), 2),
+    # anisotropic shapes of the paper's experiments: n x 2 and n x 2 x 2
+    ((16384, 2), 2), ((65536, 2), 4), ((4096, 2, 2), 2), ((16384, 2, 2), 8), ((6561, 3), 3),
 ]
 
 
