@@ -6,7 +6,6 @@
 
 namespace pac {
 
-constexpr int kMaxRounds = 6;
 constexpr int kTileBytes = 32 * 1024;  // target data bytes of one tile
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }

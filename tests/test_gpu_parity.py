@@ -198,6 +198,33 @@ def test_shifted_delta_is_roll():
     assert oracle.rel_l2(y, np.roll(x, (5, 20), axis=(0, 1))) < 1e-13
 
 
+LARGE_GROUP_SHAPES = [((2187, 2187), 3, "c64"), ((3125, 3125), 5, "c64"), ((729, 81), 3, "c64"), ((625, 25), 5, "c64"),
+                ((2187, 9), 3, "c128"), ((3125, 5), 5, "c128"), ((27, 729), 3, "c64"), ((3, 2187), 3, "c128"),
+                ((25, 625), 5, "c128")]
+
+
+@pytest.mark.parametrize("dims,radix,dtype", LARGE_GROUP_SHAPES,
+                         ids=[f"{'x'.join(map(str, d))}-r{r}-{t}" for d, r, t in LARGE_GROUP_SHAPES])
+def test_large_groups_match_oracle(dims, radix, dtype):
+    """Large groups (729, 2187, 625, 3125 rows or lines; forward, fused and
+    inverse passes): the convolution against the oracle and the forward
+    transform against the DFT in index-reversed order."""
+    fs, h, x = separable_case(dims, dtype, seed=dims[0] + dims[-1])
+    ref = oracle.conv_separable(fs, x)
+    y = gpu_conv(dims, radix, dtype, h, x)
+    check(y, ref, dtype, int(np.prod(dims)), f"large group {dims}")
+    pac = pac_mod()
+    xu = pin.as_dtype(pin.complex_uniform(dims, 5), dtype)
+    plan = pac.Plan(dims, radix, dtype)
+    try:
+        stages = [plan.stages(a) for a in range(len(dims))]
+        xh = plan.forward_unordered(dev(xu))
+        torch.cuda.synchronize()
+        check(xh.cpu().numpy(), oracle.unordered_forward(xu, stages), dtype, xu.size, "large group A^T x")
+    finally:
+        plan.close()
+
+
 # ------------------------------------------------------- unordered transform
 
 
@@ -493,6 +520,46 @@ def test_queue_alone_and_in_the_mix_agree():
             dtype = p.dtype
             assert oracle.rel_l2(got, a) <= tol(dtype, got.size)
         assert all(lat > 0 for lat in lats)
+    finally:
+        for p in plans.values():
+            p.close()
+
+
+def test_served_workload_sample_matches_oracle():
+    """Requests drawn from the serving workload's recipe (1-D/2-D/3-D, radix 2
+    or 3, FP32 and FP64, Gaussian / exponential filters from the pool), kept
+    to at most 2^16 elements, pushed through the queue together; each result
+    is checked against the direct definition (O1) at 32 seeded points."""
+    pac = pac_mod()
+    reqs = pin.c5_requests(0.02, max_elems=1 << 16)[:32]
+    assert len(reqs) >= 16
+    pool = pin.c5_filter_pool()
+    plans, items = {}, []
+    try:
+        for i, r in enumerate(reqs):
+            c = r.conv
+            kind, param = pool[r.filter_id]
+            fs = pin.gaussian_factors(c.dims, param) if kind == "gauss" else pin.exponential_factors(c.dims, param)
+            h = pin.as_dtype(pin.outer(fs), c.dtype)
+            key = (c.dims, c.radix, c.dtype, r.filter_id)
+            if key not in plans:
+                p = pac.Plan(c.dims, c.radix, c.dtype)
+                p.filter_spectrum(dev(h))
+                plans[key] = p
+            x = pin.make_x(c)
+            xd = dev(x)
+            items.append((plans[key], c, h, x, xd, torch.empty_like(xd)))
+        q = pac.pac_queue_create(1 << 30, 8)
+        tickets = [pac.pac_submit(q, p.handle, xd, yd) for p, _, _, _, xd, yd in items]
+        pac.pac_queue_drain(q, 60000)
+        for t in tickets:
+            assert pac.pac_poll(q, t)[0] == pac.Status.OK
+        pac.pac_queue_destroy(q)
+        for i, (_, c, h, x, _, yd) in enumerate(items):
+            idx = pin.sample_points(c.n_total, 32, seed=900 + i)
+            ref = oracle.conv_direct_points(h, x, idx)
+            got = yd.cpu().numpy().reshape(-1)[idx]
+            assert oracle.rel_l2(got, ref) <= tol(c.dtype, c.n_total), f"request {i} {c.dims} {c.dtype}"
     finally:
         for p in plans.values():
             p.close()
