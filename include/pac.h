@@ -248,6 +248,9 @@ int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void* y_dev, vo
  * read from that file on first use and appended to it.  Allocates and frees
  * device memory (twice the problem) and synchronises the device.
  * best_us (may be NULL) receives the winner's median time per convolution.
+ * With PAC_TUNE=search in the environment, pac_plan_create tunes a problem
+ * the first time a plan is made for it.  PAC_LOG=1 makes every plan print
+ * its pass schedule (groups, plane pass) to stderr.
  */
 int pac_tune(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int reps, double* best_us);
 

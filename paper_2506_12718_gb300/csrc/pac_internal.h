@@ -38,7 +38,7 @@ struct Schedule {
 };
 int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out);
 // the tuned schedule for a problem, if pac_tune (or the tuning file) has one (tune.cu)
-void tuned_schedule(int ndim, const int64_t* dims, int radix, pac_dtype dtype, Schedule* out);
+bool tuned_schedule(int ndim, const int64_t* dims, int radix, pac_dtype dtype, Schedule* out);
 
 void set_error(const char* fmt, ...);
 int fail(int status, const char* fmt, ...);

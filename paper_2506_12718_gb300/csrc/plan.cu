@@ -230,10 +230,34 @@ static void free_plan(pac_plan p) {
     delete p;
 }
 
+// PAC_LOG=1 in the environment: each plan prints its pass schedule to stderr.
+static void log_plan(const pac_plan p) {
+    static const bool on = [] {
+        const char* e = std::getenv("PAC_LOG");
+        return e && e[0] != '0';
+    }();
+    if (!on) return;
+    std::fprintf(stderr, "pac: plan dims");
+    for (int a = 0; a < p->ndim; ++a) std::fprintf(stderr, " %lld", (long long)p->dims[a]);
+    std::fprintf(stderr, " radix %d %s cap %d:", p->radix, p->esize == 8 ? "c64" : "c128", p->schedule.cap);
+    for (const GroupPlan& g : p->groups) std::fprintf(stderr, " [axis %d M %d C %lld]", g.axis, g.M, (long long)g.C);
+    if (p->plane) std::fprintf(stderr, " plane %dx%d K=%d", p->groups[p->plane_g1].M, p->groups[p->plane_g1 + 1].M,
+                               p->plane_k);
+    std::fprintf(stderr, "\n");
+}
+
 extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, pac_plan* out) {
     Schedule sch;
-    tuned_schedule(ndim, dims, radix, dtype, &sch);
-    return plan_build(ndim, dims, radix, dtype, sch, out);
+    bool have = tuned_schedule(ndim, dims, radix, dtype, &sch);
+    // PAC_TUNE=search: tune a problem the first time a plan is made for it
+    const char* tune = std::getenv("PAC_TUNE");
+    if (!have && tune && std::strcmp(tune, "search") == 0 && ndim >= 1 && ndim <= 3 && dims) {
+        double us = 0;
+        if (pac_tune(ndim, dims, radix, dtype, 5, &us) == PAC_OK) tuned_schedule(ndim, dims, radix, dtype, &sch);
+    }
+    int rc = plan_build(ndim, dims, radix, dtype, sch, out);
+    if (rc == PAC_OK) log_plan(*out);
+    return rc;
 }
 
 namespace pac {

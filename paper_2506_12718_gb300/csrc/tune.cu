@@ -125,13 +125,15 @@ int time_plan(pac_plan p, void* x, void* y, int reps, double* us) {
 
 namespace pac {
 
-void tuned_schedule(int ndim, const int64_t* dims, int radix, pac_dtype dtype, Schedule* out) {
+bool tuned_schedule(int ndim, const int64_t* dims, int radix, pac_dtype dtype, Schedule* out) {
     *out = Schedule();
-    if (ndim < 1 || ndim > 3 || !dims) return;
+    if (ndim < 1 || ndim > 3 || !dims) return false;
     std::lock_guard<std::mutex> lk(g_mu);
     load_file_locked();
     auto it = g_tuned.find(make_key(ndim, dims, radix, dtype));
-    if (it != g_tuned.end()) *out = it->second.sch;
+    if (it == g_tuned.end()) return false;
+    *out = it->second.sch;
+    return true;
 }
 
 }  // namespace pac

@@ -473,6 +473,22 @@ def test_tune_file_round_trip(tmp_path):
     assert int(out.stdout.strip().splitlines()[-1]) == int(line[6])
 
 
+def test_tune_search_at_plan_creation_and_plan_log():
+    """PAC_TUNE=search tunes a problem when its first plan is made; PAC_LOG=1
+    prints the plan's pass schedule."""
+    import subprocess
+    import sys
+    env = dict(os.environ, PAC_TUNE="search", PAC_LOG="1")
+    env.pop("PAC_TUNE_FILE", None)
+    code = ("import paper_2506_12718_gb300 as pac; pac.load(); import torch; torch.cuda.init(); "
+            "p = pac.Plan((64, 64, 64), 2, 'c64'); print('cap', p.query(pac.Q_GROUP_CAP)); p.close()")
+    out = subprocess.run([sys.executable, "-c", code], env=env, check=True, capture_output=True, text=True,
+                         cwd=os.path.dirname(os.path.dirname(__file__)))
+    cap = int(out.stdout.strip().splitlines()[-1].split()[1])
+    assert cap >= 1  # a tuned schedule (an untuned plan reports 0)
+    assert "pac: plan dims 64 64 64 radix 2 c64" in out.stderr
+
+
 def _queue_setup(n_req=24):
     pac = pac_mod()
     shapes = [((4096,), 2), ((81, 81), 3), ((32, 32, 32), 2), ((125, 25), 5), ((1024,), 4)]
