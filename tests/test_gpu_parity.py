@@ -173,6 +173,61 @@ def test_nonseparable_direct(dims, radix, dtype):
     check(y, oracle.conv_direct(h, x), dtype, int(np.prod(dims)))
 
 
+MAX_SHAPES = [((1 << 28,), 4, "c64"), ((16384, 16384), 2, "c64"), ((512, 512, 512), 8, "c64"),
+              ((1 << 27,), 2, "c128"), ((59049, 2187), 3, "c64")]
+
+
+@pytest.mark.parametrize("dims,radix,dtype", MAX_SHAPES,
+                         ids=[f"{'x'.join(map(str, d))}-r{r}-{t}" for d, r, t in MAX_SHAPES])
+def test_maximum_sizes_sampled(dims, radix, dtype):
+    """The largest arrays a plan takes (N up to 2^28, offsets near the 32-bit
+    limit of the kernels), checked at 6 seeded output points against the
+    direct definition (O1); inputs generated on the device from a seed."""
+    pac = pac_mod()
+    n = int(np.prod(dims))
+    real = torch.float32 if dtype == "c64" else torch.float64
+    g = torch.Generator(device="cuda")
+    g.manual_seed(n % 1000003)
+    x = torch.view_as_complex(torch.rand(*dims, 2, generator=g, device="cuda", dtype=real) * 2 - 1)
+    h = torch.view_as_complex(torch.rand(*dims, 2, generator=g, device="cuda", dtype=real) * 2 - 1)
+    plan = pac.Plan(dims, radix, dtype)
+    try:
+        plan.filter_spectrum(h)
+        y = plan.convolve(x)
+        torch.cuda.synchronize()
+        idx = pin.sample_points(n, 6, seed=n % 7919)
+        ref = oracle.conv_direct_points(h.cpu().numpy(), x.cpu().numpy(), idx)
+        got = y.reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
+        err = oracle.rel_l2(got, ref)
+        assert err <= tol(dtype, n), f"{dims}: rel_l2 {err:.3e}"
+    finally:
+        plan.close()
+        del x, h
+        torch.cuda.empty_cache()
+
+
+def test_empty_batch_and_n1_in_batch():
+    pac = pac_mod()
+    pac.pac_convolve_many([], [], [])  # nothing to do
+    p1 = pac.Plan((1,), 2, "c128")
+    p2 = pac.Plan((64,), 4, "c128")
+    try:
+        h1 = torch.tensor([2.0 - 1.0j], dtype=torch.complex128, device="cuda")
+        x1 = torch.tensor([0.5 + 3.0j], dtype=torch.complex128, device="cuda")
+        p1.filter_spectrum(h1)
+        fs, h2, x2 = separable_case((64,), "c128", 3)
+        p2.filter_spectrum(dev(h2))
+        x2d = dev(x2)
+        y1, y2 = torch.empty_like(x1), torch.empty_like(x2d)
+        pac.pac_convolve_many([p1.handle, p2.handle], [x1, x2d], [y1, y2])
+        torch.cuda.synchronize()
+        assert abs(y1.item() - (2.0 - 1.0j) * (0.5 + 3.0j)) < 1e-15
+        check(y2.cpu().numpy(), oracle.conv_separable(fs, x2), "c128", 64, "batch with N = 1")
+    finally:
+        p1.close()
+        p2.close()
+
+
 def test_single_element():
     h = np.array([2.0 - 1.0j], np.complex128)
     x = np.array([0.5 + 3.0j], np.complex128)
