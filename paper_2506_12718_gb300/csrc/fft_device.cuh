@@ -373,14 +373,6 @@ template <typename GEO> __device__ __forceinline__ void round_sync() {
 enum : int { kFromSmem = 0, kFromNatural = 1, kFromPlaced = 2 };
 enum : int { kToSmem = 0, kToNatural = 1, kToPlaced = 2 };
 
-// One round of a tile.  SRC: shared memory, natural global rows, or global
-// rows in the pass' output placement (row r of the tile's rounds holds the
-// data of global row r2g[r]).  Forward: DFT_R, then w_S^{jp k} (SP > 1).
-// Inverse (adjoint): conj twiddles, then the conjugate DFT.  MUL (the last
-// forward round of a fused pass): DFT, product with the filter spectrum at
-// the same global position, conjugate DFT.  DST as SRC; a placed store also
-// applies w_L^{j k'} and the scale, a placed load (first inverse round) the
-// conjugate w_L^{j k'}.
 // Global position of a task's column: offset of its row 0, external-twiddle
 // column, and whether the column exists.
 struct TaskCol {
@@ -740,11 +732,11 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, size
 //
 // Plane pass: the last group of axis d-2 (n1 = its size M1; it never carries
 // an external twiddle) and the single group of axis d-1 (M2) for whole
-// M1 x M2 planes in one CTA's shared memory.  Axis d-1 forward (first round from global, lines
-// coalesced), axis d-2 forward with the product in its last round, axis d-2
-// inverse, axis d-1 inverse (last round to global): the convolution of the
-// two innermost axes in one pass, so a 3-D convolution takes 3 passes and a
-// 2-D one a single launch.
+// M1 x M2 planes in one CTA's shared memory.  Axis d-1 forward (first round
+// from global, lines coalesced), axis d-2 forward with the product in its
+// last round, axis d-2 inverse, axis d-1 inverse (last round to global): the
+// convolution of the two innermost axes in one pass, so a 3-D convolution
+// takes 3 passes and a 2-D one a single launch.
 
 // K = 1: one CTA per plane.  K > 1: a cluster of K CTAs per plane, CTA k
 // holding plane rows [k n1/K, (k+1) n1/K) (its own lines of axis d-1) and,
