@@ -52,7 +52,7 @@ def parse_args(argv=None):
     ap.add_argument("--quick", action="store_true", help="main leg only (for profiler runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
-    ap.add_argument("--legs", default="configs,batched,served",
+    ap.add_argument("--legs", default="configs,batched,served",  # "none": the main leg only
                     help="extra legs after the main one: configs (every workload shape, dtype and radix, "
                          "with its permuted form and cuFFT), batched (4096 mixed convolutions in one call), "
                          "served (Poisson request stream through the queue)")
@@ -302,7 +302,8 @@ def reference_arm(a):
 def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
     """Every single-convolution workload: 1-D 2^10 FP64 radix 2; 3-D 128^3
     radix 2/4/8 FP32 and FP64; 2-D 2187^2 radix 3 and 3125^2 radix 5, FP32
-    and FP64.  Each: GB/s of 3 N S, the permuted form and cuFFT on the same
+    and FP64; mixed radix (2^a 3^b 5^c) 2-D 1000^2 and 6000^2 and 3-D 120^3,
+    FP32.  Each: GB/s of 3 N S, the permuted form and cuFFT on the same
     GPU, launches per convolution and the pass schedule (autotuned unless
     --no-tune).  Inputs of each workload's recipe, generated on the device
     from a seed (x: re, im N(0,1) or U[-1,1]; the workload's filter)."""
@@ -310,7 +311,7 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
     fma_peak = {dt: pac.pac_measure_fma_peak(dt) for dt in ("c64", "c128")}
     # algorithmic flops per convolution: 2 c_r N log2 N + 6 N, c_r = 5, 4.25, 4.08 for
     # radix 2, 4, 8 (the paper's per-transform counts); 5.9 for radix 3 and 5 (estimates)
-    c_r = {2: 5.0, 4: 4.25, 8: 4.08, 3: 5.9, 5: 5.9}
+    c_r = {2: 5.0, 4: 4.25, 8: 4.08, 3: 5.9, 5: 5.9, 0: 5.0}  # 0: mixed radix, taken as radix 2's
     cases = [(pin.c1(), "1-D n=2^10, radix 2, complex FP64")]
     for dt in ("c64", "c128"):
         for r in (2, 4, 8):
@@ -319,6 +320,10 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
         for r in (3, 5):
             c = pin.c3(r, dt)
             cases.append((c, f"2-D {c.dims[0]}^2, radix {r}, complex {'FP32' if dt == 'c64' else 'FP64'}"))
+    # mixed radix (Section 6.1): 1000 = 2^3 5^3, 6000 = 2^4 3 5^3, 120 = 2^3 3 5
+    cases.append((pin.mixed((1000, 1000)), "2-D 1000^2, mixed radix 2^3 5^3, complex FP32"))
+    cases.append((pin.mixed((6000, 6000)), "2-D 6000^2, mixed radix 2^4 3 5^3, complex FP32"))
+    cases.append((pin.mixed((120, 120, 120)), "3-D 120^3, mixed radix 2^3 3 5, complex FP32"))
     sh = stream.cuda_stream
     for c, name in cases:
         N, S = c.n_total, c.elem_bytes

@@ -56,7 +56,7 @@ typedef enum {
     PAC_OK = 0,
     PAC_PENDING = 1,          /* pac_poll: request not finished yet */
     PAC_ERR_ARG = -1,         /* null pointer, bad enum, misaligned pointer */
-    PAC_ERR_SIZE = -2,        /* a dim is not a power of the radix's prime, or too large */
+    PAC_ERR_SIZE = -2,        /* a dim does not fit the radix or stage list, or is too large */
     PAC_ERR_NO_SPECTRUM = -3, /* pac_convolve before pac_filter_spectrum */
     PAC_ERR_NOMEM = -4,       /* device or host allocation failed / over budget */
     PAC_ERR_CUDA = -5,        /* a CUDA runtime call failed */
@@ -69,24 +69,45 @@ typedef enum {
 
 /*
  * Create a plan for d-D convolutions of shape dims[0] x ... x dims[ndim-1].
- * ndim in {1,2,3}; radix in {2,3,4,5,8}.  Each dim must be a power of the
- * radix's prime p (p = 2 for radix 4 and 8).  The per-axis decimation-in-
- * frequency stage list is [r, r, ..., r] (Section 2.1); when the exponent is
- * not a multiple of log_p r the leftover factor becomes one smaller stage of
- * base p placed last (e.g. 128 with radix 4 -> [4,4,4,2]; with radix 8 ->
- * [8,8,2]), the mixed-radix framework of Section 6.1.  A dim of 1 is allowed
- * (empty stage list).  Builds twiddle tables in FP64, rounds them once to
- * dtype and uploads them to the current device.  On success *out owns device
- * memory until pac_plan_destroy.  Errors: PAC_ERR_ARG, PAC_ERR_SIZE,
- * PAC_ERR_NOMEM, PAC_ERR_CUDA.
+ * ndim in {1,2,3}; radix in {0,2,3,4,5,8}.  For radix r != 0 each dim must
+ * be a power of the radix's prime p (p = 2 for radix 4 and 8).  The per-axis
+ * decimation-in-frequency stage list is [r, r, ..., r] (Section 2.1); when
+ * the exponent is not a multiple of log_p r the leftover factor becomes one
+ * smaller stage of base p placed last (e.g. 128 with radix 4 -> [4,4,4,2];
+ * with radix 8 -> [8,8,2]), the mixed-radix framework of Section 6.1.
+ * radix 0 (mixed radix, Section 6.1): each dim is any 2^a 3^b 5^c, with the
+ * stage list [4,..,4,(2), 3,..,3, 5,..,5] (the factor 2^a in radix-4 stages,
+ * a leftover 2 last, then the 3s and the 5s).  A dim of 1 is allowed (empty
+ * stage list).  Builds twiddle tables in FP64, rounds them once to dtype and
+ * uploads them to the current device.  On success *out owns device memory
+ * until pac_plan_destroy.  Errors: PAC_ERR_ARG, PAC_ERR_SIZE, PAC_ERR_NOMEM,
+ * PAC_ERR_CUDA.
  */
 int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, pac_plan* out);
+
+/*
+ * The same from explicit per-axis DIF stage lists, in any order (the
+ * mixed-radix framework of Section 6.1: A_rho with rho the list reversed,
+ * so stages[0] of an axis acts first, on the full length).  nstages[a]
+ * stages for axis a, concatenated in `stages` (host memory, read only
+ * during the call).  Each stage is a power of 2, 3 or 5 in [2, 32]; the
+ * stages of axis a multiply to dims[a] (nstages[a] = 0 for a dim of 1).
+ * The unordered transform (pac_forward_unordered) leaves frequency
+ * k = k_1 + s_1 k_2 + s_1 s_2 k_3 + ... at position
+ * sum_i k_i prod_{j>i} s_j of each axis.  Stages of one prime base that are
+ * adjacent run in one pass; each change of base starts a new pass.  Such
+ * plans are not autotuned.  Errors: PAC_ERR_ARG (ndim, null pointers, more
+ * than 64 stages), PAC_ERR_SIZE (a stage or product rule broken), as
+ * pac_plan_create otherwise.
+ */
+int pac_plan_create_stages(int ndim, const int64_t* dims, const int* nstages, const int* stages, pac_dtype dtype,
+                           pac_plan* out);
 
 /* Release a plan and everything it owns. Waits for the plan's pending work. */
 int pac_plan_destroy(pac_plan p);
 
 /*
- * Algorithm 11, line 1: store Hhat = A^T h / N (all axes, with the
+ * The filter-spectrum step of Algorithm 11: store Hhat = A^T h / N (all axes, with the
  * inverse's 1/N folded in) in plan-owned device memory, in the order the
  * fused forward/product/inverse pass reads it.
  * h_dev is read, not retained.  Synchronises the plan's internal stream.
@@ -95,7 +116,7 @@ int pac_plan_destroy(pac_plan p);
 int pac_filter_spectrum(pac_plan p, const void* h_dev);
 
 /*
- * Algorithm 11, lines 2-4 (permutation-avoiding convolution, Eq. 35/80):
+ * The convolution of Algorithm 11 (permutation-avoiding, Eq. 35/80):
  * y = conj(A)((A^T x) o Hhat).  x_dev and y_dev hold N elements of the plan's
  * dtype; y_dev may equal x_dev (in place).  y_dev is also the working buffer
  * of the intermediate passes.  Asynchronous on `stream`.
@@ -280,7 +301,8 @@ enum {
  */
 int pac_measure_fma_peak(int dtype, double* gflops);
 
-/* Host-only helpers (no device needed): the stage list and reversal table rules. */
+/* Host-only helpers (no device needed): the stage list of pac_plan_create
+ * (radix 0 included) and the reversal table of a stage list. */
 int pac_stage_list(int64_t n, int radix, int* radices, int* count);
 int pac_reverse_table(int nstages, const int* radices, int64_t* pos_to_freq);
 

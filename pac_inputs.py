@@ -168,6 +168,12 @@ def c3(radix: int = 3, dtype: str = "c64") -> Conv:
     return Conv((n, n), radix, dtype, "uniform", "exp", seed=3, h_param=20.0)
 
 
+def mixed(dims=(1000, 1000), dtype: str = "c64") -> Conv:
+    """Mixed-radix shapes, every dim 2^a 3^b 5^c (radix 0), with c3's recipe
+    (x ~ U[-1,1], separable exponential of length 20), seed 6."""
+    return Conv(tuple(int(d) for d in dims), 0, dtype, "uniform", "exp", seed=6, h_param=20.0)
+
+
 # Size classes of the batched workload: 1-D {2^8..2^16} (9 classes),
 # 1-D {3^5..3^10} (6 classes) and 2-D {2^6..2^10}^2 (5 classes).
 C4_CLASSES = ([((2 ** e,), 2) for e in range(8, 17)]

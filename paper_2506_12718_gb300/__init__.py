@@ -43,6 +43,8 @@ Q_NDIM, Q_N_TOTAL, Q_ELEM_BYTES, Q_LAUNCHES_CONVOLVE, Q_LAUNCHES_PERMUTED, Q_LAU
 _vp, _i64, _i32, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64
 _SIGS = {
     "pac_plan_create": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, ctypes.POINTER(_vp)]),
+    "pac_plan_create_stages": (_i32, [_i32, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int), _i32, ctypes.POINTER(_vp)]),
     "pac_plan_destroy": (_i32, [_vp]),
     "pac_filter_spectrum": (_i32, [_vp, _vp]),
     "pac_convolve": (_i32, [_vp, _vp, _vp, _vp]),
@@ -159,6 +161,19 @@ def pac_plan_create(ndim: int, dims, radix: int, dtype: int) -> int:
     d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
     out = ctypes.c_void_p()
     _check(load().pac_plan_create(int(ndim), d, int(radix), int(dtype), ctypes.byref(out)))
+    return out.value
+
+
+def pac_plan_create_stages(dims, stages_per_axis, dtype: int) -> int:
+    vals = [int(v) for v in dims]
+    if len(stages_per_axis) != len(vals):
+        raise ValueError("one stage list per axis")
+    d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
+    counts = (ctypes.c_int * max(1, len(vals)))(*[len(st) for st in stages_per_axis])
+    flat = [int(r) for st in stages_per_axis for r in st]
+    arr = (ctypes.c_int * max(1, len(flat)))(*flat)
+    out = ctypes.c_void_p()
+    _check(load().pac_plan_create_stages(len(vals), d, counts, arr, int(dtype), ctypes.byref(out)))
     return out.value
 
 
@@ -294,11 +309,17 @@ def pac_queue_destroy(queue: int) -> None:
 class Plan:
     """A convolution plan bound to torch tensors (complex64 / complex128, on CUDA)."""
 
-    def __init__(self, dims, radix: int, dtype: str = "c64"):
+    def __init__(self, dims, radix: int, dtype: str = "c64", stages=None):
+        """radix in {2,3,4,5,8}, or 0 for mixed radix (dims 2^a 3^b 5^c); or
+        explicit per-axis DIF stage lists `stages` (radix is then ignored)."""
         self.dims = tuple(int(d) for d in dims)
-        self.radix = int(radix)
+        self.radix = int(radix) if stages is None else -1
         self.dtype = dtype
-        self.handle = pac_plan_create(len(self.dims), self.dims, self.radix, C64 if dtype == "c64" else C128)
+        code = C64 if dtype == "c64" else C128
+        if stages is None:
+            self.handle = pac_plan_create(len(self.dims), self.dims, self.radix, code)
+        else:
+            self.handle = pac_plan_create_stages(self.dims, [list(st) for st in stages], code)
 
     def _tensor_check(self, t, name):
         import torch

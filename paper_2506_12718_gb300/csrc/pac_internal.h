@@ -37,6 +37,9 @@ struct Schedule {
     bool plane = true;
 };
 int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out);
+// the same from explicit per-axis DIF stage lists (radix: the label the plan reports; -1 = explicit)
+int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vector<int>>& stages, int radix,
+                      pac_dtype dtype, const Schedule& sch, pac_plan* out);
 // the tuned schedule for a problem, if pac_tune (or the tuning file) has one (tune.cu)
 bool tuned_schedule(int ndim, const int64_t* dims, int radix, pac_dtype dtype, Schedule* out);
 

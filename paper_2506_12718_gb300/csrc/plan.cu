@@ -102,12 +102,40 @@ static int exact_log(int64_t n, int p) {
     return n == 1 ? e : -1;
 }
 
-// DIF stage list of an axis: [r]*(e/f) then a leftover stage p^(e mod f).
+// Prime base of a stage radix (a power of 2, 3 or 5 that a kernel round
+// takes whole), 0 for anything else.
+static int stage_base(int r) {
+    if (r < 2 || r > 32) return 0;
+    for (int p : {2, 3, 5})
+        if (exact_log(r, p) >= 1) return p;
+    return 0;
+}
+
+// DIF stage list of an axis.  radix in {2,3,4,5,8}: [r]*(e/f) then a
+// leftover stage p^(e mod f).  radix 0, the mixed-radix framework of
+// Section 6.1 for n = 2^a 3^b 5^c: the factor 2^a as radix-4 stages (a
+// leftover 2 last), then b stages of 3, then c stages of 5.
 static int stage_list(int64_t n, int radix, std::vector<int>& out) {
     out.clear();
-    const int p = prime_of(radix);
-    if (p == 0) return fail(PAC_ERR_ARG, "radix %d not in {2,3,4,5,8}", radix);
     if (n < 1) return fail(PAC_ERR_SIZE, "dimension %lld < 1", (long long)n);
+    if (radix == 0) {
+        int64_t m = n;
+        int e[3] = {0, 0, 0};
+        const int ps[3] = {2, 3, 5};
+        for (int i = 0; i < 3; ++i)
+            while (m % ps[i] == 0) {
+                m /= ps[i];
+                ++e[i];
+            }
+        if (m != 1) return fail(PAC_ERR_SIZE, "dimension %lld is not of the form 2^a 3^b 5^c", (long long)n);
+        for (int i = 0; i < e[0] / 2; ++i) out.push_back(4);
+        if (e[0] % 2) out.push_back(2);
+        for (int i = 0; i < e[1]; ++i) out.push_back(3);
+        for (int i = 0; i < e[2]; ++i) out.push_back(5);
+        return PAC_OK;
+    }
+    const int p = prime_of(radix);
+    if (p == 0) return fail(PAC_ERR_ARG, "radix %d not in {0,2,3,4,5,8}", radix);
     const int e = exact_log(n, p);
     if (e < 0) return fail(PAC_ERR_SIZE, "dimension %lld is not a power of %d (radix %d)", (long long)n, p, radix);
     const int f = exact_log(radix, p);
@@ -133,23 +161,23 @@ static void reverse_table(const int* st, int T, int64_t* p2f) {
     }
 }
 
-// Split an axis' stage list into consecutive groups with product <= the
-// largest column one CTA handles (or p^cap, a schedule's cap), balanced in size.
-static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st, int p, int esize, int cap) {
-    std::vector<std::pair<int, int>> out;
-    const int T = (int)st.size();
-    if (T == 0) return out;
-    std::vector<int> ex(T);
+// Split stages [lo, hi) of an axis' stage list, all of prime base p, into
+// consecutive groups with product <= the largest column one CTA handles (or
+// p^cap, a schedule's cap), balanced in size.
+static void split_run(const std::vector<int>& st, int lo, int hi, int p, int esize, int cap,
+                      std::vector<std::pair<int, int>>& out) {
+    const int T = hi;
+    std::vector<int> ex(T, 0);
     int etot = 0;
-    for (int i = 0; i < T; ++i) {
+    for (int i = lo; i < T; ++i) {
         ex[i] = exact_log(st[i], p);
         etot += ex[i];
     }
     int emax = exact_log(group_mmax(p, esize), p);
     if (cap > 0 && cap < emax) emax = cap;  // a schedule's smaller group cap (more, smaller passes)
-    for (int i = 0; i < T; ++i) emax = std::max(emax, ex[i]);  // a single stage is never split
+    for (int i = lo; i < T; ++i) emax = std::max(emax, ex[i]);  // a single stage is never split
     int ngroups = (etot + emax - 1) / emax;
-    int i = 0, erem = etot;
+    int i = lo, erem = etot;
     for (int gi = 0; gi < ngroups && i < T; ++gi) {
         const int target = (erem + (ngroups - gi) - 1) / (ngroups - gi);
         int acc = 0, first = i;
@@ -166,6 +194,22 @@ static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st,
     while (i < T) {  // defensive: any leftover becomes one more group
         out.push_back({i, T - i});
         i = T;
+    }
+}
+
+// Groups of an axis' stage list: a group holds stages of one prime base (a
+// CTA's in-register rounds take one base), so each maximal run of equal
+// base is split on its own (one run for a uniform radix).
+static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st, int esize, int cap) {
+    std::vector<std::pair<int, int>> out;
+    const int T = (int)st.size();
+    int i = 0;
+    while (i < T) {
+        const int p = stage_base(st[i]);
+        int j = i;
+        while (j < T && stage_base(st[j]) == p) ++j;
+        split_run(st, i, j, p, esize, cap, out);
+        i = j;
     }
     return out;
 }
@@ -260,15 +304,60 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
     return rc;
 }
 
+extern "C" int pac_plan_create_stages(int ndim, const int64_t* dims, const int* nstages, const int* stages,
+                                      pac_dtype dtype, pac_plan* out) {
+    if (!out) return fail(PAC_ERR_ARG, "null out");
+    *out = nullptr;
+    if (ndim < 1 || ndim > 3 || !dims || !nstages) return fail(PAC_ERR_ARG, "ndim must be 1, 2 or 3");
+    std::vector<std::vector<int>> st(ndim);
+    int at = 0;
+    for (int a = 0; a < ndim; ++a) {
+        if (nstages[a] < 0 || nstages[a] > 64) return fail(PAC_ERR_ARG, "axis %d: %d stages", a, nstages[a]);
+        if (nstages[a] > 0 && !stages) return fail(PAC_ERR_ARG, "null stages");
+        st[a].assign(stages + at, stages + at + nstages[a]);
+        at += nstages[a];
+    }
+    int rc = plan_build_stages(ndim, dims, st, -1, dtype, Schedule(), out);
+    if (rc == PAC_OK) log_plan(*out);
+    return rc;
+}
+
 namespace pac {
 
 int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out) {
     if (!out) return fail(PAC_ERR_ARG, "null out");
     *out = nullptr;
     if (ndim < 1 || ndim > 3 || !dims) return fail(PAC_ERR_ARG, "ndim must be 1, 2 or 3");
+    if (radix != 0 && prime_of(radix) == 0) return fail(PAC_ERR_ARG, "radix %d not in {0,2,3,4,5,8}", radix);
+    std::vector<std::vector<int>> st(ndim);
+    for (int a = 0; a < ndim; ++a) {
+        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
+            return fail(PAC_ERR_SIZE, "dimension %lld out of range", (long long)dims[a]);
+        int rc = stage_list(dims[a], radix, st[a]);
+        if (rc) return rc;
+    }
+    return plan_build_stages(ndim, dims, st, radix, dtype, sch, out);
+}
+
+int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vector<int>>& stages, int radix,
+                      pac_dtype dtype, const Schedule& sch, pac_plan* out) {
+    if (!out) return fail(PAC_ERR_ARG, "null out");
+    *out = nullptr;
+    if (ndim < 1 || ndim > 3 || !dims || (int)stages.size() != ndim) return fail(PAC_ERR_ARG, "ndim must be 1, 2 or 3");
     if (dtype != PAC_C64 && dtype != PAC_C128) return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
-    const int p = prime_of(radix);
-    if (p == 0) return fail(PAC_ERR_ARG, "radix %d not in {2,3,4,5,8}", radix);
+    for (int a = 0; a < ndim; ++a) {
+        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
+            return fail(PAC_ERR_SIZE, "dimension %lld out of range", (long long)dims[a]);
+        int64_t prod = 1;
+        for (int r : stages[a]) {
+            if (stage_base(r) == 0)
+                return fail(PAC_ERR_SIZE, "stage %d of axis %d is not a power of 2, 3 or 5 in [2, 32]", r, a);
+            prod *= r;
+            if (prod > dims[a]) break;
+        }
+        if (prod != dims[a])
+            return fail(PAC_ERR_SIZE, "the stages of axis %d do not multiply to %lld", a, (long long)dims[a]);
+    }
 
     pac_plan pl = new (std::nothrow) pac_plan_s();
     if (!pl) return fail(PAC_ERR_NOMEM, "host allocation failed");
@@ -279,24 +368,15 @@ int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const 
     pl->N = 1;
     for (int a = 0; a < ndim; ++a) {
         pl->dims[a] = dims[a];
-        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30)) {
-            delete pl;
-            return fail(PAC_ERR_SIZE, "dimension %lld out of range", (long long)dims[a]);
-        }
         pl->N *= dims[a];
     }
     if (pl->N >= (int64_t(1) << 31)) {
         delete pl;
         return fail(PAC_ERR_SIZE, "N = %lld too large", (long long)pl->N);
     }
-    pl->stages.resize(ndim);
+    pl->stages = stages;
     pl->pos_to_freq.resize(ndim);
     for (int a = 0; a < ndim; ++a) {
-        int rc = stage_list(dims[a], radix, pl->stages[a]);
-        if (rc) {
-            delete pl;
-            return rc;
-        }
         pl->pos_to_freq[a].resize(dims[a]);
         reverse_table(pl->stages[a].data(), (int)pl->stages[a].size(), pl->pos_to_freq[a].data());
     }
@@ -307,7 +387,7 @@ int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const 
         int64_t inner = 1;
         for (int b = a + 1; b < ndim; ++b) inner *= dims[b];
         int64_t Lcur = dims[a];
-        for (auto [first, cnt] : split_groups(pl->stages[a], p, pl->esize, sch.cap)) {
+        for (auto [first, cnt] : split_groups(pl->stages[a], pl->esize, sch.cap)) {
             GroupPlan g;
             g.axis = a;
             g.first_stage = first;
@@ -324,10 +404,23 @@ int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const 
                 delete pl;
                 return fail(PAC_ERR_SIZE, "no pass kernel for group size %d", g.M);
             }
-            // two-level split of the external exponent: T = p^ceil(e/2)
-            const int eL = exact_log(g.L, p);
-            g.tw_T = ipow(p, (eL + 1) / 2);
-            g.tw_shift = (p == 2) ? (eL + 1) / 2 : -1;
+            // two-level split of the external exponent e = hi T + lo: T = p^ceil(e/2)
+            // when L = p^e, else (mixed radix) T = ceil(sqrt(L))
+            g.tw_T = 0;
+            for (int q : {2, 3, 5}) {
+                const int eL = exact_log(g.L, q);
+                if (eL >= 0) {
+                    g.tw_T = ipow(q, (eL + 1) / 2);
+                    g.tw_shift = (q == 2) ? (eL + 1) / 2 : -1;
+                    break;
+                }
+            }
+            if (g.tw_T == 0) {
+                int64_t T = (int64_t)std::sqrt((double)g.L);
+                while (T * T < g.L) ++T;
+                g.tw_T = (int)T;
+                g.tw_shift = -1;
+            }
             g.off_twi = off;
             off = align16(off + (size_t)g.M * pl->esize);
             if (g.has_ext) {
@@ -627,7 +720,7 @@ static cudaError_t timed_permute(pac_plan p, const int64_t* const* idx, const vo
     return e;
 }
 
-// Algorithm 11, lines 2-4, on device pointers: forward groups (the last fused
+// The convolution of Algorithm 11 on device pointers: forward groups (the last fused
 // with the product and the first inverse group), then the inverse groups.
 int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s, bool allow_single) {
     const int G = (int)p->groups.size();
@@ -642,7 +735,7 @@ int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s, bool allow_
     return run_steps(p, steps, s, allow_single);
 }
 
-// Algorithm 11, lines 2-4, as a pass sequence: forward groups (the last fused
+// The convolution of Algorithm 11 as a pass sequence: forward groups (the last fused
 // with the product and the first inverse group), then the inverse groups.
 // With a plane pass, the groups of the last two axes are one step.
 void convolve_steps(pac_plan p, const void* x, void* y, std::vector<Step>& steps) {

@@ -44,6 +44,9 @@ def test_version():
 @pytest.mark.parametrize("n,radix,want", [
     (128, 2, [2] * 7), (128, 4, [4, 4, 4, 2]), (128, 8, [8, 8, 2]), (1024, 4, [4] * 5),
     (2187, 3, [3] * 7), (3125, 5, [5] * 5), (64, 8, [8, 8]), (2, 8, [2]), (1, 2, []), (32, 4, [4, 4, 2]),
+    # radix 0: mixed radix (Section 6.1), 2^a as radix-4 stages (a leftover 2 last), then 3s, then 5s
+    (1000, 0, [4, 2, 5, 5, 5]), (360, 0, [4, 2, 3, 3, 5]), (128, 0, [4, 4, 4, 2]), (81, 0, [3] * 4),
+    (30, 0, [2, 3, 5]), (1, 0, []), (5, 0, [5]), (6000, 0, [4, 4, 3, 5, 5, 5]),
 ])
 def test_stage_list(n, radix, want):
     assert pac.pac_stage_list(n, radix) == want
@@ -51,7 +54,8 @@ def test_stage_list(n, radix, want):
 
 @pytest.mark.parametrize("n,radix,status", [
     (100, 2, pac.Status.ERR_SIZE), (96, 4, pac.Status.ERR_SIZE), (243, 2, pac.Status.ERR_SIZE),
-    (64, 6, pac.Status.ERR_ARG), (64, 0, pac.Status.ERR_ARG), (0, 2, pac.Status.ERR_SIZE),
+    (64, 6, pac.Status.ERR_ARG), (64, 7, pac.Status.ERR_ARG), (0, 2, pac.Status.ERR_SIZE),
+    (7, 0, pac.Status.ERR_SIZE), (14, 0, pac.Status.ERR_SIZE), (0, 0, pac.Status.ERR_SIZE),
 ])
 def test_stage_list_errors(n, radix, status):
     with pytest.raises(pac.PacError) as ei:
@@ -61,7 +65,8 @@ def test_stage_list_errors(n, radix, status):
 
 
 STAGE_LISTS = [[2] * 7, [4, 4, 4, 2], [8, 8, 2], [3] * 7, [5] * 5, [2, 4, 4, 4], [2, 8, 8], [2, 3, 4],
-               [4] * 5, [8] * 4, [3, 3], [16, 4], [2]]
+               [4] * 5, [8] * 4, [3, 3], [16, 4], [2], [4, 2, 5, 5, 5], [4, 2, 3, 3, 5], [5, 2, 5, 4, 5],
+               [3, 5, 2, 3], [5, 3, 4]]
 
 
 @pytest.mark.parametrize("stages", STAGE_LISTS)
@@ -85,6 +90,26 @@ def test_plan_create_without_gpu_fails_cleanly():
     with pytest.raises(pac.PacError) as ei:
         pac.pac_plan_create(1, [64], 2, pac.C64)
     assert ei.value.status in (pac.Status.ERR_CUDA, pac.Status.ERR_NOMEM)
+
+
+@pytest.mark.parametrize("dims,stages,status", [
+    ([12], [[2, 3]], pac.Status.ERR_SIZE),          # product 6, not 12
+    ([14], [[2, 7]], pac.Status.ERR_SIZE),          # 7 is no stage
+    ([12], [[6, 2]], pac.Status.ERR_SIZE),          # 6 is not a prime power
+    ([64], [[64]], pac.Status.ERR_SIZE),            # a stage above 32
+    ([4, 6], [[4], []], pac.Status.ERR_SIZE),       # an empty list for a dim > 1
+    ([2, 2, 2, 2], [[2]] * 4, pac.Status.ERR_ARG),  # ndim 4
+    ([0], [[]], pac.Status.ERR_SIZE),
+])
+def test_plan_create_stages_rejects_bad_lists_before_touching_the_device(dims, stages, status):
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_plan_create_stages(dims, stages, pac.C64)
+    assert ei.value.status == status
+
+
+def test_plan_create_stages_wants_one_list_per_axis():
+    with pytest.raises(ValueError):
+        pac.pac_plan_create_stages([4, 6], [[4]], pac.C64)
 
 
 def test_plan_create_rejects_bad_arguments_before_touching_the_device():

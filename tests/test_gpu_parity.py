@@ -335,6 +335,123 @@ def test_ordered_fft_is_the_dft(dims, radix, dtype):
         plan.close()
 
 
+# ------------------------------------------------------------- mixed radix
+
+MIXED_SHAPES = [((30,), "c128"), ((360,), "c64"), ((1000,), "c128"), ((2700,), "c64"), ((6000,), "c64"),
+                ((12, 20), "c128"), ((60, 90), "c64"), ((100, 120), "c128"), ((250, 48), "c64"), ((1, 45), "c64"),
+                ((6, 10, 15), "c128"), ((12, 20, 30), "c64"), ((40, 36, 50), "c64"), ((96, 2, 2), "c128"),
+                ((1000, 1000), "c64")]
+
+
+@pytest.mark.parametrize("dims,dtype", MIXED_SHAPES, ids=[f"{'x'.join(map(str, d))}-{t}" for d, t in MIXED_SHAPES])
+def test_mixed_radix_plans(dims, dtype):
+    """radix 0, n = 2^a 3^b 5^c per axis (Section 6.1): one pass per run of one
+    prime base, external twiddles of non-prime-power lengths; the
+    convolution against the oracle."""
+    fs, h, x = separable_case(dims, dtype, seed=sum(dims))
+    y = gpu_conv(dims, 0, dtype, h, x)
+    check(y, oracle.conv_separable(fs, x), dtype, int(np.prod(dims)), f"mixed {dims}")
+
+
+STAGE_ORDERS = [((60,), [[3, 4, 5]], "c128"), ((60,), [[5, 3, 2, 2]], "c128"), ((1000,), [[5, 2, 5, 4, 5]], "c64"),
+                ((120, 90), [[2, 3, 4, 5], [3, 5, 2, 3]], "c64"), ((18, 20, 24), [[3, 2, 3], [5, 4], [4, 3, 2]], "c128"),
+                ((1024,), [[2] * 10], "c64"), ((72, 1), [[2, 3, 4, 3], []], "c128"), ((25, 27), [[5, 5], [3, 9]], "c64"),
+                ((64, 48), [[16, 4], [16, 3]], "c64")]
+
+
+@pytest.mark.parametrize("dims,stages,dtype", STAGE_ORDERS,
+                         ids=[f"{'x'.join(map(str, d))}-{'_'.join('.'.join(map(str, s)) for s in st)}-{t}"
+                              for d, st, t in STAGE_ORDERS])
+def test_explicit_stage_lists(dims, stages, dtype):
+    """Any stage order (Section 6.1, A_rho with rho = the DIF list reversed):
+    the unordered transform is the DFT in that list's digit-reversed order
+    (the oracle's P_rho), and the convolution does not depend on the order."""
+    pac = pac_mod()
+    fs, h, x = separable_case(dims, dtype, seed=7 * len(dims))
+    plan = pac.Plan(dims, 0, dtype, stages=stages)
+    try:
+        for a in range(len(dims)):
+            assert plan.stages(a) == list(stages[a])
+            assert np.array_equal(np.array(plan.reverse_table(a)), pf.pos_to_freq(stages[a]))
+        plan.filter_spectrum(dev(h))
+        y = plan.convolve(dev(x))
+        xh = plan.forward_unordered(dev(x))
+        torch.cuda.synchronize()
+        n = int(np.prod(dims))
+        check(y.cpu().numpy(), oracle.conv_separable(fs, x), dtype, n, f"stages {stages}")
+        check(xh.cpu().numpy(), oracle.unordered_forward(x, stages), dtype, n, f"A^T x, stages {stages}")
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("dims,dtype", [((60, 90), "c128"), ((1000,), "c64"), ((12, 20, 30), "c64")])
+def test_mixed_radix_comparator_and_ordered_fft(dims, dtype):
+    """The permuted form (explicit index reversals) and the ordered transform
+    on mixed-radix plans."""
+    pac = pac_mod()
+    fs, h, x = separable_case(dims, dtype, seed=21)
+    ref = oracle.conv_separable(fs, x)
+    check(gpu_conv(dims, 0, dtype, h, x, permuted=True), ref, dtype, int(np.prod(dims)), "mixed permuted")
+    plan = pac.Plan(dims, 0, dtype)
+    try:
+        xd = dev(x)
+        X = torch.empty_like(xd)
+        pac.pac_fft(plan.handle, xd, X)
+        torch.cuda.synchronize()
+        check(X.cpu().numpy(), oracle.dft(x), dtype, x.size, "mixed F x")
+    finally:
+        plan.close()
+
+
+def test_mixed_radix_in_a_batch():
+    """Mixed-radix plans merged with uniform-radix ones in one pac_convolve_many call."""
+    pac = pac_mod()
+    cases = [((60, 90), 0), ((1000,), 0), ((64, 64), 4), ((360,), 0), ((1000,), 0)]
+    plans, xs, ys, refs = [], [], [], []
+    try:
+        for i, (dims, radix) in enumerate(cases):
+            fs, h, x = separable_case(dims, "c64", seed=40 + i)
+            p = pac.Plan(dims, radix, "c64")
+            plans.append(p)
+            p.filter_spectrum(dev(h))
+            xs.append(dev(x))
+            ys.append(torch.empty_like(xs[-1]))
+            refs.append(oracle.conv_separable(fs, x))
+        pac.pac_convolve_many([p.handle for p in plans], xs, ys)
+        torch.cuda.synchronize()
+        for (dims, _), y, ref in zip(cases, ys, refs):
+            check(y.cpu().numpy(), ref, "c64", int(np.prod(dims)), f"batched mixed {dims}")
+    finally:
+        for p in plans:
+            p.close()
+
+
+@pytest.mark.parametrize("dims,dtype", [((6000, 6000), "c64"), ((1024 * 243 * 125,), "c64"), ((360, 360, 360), "c64"),
+                                        ((2 ** 10 * 3 ** 4 * 5 ** 3,), "c128")])
+def test_mixed_radix_large_sampled(dims, dtype):
+    """Large mixed-radix arrays at 6 seeded output points against the direct definition."""
+    pac = pac_mod()
+    n = int(np.prod(dims))
+    real = torch.float32 if dtype == "c64" else torch.float64
+    g = torch.Generator(device="cuda")
+    g.manual_seed(n % 1000003)
+    x = torch.view_as_complex(torch.rand(*dims, 2, generator=g, device="cuda", dtype=real) * 2 - 1)
+    h = torch.view_as_complex(torch.rand(*dims, 2, generator=g, device="cuda", dtype=real) * 2 - 1)
+    plan = pac.Plan(dims, 0, dtype)
+    try:
+        plan.filter_spectrum(h)
+        y = plan.convolve(x)
+        torch.cuda.synchronize()
+        idx = pin.sample_points(n, 6, seed=n % 7919)
+        ref = oracle.conv_direct_points(h.cpu().numpy(), x.cpu().numpy(), idx)
+        got = y.reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy()
+        assert oracle.rel_l2(got, ref) <= tol(dtype, n)
+    finally:
+        plan.close()
+        del x, h
+        torch.cuda.empty_cache()
+
+
 # -------------------------------------------------------------- comparator
 
 

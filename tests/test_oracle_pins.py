@@ -21,7 +21,9 @@ from oracle import paper_forms as pf
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 RADIX_LISTS = [[2] * 4, [4, 4], [8, 8], [3, 3, 3], [5, 5], [2] * 6, [3] * 4,
-               [4, 4, 4, 2], [2, 4, 4, 4], [8, 8, 2], [2, 8, 8], [2, 3, 4], [4, 2, 2]]
+               [4, 4, 4, 2], [2, 4, 4, 4], [8, 8, 2], [2, 8, 8], [2, 3, 4], [4, 2, 2],
+               # mixed prime bases in any order (Section 6.1): 2^a 3^b 5^c
+               [2, 3, 5], [5, 3, 2, 2], [3, 5, 2, 3], [4, 2, 5, 5], [5, 2, 5, 4]]
 
 
 def rand_c(shape, seed):
@@ -250,7 +252,8 @@ def test_eq35_equals_definition(stages):
 
 
 @pytest.mark.parametrize("stage_lists", [([2, 2, 2], [4, 2]), ([3, 3], [3, 3, 3]), ([5], [5, 5]),
-                                         ([2, 2], [2, 2], [2, 2]), ([4], [2, 2], [8])])
+                                         ([2, 2], [2, 2], [2, 2]), ([4], [2, 2], [8]), ([2, 3], [5, 2]),
+                                         ([3, 2], [2], [5])])
 def test_eq80_equals_definition(stage_lists):
     shape = tuple(int(np.prod(s)) for s in stage_lists)
     h, x = rand_c(shape, 15), rand_c(shape, 16)
