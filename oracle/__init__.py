@@ -16,7 +16,9 @@ Routes (all FP64, interleaved complex, row-major with the last index fastest):
 * ``dft`` / ``idft``      O3: naive per-axis DFT (Section 2, w_n = exp(-2 pi i/n))
 * ``unordered_forward``   A^T x = P^T F x per axis, with P from the paper's
                           definition (``paper_forms.pos_to_freq``)
-* ``paper_forms``         the paper's matrix forms for tiny n (Eq. 25, Eq. 35, Eq. 80)
+* ``paper_forms``         the paper's matrix forms for tiny n (Eq. 25, Eq. 35, Eq. 80),
+                          the mixed-radix A_rho, P_rho (Section 6.1) and the prime factor
+                          maps and convolution (Section 6.2)
 
 Parity: every route is pinned by ``tests/test_oracle_pins.py`` (brute force,
 library routines, closed forms and invariants); none is unpinned.

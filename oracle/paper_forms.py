@@ -12,6 +12,9 @@ definitions in its notation; nothing is blocked, fused or reordered.
 * ``a_mixed(rho)``, ``p_mixed(rho)``  A_rho and P_rho of the mixed-radix framework   (Section 6.1)
 * ``conv_eq35(h, x, ...)``      conj(A)((A^T h) o (A^T x)) / n                          (Eq. 35)
 * ``conv_eq80(H, X, ...)``      the 2-D / d-D Kronecker form                           (Eq. 80, Section 4.1)
+* ``coprime_factors(n)``, ``crt_gamma``, ``ruritanian_upsilon``, ``conv_pfa``
+                                the prime factor framework: F_n = Gamma (F_{n_t} (x) ... (x) F_{n_1}) Upsilon^T
+                                and the convolution with three permutations               (Section 6.2)
 
 Index conventions are zero-based.  A permutation matrix is returned as an
 index array ``perm`` with (P v)[p] = v[perm[p]].
@@ -195,3 +198,75 @@ def conv_eq80(h: np.ndarray, x: np.ndarray, stages_per_axis) -> np.ndarray:
     xv = x.reshape(-1)
     y = np.conj(kt.T) @ ((kt @ hv) * (kt @ xv)) / n
     return y.reshape(x.shape)
+
+
+# ------------------------------------------------- prime factor framework (Section 6.2)
+
+
+def coprime_factors(n: int) -> list:
+    """n = 2^a 3^b 5^c as its pairwise coprime prime powers [n_1, ..., n_t], ascending
+    (the factors of Section 6.2; [] for n = 1)."""
+    out = []
+    for p in (2, 3, 5):
+        q = 1
+        while n % p == 0:
+            n //= p
+            q *= p
+        if q > 1:
+            out.append(q)
+    if n != 1:
+        raise ValueError("n is not of the form 2^a 3^b 5^c")
+    return sorted(out)
+
+
+def _tensor_index(idx, factors) -> int:
+    """Row-major position of (i_t, ..., i_1) in the tensor of shape (n_t, ..., n_1),
+    idx[q] = i_{q+1}: the ordering of F_{n_t} (x) ... (x) F_{n_1}."""
+    pos = 0
+    for q in reversed(range(len(factors))):
+        pos = pos * factors[q] + idx[q]
+    return pos
+
+
+def crt_gamma(factors) -> np.ndarray:
+    """Gamma of Section 6.2 as an index array, (Gamma v)[k] = v[gamma[k]]: output k of
+    the length-n transform is tensor entry (k mod n_t, ..., k mod n_1) (Chinese remainders)."""
+    n = int(np.prod(factors)) if len(factors) else 1
+    return np.array([_tensor_index([k % m for m in factors], factors) for k in range(n)], dtype=np.int64)
+
+
+def ruritanian_upsilon(factors) -> np.ndarray:
+    """Upsilon of Section 6.2 as an index array, (Upsilon v)[i] = v[upsilon[i]]: input
+    i = sum_q (n / n_q) i_q mod n is tensor entry (i_t, ..., i_1), i.e.
+    i_q = i (n / n_q)^{-1} mod n_q."""
+    n = int(np.prod(factors)) if len(factors) else 1
+    inv = [pow((n // m) % m, -1, m) if m > 1 else 0 for m in factors]
+    return np.array([_tensor_index([(i * inv[q]) % m for q, m in enumerate(factors)], factors)
+                     for i in range(n)], dtype=np.int64)
+
+
+def kron_fourier(factors) -> np.ndarray:
+    """F_{n_t} (x) ... (x) F_{n_1} (dense)."""
+    k = np.eye(1, dtype=complex)
+    for m in reversed(list(factors)):
+        k = np.kron(k, fourier(m))
+    return k
+
+
+def conv_pfa(h: np.ndarray, x: np.ndarray, factors) -> np.ndarray:
+    """Prime factor convolution of Section 6.2 for a 1-D length n = n_1 ... n_t:
+    Gamma (conj A_{n_t} (x) ... (x) conj A_{n_1}) [((A^T ...) Gamma^T h) o ((A^T ...) Gamma^T x)] / n,
+    the three permutations being Gamma^T h, Gamma^T x and Gamma.  Each A_{n_q} is
+    the uniform-radix A of its prime (Section 2.1); the bracket is the d-D form of
+    Eq. (80) on the tensor of shape (n_t, ..., n_1)."""
+    g = crt_gamma(factors)
+    gt = inverse_perm(g)  # (Gamma^T v)[j] = v[gt[j]]
+    shape = tuple(reversed(list(factors)))
+    stages = []
+    for m in shape:
+        p = next(q for q in (2, 3, 5) if m % q == 0)
+        stages.append([p] * int(round(np.log(m) / np.log(p))))
+    hh = np.asarray(h, dtype=complex)[gt].reshape(shape)
+    xx = np.asarray(x, dtype=complex)[gt].reshape(shape)
+    y = conv_eq80(hh, xx, stages).reshape(-1)
+    return y[g]

@@ -319,3 +319,60 @@ def test_mutation_transposed_stage_list_caught():
     x = rand_c((32,), 22)
     wrong = pf.inverse_perm(pf.p_mixed(stages))
     assert not np.allclose(pf.a_transpose(stages) @ x, oracle.dft(x)[wrong], atol=1e-6)
+
+
+# ----------------------------------------------- prime factor framework (Section 6.2)
+
+
+@pytest.mark.parametrize("n,want", [(6, [2, 3]), (10, [2, 5]), (60, [3, 4, 5]), (1000, [8, 125]), (81, [81]),
+                                    (1, []), (2 ** 10 * 3 ** 5 * 5 ** 3, [125, 243, 1024])])
+def test_coprime_factors(n, want):
+    assert pf.coprime_factors(n) == want
+
+
+@pytest.mark.parametrize("n", [6, 10, 12, 15, 30, 60, 90])
+def test_prime_factor_fourier_factorisation(n):
+    """Section 6.2: F_n = Gamma (F_{n_t} (x) ... (x) F_{n_1}) Upsilon^T with Gamma the
+    Chinese-remainder output map and Upsilon the Ruritanian input map; both are
+    permutations.  Where the two maps differ (n / n_q != 1 mod n_q for some q;
+    for n = 30 they coincide), Gamma on both sides does not factor F_n."""
+    f = pf.coprime_factors(n)
+    g, u = pf.crt_gamma(f), pf.ruritanian_upsilon(f)
+    assert sorted(g) == list(range(n)) and sorted(u) == list(range(n))
+    lhs = pf.perm_matrix(g) @ pf.kron_fourier(f) @ pf.perm_matrix(u).T
+    np.testing.assert_allclose(lhs, pf.fourier(n), atol=1e-12)
+    if not np.array_equal(g, u):
+        wrong = pf.perm_matrix(g) @ pf.kron_fourier(f) @ pf.perm_matrix(g).T
+        assert not np.allclose(wrong, pf.fourier(n), atol=1e-6)
+
+
+@pytest.mark.parametrize("n", [6, 10, 12, 15, 30, 60, 90, 120])
+def test_prime_factor_convolution_equals_definition(n):
+    """Section 6.2's convolution with three permutations equals the definition (O1)."""
+    h, x = rand_c((n,), 30 + n), rand_c((n,), 31 + n)
+    assert oracle.rel_l2(pf.conv_pfa(h, x, pf.coprime_factors(n)), oracle.conv_direct(h, x)) < 1e-13
+
+
+def test_gamma_is_additive():
+    """Gamma^T takes a cyclic shift by s to the tensor shift by (s mod n_q) per axis,
+    which is why a cyclic convolution of length n becomes a d-D cyclic one."""
+    f = [4, 3, 5]
+    n = 60
+    gt = pf.inverse_perm(pf.crt_gamma(f))
+    x = rand_c((n,), 32)
+    s = 7
+    lhs = np.roll(x, s)[gt].reshape(5, 3, 4)
+    rhs = np.roll(x[gt].reshape(5, 3, 4), (s % 5, s % 3, s % 4), axis=(0, 1, 2))
+    np.testing.assert_allclose(lhs, rhs, atol=0)
+
+
+def test_mutation_pfa_with_ruritanian_gather_caught():
+    # gathering with Upsilon^T but scattering with Gamma mixes two maps: wrong result
+    n = 60
+    f = pf.coprime_factors(n)
+    h, x = rand_c((n,), 33), rand_c((n,), 34)
+    g, u = pf.crt_gamma(f), pf.ruritanian_upsilon(f)
+    ut = pf.inverse_perm(u)
+    shape = tuple(reversed(f))
+    y = pf.conv_eq80(h[ut].reshape(shape), x[ut].reshape(shape), [[m] for m in shape]).reshape(-1)[g]
+    assert oracle.rel_l2(y, oracle.conv_direct(h, x)) > 0.1
