@@ -392,7 +392,52 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
         plan.close()
         del x, y, h, yc, Hn
         torch.cuda.empty_cache()
+    out.append(prime_factor_entry(torch, pac, dev, stream, flush, peak))
     return out
+
+
+def prime_factor_entry(torch, pac, dev, stream, flush, peak):
+    """The prime factor form (Section 6.2) of a 1-D length n = 2^10 3^5 5^3
+    (FP32): three permutations around the 3-D convolution of shape
+    (1024, 243, 125), against the permutation-free mixed-radix 1-D plan of
+    the same n and cuFFT; the two per-call permutations' share of the prime
+    factor form's time.  x: re, im U[-1,1]; h: re, im U[-1,1] (seeded)."""
+    n = 2 ** 10 * 3 ** 5 * 5 ** 3
+    B = 3 * n * 8
+    g = torch.Generator(device=dev)
+    g.manual_seed(7)
+    x = torch.view_as_complex(torch.rand(n, 2, generator=g, device=dev) * 2 - 1)
+    h = torch.view_as_complex(torch.rand(n, 2, generator=g, device=dev) * 2 - 1)
+    y = torch.empty_like(x)
+    sh = stream.cuda_stream
+    pfa = pac.Pfa(n, "c64")
+    plan = pac.Plan((n,), 0, "c64")
+    try:
+        pfa.filter_spectrum(h)
+        plan.filter_spectrum(h)
+        inner = pac.pac_pfa_plan(pfa.handle)
+        xt = torch.empty_like(x)
+        ms_pfa = time_steps(torch, lambda: pac.pac_pfa_convolve(pfa.handle, x, y, sh), 10, 3, flush, stream)
+        ms_inner = time_steps(torch, lambda: pac.pac_convolve(inner, x, xt, sh), 10, 3, flush, stream)
+        ms_ct = time_steps(torch, lambda: pac.pac_convolve(plan.handle, x, y, sh), 10, 3, flush, stream)
+        Hn = torch.fft.fft(h)
+        ms_cufft = time_steps(torch, lambda: torch.fft.ifft(torch.fft.fft(x) * Hn, out=xt), 10, 3, flush, stream)
+        t_pfa, t_inner, t_ct, t_cu = (statistics.median(v) for v in (ms_pfa, ms_inner, ms_ct, ms_cufft))
+        return {"workload": "1-D n=2^10 3^5 5^3 (31.1 M), complex FP32: prime factor form (Section 6.2) "
+                            "against the mixed-radix plan",
+                "dims": [n], "radix": 0, "dtype": "c64", "ms": t_ct, "GBps": B / (t_ct * 1e-3) / 1e9,
+                "pct_hbm_roofline": B / (t_ct * 1e-3) / 1e9 / peak,
+                "launches": plan.query(pac.Q_LAUNCHES_CONVOLVE), "groups": plan.query(pac.Q_GROUPS),
+                "cufft_GBps": B / (t_cu * 1e-3) / 1e9, "speedup_vs_cufft": t_cu / t_ct,
+                "prime_factor": {"shape": list(pfa.shape), "ms": t_pfa, "GBps": B / (t_pfa * 1e-3) / 1e9,
+                                 "launches": pfa.query(pac.Q_LAUNCHES_CONVOLVE),
+                                 "permutation_share": max(0.0, 1.0 - t_inner / t_pfa),
+                                 "mixed_radix_speedup": t_pfa / t_ct}}
+    finally:
+        pfa.close()
+        plan.close()
+        del x, y, h
+        torch.cuda.empty_cache()
 
 
 def batched_leg(a, torch, pac, pin, dev, stream, flush):

@@ -49,6 +49,7 @@ extern "C" {
 
 typedef struct pac_plan_s* pac_plan;   /* opaque, library-owned */
 typedef struct pac_queue_s* pac_queue; /* opaque, library-owned */
+typedef struct pac_pfa_s* pac_pfa;     /* opaque, library-owned */
 
 typedef enum { PAC_C64 = 0, PAC_C128 = 1 } pac_dtype;
 
@@ -148,6 +149,41 @@ int pac_convolve_many(int count, const pac_plan* plans, const void* const* x_dev
  * only; no device work.
  */
 int pac_convolve_many_launches(int count, const pac_plan* plans, int* launches);
+
+/* ------------------------------------------------------ prime factor form */
+
+/*
+ * Prime factor convolution (Section 6.2) of a 1-D length n = 2^a 3^b 5^c:
+ * with the pairwise coprime factors n_1 < ... < n_t (the nonzero prime
+ * powers of n, t <= 3),
+ *   y = Gamma (conj A_{n_t} x ... x conj A_{n_1})
+ *         [((A^T_{n_t} x ... x A^T_{n_1}) Gamma^T h) o ((...) Gamma^T x)] / n,
+ * where Gamma^T gathers a length-n vector into the tensor of shape
+ * (n_t, ..., n_1) (entry (i_t, ..., i_1) = element i with i = i_q mod n_q,
+ * Chinese remainders) and Gamma gathers it back (y[k] = tensor entry
+ * (k mod n_t, ..., k mod n_1)).  Three permutations per convolution
+ * (Gamma^T h is made once by pac_pfa_filter_spectrum); the bracket is the
+ * t-D convolution of a radix-0 plan of that shape.  The result equals
+ * pac_convolve of a 1-D plan of length n.
+ * pac_pfa_create: errors PAC_ERR_ARG (dtype, null out), PAC_ERR_SIZE (n not
+ * 2^a 3^b 5^c or >= 2^31), as pac_plan_create otherwise.  The object owns
+ * the inner plan and one n-element scratch array: calls of
+ * pac_pfa_convolve on one object must not overlap (one stream, or ordered
+ * streams).  pac_pfa_filter_spectrum synchronises the device.
+ * pac_pfa_convolve is asynchronous on `stream` (3 + inner launches); y_dev
+ * may equal x_dev.  Pointers as pac_convolve.
+ */
+int pac_pfa_create(int64_t n, pac_dtype dtype, pac_pfa* out);
+int pac_pfa_destroy(pac_pfa p);
+int pac_pfa_filter_spectrum(pac_pfa p, const void* h_dev);
+int pac_pfa_convolve(pac_pfa p, const void* x_dev, void* y_dev, void* stream);
+/* t and the tensor shape, padded on the left with 1s to three axes */
+int pac_pfa_shape(pac_pfa p, int* t, int64_t* dims);
+/* PAC_Q_* keys: NDIM = t, N_TOTAL = n, LAUNCHES_CONVOLVE and DEVICE_BYTES of
+ * the whole object, others of the inner plan */
+int pac_pfa_query(pac_pfa p, int key, int64_t* value);
+/* The inner t-D plan (owned by the object; not to be destroyed by the caller). */
+int pac_pfa_plan(pac_pfa p, pac_plan* inner);
 
 /* ----------------------------------------------------------------- serving */
 

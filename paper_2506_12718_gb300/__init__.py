@@ -71,6 +71,13 @@ _SIGS = {
     "pac_stage_list": (_i32, [_i64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "pac_reverse_table": (_i32, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "pac_version": (ctypes.c_char_p, []),
+    "pac_pfa_create": (_i32, [_i64, _i32, ctypes.POINTER(_vp)]),
+    "pac_pfa_destroy": (_i32, [_vp]),
+    "pac_pfa_filter_spectrum": (_i32, [_vp, _vp]),
+    "pac_pfa_convolve": (_i32, [_vp, _vp, _vp, _vp]),
+    "pac_pfa_shape": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "pac_pfa_query": (_i32, [_vp, _i32, ctypes.POINTER(_i64)]),
+    "pac_pfa_plan": (_i32, [_vp, ctypes.POINTER(_vp)]),
 }
 
 
@@ -270,6 +277,43 @@ def pac_tune(dims, radix: int, dtype: str = "c64", reps: int = 5) -> float:
     return us.value
 
 
+def pac_pfa_create(n: int, dtype: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().pac_pfa_create(int(n), int(dtype), ctypes.byref(out)))
+    return out.value
+
+
+def pac_pfa_destroy(p: int) -> None:
+    _check(load().pac_pfa_destroy(p))
+
+
+def pac_pfa_filter_spectrum(p: int, h_dev) -> None:
+    _check(load().pac_pfa_filter_spectrum(p, _ptr(h_dev)))
+
+
+def pac_pfa_convolve(p: int, x_dev, y_dev, stream=None) -> None:
+    _check(load().pac_pfa_convolve(p, _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+def pac_pfa_shape(p: int) -> tuple:
+    t = ctypes.c_int()
+    dims = (ctypes.c_int64 * 3)()
+    _check(load().pac_pfa_shape(p, ctypes.byref(t), dims))
+    return tuple(dims[3 - max(t.value, 1):])
+
+
+def pac_pfa_query(p: int, key: int) -> int:
+    v = ctypes.c_int64()
+    _check(load().pac_pfa_query(p, int(key), ctypes.byref(v)))
+    return v.value
+
+
+def pac_pfa_plan(p: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load().pac_pfa_plan(p, ctypes.byref(out)))
+    return out.value
+
+
 def pac_plan_query(plan: int, key: int) -> int:
     v = ctypes.c_int64()
     _check(load().pac_plan_query(plan, int(key), ctypes.byref(v)))
@@ -368,6 +412,54 @@ class Plan:
     def close(self) -> None:
         if self.handle:
             pac_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Pfa:
+    """Prime factor convolution of a 1-D length n = 2^a 3^b 5^c (Section 6.2),
+    bound to torch tensors (complex64 / complex128, on CUDA)."""
+
+    def __init__(self, n: int, dtype: str = "c64"):
+        self.n = int(n)
+        self.dtype = dtype
+        self.handle = pac_pfa_create(self.n, C64 if dtype == "c64" else C128)
+
+    @property
+    def shape(self) -> tuple:
+        """The tensor shape (n_t, ..., n_1) the convolution runs on."""
+        return pac_pfa_shape(self.handle)
+
+    def _tensor_check(self, t, name):
+        import torch
+        want = torch.complex64 if self.dtype == "c64" else torch.complex128
+        if t.dtype != want or not t.is_cuda or not t.is_contiguous() or t.numel() != self.n:
+            raise ValueError(f"{name}: need a contiguous CUDA {want} tensor of {self.n} elements")
+
+    def filter_spectrum(self, h) -> None:
+        self._tensor_check(h, "h")
+        pac_pfa_filter_spectrum(self.handle, h)
+
+    def convolve(self, x, y=None, stream=None):
+        import torch
+        self._tensor_check(x, "x")
+        if y is None:
+            y = torch.empty_like(x)
+        self._tensor_check(y, "y")
+        pac_pfa_convolve(self.handle, x, y, stream)
+        return y
+
+    def query(self, key: int) -> int:
+        return pac_pfa_query(self.handle, key)
+
+    def close(self) -> None:
+        if self.handle:
+            pac_pfa_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -122,3 +122,14 @@ def test_plan_create_rejects_bad_arguments_before_touching_the_device():
     with pytest.raises(pac.PacError) as ei:
         pac.pac_plan_create(1, [64], 7, pac.C64)
     assert ei.value.status == pac.Status.ERR_ARG
+
+
+@pytest.mark.parametrize("n,status", [(7, pac.Status.ERR_SIZE), (0, pac.Status.ERR_SIZE), (1 << 31, pac.Status.ERR_SIZE),
+                                      (2 * 7 * 5, pac.Status.ERR_SIZE)])
+def test_prime_factor_object_rejects_bad_lengths_before_touching_the_device(n, status):
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_pfa_create(n, pac.C64)
+    assert ei.value.status == status
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_pfa_create(60, 7)
+    assert ei.value.status == pac.Status.ERR_ARG

@@ -452,6 +452,73 @@ def test_mixed_radix_large_sampled(dims, dtype):
         torch.cuda.empty_cache()
 
 
+# ------------------------------------------------ prime factor form (Section 6.2)
+
+PFA_CASES = [(6, "c128"), (10, "c64"), (12, "c128"), (60, "c128"), (360, "c64"), (1000, "c128"), (6000, "c64"),
+             (81, "c64"), (1, "c128"), (2 ** 6 * 3 ** 3 * 5 ** 2, "c64"), (2 ** 5 * 125, "c128")]
+
+
+@pytest.mark.parametrize("n,dtype", PFA_CASES, ids=[f"{n}-{t}" for n, t in PFA_CASES])
+def test_prime_factor_convolution(n, dtype):
+    """Three permutations around a t-D convolution of shape (n_t, ..., n_1)
+    (Section 6.2): against the definition, in place, and equal to the
+    permutation-free mixed-radix 1-D plan."""
+    pac = pac_mod()
+    h = pin.as_dtype(pin.complex_uniform((n,), 50 + n % 97), dtype)
+    x = pin.as_dtype(pin.complex_normal((n,), 51 + n % 89), dtype)
+    ref = oracle.conv_direct(h, x)
+    p = pac.Pfa(n, dtype)
+    try:
+        assert p.shape == tuple(reversed(pf.coprime_factors(n))) or (n == 1 and p.shape == (1,))
+        p.filter_spectrum(dev(h))
+        y = p.convolve(dev(x))
+        xd = dev(x)
+        p.convolve(xd, xd)  # in place
+        torch.cuda.synchronize()
+        check(y.cpu().numpy(), ref, dtype, n, f"pfa {n}")
+        check(xd.cpu().numpy(), ref, dtype, n, f"pfa {n} in place")
+        assert p.query(pac.Q_LAUNCHES_CONVOLVE) >= 3
+    finally:
+        p.close()
+    check(gpu_conv((n,), 0, dtype, h, x), ref, dtype, n, f"mixed radix 1-D {n}")
+
+
+def test_prime_factor_convolution_large_sampled():
+    """n = 2^10 3^5 5^3 (31.1 M points, FP32): 6 seeded outputs against the definition."""
+    pac = pac_mod()
+    n = 2 ** 10 * 3 ** 5 * 5 ** 3
+    g = torch.Generator(device="cuda")
+    g.manual_seed(17)
+    x = torch.view_as_complex(torch.rand(n, 2, generator=g, device="cuda") * 2 - 1)
+    h = torch.view_as_complex(torch.rand(n, 2, generator=g, device="cuda") * 2 - 1)
+    p = pac.Pfa(n, "c64")
+    try:
+        assert p.shape == (1024, 243, 125)
+        p.filter_spectrum(h)
+        y = p.convolve(x)
+        torch.cuda.synchronize()
+        idx = pin.sample_points(n, 6, seed=23)
+        ref = oracle.conv_direct_points(h.cpu().numpy(), x.cpu().numpy(), idx)
+        got = y[torch.from_numpy(idx).cuda()].cpu().numpy()
+        assert oracle.rel_l2(got, ref) <= tol("c64", n)
+    finally:
+        p.close()
+        del x, h
+        torch.cuda.empty_cache()
+
+
+def test_prime_factor_without_spectrum_fails():
+    pac = pac_mod()
+    p = pac.Pfa(60, "c64")
+    try:
+        x = torch.zeros(60, dtype=torch.complex64, device="cuda")
+        with pytest.raises(pac.PacError) as ei:
+            p.convolve(x)
+        assert ei.value.status == pac.Status.ERR_NO_SPECTRUM
+    finally:
+        p.close()
+
+
 # -------------------------------------------------------------- comparator
 
 
