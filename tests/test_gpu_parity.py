@@ -674,7 +674,7 @@ def test_convolve_many_batched_workload_sample():
 
 
 @pytest.mark.parametrize("dims,radix,dtype", [((4096,), 2, "c64"), ((243, 243), 3, "c64"), ((32, 64, 64), 4, "c128"),
-                                             ((65536,), 4, "c64")])
+                                             ((65536,), 4, "c64"), ((1000, 1000), 0, "c64"), ((60, 90, 30), 0, "c128")])
 def test_autotuned_schedule_matches_oracle(dims, radix, dtype):
     """pac_tune times the candidate pass schedules and keeps the fastest; a
     plan created afterwards uses it and still matches the oracle."""
@@ -777,6 +777,40 @@ def test_queue_alone_and_in_the_mix_agree():
         assert all(lat > 0 for lat in lats)
     finally:
         for p in plans.values():
+            p.close()
+
+
+def test_mixed_radix_host_buffers_and_queue():
+    """Mixed-radix plans through the host-buffer call and the request queue."""
+    pac = pac_mod()
+    cases = [((60, 90), "c64"), ((1000,), "c128"), ((12, 20, 30), "c64")]
+    plans, xs, refs = [], [], []
+    try:
+        for i, (dims, dtype) in enumerate(cases):
+            fs, h, x = separable_case(dims, dtype, seed=60 + i)
+            p = pac.Plan(dims, 0, dtype)
+            p.filter_spectrum(dev(h))
+            plans.append(p)
+            xs.append(x)
+            refs.append(oracle.conv_separable(fs, x))
+        for p, x, ref, (dims, dtype) in zip(plans, xs, refs, cases):
+            xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+            yh = torch.empty_like(xh).pin_memory()
+            pac.pac_convolve_host(p.handle, xh, yh)
+            torch.cuda.synchronize()
+            check(yh.numpy(), ref, dtype, x.size, f"host {dims}")
+        q = pac.pac_queue_create(1 << 30, 4)
+        xd = [dev(x) for x in xs]
+        ys = [torch.empty_like(x) for x in xd]
+        tickets = [pac.pac_submit(q, p.handle, x, y) for p, x, y in zip(plans, xd, ys)]
+        pac.pac_queue_drain(q, 60000)
+        for t in tickets:
+            assert pac.pac_poll(q, t)[0] == pac.Status.OK
+        pac.pac_queue_destroy(q)
+        for y, ref, (dims, dtype) in zip(ys, refs, cases):
+            check(y.cpu().numpy(), ref, dtype, ref.size, f"queue {dims}")
+    finally:
+        for p in plans:
             p.close()
 
 

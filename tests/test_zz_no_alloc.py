@@ -36,7 +36,8 @@ def rel_l2(a, b):
 
 
 @pytest.mark.parametrize("dims,radix,dtype", [((64, 64, 64), 4, "c64"), ((243, 81), 3, "c128"),
-                                             ((1024, 1024), 8, "c64"), ((3125,), 5, "c128")])
+                                             ((1024, 1024), 8, "c64"), ((3125,), 5, "c128"),
+                                             ((60, 90), 0, "c128"), ((1000,), 0, "c64")])
 def test_noalloc_matches_permuted_twice(pac, dims, radix, dtype):
     tol = 1e-12 if dtype == "c128" else 1e-5 * math.log2(int(np.prod(dims)))
     h = pin.as_dtype(pin.complex_uniform(dims, 31), dtype)
