@@ -307,7 +307,10 @@ int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void* y_dev, vo
  * best_us (may be NULL) receives the winner's median time per convolution.
  * With PAC_TUNE=search in the environment, pac_plan_create tunes a problem
  * the first time a plan is made for it.  PAC_LOG=1 makes every plan print
- * its pass schedule (groups, plane pass) to stderr.
+ * its pass schedule (groups, plane pass) to stderr.  For stage lists of
+ * several prime bases (radix 0) the candidates include groups spanning bases
+ * (the runtime-radix kernel; off by default, PAC_MIXED=1 / 0 in the
+ * environment forces them on / off for every plan).
  */
 int pac_tune(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int reps, double* best_us);
 

@@ -70,7 +70,7 @@ ShapeKey shape_key(pac_plan p, const Step& st) {
     if (st.mode == kPlane)
         return ShapeKey(p->esize, p->groups[p->plane_g1].M, p->plane_k, p->groups[p->plane_g1 + 1].M);
     const GroupPlan& g = p->groups[st.group];
-    return ShapeKey(p->esize, g.M, g.C == 1 ? 1 : 0, 0);
+    return ShapeKey(p->esize, g.mix_nr > 0 ? -g.M : g.M, g.C == 1 ? 1 : 0, 0);  // -M: a mixed group
 }
 
 // Append one merged launch (arguments, then tile starts) to the host image.

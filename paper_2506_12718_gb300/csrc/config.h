@@ -109,6 +109,22 @@ constexpr int min_blocks(int m, int esize) {
     return clampi(65536 / (pass_threads(m, esize) * reg_target(m, esize)), 1, 8);
 }
 
+// ------------------------------------------------------------ mixed groups
+// A group whose stages have more than one prime base (mixed radix, Section
+// 6.1) runs in the runtime-radix kernel (mix.cuh): the tile is copied into
+// shared memory, transformed by rounds whose radices are the prime-power
+// parts of M (each split like a one-base group: at most 16 for base 2, 9 for
+// base 3, 25 for base 5; larger first), and copied out.
+constexpr int kMixThreads = 256;
+constexpr int kMixMaxRounds = 8;
+constexpr int kMixMmax = 2048;  // largest mixed group
+constexpr int mix_rmax(int base) { return base == 2 ? 16 : base == 3 ? 9 : 25; }
+constexpr int mix_w(int m, int esize) { return clampi(floor_pow2(kTileBytes / (m * esize)), 32 / esize, 256 / esize); }
+constexpr int mix_pitch(int m, int esize) { return mix_w(m, esize) + 1; }
+constexpr int mix_smem_bytes(int m, int esize) { return m * mix_pitch(m, esize) * esize; }
+// the largest tile: about kTileBytes of data plus one pitch column of padding
+constexpr int kMixSmemMax = 2 * kTileBytes + kMixMmax * 16;
+
 // ------------------------------------------------------------------ planes
 // A plane pass holds whole n1 x n2 planes (the last two axes) in one CTA's
 // shared memory, element (i1, i2) at i1 * plane_pitch + i2.  Padding chosen

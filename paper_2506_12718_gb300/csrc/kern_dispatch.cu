@@ -17,7 +17,12 @@ cudaError_t launch_conv_c64_p35(int M, ConvArgs& args, int grid, cudaStream_t s)
 cudaError_t launch_conv_c128_p2(int M, ConvArgs& args, int grid, cudaStream_t s);
 cudaError_t launch_conv_c128_p35(int M, ConvArgs& args, int grid, cudaStream_t s);
 
+cudaError_t launch_mix(int esize, bool lines, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_mix_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+                             int64_t total, cudaStream_t s);
+
 cudaError_t launch_pass(int esize, int M, const PassArgs& a, cudaStream_t s) {
+    if (a.mix_nr > 0) return launch_mix(esize, a.C == 1, a, s);
     if (esize == 8) return (M % 2 == 0) ? launch_pass_c64_p2(M, a, s) : launch_pass_c64_p35(M, a, s);
     return (M % 2 == 0) ? launch_pass_c128_p2(M, a, s) : launch_pass_c128_p35(M, a, s);
 }
@@ -43,6 +48,7 @@ cudaError_t launch_multi_c128_p35(int M, bool lines, const PassArgs* list, const
 
 cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
                          int64_t total, cudaStream_t s) {
+    if (M < 0) return launch_mix_multi(esize, -M, lines, list, starts, n, total, s);  // mixed groups of size -M
     if (esize == 8)
         return (M % 2 == 0) ? launch_multi_c64_p2(M, lines, list, starts, n, total, s)
                             : launch_multi_c64_p35(M, lines, list, starts, n, total, s);

@@ -27,14 +27,20 @@ struct GroupPlan {
     int64_t Q = 1;          // columns = N / M
     int tw_T = 1, tw_shift = 0;
     bool has_ext = false;
+    int mix_nr = 0;         // > 0: a mixed group (several prime bases), rounds mix_r of the runtime-radix kernel
+    int mix_r[kMixMaxRounds] = {0};
     size_t off_twi = 0, off_lo = 0, off_hi = 0, off_rowmap = 0, off_freq = 0, off_r2g = 0, off_r2f = 0;  // in tables
 };
+
+// tile width of a group's pass
+inline int group_w(const GroupPlan& g, int esize) { return g.mix_nr > 0 ? mix_w(g.M, esize) : tile_w(g.M, esize); }
 
 // A pass schedule: the largest group exponent per pass (0: the largest a CTA
 // takes) and whether the last two axes may run as a plane pass.
 struct Schedule {
     int cap = 0;
     bool plane = true;
+    bool mixed = false;  // stage lists of several prime bases: groups may span bases (runtime-radix kernel)
 };
 int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out);
 // the same from explicit per-axis DIF stage lists (radix: the label the plan reports; -1 = explicit)

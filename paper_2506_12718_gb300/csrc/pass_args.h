@@ -29,6 +29,13 @@ struct PassArgs {
     int mode;               // PassMode
     int has_ext;            // apply w_L^{j k'} (L' > 1)
     double scale;           // applied on store in kFwd (filter spectrum 1/N); 1 = none
+    // mixed group (stages of several prime bases, the runtime-radix kernel):
+    // mix_nr rounds of radices mix_r (0: a one-base group), group size mix_m,
+    // tile width mix_w
+    int mix_nr;
+    int mix_m;
+    int mix_w;
+    int mix_r[8];
 };
 
 // A plane pass (the last two axes, one group each, whole planes in one CTA):

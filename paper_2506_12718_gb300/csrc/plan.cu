@@ -197,21 +197,94 @@ static void split_run(const std::vector<int>& st, int lo, int hi, int p, int esi
     }
 }
 
-// Groups of an axis' stage list: a group holds stages of one prime base (a
-// CTA's in-register rounds take one base), so each maximal run of equal
-// base is split on its own (one run for a uniform radix).
-static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st, int esize, int cap) {
+// Groups of a stage list that may span prime bases (the runtime-radix
+// kernel): the fewest groups with product <= kMixMmax (a stage is never
+// split), balanced in size: a group takes the next stage while that brings
+// its size closer to the geometric mean of what is left.  Falls back to
+// greedy packing if balancing leaves the last group too large.
+static std::vector<std::pair<int, int>> split_mixed(const std::vector<int>& st) {
+    const int T = (int)st.size();
+    std::vector<std::pair<int, int>> greedy;
+    for (int i = 0; i < T;) {
+        int64_t acc = 1;
+        const int first = i;
+        while (i < T && (acc == 1 || acc * st[i] <= kMixMmax)) acc *= st[i++];
+        greedy.push_back({first, i - first});
+    }
+    const int ng = (int)greedy.size();
+    std::vector<std::pair<int, int>> out;
+    double rem = 0;
+    for (int r : st) rem += std::log((double)r);
+    int i = 0;
+    for (int gi = 0; gi < ng && i < T; ++gi) {
+        const int first = i;
+        if (gi == ng - 1) {
+            int64_t acc = 1;
+            for (int k = i; k < T; ++k) acc *= st[k];
+            if (acc > kMixMmax) return greedy;
+            out.push_back({i, T - i});
+            i = T;
+            break;
+        }
+        const double target = rem / (ng - gi);
+        int64_t acc = 1;
+        double lacc = 0;
+        while (i < T && (acc == 1 || (acc * st[i] <= kMixMmax &&
+                                      std::fabs(lacc + std::log((double)st[i]) - target) < std::fabs(lacc - target)))) {
+            acc *= st[i];
+            lacc += std::log((double)st[i]);
+            ++i;
+        }
+        out.push_back({first, i - first});
+        rem -= lacc;
+    }
+    if (i < T) return greedy;
+    return out;
+}
+
+// Groups of an axis' stage list.  One-base groups (a CTA's in-register rounds
+// of the one-base kernels take one base): each maximal run of equal base is
+// split on its own (one run for a uniform radix).  With several bases and
+// sch.mixed, groups spanning bases (split_mixed) are taken instead when they
+// are fewer.
+static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st, int esize, const Schedule& sch) {
     std::vector<std::pair<int, int>> out;
     const int T = (int)st.size();
-    int i = 0;
+    int i = 0, runs = 0;
     while (i < T) {
         const int p = stage_base(st[i]);
         int j = i;
         while (j < T && stage_base(st[j]) == p) ++j;
-        split_run(st, i, j, p, esize, cap, out);
+        split_run(st, i, j, p, esize, sch.cap, out);
+        ++runs;
         i = j;
     }
+    if (runs > 1 && sch.mixed) {
+        std::vector<std::pair<int, int>> mixed = split_mixed(st);
+        if (mixed.size() < out.size()) return mixed;
+    }
     return out;
+}
+
+// Round radices of a mixed group of size M: each prime-power part of M split
+// into the fewest rounds of at most mix_rmax, evenly, then all sorted larger
+// first.  Returns the round count.
+static int mix_round_list(int M, int* r) {
+    int n = 0;
+    for (int p : {2, 3, 5}) {
+        int e = 0, m = M;
+        while (m % p == 0) {
+            m /= p;
+            ++e;
+        }
+        if (e == 0) continue;
+        int er = 0;
+        for (int v = mix_rmax(p); v > 1; v /= p) ++er;
+        const int nr = (e + er - 1) / er;
+        for (int k = 0; k < nr && n < kMixMaxRounds; ++k) r[n++] = ipow(p, e / nr + (k < e % nr ? 1 : 0));
+    }
+    std::sort(r, r + n, [](int x, int y) { return x > y; });
+    return n;
 }
 
 }  // namespace pac
@@ -284,7 +357,8 @@ static void log_plan(const pac_plan p) {
     std::fprintf(stderr, "pac: plan dims");
     for (int a = 0; a < p->ndim; ++a) std::fprintf(stderr, " %lld", (long long)p->dims[a]);
     std::fprintf(stderr, " radix %d %s cap %d:", p->radix, p->esize == 8 ? "c64" : "c128", p->schedule.cap);
-    for (const GroupPlan& g : p->groups) std::fprintf(stderr, " [axis %d M %d C %lld]", g.axis, g.M, (long long)g.C);
+    for (const GroupPlan& g : p->groups)
+        std::fprintf(stderr, " [axis %d M %d C %lld%s]", g.axis, g.M, (long long)g.C, g.mix_nr > 0 ? " mixed" : "");
     if (p->plane) std::fprintf(stderr, " plane %dx%d K=%d", p->groups[p->plane_g1].M, p->groups[p->plane_g1 + 1].M,
                                p->plane_k);
     std::fprintf(stderr, "\n");
@@ -381,13 +455,17 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
         reverse_table(pl->stages[a].data(), (int)pl->stages[a].size(), pl->pos_to_freq[a].data());
     }
 
-    // groups, forward order: axis 0 (outermost) first, the contiguous axis last
+    // groups, forward order: axis 0 (outermost) first, the contiguous axis last;
+    // PAC_MIXED=1 / 0 in the environment forces groups spanning prime bases on / off
+    Schedule gs = sch;
+    const char* me = std::getenv("PAC_MIXED");
+    if (me && (me[0] == '0' || me[0] == '1')) gs.mixed = me[0] == '1';
     size_t off = 0;
     for (int a = 0; a < ndim; ++a) {
         int64_t inner = 1;
         for (int b = a + 1; b < ndim; ++b) inner *= dims[b];
         int64_t Lcur = dims[a];
-        for (auto [first, cnt] : split_groups(pl->stages[a], pl->esize, sch.cap)) {
+        for (auto [first, cnt] : split_groups(pl->stages[a], pl->esize, gs)) {
             GroupPlan g;
             g.axis = a;
             g.first_stage = first;
@@ -400,7 +478,16 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
             g.C = g.Lp * inner;
             g.Q = pl->N / g.M;
             g.has_ext = g.Lp > 1;
-            if (!pass_kernel_supported(g.M, pl->esize)) {
+            bool one_base = true;
+            for (int i = 1; i < cnt; ++i)
+                if (stage_base(pl->stages[a][first + i]) != stage_base(pl->stages[a][first])) one_base = false;
+            if (!one_base) {
+                g.mix_nr = mix_round_list(g.M, g.mix_r);
+                if (g.M > kMixMmax) {
+                    delete pl;
+                    return fail(PAC_ERR_SIZE, "mixed group size %d above %d", g.M, kMixMmax);
+                }
+            } else if (!pass_kernel_supported(g.M, pl->esize)) {
                 delete pl;
                 return fail(PAC_ERR_SIZE, "no pass kernel for group size %d", g.M);
             }
@@ -471,7 +558,7 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     if (!pl->groups.empty()) {
         pl->uniform_m = pl->groups[0].M;
         for (const GroupPlan& g : pl->groups)
-            if (g.M != pl->uniform_m) pl->uniform_m = 0;
+            if (g.M != pl->uniform_m || g.mix_nr > 0) pl->uniform_m = 0;
     }
 
     // host blob of every table
@@ -497,9 +584,9 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
         reverse_table(pl->stages[g.axis].data() + g.first_stage, g.nstages, f.data());
         // shared-memory row of frequency k after the in-place rounds: digit
         // reversal over the round radices (larger rounds first)
-        const int nr = round_count(g.M, pl->esize);
+        const int nr = g.mix_nr > 0 ? g.mix_nr : round_count(g.M, pl->esize);
         std::vector<int> rr(nr);
-        for (int i = 0; i < nr; ++i) rr[i] = round_radix(g.M, pl->esize, i);
+        for (int i = 0; i < nr; ++i) rr[i] = g.mix_nr > 0 ? g.mix_r[i] : round_radix(g.M, pl->esize, i);
         std::vector<int64_t> row_freq(g.M);
         reverse_table(rr.data(), nr, row_freq.data());
         std::vector<int> f2r(g.M);
@@ -536,7 +623,7 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     pl->spec_elems = pl->N;
     if (!pl->groups.empty() && !pl->plane) {  // whole tiles of the fused pass (see SpecOrder)
         const GroupPlan& f = pl->groups.back();
-        const int64_t W = tile_w(f.M, pl->esize);
+        const int64_t W = group_w(f, pl->esize);
         pl->spec_elems = (f.Q + W - 1) / W * W * f.M;
     }
     e = cudaMalloc(&pl->d_spec, (size_t)pl->spec_elems * pl->esize);
@@ -616,10 +703,14 @@ SpecOrder spec_order_of(pac_plan p) {
     }
     o.K = 1;
     o.M = (uint32_t)f.M;
-    o.W = (uint32_t)tile_w(f.M, p->esize);
+    o.W = (uint32_t)group_w(f, p->esize);
     o.C = (uint32_t)f.C;
-    const int nr = round_count(f.M, p->esize);
-    o.R = (uint32_t)round_radix(f.M, p->esize, nr - 1);
+    if (f.mix_nr > 0) {
+        o.R = (uint32_t)f.mix_r[f.mix_nr - 1];
+    } else {
+        const int nr = round_count(f.M, p->esize);
+        o.R = (uint32_t)round_radix(f.M, p->esize, nr - 1);
+    }
     o.tasks = o.W * o.M / o.R;
     o.rowmap = reinterpret_cast<const int*>(static_cast<const unsigned char*>(p->d_tables) + f.off_rowmap);
     return o;
@@ -641,13 +732,17 @@ PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, vo
     a.Q = g.Q;
     a.C = g.C;
     a.I = g.I;
-    const int W = tile_w(g.M, p->esize);
+    const int W = group_w(g, p->esize);
     a.tiles = (g.Q + W - 1) / W;
     a.tw_T = g.tw_T;
     a.tw_shift = g.tw_shift;
     a.mode = mode;
     a.has_ext = g.has_ext ? 1 : 0;
     a.scale = scale;
+    a.mix_nr = g.mix_nr;
+    a.mix_m = g.M;
+    a.mix_w = W;
+    for (int i = 0; i < 8; ++i) a.mix_r[i] = i < g.mix_nr ? g.mix_r[i] : 0;
     return a;
 }
 

@@ -353,19 +353,49 @@ def test_mixed_radix_plans(dims, dtype):
     check(y, oracle.conv_separable(fs, x), dtype, int(np.prod(dims)), f"mixed {dims}")
 
 
+@pytest.mark.parametrize("dims,dtype,mixed_launches,onebase_launches",
+                         [((1000, 1000), "c64", 3, 7), ((120, 120, 120), "c64", 5, 17), ((60, 90), "c128", 3, 11),
+                          ((6000,), "c64", 3, 5), ((30,), "c128", 1, 5), ((72, 75), "c64", 3, 7)])
+def test_mixed_groups_against_one_base_groups(dims, dtype, mixed_launches, onebase_launches, monkeypatch):
+    """Groups spanning prime bases (the runtime-radix kernel, PAC_MIXED=1)
+    against one-base groups (the default, PAC_MIXED=0): fewer launches, the
+    same convolution."""
+    pac = pac_mod()
+    fs, h, x = separable_case(dims, dtype, seed=3 * sum(dims))
+    ref = oracle.conv_separable(fs, x)
+    n = int(np.prod(dims))
+    monkeypatch.setenv("PAC_MIXED", "1")
+    plan = pac.Plan(dims, 0, dtype)
+    try:
+        assert plan.query(pac.Q_LAUNCHES_CONVOLVE) == mixed_launches
+    finally:
+        plan.close()
+    check(gpu_conv(dims, 0, dtype, h, x), ref, dtype, n, f"mixed groups {dims}")
+    monkeypatch.setenv("PAC_MIXED", "0")
+    plan = pac.Plan(dims, 0, dtype)
+    try:
+        assert plan.query(pac.Q_LAUNCHES_CONVOLVE) == onebase_launches
+    finally:
+        plan.close()
+    check(gpu_conv(dims, 0, dtype, h, x), ref, dtype, n, f"one-base groups {dims}")
+
+
 STAGE_ORDERS = [((60,), [[3, 4, 5]], "c128"), ((60,), [[5, 3, 2, 2]], "c128"), ((1000,), [[5, 2, 5, 4, 5]], "c64"),
                 ((120, 90), [[2, 3, 4, 5], [3, 5, 2, 3]], "c64"), ((18, 20, 24), [[3, 2, 3], [5, 4], [4, 3, 2]], "c128"),
                 ((1024,), [[2] * 10], "c64"), ((72, 1), [[2, 3, 4, 3], []], "c128"), ((25, 27), [[5, 5], [3, 9]], "c64"),
                 ((64, 48), [[16, 4], [16, 3]], "c64")]
 
 
+@pytest.mark.parametrize("mixed", ["0", "1"])
 @pytest.mark.parametrize("dims,stages,dtype", STAGE_ORDERS,
                          ids=[f"{'x'.join(map(str, d))}-{'_'.join('.'.join(map(str, s)) for s in st)}-{t}"
                               for d, st, t in STAGE_ORDERS])
-def test_explicit_stage_lists(dims, stages, dtype):
+def test_explicit_stage_lists(dims, stages, dtype, mixed, monkeypatch):
     """Any stage order (Section 6.1, A_rho with rho = the DIF list reversed):
     the unordered transform is the DFT in that list's digit-reversed order
-    (the oracle's P_rho), and the convolution does not depend on the order."""
+    (the oracle's P_rho), and the convolution does not depend on the order;
+    with one-base groups and with groups spanning bases."""
+    monkeypatch.setenv("PAC_MIXED", mixed)
     pac = pac_mod()
     fs, h, x = separable_case(dims, dtype, seed=7 * len(dims))
     plan = pac.Plan(dims, 0, dtype, stages=stages)
@@ -403,8 +433,11 @@ def test_mixed_radix_comparator_and_ordered_fft(dims, dtype):
         plan.close()
 
 
-def test_mixed_radix_in_a_batch():
-    """Mixed-radix plans merged with uniform-radix ones in one pac_convolve_many call."""
+@pytest.mark.parametrize("mixed", ["0", "1"])
+def test_mixed_radix_in_a_batch(mixed, monkeypatch):
+    """Mixed-radix plans merged with uniform-radix ones in one pac_convolve_many
+    call (with groups spanning bases: the batched runtime-radix kernel)."""
+    monkeypatch.setenv("PAC_MIXED", mixed)
     pac = pac_mod()
     cases = [((60, 90), 0), ((1000,), 0), ((64, 64), 4), ((360,), 0), ((1000,), 0)]
     plans, xs, ys, refs = [], [], [], []

@@ -8,6 +8,7 @@ fixed 8 MiB static buffer inside the library.  This file is collected last
 every other test; it also passes on its own in a fresh process.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -37,12 +38,19 @@ def rel_l2(a, b):
 
 @pytest.mark.parametrize("dims,radix,dtype", [((64, 64, 64), 4, "c64"), ((243, 81), 3, "c128"),
                                              ((1024, 1024), 8, "c64"), ((3125,), 5, "c128"),
-                                             ((60, 90), 0, "c128"), ((1000,), 0, "c64")])
+                                             ((60, 90), 0, "c128"), ((1000,), 0, "c64"), ((360,), -1, "c64")])
 def test_noalloc_matches_permuted_twice(pac, dims, radix, dtype):
     tol = 1e-12 if dtype == "c128" else 1e-5 * math.log2(int(np.prod(dims)))
     h = pin.as_dtype(pin.complex_uniform(dims, 31), dtype)
     x = pin.as_dtype(pin.complex_normal(dims, 32), dtype)
-    plan = pac.Plan(dims, radix, dtype)
+    if radix == -1:  # a mixed group (runtime-radix kernel)
+        os.environ["PAC_MIXED"] = "1"
+        try:
+            plan = pac.Plan(dims, 0, dtype)
+        finally:
+            del os.environ["PAC_MIXED"]
+    else:
+        plan = pac.Plan(dims, radix, dtype)
     try:
         plan.filter_spectrum(torch.from_numpy(h).cuda())
         xd = torch.from_numpy(x).cuda()
