@@ -197,7 +197,11 @@ int pac_pfa_plan(pac_pfa p, pac_plan* inner);
  * and spectra stay resident; the queue does not own them.  Requests of at
  * most 8 MiB of device bytes are "small": they run on high-priority streams
  * and a quarter of the slots is kept for them, so large requests cannot hold
- * every slot; within each class admission is in arrival order.
+ * every slot; within each class admission is in arrival order.  Requests
+ * run on max_inflight streams: set CUDA_DEVICE_MAX_CONNECTIONS (in the
+ * environment, before CUDA starts in the process) to at least max_inflight,
+ * else streams share the GPU's hardware work queues (8 by default) and a
+ * small request's kernels can wait behind a large request's.
  */
 int pac_queue_create(size_t hbm_budget_bytes, int max_inflight, pac_queue* out);
 
