@@ -331,7 +331,7 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
     """Every single-convolution workload: 1-D 2^10 FP64 radix 2; 3-D 128^3
     radix 2/4/8 FP32 and FP64; 2-D 2187^2 radix 3 and 3125^2 radix 5, FP32
     and FP64; mixed radix (2^a 3^b 5^c) 2-D 1000^2 and 6000^2 and 3-D 120^3,
-    FP32.  Each: GB/s of 3 N S, the permuted form and cuFFT on the same
+    FP32; the anisotropic 2^24 x 2 and 2^22 x 2 x 2, FP32.  Each: GB/s of 3 N S, the permuted form and cuFFT on the same
     GPU, launches per convolution and the pass schedule (autotuned unless
     --no-tune).  Inputs of each workload's recipe, generated on the device
     from a seed (x: re, im N(0,1) or U[-1,1]; the workload's filter)."""
@@ -352,6 +352,9 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
     cases.append((pin.mixed((1000, 1000)), "2-D 1000^2, mixed radix 2^3 5^3, complex FP32"))
     cases.append((pin.mixed((6000, 6000)), "2-D 6000^2, mixed radix 2^4 3 5^3, complex FP32"))
     cases.append((pin.mixed((120, 120, 120)), "3-D 120^3, mixed radix 2^3 3 5, complex FP32"))
+    # the paper's anisotropic shapes (a long axis with axes of 2)
+    cases.append((pin.aniso((2 ** 24, 2)), "2-D 2^24 x 2, radix 2, complex FP32 (anisotropic)"))
+    cases.append((pin.aniso((2 ** 22, 2, 2)), "3-D 2^22 x 2 x 2, radix 2, complex FP32 (anisotropic)"))
     sh = stream.cuda_stream
     for c, name in cases:
         N, S = c.n_total, c.elem_bytes

@@ -174,6 +174,12 @@ def mixed(dims=(1000, 1000), dtype: str = "c64") -> Conv:
     return Conv(tuple(int(d) for d in dims), 0, dtype, "uniform", "exp", seed=6, h_param=20.0)
 
 
+def aniso(dims=(2 ** 24, 2), dtype: str = "c64") -> Conv:
+    """The paper's anisotropic shapes, n x 2 and n x 2 x 2 (radix 2), with c3's
+    recipe (x ~ U[-1,1], separable exponential of length 20), seed 8."""
+    return Conv(tuple(int(d) for d in dims), 2, dtype, "uniform", "exp", seed=8, h_param=20.0)
+
+
 # Size classes of the batched workload: 1-D {2^8..2^16} (9 classes),
 # 1-D {3^5..3^10} (6 classes) and 2-D {2^6..2^10}^2 (5 classes).
 C4_CLASSES = ([((2 ** e,), 2) for e in range(8, 17)]
