@@ -1,6 +1,7 @@
 // Auxiliary kernels: the index-reversal permutation of the comparator
 // (Algorithm 1, a gather through per-axis index tables, optionally fused with
-// the Hadamard product), the one-time reordering of a filter spectrum into
+// the Hadamard product; one block per row, or one thread per element for
+// short rows), the one-time reordering of a filter spectrum into
 // its storage order, and a pointwise product for the degenerate N = 1 plan.
 #include <algorithm>
 
@@ -28,6 +29,26 @@ __global__ void permute_kernel(int64_t d0, int64_t d1, int64_t d2, const int64_t
             if (scale != 1.0) v = cscale(v, (typename Real<V>::T)scale);
             drow[i2] = v;
         }
+    }
+}
+
+// The same gather for short rows (d2 small: one block per row would leave
+// most of its threads idle): one thread per output element, grid-stride,
+// 32-bit indices (a plan keeps N < 2^31).
+template <typename V>
+__global__ void permute_flat_kernel(uint32_t n, uint32_t d1, uint32_t d2, const int64_t* __restrict__ t0,
+                                    const int64_t* __restrict__ t1, const int64_t* __restrict__ t2, const V* src,
+                                    V* dst, const V* __restrict__ mul, double scale) {
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const uint32_t row = e / d2, i2 = e - row * d2;
+        const uint32_t i0 = row / d1, i1 = row - i0 * d1;
+        const uint32_t s0 = t0 ? (uint32_t)__ldg(t0 + i0) : i0;
+        const uint32_t s1 = t1 ? (uint32_t)__ldg(t1 + i1) : i1;
+        const uint32_t s2 = t2 ? (uint32_t)__ldg(t2 + i2) : i2;
+        V v = src[(s0 * d1 + s1) * d2 + s2];
+        if (mul) v = cmul(v, __ldg(mul + e));
+        if (scale != 1.0) v = cscale(v, (typename Real<V>::T)scale);
+        dst[e] = v;
     }
 }
 
@@ -77,6 +98,22 @@ cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64
         t[3 - ndim + a] = idx_dev[a];
     }
     const int64_t rows = d[0] * d[1];
+    if (d[2] < 64) {  // short rows: one thread per element
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const int64_t n = rows * d[2];
+        const unsigned blocks =
+            (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)device_sm_count(dev) * 16));
+        if (esize == 8)
+            permute_flat_kernel<float2><<<blocks, 256, 0, s>>>((uint32_t)n, (uint32_t)d[1], (uint32_t)d[2], t[0], t[1],
+                                                               t[2], (const float2*)src, (float2*)dst,
+                                                               (const float2*)mul, scale);
+        else
+            permute_flat_kernel<double2><<<blocks, 256, 0, s>>>((uint32_t)n, (uint32_t)d[1], (uint32_t)d[2], t[0],
+                                                                t[1], t[2], (const double2*)src, (double2*)dst,
+                                                                (const double2*)mul, scale);
+        return cudaGetLastError();
+    }
     const int threads = (int)std::min<int64_t>(256, ((d[2] + 31) / 32) * 32);
     const int64_t gx = std::min<int64_t>((d[2] + threads - 1) / threads, 4096);
     const int64_t gy = std::min<int64_t>(rows, 65535);
