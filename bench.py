@@ -62,6 +62,7 @@ def parse_args(argv=None):
                     help="extra legs after the main one: configs (every workload shape, dtype and radix, "
                          "with its permuted form and cuFFT), batched (4096 mixed convolutions in one call), "
                          "served (Poisson request stream through the queue)")
+    ap.add_argument("--max-inflight", type=int, default=16, help="served leg: requests running at once")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default pass schedules)")
     ap.add_argument("--flush-mb", type=int, default=FLUSH_BYTES >> 20,
@@ -531,7 +532,7 @@ def served_leg(a, torch, pac, pin, dev):
     (Gaussian / exponential); latency = submit to completion."""
     reqs = pin.c5_requests(a.serve_seconds)
     pool = pin.c5_filter_pool()
-    max_inflight, budget = 16, 64 << 30
+    max_inflight, budget = a.max_inflight, 64 << 30
     t_setup = time.perf_counter()
     plans, xbuf, ybuf, rr = {}, {}, {}, {}
     K = max_inflight + 2
