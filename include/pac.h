@@ -344,6 +344,18 @@ enum {
  */
 int pac_measure_fma_peak(int dtype, double* gflops);
 
+/*
+ * Host only (no device): the pass groups a plan of this problem gets, in
+ * forward order (axis 0 first), without the plane pass.  flags bit 0:
+ * groups may span prime bases (as PAC_MIXED=1); cap: a schedule's
+ * group-exponent cap (0: none).  For group g: axis[g], size[g] (its M) and
+ * rounds[8 g .. 8 g + 7] (its in-CTA round radices, 0-padded).  *count: in,
+ * the room of the arrays (groups; ignored when all three are NULL); out, the
+ * number of groups.  Errors as pac_plan_create, before any device call.
+ */
+int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int flags, int cap, int* axis,
+                    int* size, int* rounds, int* count);
+
 /* Host-only helpers (no device needed): the stage list of pac_plan_create
  * (radix 0 included) and the reversal table of a stage list. */
 int pac_stage_list(int64_t n, int radix, int* radices, int* count);

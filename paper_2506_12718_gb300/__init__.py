@@ -69,6 +69,8 @@ _SIGS = {
     "pac_convolve_timed": (_i32, [_vp, _i32, _vp, _vp, _vp, _i32, ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "pac_stage_list": (_i32, [_i64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "pac_plan_groups": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _i32, ctypes.POINTER(_i32),
+                               ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "pac_reverse_table": (_i32, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "pac_version": (ctypes.c_char_p, []),
     "pac_pfa_create": (_i32, [_i64, _i32, ctypes.POINTER(_vp)]),
@@ -143,6 +145,20 @@ def pac_version() -> str:
 
 def pac_last_error() -> str:
     return load().pac_last_error().decode(errors="replace")
+
+
+def pac_plan_groups(dims, radix: int, dtype: int = 0, mixed: bool = False, cap: int = 0) -> list:
+    """Host only: the pass groups of a plan, forward order, as (axis, M, rounds)."""
+    vals = [int(v) for v in dims]
+    d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
+    room = 64
+    ax = (ctypes.c_int * room)()
+    sz = (ctypes.c_int * room)()
+    rr = (ctypes.c_int * (8 * room))()
+    cnt = ctypes.c_int(room)
+    _check(load().pac_plan_groups(len(vals), d, int(radix), int(dtype), 1 if mixed else 0, int(cap), ax, sz, rr,
+                                  ctypes.byref(cnt)))
+    return [(ax[g], sz[g], [r for r in rr[8 * g:8 * g + 8] if r]) for g in range(cnt.value)]
 
 
 def pac_stage_list(n: int, radix: int) -> list[int]:

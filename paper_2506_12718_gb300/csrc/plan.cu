@@ -378,6 +378,46 @@ extern "C" int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dty
     return rc;
 }
 
+namespace pac {
+static int form_groups(int ndim, const int64_t* dims, const std::vector<std::vector<int>>& stages, int esize,
+                       const Schedule& sch, std::vector<GroupPlan>& out);
+}  // namespace pac
+
+extern "C" int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int flags, int cap,
+                               int* axis, int* size, int* rounds, int* count) {
+    if (ndim < 1 || ndim > 3 || !dims || !count) return fail(PAC_ERR_ARG, "bad arguments");
+    if (dtype != PAC_C64 && dtype != PAC_C128) return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
+    if (radix != 0 && prime_of(radix) == 0) return fail(PAC_ERR_ARG, "radix %d not in {0,2,3,4,5,8}", radix);
+    std::vector<std::vector<int>> st(ndim);
+    for (int a = 0; a < ndim; ++a) {
+        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
+            return fail(PAC_ERR_SIZE, "dimension %lld out of range", (long long)dims[a]);
+        if (int rc = stage_list(dims[a], radix, st[a])) return rc;
+    }
+    Schedule sch;
+    sch.cap = cap;
+    sch.mixed = (flags & 1) != 0;
+    std::vector<GroupPlan> gr;
+    if (int rc = form_groups(ndim, dims, st, dtype == PAC_C64 ? 8 : 16, sch, gr)) return rc;
+    const int n = (int)gr.size();
+    if (axis || size || rounds) {
+        if (*count < n) return fail(PAC_ERR_ARG, "room for %d groups, %d needed", *count, n);
+        for (int g = 0; g < n; ++g) {
+            const GroupPlan& p = gr[g];
+            const int esize = dtype == PAC_C64 ? 8 : 16;
+            if (axis) axis[g] = p.axis;
+            if (size) size[g] = p.M;
+            if (rounds) {
+                const int nr = p.mix_nr > 0 ? p.mix_nr : round_count(p.M, esize);
+                for (int i = 0; i < 8; ++i)
+                    rounds[8 * g + i] = i < nr ? (p.mix_nr > 0 ? p.mix_r[i] : round_radix(p.M, esize, i)) : 0;
+            }
+        }
+    }
+    *count = n;
+    return PAC_OK;
+}
+
 extern "C" int pac_plan_create_stages(int ndim, const int64_t* dims, const int* nstages, const int* stages,
                                       pac_dtype dtype, pac_plan* out) {
     if (!out) return fail(PAC_ERR_ARG, "null out");
@@ -397,6 +437,65 @@ extern "C" int pac_plan_create_stages(int ndim, const int64_t* dims, const int* 
 }
 
 namespace pac {
+
+// The pass groups of a problem, forward order (axis 0 first, the contiguous
+// axis last): per axis, the stage list split by split_groups; for each group
+// its size, block length L, row stride, columns, external-factor split and,
+// for a group spanning prime bases, its round radices.  Host only.
+static int form_groups(int ndim, const int64_t* dims, const std::vector<std::vector<int>>& stages, int esize,
+                       const Schedule& sch, std::vector<GroupPlan>& out) {
+    out.clear();
+    int64_t N = 1;
+    for (int a = 0; a < ndim; ++a) N *= dims[a];
+    for (int a = 0; a < ndim; ++a) {
+        int64_t inner = 1;
+        for (int b = a + 1; b < ndim; ++b) inner *= dims[b];
+        int64_t Lcur = dims[a];
+        for (auto [first, cnt] : split_groups(stages[a], esize, sch)) {
+            GroupPlan g;
+            g.axis = a;
+            g.first_stage = first;
+            g.nstages = cnt;
+            g.M = 1;
+            for (int i = 0; i < cnt; ++i) g.M *= stages[a][first + i];
+            g.L = Lcur;
+            g.Lp = Lcur / g.M;
+            g.I = inner;
+            g.C = g.Lp * inner;
+            g.Q = N / g.M;
+            g.has_ext = g.Lp > 1;
+            bool one_base = true;
+            for (int i = 1; i < cnt; ++i)
+                if (stage_base(stages[a][first + i]) != stage_base(stages[a][first])) one_base = false;
+            if (!one_base) {
+                g.mix_nr = mix_round_list(g.M, g.mix_r);
+                if (g.M > kMixMmax) return fail(PAC_ERR_SIZE, "mixed group size %d above %d", g.M, kMixMmax);
+            } else if (!pass_kernel_supported(g.M, esize)) {
+                return fail(PAC_ERR_SIZE, "no pass kernel for group size %d", g.M);
+            }
+            // two-level split of the external exponent e = hi T + lo: T = p^ceil(e/2)
+            // when L = p^e, else (mixed radix) T = ceil(sqrt(L))
+            g.tw_T = 0;
+            for (int q : {2, 3, 5}) {
+                const int eL = exact_log(g.L, q);
+                if (eL >= 0) {
+                    g.tw_T = ipow(q, (eL + 1) / 2);
+                    g.tw_shift = (q == 2) ? (eL + 1) / 2 : -1;
+                    break;
+                }
+            }
+            if (g.tw_T == 0) {
+                int64_t T = (int64_t)std::sqrt((double)g.L);
+                while (T * T < g.L) ++T;
+                g.tw_T = (int)T;
+                g.tw_shift = -1;
+            }
+            out.push_back(g);
+            Lcur = g.Lp;
+        }
+    }
+    return PAC_OK;
+}
 
 int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out) {
     if (!out) return fail(PAC_ERR_ARG, "null out");
@@ -460,73 +559,28 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     Schedule gs = sch;
     const char* me = std::getenv("PAC_MIXED");
     if (me && (me[0] == '0' || me[0] == '1')) gs.mixed = me[0] == '1';
-    size_t off = 0;
-    for (int a = 0; a < ndim; ++a) {
-        int64_t inner = 1;
-        for (int b = a + 1; b < ndim; ++b) inner *= dims[b];
-        int64_t Lcur = dims[a];
-        for (auto [first, cnt] : split_groups(pl->stages[a], pl->esize, gs)) {
-            GroupPlan g;
-            g.axis = a;
-            g.first_stage = first;
-            g.nstages = cnt;
-            g.M = 1;
-            for (int i = 0; i < cnt; ++i) g.M *= pl->stages[a][first + i];
-            g.L = Lcur;
-            g.Lp = Lcur / g.M;
-            g.I = inner;
-            g.C = g.Lp * inner;
-            g.Q = pl->N / g.M;
-            g.has_ext = g.Lp > 1;
-            bool one_base = true;
-            for (int i = 1; i < cnt; ++i)
-                if (stage_base(pl->stages[a][first + i]) != stage_base(pl->stages[a][first])) one_base = false;
-            if (!one_base) {
-                g.mix_nr = mix_round_list(g.M, g.mix_r);
-                if (g.M > kMixMmax) {
-                    delete pl;
-                    return fail(PAC_ERR_SIZE, "mixed group size %d above %d", g.M, kMixMmax);
-                }
-            } else if (!pass_kernel_supported(g.M, pl->esize)) {
-                delete pl;
-                return fail(PAC_ERR_SIZE, "no pass kernel for group size %d", g.M);
-            }
-            // two-level split of the external exponent e = hi T + lo: T = p^ceil(e/2)
-            // when L = p^e, else (mixed radix) T = ceil(sqrt(L))
-            g.tw_T = 0;
-            for (int q : {2, 3, 5}) {
-                const int eL = exact_log(g.L, q);
-                if (eL >= 0) {
-                    g.tw_T = ipow(q, (eL + 1) / 2);
-                    g.tw_shift = (q == 2) ? (eL + 1) / 2 : -1;
-                    break;
-                }
-            }
-            if (g.tw_T == 0) {
-                int64_t T = (int64_t)std::sqrt((double)g.L);
-                while (T * T < g.L) ++T;
-                g.tw_T = (int)T;
-                g.tw_shift = -1;
-            }
-            g.off_twi = off;
-            off = align16(off + (size_t)g.M * pl->esize);
-            if (g.has_ext) {
-                g.off_lo = off;
-                off = align16(off + (size_t)g.tw_T * pl->esize);
-                g.off_hi = off;
-                off = align16(off + (size_t)((g.L + g.tw_T - 1) / g.tw_T) * pl->esize);
-            }
-            g.off_rowmap = off;
-            off = align16(off + (size_t)g.M * sizeof(int));
-            g.off_freq = off;
-            off = align16(off + (size_t)g.M * sizeof(int));
-            g.off_r2g = off;
-            off = align16(off + (size_t)g.M * sizeof(int));
-            g.off_r2f = off;
-            off = align16(off + (size_t)g.M * sizeof(int));
-            pl->groups.push_back(g);
-            Lcur = g.Lp;
+    if (int rc = form_groups(ndim, dims, pl->stages, pl->esize, gs, pl->groups)) {
+        delete pl;
+        return rc;
+    }
+    size_t off = 0;  // the groups' tables in one device allocation
+    for (GroupPlan& g : pl->groups) {
+        g.off_twi = off;
+        off = align16(off + (size_t)g.M * pl->esize);
+        if (g.has_ext) {
+            g.off_lo = off;
+            off = align16(off + (size_t)g.tw_T * pl->esize);
+            g.off_hi = off;
+            off = align16(off + (size_t)((g.L + g.tw_T - 1) / g.tw_T) * pl->esize);
         }
+        g.off_rowmap = off;
+        off = align16(off + (size_t)g.M * sizeof(int));
+        g.off_freq = off;
+        off = align16(off + (size_t)g.M * sizeof(int));
+        g.off_r2g = off;
+        off = align16(off + (size_t)g.M * sizeof(int));
+        g.off_r2f = off;
+        off = align16(off + (size_t)g.M * sizeof(int));
     }
 
     // single-launch (cooperative) form of the pass sequence: opt-in per plan,

@@ -133,3 +133,60 @@ def test_prime_factor_object_rejects_bad_lengths_before_touching_the_device(n, s
     with pytest.raises(pac.PacError) as ei:
         pac.pac_pfa_create(60, 7)
     assert ei.value.status == pac.Status.ERR_ARG
+
+
+# ---------------------------------------------------------- pass schedule (host only)
+
+@pytest.mark.parametrize("dims,radix,dtype,mixed,cap,want", [
+    ((128, 128, 128), 4, 0, False, 0, [(0, 128, [16, 8]), (1, 128, [16, 8]), (2, 128, [16, 8])]),
+    ((3125, 3125), 5, 0, False, 0, [(0, 3125, [25, 25, 5]), (1, 3125, [25, 25, 5])]),
+    ((2187,), 3, 0, False, 0, [(0, 2187, [27, 9, 9])]),
+    ((2187,), 3, 1, False, 0, [(0, 2187, [9, 9, 9, 3])]),             # FP64 rounds of base 3 stop at 9
+    ((1 << 20,), 4, 0, False, 0, [(0, 1024, [16, 8, 8]), (0, 1024, [16, 8, 8])]),
+    ((1 << 20,), 4, 0, False, 9, [(0, 64, [8, 8]), (0, 64, [8, 8]), (0, 256, [16, 16])]),  # a schedule's cap
+    ((4096,), 2, 1, False, 0, [(0, 64, [8, 8]), (0, 64, [8, 8])]),     # FP64 groups stop at 2048
+    ((1000,), 0, 0, False, 0, [(0, 8, [8]), (0, 125, [25, 5])]),       # one-base groups (default)
+    ((1000,), 0, 0, True, 0, [(0, 1000, [25, 8, 5])]),                 # one group spanning bases
+    ((6000,), 0, 0, False, 0, [(0, 16, [16]), (0, 3, [3]), (0, 125, [25, 5])]),
+    ((6000,), 0, 0, True, 0, [(0, 48, [16, 3]), (0, 125, [25, 5])]),
+    ((2 ** 10 * 3 ** 5 * 5 ** 3,), 0, 0, True, 0,                       # spanning bases would not be fewer
+     [(0, 1024, [16, 8, 8]), (0, 243, [27, 9]), (0, 125, [25, 5])]),
+])
+def test_plan_groups(dims, radix, dtype, mixed, cap, want):
+    """The pass schedule rules, pinned on the host: one-base runs split evenly
+    under the CTA's group limit (or a cap), groups spanning bases only when
+    fewer, and each group's in-CTA round radices."""
+    assert pac.pac_plan_groups(dims, radix, dtype, mixed, cap) == want
+
+
+@pytest.mark.parametrize("dims", [(30,), (360, 360), (12, 20, 30), (6000, 6000), (2 ** 7 * 3 ** 4 * 5 ** 2,), (64, 81, 25),
+                                  (2, 3, 5), (1, 1000), (4 * 27 * 125,), (3 ** 7 * 2,)])
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("mixed", [False, True])
+def test_plan_groups_invariants(dims, dtype, mixed):
+    """Any 2^a 3^b 5^c shape: per axis the group sizes multiply to the dim,
+    each group's rounds multiply to its size and are radices the kernels have,
+    one-base groups stay within the CTA limit, groups spanning bases within 2048,
+    and allowing groups spanning bases never adds groups."""
+    groups = pac.pac_plan_groups(dims, 0, dtype, mixed)
+    for a, n in enumerate(dims):
+        sizes = [m for ax, m, _ in groups if ax == a]
+        assert int(np.prod(sizes)) == n
+    limits = {2: 4096 if dtype == 0 else 2048, 3: 2187, 5: 3125}
+    for _, m, rounds in groups:
+        assert int(np.prod(rounds)) == m
+        assert set(rounds) <= {2, 3, 4, 5, 8, 9, 16, 25, 27}
+        bases = {p for p in (2, 3, 5) if m % p == 0}
+        if len(bases) == 1:
+            assert m <= limits[bases.pop()]
+        else:
+            assert mixed and m <= 2048
+    assert len(groups) <= len(pac.pac_plan_groups(dims, 0, dtype, False))
+
+
+def test_plan_groups_rejects_bad_problems():
+    for dims, radix, status in [((7,), 0, pac.Status.ERR_SIZE), ((100,), 2, pac.Status.ERR_SIZE),
+                                ((64,), 6, pac.Status.ERR_ARG), ((2, 2, 2, 2), 2, pac.Status.ERR_ARG)]:
+        with pytest.raises(pac.PacError) as ei:
+            pac.pac_plan_groups(dims, radix)
+        assert ei.value.status == status
