@@ -327,7 +327,8 @@ enum {
     PAC_Q_LAUNCHES_CONVOLVE = 3,  /* kernel launches per pac_convolve */
     PAC_Q_LAUNCHES_PERMUTED = 4,  /* kernel launches per pac_convolve_permuted */
     PAC_Q_LAUNCHES_FORWARD = 5,   /* kernel launches per pac_forward_unordered */
-    PAC_Q_DEVICE_BYTES = 6,       /* device memory the plan owns */
+    PAC_Q_DEVICE_BYTES = 6,       /* device memory the plan owns (tables it shares with plans of the
+                                     same shape, radix, dtype and schedule counted in full) */
     PAC_Q_HAS_SPECTRUM = 7,
     PAC_Q_DEVICE_ERROR = 8,       /* synchronises; returns and clears the device error word
                                      (1: a bounded grid-barrier wait gave up) */

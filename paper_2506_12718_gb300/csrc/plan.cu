@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 
 #include "pac_internal.h"
@@ -336,9 +337,63 @@ size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
 }  // namespace
 
+// Device copies of plan tables (twiddles and placement tables), shared by
+// every plan whose tables are the same bytes on the same device, with a
+// reference count: plans of one shape, radix, precision and schedule (a
+// batch of many instances of one class, the requests of a serving pool)
+// upload them once.
+namespace {
+
+struct SharedTables {
+    void* d = nullptr;
+    int refs = 0;
+};
+using TableKey = std::pair<int, std::vector<unsigned char>>;
+std::mutex g_tab_mu;
+std::map<TableKey, SharedTables> g_tables;
+std::map<void*, std::map<TableKey, SharedTables>::iterator> g_table_of;
+
+int acquire_tables(int device, const std::vector<unsigned char>& blob, void** out) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    TableKey key(device, blob);
+    auto it = g_tables.find(key);
+    if (it != g_tables.end()) {
+        ++it->second.refs;
+        *out = it->second.d;
+        return PAC_OK;
+    }
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, blob.size());
+    if (e != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(PAC_ERR_NOMEM, "device tables: out of memory")
+                                              : cuda_fail(e, "cudaMalloc(tables)");
+    e = cudaMemcpy(d, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "cudaMemcpy(tables)");
+    }
+    auto ins = g_tables.emplace(std::move(key), SharedTables{d, 1}).first;
+    g_table_of[d] = ins;
+    *out = d;
+    return PAC_OK;
+}
+
+void release_tables(void* d) {
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    auto w = g_table_of.find(d);
+    if (w == g_table_of.end()) return;
+    if (--w->second->second.refs == 0) {
+        cudaFree(d);
+        g_tables.erase(w->second);
+        g_table_of.erase(w);
+    }
+}
+
+}  // namespace
+
 static void free_plan(pac_plan p) {
     if (!p) return;
-    if (p->d_tables) cudaFree(p->d_tables);
+    if (p->d_tables) release_tables(p->d_tables);
     if (p->d_spec) cudaFree(p->d_spec);
     if (p->d_spec_nat) cudaFree(p->d_spec_nat);
     if (p->d_scratch) cudaFree(p->d_scratch);
@@ -663,16 +718,9 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
         return cuda_fail(e, "cudaGetDevice");
     }
     pl->tables_bytes = blob.size();
-    e = cudaMalloc(&pl->d_tables, pl->tables_bytes);
-    if (e != cudaSuccess) {
+    if (int rc = acquire_tables(pl->device, blob, &pl->d_tables)) {
         free_plan(pl);
-        return e == cudaErrorMemoryAllocation ? fail(PAC_ERR_NOMEM, "device tables: out of memory")
-                                              : cuda_fail(e, "cudaMalloc(tables)");
-    }
-    e = cudaMemcpy(pl->d_tables, blob.data(), blob.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        free_plan(pl);
-        return cuda_fail(e, "cudaMemcpy(tables)");
+        return rc;
     }
     pl->spec_elems = pl->N;
     if (!pl->groups.empty() && !pl->plane) {  // whole tiles of the fused pass (see SpecOrder)

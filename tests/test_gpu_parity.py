@@ -228,6 +228,33 @@ def test_empty_batch_and_n1_in_batch():
         p2.close()
 
 
+def test_shared_tables_outlive_another_plan():
+    """Plans of one problem share their device tables (reference counted):
+    destroying one leaves the others' tables in place."""
+    pac = pac_mod()
+    dims, radix, dtype = (64, 64), 4, "c64"
+    fs, h, x = separable_case(dims, dtype, seed=71)
+    ref = oracle.conv_separable(fs, x)
+    plans = [pac.Plan(dims, radix, dtype) for _ in range(3)]
+    try:
+        for p in plans:
+            p.filter_spectrum(dev(h))
+        plans[0].close()
+        plans[1].close()
+        y = plans[2].convolve(dev(x))
+        torch.cuda.synchronize()
+        check(y.cpu().numpy(), ref, dtype, x.size, "after two plans of the same problem were destroyed")
+        again = pac.Plan(dims, radix, dtype)  # takes the surviving copy
+        try:
+            again.filter_spectrum(dev(h))
+            check(again.convolve(dev(x)).cpu().numpy(), ref, dtype, x.size, "a new plan of the same problem")
+        finally:
+            again.close()
+    finally:
+        for p in plans:
+            p.close()
+
+
 def test_single_element():
     h = np.array([2.0 - 1.0j], np.complex128)
     x = np.array([0.5 + 3.0j], np.complex128)
