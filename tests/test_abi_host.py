@@ -190,3 +190,25 @@ def test_plan_groups_rejects_bad_problems():
         with pytest.raises(pac.PacError) as ei:
             pac.pac_plan_groups(dims, radix)
         assert ei.value.status == status
+
+
+def test_header_is_c_and_the_library_links_from_c():
+    """include/pac.h compiles as C99 with warnings as errors, a C program links
+    libpac.so and calls the host-only entry points (no GPU)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    lib_dir = os.path.dirname(pac.LIB_PATH)
+    exe = os.path.join(lib_dir, "_build", "abi_host")  # beside the library's other build products
+    os.makedirs(os.path.dirname(exe), exist_ok=True)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_host.c"), "-L", lib_dir, "-lpac", f"-Wl,-rpath,{lib_dir}",
+                    "-o", exe], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines()
+    assert out[0] == "stages 4 2 5 5 5"
+    assert out[1] == "reverse " + " ".join(str(v) for v in pf.pos_to_freq([4, 4, 2])[[0, 1, 31]])
+    assert out[2] == "groups 2 48 125"
+    assert out[3] == f"error {int(pac.Status.ERR_SIZE)} message"
+    assert out[4].startswith("version ") and "sm_103a" in out[4]
