@@ -128,7 +128,8 @@ extern "C" int pac_pfa_create(int64_t n, pac_dtype dtype, pac_pfa* out) {
         if (pq > 1) f[t++] = pq;
     }
     if (m != 1) return fail(PAC_ERR_SIZE, "length %lld is not of the form 2^a 3^b 5^c", (long long)n);
-    std::sort(f, f + t);  // n_1 <= ... <= n_t
+    for (int i = 1; i < t; ++i)  // ascending: n_1 <= ... <= n_t
+        for (int j = i; j > 0 && f[j - 1] > f[j]; --j) std::swap(f[j - 1], f[j]);
     pac_pfa p = new (std::nothrow) pac_pfa_s();
     if (!p) return fail(PAC_ERR_NOMEM, "host allocation failed");
     p->n = n;

@@ -599,8 +599,9 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
         pl->N *= dims[a];
     }
     if (pl->N >= (int64_t(1) << 31)) {
+        const long long n = (long long)pl->N;
         delete pl;
-        return fail(PAC_ERR_SIZE, "N = %lld too large", (long long)pl->N);
+        return fail(PAC_ERR_SIZE, "N = %lld too large (the kernels take N < 2^31)", n);
     }
     pl->stages = stages;
     pl->pos_to_freq.resize(ndim);

@@ -107,6 +107,13 @@ def test_plan_create_stages_rejects_bad_lists_before_touching_the_device(dims, s
     assert ei.value.status == status
 
 
+def test_plan_create_rejects_arrays_of_2_31_elements_or_more():
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_plan_create(3, [2048, 2048, 512], 2, pac.C64)
+    assert ei.value.status == pac.Status.ERR_SIZE
+    assert "2147483648" in str(ei.value)
+
+
 def test_plan_create_stages_wants_one_list_per_axis():
     with pytest.raises(ValueError):
         pac.pac_plan_create_stages([4, 6], [[4]], pac.C64)
