@@ -349,7 +349,7 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
         for r in (3, 5):
             c = pin.c3(r, dt)
             cases.append((c, f"2-D {c.dims[0]}^2, radix {r}, complex {'FP32' if dt == 'c64' else 'FP64'}"))
-    # mixed radix (Section 6.1): 1000 = 2^3 5^3, 6000 = 2^4 3 5^3, 120 = 2^3 3 5
+    # mixed radix (Section 7.1): 1000 = 2^3 5^3, 6000 = 2^4 3 5^3, 120 = 2^3 3 5
     cases.append((pin.mixed((1000, 1000)), "2-D 1000^2, mixed radix 2^3 5^3, complex FP32"))
     cases.append((pin.mixed((6000, 6000)), "2-D 6000^2, mixed radix 2^4 3 5^3, complex FP32"))
     cases.append((pin.mixed((120, 120, 120)), "3-D 120^3, mixed radix 2^3 3 5, complex FP32"))
@@ -429,7 +429,7 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
 
 
 def prime_factor_entry(torch, pac, dev, stream, flush, peak):
-    """The prime factor form (Section 6.2) of a 1-D length n = 2^10 3^5 5^3
+    """The prime factor form (Section 7.2) of a 1-D length n = 2^10 3^5 5^3
     (FP32): three permutations around the 3-D convolution of shape
     (1024, 243, 125), against the permutation-free mixed-radix 1-D plan of
     the same n and cuFFT; the two per-call permutations' share of the prime
@@ -455,7 +455,7 @@ def prime_factor_entry(torch, pac, dev, stream, flush, peak):
         Hn = torch.fft.fft(h)
         ms_cufft = time_steps(torch, lambda: torch.fft.ifft(torch.fft.fft(x) * Hn, out=xt), 10, 3, flush, stream)
         t_pfa, t_inner, t_ct, t_cu = (statistics.median(v) for v in (ms_pfa, ms_inner, ms_ct, ms_cufft))
-        return {"workload": "1-D n=2^10 3^5 5^3 (31.1 M), complex FP32: prime factor form (Section 6.2) "
+        return {"workload": "1-D n=2^10 3^5 5^3 (31.1 M), complex FP32: prime factor form (Section 7.2) "
                             "against the mixed-radix plan",
                 "dims": [n], "radix": 0, "dtype": "c64", "ms": t_ct, "GBps": B / (t_ct * 1e-3) / 1e9,
                 "pct_hbm_roofline": B / (t_ct * 1e-3) / 1e9 / peak,

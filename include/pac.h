@@ -16,7 +16,7 @@
  * that multiplies by it reads it (a fixed rearrangement of the
  * index-reversed order, applied once when the spectrum is made), so the
  * convolution itself never permutes anything.  Per axis, n = r^t or a
- * mixed-radix product (Section 6.1).
+ * mixed-radix product (Section 7.1).
  *
  * Conventions shared by every entry point:
  *  - Arrays are complex, interleaved (re, im), row-major with the last index
@@ -75,8 +75,8 @@ typedef enum {
  * decimation-in-frequency stage list is [r, r, ..., r] (Section 2.1); when
  * the exponent is not a multiple of log_p r the leftover factor becomes one
  * smaller stage of base p placed last (e.g. 128 with radix 4 -> [4,4,4,2];
- * with radix 8 -> [8,8,2]), the mixed-radix framework of Section 6.1.
- * radix 0 (mixed radix, Section 6.1): each dim is any 2^a 3^b 5^c, with the
+ * with radix 8 -> [8,8,2]), the mixed-radix framework of Section 7.1.
+ * radix 0 (mixed radix, Section 7.1): each dim is any 2^a 3^b 5^c, with the
  * stage list [4,..,4,(2), 3,..,3, 5,..,5] (the factor 2^a in radix-4 stages,
  * a leftover 2 last, then the 3s and the 5s).  A dim of 1 is allowed (empty
  * stage list).  Builds twiddle tables in FP64, rounds them once to dtype and
@@ -88,7 +88,7 @@ int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, p
 
 /*
  * The same from explicit per-axis DIF stage lists, in any order (the
- * mixed-radix framework of Section 6.1: A_rho with rho the list reversed,
+ * mixed-radix framework of Section 7.1: A_rho with rho the list reversed,
  * so stages[0] of an axis acts first, on the full length).  nstages[a]
  * stages for axis a, concatenated in `stages` (host memory, read only
  * during the call).  Each stage is a power of 2, 3 or 5 in [2, 32]; the
@@ -153,7 +153,7 @@ int pac_convolve_many_launches(int count, const pac_plan* plans, int* launches);
 /* ------------------------------------------------------ prime factor form */
 
 /*
- * Prime factor convolution (Section 6.2) of a 1-D length n = 2^a 3^b 5^c:
+ * Prime factor convolution (Section 7.2) of a 1-D length n = 2^a 3^b 5^c:
  * with the pairwise coprime factors n_1 < ... < n_t (the nonzero prime
  * powers of n, t <= 3),
  *   y = Gamma (conj A_{n_t} x ... x conj A_{n_1})
@@ -234,7 +234,7 @@ int pac_plan_stages(pac_plan p, int axis, int* radices, int* count);
 /*
  * Per-axis index-reversal table of a plan: pos_to_freq[p] = the frequency that
  * the unordered (A^T) output holds at position p along that axis (F = P A^T,
- * Section 2.1; F = P_rho A_rho^T, Section 6.1).  Host copy of dims[axis] entries.
+ * Section 2.1; F = P_rho A_rho^T, Section 7.1).  Host copy of dims[axis] entries.
  */
 int pac_plan_reverse_table(pac_plan p, int axis, int64_t* pos_to_freq);
 
@@ -295,7 +295,11 @@ int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, vo
  * calls whose work overlaps on the GPU race (serialise them on one stream).
  * The buffer needs no clearing (every element is written before it is read).
  * The first call on each device looks up the buffer's device address; make it
- * before any stream capture.  Asynchronous on `stream`; y_dev may equal x_dev.
+ * before any stream capture.  That address is kept for the life of the
+ * process: after cudaDeviceReset (or anything else that destroys the
+ * device's primary context) it is stale, like every plan made before the
+ * reset, so the library must not be used across a device reset.
+ * Asynchronous on `stream`; y_dev may equal x_dev.
  */
 int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void* y_dev, void* stream);
 

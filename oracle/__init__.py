@@ -17,8 +17,8 @@ Routes (all FP64, interleaved complex, row-major with the last index fastest):
 * ``unordered_forward``   A^T x = P^T F x per axis, with P from the paper's
                           definition (``paper_forms.pos_to_freq``)
 * ``paper_forms``         the paper's matrix forms for tiny n (Eq. 25, Eq. 35, Eq. 80),
-                          the mixed-radix A_rho, P_rho (Section 6.1) and the prime factor
-                          maps and convolution (Section 6.2)
+                          the mixed-radix A_rho, P_rho (Section 7.1) and the prime factor
+                          maps and convolution (Section 7.2)
 
 Parity: every route is pinned by ``tests/test_oracle_pins.py`` (brute force,
 library routines, closed forms and invariants); none is unpinned.
@@ -149,7 +149,7 @@ def unordered_forward(x, stages_per_axis) -> np.ndarray:
     """A^T x per axis (DIF output): DFT then the paper's index-reversal order.
 
     Along each axis position p holds frequency pos_to_freq(stages)[p]
-    (F = P A^T, Section 2.1; F = P_rho A_rho^T, Section 6.1).
+    (F = P A^T, Section 2.1; F = P_rho A_rho^T, Section 7.1).
     """
     X = dft(x)
     for a, st in enumerate(stages_per_axis):

@@ -9,12 +9,12 @@ definitions in its notation; nothing is blocked, fused or reordered.
 * ``index_reversal(r, n)``      P_{r,n} = R_{r,t,n} ... R_{r,1,n}                      (Section 2.1)
 * ``butterfly(r, k)``           B_{r,k} = (F_r (x) I_{k/r}) diag(I, W, ..., W^{r-1})    (Eq. 25)
 * ``a_uniform(r, n)``           A_{r,n} = B_{r,t,n} ... B_{r,1,n}                      (Section 2.1)
-* ``a_mixed(rho)``, ``p_mixed(rho)``  A_rho and P_rho of the mixed-radix framework   (Section 6.1)
+* ``a_mixed(rho)``, ``p_mixed(rho)``  A_rho and P_rho of the mixed-radix framework   (Section 7.1)
 * ``conv_eq35(h, x, ...)``      conj(A)((A^T h) o (A^T x)) / n                          (Eq. 35)
-* ``conv_eq80(H, X, ...)``      the 2-D / d-D Kronecker form                           (Eq. 80, Section 4.1)
+* ``conv_eq80(H, X, ...)``      the 2-D / d-D Kronecker form                           (Eq. 80, Sections 3.1 and 4.1)
 * ``coprime_factors(n)``, ``crt_gamma``, ``ruritanian_upsilon``, ``conv_pfa``
                                 the prime factor framework: F_n = Gamma (F_{n_t} (x) ... (x) F_{n_1}) Upsilon^T
-                                and the convolution with three permutations               (Section 6.2)
+                                and the convolution with three permutations               (Section 7.2)
 
 Index conventions are zero-based.  A permutation matrix is returned as an
 index array ``perm`` with (P v)[p] = v[perm[p]].
@@ -72,7 +72,7 @@ def mod_sort(r: int, n: int) -> np.ndarray:
 
 
 def perfect_shuffle(r: int, n: int) -> np.ndarray:
-    """Pi_{r,n}: the inverse of the modulo-r sort (Section 6.1)."""
+    """Pi_{r,n}: the inverse of the modulo-r sort (Section 7.1)."""
     s = mod_sort(r, n)
     inv = np.empty_like(s)
     inv[s] = np.arange(n)
@@ -116,7 +116,7 @@ def a_uniform(r: int, n: int) -> np.ndarray:
 
 
 def a_mixed(rho) -> np.ndarray:
-    """A_rho = B_{r_t,n} (I (x) B_{r_{t-1}, r_1..r_{t-1}}) ... (I_{n/r_1} (x) B_{r_1,r_1}) (Section 6.1)."""
+    """A_rho = B_{r_t,n} (I (x) B_{r_{t-1}, r_1..r_{t-1}}) ... (I_{n/r_1} (x) B_{r_1,r_1}) (Section 7.1)."""
     n = int(np.prod(rho))
     a = np.eye(n, dtype=complex)
     k = 1
@@ -127,7 +127,7 @@ def a_mixed(rho) -> np.ndarray:
 
 
 def p_mixed(rho) -> np.ndarray:
-    """P_rho = Pi_{r_t,n} (I (x) Pi_{r_{t-1}, r_1..r_{t-1}}) ... (I_{n/r_1} (x) Pi_{r_1,r_1}) (Section 6.1)."""
+    """P_rho = Pi_{r_t,n} (I (x) Pi_{r_{t-1}, r_1..r_{t-1}}) ... (I_{n/r_1} (x) Pi_{r_1,r_1}) (Section 7.1)."""
     n = int(np.prod(rho))
     perm = np.arange(n)
     k = 1
@@ -156,7 +156,7 @@ def pos_to_freq(stages) -> np.ndarray:
     """Frequency held at each position of the DIF (A^T) output for a stage list.
 
     From F = P A^T with P symmetric (uniform radix, Section 2.1) or
-    F = P_rho A_rho^T (Section 6.1): A^T x = P^T F x, so position p holds
+    F = P_rho A_rho^T (Section 7.1): A^T x = P^T F x, so position p holds
     frequency (P^T idx)[p].
     """
     stages = list(stages)
@@ -184,7 +184,7 @@ def conv_eq35(h: np.ndarray, x: np.ndarray, stages) -> np.ndarray:
 
 
 def conv_eq80(h: np.ndarray, x: np.ndarray, stages_per_axis) -> np.ndarray:
-    """d-D permutation-avoiding convolution (Eq. 80 and Section 4.1), Kronecker form.
+    """d-D permutation-avoiding convolution (Eq. 80 of Section 3.1 and its d-D form, Section 4.1), Kronecker form.
 
     vec(F_H(X)) = (conj A_1 (x) ... (x) conj A_d)[((A_1^T (x)..) vec H) o ((A_1^T (x)..) vec X)] / N
     with row-major vec (last index fastest).
@@ -200,12 +200,12 @@ def conv_eq80(h: np.ndarray, x: np.ndarray, stages_per_axis) -> np.ndarray:
     return y.reshape(x.shape)
 
 
-# ------------------------------------------------- prime factor framework (Section 6.2)
+# ------------------------------------------------- prime factor framework (Section 7.2)
 
 
 def coprime_factors(n: int) -> list:
     """n = 2^a 3^b 5^c as its pairwise coprime prime powers [n_1, ..., n_t], ascending
-    (the factors of Section 6.2; [] for n = 1)."""
+    (the factors of Section 7.2; [] for n = 1)."""
     out = []
     for p in (2, 3, 5):
         q = 1
@@ -229,14 +229,14 @@ def _tensor_index(idx, factors) -> int:
 
 
 def crt_gamma(factors) -> np.ndarray:
-    """Gamma of Section 6.2 as an index array, (Gamma v)[k] = v[gamma[k]]: output k of
+    """Gamma of Section 7.2 as an index array, (Gamma v)[k] = v[gamma[k]]: output k of
     the length-n transform is tensor entry (k mod n_t, ..., k mod n_1) (Chinese remainders)."""
     n = int(np.prod(factors)) if len(factors) else 1
     return np.array([_tensor_index([k % m for m in factors], factors) for k in range(n)], dtype=np.int64)
 
 
 def ruritanian_upsilon(factors) -> np.ndarray:
-    """Upsilon of Section 6.2 as an index array, (Upsilon v)[i] = v[upsilon[i]]: input
+    """Upsilon of Section 7.2 as an index array, (Upsilon v)[i] = v[upsilon[i]]: input
     i = sum_q (n / n_q) i_q mod n is tensor entry (i_t, ..., i_1), i.e.
     i_q = i (n / n_q)^{-1} mod n_q."""
     n = int(np.prod(factors)) if len(factors) else 1
@@ -254,7 +254,7 @@ def kron_fourier(factors) -> np.ndarray:
 
 
 def conv_pfa(h: np.ndarray, x: np.ndarray, factors) -> np.ndarray:
-    """Prime factor convolution of Section 6.2 for a 1-D length n = n_1 ... n_t:
+    """Prime factor convolution of Section 7.2 for a 1-D length n = n_1 ... n_t:
     Gamma (conj A_{n_t} (x) ... (x) conj A_{n_1}) [((A^T ...) Gamma^T h) o ((A^T ...) Gamma^T x)] / n,
     the three permutations being Gamma^T h, Gamma^T x and Gamma.  Each A_{n_q} is
     the uniform-radix A of its prime (Section 2.1); the bracket is the d-D form of

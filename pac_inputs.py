@@ -5,7 +5,7 @@ holds input construction only (random signals, filters, workload mixes) and
 none of the convolution arithmetic: no DFT, no butterfly, no index reversal.
 
 Workloads follow the shapes the paper benchmarks (1-D, 2-D and 3-D arrays
-whose axes are powers of the radix, Section 5) with the distributions stated
+whose axes are powers of the radix, Section 6) with the distributions stated
 for this build's five workloads:
 
 * ``c1``: 1-D n=2^10, radix 2, complex FP64, x and h with re/im ~ U[-1,1].

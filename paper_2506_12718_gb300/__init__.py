@@ -438,7 +438,7 @@ class Plan:
 
 
 class Pfa:
-    """Prime factor convolution of a 1-D length n = 2^a 3^b 5^c (Section 6.2),
+    """Prime factor convolution of a 1-D length n = 2^a 3^b 5^c (Section 7.2),
     bound to torch tensors (complex64 / complex128, on CUDA)."""
 
     def __init__(self, n: int, dtype: str = "c64"):

@@ -111,7 +111,7 @@ constexpr int min_blocks(int m, int esize) {
 
 // ------------------------------------------------------------ mixed groups
 // A group whose stages have more than one prime base (mixed radix, Section
-// 6.1) runs in the runtime-radix kernel (mix.cuh): the tile is copied into
+// 7.1) runs in the runtime-radix kernel (mix.cuh): the tile is copied into
 // shared memory, transformed by rounds whose radices are the prime-power
 // parts of M (each split like a one-base group: at most 16 for base 2, 9 for
 // base 3, 25 for base 5; larger first), and copied out.

@@ -9,7 +9,7 @@
 // column j in [0, L') of a block, an M-point DFT over the elements j + L' m,
 // then the factor w_L^{j k'} on output frequency k', written to block
 // position p(k') * L' + j, where p is the digit-reversed position of k' for
-// the group's stage list (Sections 2.1 and 6.1).  The kernel computes exactly
+// the group's stage list (Sections 2.1 and 7.1).  The kernel computes exactly
 // that map; inside the CTA it evaluates the M-point DFT in "rounds" of
 // in-register DFTs through shared memory.  Only the placement p matters for
 // the result, and it comes from the plan's tables.

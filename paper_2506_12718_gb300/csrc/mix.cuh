@@ -1,4 +1,4 @@
-// Runtime-radix pass kernel for mixed groups (mixed radix, Section 6.1).
+// Runtime-radix pass kernel for mixed groups (mixed radix, Section 7.1).
 //
 // A mixed group is a run of DIF stages of several prime bases (e.g. 48 =
 // 16 x 3 or 1000 = 8 x 125 of an axis 2^a 3^b 5^c).  One kernel serves every

@@ -96,7 +96,11 @@ std::mutex g_mu;
 void* g_ptr[64];
 bool g_ready[64];
 
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device, looked up once
+// per device and kept for the life of the process.  A device reset destroys
+// the primary context and reloads the module at another address, so the
+// cached address (like every plan's device memory) is stale after one: the
+// library is not used across a device reset.
 int scratch_address(int device, void** out) {
     if (device < 0 || device >= 64) return fail(PAC_ERR_ARG, "device %d out of range", device);
     std::lock_guard<std::mutex> lk(g_mu);

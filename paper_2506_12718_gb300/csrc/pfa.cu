@@ -1,4 +1,4 @@
-// Prime factor convolution (Section 6.2).
+// Prime factor convolution (Section 7.2).
 //
 // A 1-D length n = n_1 ... n_t with pairwise coprime factors (the prime
 // powers 2^a, 3^b, 5^c of n, ascending) is convolved as a t-D

@@ -1,7 +1,7 @@
 // Plan builder and the plan-level C-ABI entry points.
 //
 // A plan fixes, per axis, the decimation-in-frequency stage list (Section 2.1
-// for a uniform radix; the mixed-radix framework of Section 6.1 for the
+// for a uniform radix; the mixed-radix framework of Section 7.1 for the
 // leftover stage), splits it into groups that one CTA can transform in shared
 // memory, and builds every table the pass kernels read: round twiddles
 // w_M^u, the two-level external twiddles w_L^e, and per group the placement
@@ -114,7 +114,7 @@ static int stage_base(int r) {
 
 // DIF stage list of an axis.  radix in {2,3,4,5,8}: [r]*(e/f) then a
 // leftover stage p^(e mod f).  radix 0, the mixed-radix framework of
-// Section 6.1 for n = 2^a 3^b 5^c: the factor 2^a as radix-4 stages (a
+// Section 7.1 for n = 2^a 3^b 5^c: the factor 2^a as radix-4 stages (a
 // leftover 2 last), then b stages of 3, then c stages of 5.
 static int stage_list(int64_t n, int radix, std::vector<int>& out) {
     out.clear();
@@ -587,22 +587,26 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
             return fail(PAC_ERR_SIZE, "the stages of axis %d do not multiply to %lld", a, (long long)dims[a]);
     }
 
+    // N < 2^31 (32-bit element offsets in the kernels), checked before each
+    // multiply so that no product of up to three 2^30 dims can overflow
+    int64_t n_total = 1;
+    for (int a = 0; a < ndim; ++a) {
+        if (n_total > ((int64_t(1) << 31) - 1) / dims[a]) {
+            double n = 1.0;  // exact for the message: a product of at most three 2^30 dims
+            for (int b = 0; b < ndim; ++b) n *= (double)dims[b];
+            return fail(PAC_ERR_SIZE, "N = %.0f too large (the kernels take N < 2^31)", n);
+        }
+        n_total *= dims[a];
+    }
+
     pac_plan pl = new (std::nothrow) pac_plan_s();
     if (!pl) return fail(PAC_ERR_NOMEM, "host allocation failed");
     pl->ndim = ndim;
     pl->radix = radix;
     pl->dtype = dtype;
     pl->esize = dtype == PAC_C64 ? 8 : 16;
-    pl->N = 1;
-    for (int a = 0; a < ndim; ++a) {
-        pl->dims[a] = dims[a];
-        pl->N *= dims[a];
-    }
-    if (pl->N >= (int64_t(1) << 31)) {
-        const long long n = (long long)pl->N;
-        delete pl;
-        return fail(PAC_ERR_SIZE, "N = %lld too large (the kernels take N < 2^31)", n);
-    }
+    pl->N = n_total;
+    for (int a = 0; a < ndim; ++a) pl->dims[a] = dims[a];
     pl->stages = stages;
     pl->pos_to_freq.resize(ndim);
     for (int a = 0; a < ndim; ++a) {

@@ -3,6 +3,7 @@ its host-only rules (stage lists, index-reversal tables) match the oracle's
 reading of the paper bit for bit.  No compute call needs a GPU here."""
 import os
 import re
+import time
 
 import numpy as np
 import pytest
@@ -44,7 +45,7 @@ def test_version():
 @pytest.mark.parametrize("n,radix,want", [
     (128, 2, [2] * 7), (128, 4, [4, 4, 4, 2]), (128, 8, [8, 8, 2]), (1024, 4, [4] * 5),
     (2187, 3, [3] * 7), (3125, 5, [5] * 5), (64, 8, [8, 8]), (2, 8, [2]), (1, 2, []), (32, 4, [4, 4, 2]),
-    # radix 0: mixed radix (Section 6.1), 2^a as radix-4 stages (a leftover 2 last), then 3s, then 5s
+    # radix 0: mixed radix (Section 7.1), 2^a as radix-4 stages (a leftover 2 last), then 3s, then 5s
     (1000, 0, [4, 2, 5, 5, 5]), (360, 0, [4, 2, 3, 3, 5]), (128, 0, [4, 4, 4, 2]), (81, 0, [3] * 4),
     (30, 0, [2, 3, 5]), (1, 0, []), (5, 0, [5]), (6000, 0, [4, 4, 3, 5, 5, 5]),
 ])
@@ -112,6 +113,20 @@ def test_plan_create_rejects_arrays_of_2_31_elements_or_more():
         pac.pac_plan_create(3, [2048, 2048, 512], 2, pac.C64)
     assert ei.value.status == pac.Status.ERR_SIZE
     assert "2147483648" in str(ei.value)
+
+
+@pytest.mark.parametrize("dims,text", [([1 << 30, 1 << 30, 16], "18446744073709551616"),
+                                       ([1 << 30, 1 << 30, 2], "2305843009213693952"),
+                                       ([1 << 30, 4, 1], "4294967296")])
+def test_plan_create_rejects_products_that_overflow_64_bits(dims, text):
+    # each dim is in range, but the product of three of them exceeds 2^63: the
+    # check must come before the multiply, not after a wrapped product
+    t0 = time.perf_counter()
+    with pytest.raises(pac.PacError) as ei:
+        pac.pac_plan_create(3, dims, 2, pac.C64)
+    assert ei.value.status == pac.Status.ERR_SIZE
+    assert text in str(ei.value)
+    assert time.perf_counter() - t0 < 5.0
 
 
 def test_plan_create_stages_wants_one_list_per_axis():

@@ -316,7 +316,7 @@ def test_large_groups_match_oracle(dims, radix, dtype):
     ((6561,), 3, "c128"), ((32, 64), 8, "c64"), ((2187,), 3, "c64"),
 ])
 def test_forward_is_dft_in_index_reversed_order(dims, radix, dtype):
-    """The fixed fact of the method: A^T x = P^T F x, per axis (Sections 2.1, 6.1)."""
+    """The fixed fact of the method: A^T x = P^T F x, per axis (Sections 2.1, 7.1)."""
     pac = pac_mod()
     x = pin.as_dtype(pin.complex_uniform(dims, 11), dtype)
     plan = pac.Plan(dims, radix, dtype)
@@ -372,7 +372,7 @@ MIXED_SHAPES = [((30,), "c128"), ((360,), "c64"), ((1000,), "c128"), ((2700,), "
 
 @pytest.mark.parametrize("dims,dtype", MIXED_SHAPES, ids=[f"{'x'.join(map(str, d))}-{t}" for d, t in MIXED_SHAPES])
 def test_mixed_radix_plans(dims, dtype):
-    """radix 0, n = 2^a 3^b 5^c per axis (Section 6.1): one pass per run of one
+    """radix 0, n = 2^a 3^b 5^c per axis (Section 7.1): one pass per run of one
     prime base, external twiddles of non-prime-power lengths; the
     convolution against the oracle."""
     fs, h, x = separable_case(dims, dtype, seed=sum(dims))
@@ -418,7 +418,7 @@ STAGE_ORDERS = [((60,), [[3, 4, 5]], "c128"), ((60,), [[5, 3, 2, 2]], "c128"), (
                          ids=[f"{'x'.join(map(str, d))}-{'_'.join('.'.join(map(str, s)) for s in st)}-{t}"
                               for d, st, t in STAGE_ORDERS])
 def test_explicit_stage_lists(dims, stages, dtype, mixed, monkeypatch):
-    """Any stage order (Section 6.1, A_rho with rho = the DIF list reversed):
+    """Any stage order (Section 7.1, A_rho with rho = the DIF list reversed):
     the unordered transform is the DFT in that list's digit-reversed order
     (the oracle's P_rho), and the convolution does not depend on the order;
     with one-base groups and with groups spanning bases."""
@@ -512,7 +512,7 @@ def test_mixed_radix_large_sampled(dims, dtype):
         torch.cuda.empty_cache()
 
 
-# ------------------------------------------------ prime factor form (Section 6.2)
+# ------------------------------------------------ prime factor form (Section 7.2)
 
 PFA_CASES = [(6, "c128"), (10, "c64"), (12, "c128"), (60, "c128"), (360, "c64"), (1000, "c128"), (6000, "c64"),
              (81, "c64"), (1, "c128"), (2 ** 6 * 3 ** 3 * 5 ** 2, "c64"), (2 ** 5 * 125, "c128")]
@@ -521,7 +521,7 @@ PFA_CASES = [(6, "c128"), (10, "c64"), (12, "c128"), (60, "c128"), (360, "c64"),
 @pytest.mark.parametrize("n,dtype", PFA_CASES, ids=[f"{n}-{t}" for n, t in PFA_CASES])
 def test_prime_factor_convolution(n, dtype):
     """Three permutations around a t-D convolution of shape (n_t, ..., n_1)
-    (Section 6.2): against the definition, in place, and equal to the
+    (Section 7.2): against the definition, in place, and equal to the
     permutation-free mixed-radix 1-D plan."""
     pac = pac_mod()
     h = pin.as_dtype(pin.complex_uniform((n,), 50 + n % 97), dtype)

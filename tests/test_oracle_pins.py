@@ -22,7 +22,7 @@ from oracle import paper_forms as pf
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 RADIX_LISTS = [[2] * 4, [4, 4], [8, 8], [3, 3, 3], [5, 5], [2] * 6, [3] * 4,
                [4, 4, 4, 2], [2, 4, 4, 4], [8, 8, 2], [2, 8, 8], [2, 3, 4], [4, 2, 2],
-               # mixed prime bases in any order (Section 6.1): 2^a 3^b 5^c
+               # mixed prime bases in any order (Section 7.1): 2^a 3^b 5^c
                [2, 3, 5], [5, 3, 2, 2], [3, 5, 2, 3], [4, 2, 5, 5], [5, 2, 5, 4]]
 
 
@@ -321,7 +321,7 @@ def test_mutation_transposed_stage_list_caught():
     assert not np.allclose(pf.a_transpose(stages) @ x, oracle.dft(x)[wrong], atol=1e-6)
 
 
-# ----------------------------------------------- prime factor framework (Section 6.2)
+# ----------------------------------------------- prime factor framework (Section 7.2)
 
 
 @pytest.mark.parametrize("n,want", [(6, [2, 3]), (10, [2, 5]), (60, [3, 4, 5]), (1000, [8, 125]), (81, [81]),
@@ -332,7 +332,7 @@ def test_coprime_factors(n, want):
 
 @pytest.mark.parametrize("n", [6, 10, 12, 15, 30, 60, 90])
 def test_prime_factor_fourier_factorisation(n):
-    """Section 6.2: F_n = Gamma (F_{n_t} (x) ... (x) F_{n_1}) Upsilon^T with Gamma the
+    """Section 7.2: F_n = Gamma (F_{n_t} (x) ... (x) F_{n_1}) Upsilon^T with Gamma the
     Chinese-remainder output map and Upsilon the Ruritanian input map; both are
     permutations.  Where the two maps differ (n / n_q != 1 mod n_q for some q;
     for n = 30 they coincide), Gamma on both sides does not factor F_n."""
@@ -348,7 +348,7 @@ def test_prime_factor_fourier_factorisation(n):
 
 @pytest.mark.parametrize("n", [6, 10, 12, 15, 30, 60, 90, 120])
 def test_prime_factor_convolution_equals_definition(n):
-    """Section 6.2's convolution with three permutations equals the definition (O1)."""
+    """Section 7.2's convolution with three permutations equals the definition (O1)."""
     h, x = rand_c((n,), 30 + n), rand_c((n,), 31 + n)
     assert oracle.rel_l2(pf.conv_pfa(h, x, pf.coprime_factors(n)), oracle.conv_direct(h, x)) < 1e-13
 
