@@ -1,17 +1,22 @@
 #!/usr/bin/env python3
 """Benchmark of the permutation-avoiding FFT convolution on GB300.
 
-One step = one whole convolution y = conj(A)((A^T x) o Hhat) of the flagship
-workload (3-D periodic convolution 128^3, complex FP32, radix 4 -> stage list
-[4,4,4,2] per axis, Gaussian filter spectrum resident), inputs resident in
-HBM, L2 flushed (512 MiB write) before every step outside the timed events.
+One step = one whole convolution y = conj(A)((A^T x) o Hhat) of the main
+workload (default: 2-D periodic convolution 3125^2, complex FP64, radix 5,
+stage list [5,5,5,5,5] per axis, separable exponential filter spectrum
+resident), inputs resident in HBM, L2 flushed (512 MiB write) before every
+step outside the timed events.
 
 Metric: GB/s of compulsory traffic B = 3 N S per convolution (read x, read
-the resident spectrum, write y; N = 128^3, S = 8 bytes), next to the same GPU
-running the permuted form (same kernels plus explicit index-reversal passes)
-and a cuFFT-based convolution, with the CPU oracle timed on the host.
+the resident spectrum, write y; N = 3125^2, S = 16 bytes), next to the same
+GPU running the permuted form (same kernels plus explicit index-reversal
+passes) and a cuFFT-based convolution, with the FP64 oracle timed on the
+host and the result's relative L2 error against it.  Complex FP64 passes are
+bound by GB300's FP64 pipe, so the line's roofline is the ALU one (flops
+2 c_r N log2 N + 6 N over the FP64 peak), with the HBM fraction beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pac|reference]
+                    [--workload conv2d-r5|conv2d-r3|conv3d|conv1d] [--dtype c128|c64]
 
 With N > 1 (launched by torch.distributed.run) every rank runs an
 independent replica on its own GPU; value = all ranks' bytes / max time.
@@ -29,6 +34,8 @@ import subprocess
 import sys
 import threading
 import time
+
+import numpy as np
 
 # One hardware work queue per stream for the serving queue's request streams
 # (read when CUDA starts; the default of 8 lets a small request's kernels
@@ -50,13 +57,13 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["pac", "reference"], default="pac")
-    ap.add_argument("--radix", type=int, default=4)
-    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--radix", type=int, default=4, help="radix of the conv3d workload")
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c128")
     ap.add_argument("--n", type=int, default=128, help="edge of the 3-D cube")
-    ap.add_argument("--workload", choices=["conv3d", "conv2d-r3", "conv2d-r5", "conv1d"], default="conv3d",
-                    help="the main leg's problem (default: the 3-D n^3 workload)")
+    ap.add_argument("--workload", choices=["conv3d", "conv2d-r3", "conv2d-r5", "conv1d"], default="conv2d-r5",
+                    help="the main leg's problem (default: the 2-D 3125^2 radix-5 workload)")
     ap.add_argument("--quick", action="store_true", help="main leg only (for profiler runs)")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline and the oracle checks")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--legs", default="configs,batched,served",  # "none": the main leg only
                     help="extra legs after the main one: configs (every workload shape, dtype and radix, "
@@ -223,7 +230,237 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+# ------------------------------------------------------- roofline arithmetic
+
+# ALU peaks from the GB300's unit counts and maximum SM clock: 152 SMs at
+# 2070 MHz; FP64: 2 fused multiply-adds per clock per SM (4 flops), i.e.
+# 1.26 TFLOP/s, GB300's published FP64 rate of 1.25 TFLOP/s; FP32: 128 FMA
+# lanes per SM (256 flops per clock), 80.5 TFLOP/s.  The FMA probe of the
+# library (pac_measure_fma_peak) is reported beside them.
+SMS, SM_MAX_MHZ = 152, 2070.0
+ALU_PEAK_GFLOPS = {"c128": SMS * SM_MAX_MHZ * 4 / 1e3, "c64": SMS * SM_MAX_MHZ * 256 / 1e3}
+
+# Flops per point and log2 of the length of one transform, c_r in
+# c_r N log2 N: the paper's counts for radix 2, 4, 8 (5, 4.25, 4.08; Section
+# 5); for powers of 3 and 5 the estimate (flops(DFT_p) + 6 (p - 1)) / p per
+# point and stage over log2 p (16-flop DFT_3, 44-flop DFT_5: 5.9 both).  One
+# count per prime base, whatever radix label a plan carries: the smallest of
+# base 2's (4.08), since radix 2, 4 and 8 plans of the same size run the
+# same rounds here.
+C_BASE = {2: 4.08, 3: 5.9, 5: 5.9}
+
+
+def c_r_of(dims) -> float:
+    """c_r of a problem: the per-base counts weighted by each base's share of log2 N."""
+    tot, acc = 0.0, 0.0
+    for n in dims:
+        for p in (2, 3, 5):
+            while n % p == 0:
+                n //= p
+                acc += C_BASE[p] * math.log2(p)
+                tot += math.log2(p)
+    return acc / tot if tot else C_BASE[2]
+
+
+def alg_flops(dims) -> float:
+    """Algorithmic flops of one convolution with the spectrum resident: a forward
+    and an inverse transform (c_r N log2 N each) and the product (6 N)."""
+    N = math.prod(dims)
+    return 2 * c_r_of(dims) * N * math.log2(N) + 6 * N if N > 1 else 6.0
+
+
+def launch_table(pac, plan, c):
+    """Per launch of pac_convolve, in launch order: (kernel instantiation as ncu
+    lists it, algorithmic bytes, algorithmic flops).  A pass over group g
+    (size M) moves 2 N S and computes c_r N log2 M; the fused pass (forward,
+    product, inverse of the last group) and the plane pass (the last two
+    groups) move 3 N S and compute twice that plus the product's 6 N."""
+    N, S = c.n_total, c.elem_bytes
+    cr = c_r_of(c.dims)
+    cap = plan.query(pac.Q_GROUP_CAP)
+    groups = pac.pac_plan_groups(c.dims, c.radix, 0 if c.dtype == "c64" else 1, False, cap)
+    G = len(groups)
+    if G != plan.query(pac.Q_GROUPS):  # a schedule the host hook does not reproduce
+        return None
+    V = "float2" if c.dtype == "c64" else "double2"
+    plane = plan.query(pac.Q_PLANE) > 0
+
+    def one(g):
+        return (f"pass_kernel<{V},{groups[g][1]},{'lines' if g == G - 1 else 'rows'}>", 2 * N * S,
+                cr * N * math.log2(groups[g][1]))
+
+    if plane and G >= 2:
+        m1, m2 = groups[G - 2][1], groups[G - 1][1]
+        mid = [(f"plane_kernel<{V},{m1},{m2}>", 3 * N * S, 2 * cr * N * math.log2(m1 * m2) + 6 * N)]
+        outer = list(range(G - 2))
+    else:
+        mg = groups[G - 1][1]
+        mid = [(f"pass_kernel<{V},{mg},lines>", 3 * N * S,
+                2 * cr * N * math.log2(mg) + 6 * N)]
+        outer = list(range(G - 1))
+    return [one(g) for g in outer] + mid + [one(g) for g in reversed(outer)]
+
+
+def tolerance(c) -> float:
+    """Relative L2 tolerance: 1e-12 for complex FP64, 1e-5 log2 N for complex FP32."""
+    return 1e-12 if c.dtype == "c128" else 1e-5 * math.log2(max(2, c.n_total))
+
+
+def oracle_run(c, x, h, fs, points=None):
+    """One oracle evaluation of problem c (as it stands, on the threads set):
+    O2 over the whole array for a separable filter when points is None, else
+    O1 at the given output indices.  Returns (values, seconds, description)."""
+    import oracle
+    t0 = time.perf_counter()
+    if points is None:
+        ref = oracle.conv_separable(fs, x) if fs is not None else oracle.conv_direct(h, x)
+        what = ("separable-direct convolution over the whole array (oracle route O2, FP64)" if fs is not None
+                else "direct definition over the whole array (oracle route O1, FP64)")
+    else:
+        ref = oracle.conv_direct_points(h, x, points)
+        what = f"direct definition at {len(points)} seeded output points (oracle route O1, FP64)"
+    return ref, time.perf_counter() - t0, what
+
+
+def oracle_check(c, x, h, fs, y, whole_macs=7e10, point_macs=1e10, cache=None):
+    """Relative L2 error of the GPU result y against the FP64 oracle, with the
+    oracle's time on all host cores and on one core (the CPU baseline of
+    problem c).  Route: O2 over the whole array when the filter is separable
+    and that takes at most whole_macs multiply-adds (O1 over the whole array
+    for a non-separable filter within the same bound), else O1 at
+    P = point_macs / N seeded points (64 <= P <= 4096).  One core: the same
+    route when it would take at most about 6 s, else O1 at a smaller seeded
+    sample, timed on one core and on all cores.  GB/s = 3 N S per whole
+    convolution over the time, scaled by the computed fraction of outputs."""
+    import oracle
+    key = (c.dims, c.dtype, c.x_kind, c.h_kind, c.seed, c.h_seed, c.h_param)
+    if cache is not None and key in cache:  # same inputs (e.g. one shape at several radices)
+        ref, pts, base = cache[key]
+        yv = np.asarray(y, dtype=np.complex128).reshape(-1)
+        err = oracle.rel_l2(yv if pts is None else yv[pts], ref.reshape(-1))
+        return {**base, "rel_l2_vs_oracle": err, "within_tolerance": bool(err <= base["tolerance"])}
+    N, S = c.n_total, c.elem_bytes
+    B = 3 * N * S
+    cores = oracle.num_threads()
+    macs_whole = N * (sum(c.dims) if fs is not None else N)
+    yv = np.asarray(y, dtype=np.complex128).reshape(-1)
+    if macs_whole <= whole_macs:
+        pts = None
+        ref, dt, what = oracle_run(c, x, h, fs)
+        err = oracle.rel_l2(yv, ref.reshape(-1))
+        frac, macs = 1.0, macs_whole
+    else:
+        npts = int(min(4096, max(64, point_macs // N)))
+        pts = pin_sample(N, npts, 9000 + N % 9973)
+        ref, dt, what = oracle_run(c, x, h, fs, pts)
+        err = oracle.rel_l2(yv[pts], ref)
+        frac, macs = npts / N, N * npts
+    out = {"rel_l2_vs_oracle": err, "tolerance": tolerance(c), "within_tolerance": bool(err <= tolerance(c)),
+           "oracle_route": what,
+           "cpu_oracle": {"all_cores": {"cores": cores, "s": dt, "GBps": B * frac / dt / 1e9, "route": what}}}
+    oracle.set_threads(1)
+    try:
+        if dt * cores <= 6.0:
+            _, dt1, what1 = oracle_run(c, x, h, fs, pts)
+            out["cpu_oracle"]["one_core"] = {"cores": 1, "s": dt1, "GBps": B * frac / dt1 / 1e9, "route": what1}
+        else:
+            n1 = int(max(1, min(4096, 4e8 // N)))
+            p1 = pin_sample(N, n1, 7000 + N % 9973)
+            _, dt1, what1 = oracle_run(c, x, h, fs, p1)
+            oracle.set_threads(cores)
+            _, dta, _ = oracle_run(c, x, h, fs, p1)
+            out["cpu_oracle"]["one_core"] = {"cores": 1, "s": dt1, "GBps": B * n1 / N / dt1 / 1e9, "route": what1,
+                                             "same_sample_all_cores": {"cores": cores, "s": dta,
+                                                                       "GBps": B * n1 / N / dta / 1e9}}
+    finally:
+        oracle.set_threads(cores)
+    if cache is not None:
+        cache[key] = (ref, pts, {k: v for k, v in out.items() if k not in ("rel_l2_vs_oracle", "within_tolerance")})
+    return out
+
+
+def pin_sample(n_total, count, seed):
+    import pac_inputs as pin
+    return pin.sample_points(n_total, count, seed)
+
+
 # --------------------------------------------------------------- the legs
+
+
+def roofline_block(a, torch, pac, plan, c, x, y, stream, flush, ms_per_step, peak, peak_kind):
+    """The line's roofline.  Whole step (reproducible from the line's value):
+    complex FP64 is bound by the FP64 pipe, so bound = alu with frac =
+    flops / t / FP64 peak; complex FP32 is bound by HBM, frac = 3 N S / t /
+    the measured copy peak.  Both fractions are given.  The dominant kernel
+    (most device time per step, by CUDA events around each launch on the
+    launching stream) is described per launch: algorithmic flops and bytes,
+    its ALU fraction and its pass-model HBM fraction (bytes the pass itself
+    must move, not the compulsory 3 N S of the convolution), and the ncu DRAM
+    traffic of one launch when the committed capture matches the sources."""
+    N, S = c.n_total, c.elem_bytes
+    B = 3 * N * S
+    t = ms_per_step * 1e-3
+    flops = alg_flops(c.dims)
+    alu_peak = ALU_PEAK_GFLOPS[c.dtype]
+    probe = pac.pac_measure_fma_peak(c.dtype)
+    frac_alu = flops / t / 1e9 / alu_peak
+    frac_hbm = B / t / 1e9 / peak
+    reps = max(5, min(a.steps, 50))
+    seqs = []
+    with torch.cuda.stream(stream):
+        for k in range(reps):
+            flush()
+            seqs.append(pac.pac_convolve_timed(plan.handle, 0, x, y, stream.cuda_stream))
+    per = {}
+    for seq in seqs:
+        for name, tt in seq:
+            per.setdefault(name, []).append(tt)
+    table = launch_table(pac, plan, c)
+    byk = {}
+    if table is not None and all(len(seq) == len(table) for seq in seqs):
+        for i, (kname, bts, fl) in enumerate(table):
+            ent = byk.setdefault(kname, {"ms": [], "bytes": bts, "flops": fl})
+            ent["ms"].extend(seq[i][1] for seq in seqs)
+    kernel = None
+    if byk:
+        dom = max(byk, key=lambda k: sum(byk[k]["ms"]))
+        e = byk[dom]
+        avg = sum(e["ms"]) / len(e["ms"])
+        kernel = {"name": dom, "avg_launch_ms": avg, "launches_per_step": len(e["ms"]) / reps,
+                  "time_share": sum(e["ms"]) / sum(sum(v["ms"]) for v in byk.values()),
+                  "alg_flops_per_launch": e["flops"], "achieved_tflops": e["flops"] / (avg * 1e-3) / 1e12,
+                  "frac_alu": e["flops"] / (avg * 1e-3) / 1e9 / alu_peak,
+                  "pass_model_bytes_per_launch": e["bytes"],
+                  "pass_model_frac_hbm": e["bytes"] / (avg * 1e-3) / 1e9 / peak,
+                  "pass_model_rule": "2 N S per rows pass, 3 N S per fused or plane pass (the pass' own traffic, "
+                                     "not the convolution's compulsory bytes)"}
+    traffic = ncu_traffic(kernel["name"], traffic_key(a)) if kernel else None
+    if kernel:
+        kernel["traffic"] = traffic
+    alu = c.dtype == "c128"
+    out = {"bound": "alu" if alu else "hbm",
+           "achieved": flops / t / 1e12 if alu else B / t / 1e9,
+           "peak": alu_peak / 1e3 if alu else peak,
+           "unit": "TFLOP/s" if alu else "GB/s",
+           "frac": frac_alu if alu else frac_hbm,
+           "traffic": traffic, "traffic_kernel": kernel["name"] if kernel else None,
+           "frac_alu": frac_alu, "frac_hbm": frac_hbm,
+           "flops_per_step": flops, "bytes_per_step": B,
+           "flop_count": f"2 c_r N log2 N + 6 N with c_r = {c_r_of(c.dims):.3f} (per prime base: 2 -> 4.08, "
+                         "3 -> 5.9, 5 -> 5.9)",
+           "alu_peak_kind": ("FP64: 152 SMs x 2 FMA/clk x 2 flops x 2070 MHz (GB300's 1.25 TFLOP/s FP64)" if alu else
+                             "FP32: 152 SMs x 128 FMA lanes x 2 flops x 2070 MHz"),
+           "alu_probe_tflops": probe / 1e3,
+           "hbm_peak_gbps": peak, "hbm_peak_kind": f"{peak_kind} copy bandwidth",
+           "kernel": kernel}
+    return out, {k: sum(v) / reps for k, v in per.items()}
+
+
+def traffic_key(a) -> str:
+    """Key of the main workload in the committed ncu traffic summary."""
+    base = {"conv2d-r5": "conv2d_3125", "conv2d-r3": "conv2d_2187", "conv1d": "conv1d"}.get(
+        a.workload, f"conv3d_{a.n}")
+    return f"{base}_{a.dtype}"
 
 
 def workload_conv(a, pin):
@@ -267,20 +504,23 @@ def oracle_macs(c, fs):
     return c.n_total * (sum(c.dims) if fs is not None else c.n_total)
 
 
-def cpu_baseline_leg(a):
-    """The FP64 oracle as it stands on the host cores: one whole convolution
-    of the workload (O2 for the separable filters, O1 otherwise)."""
+def cpu_baseline_leg(a, y_gpu):
+    """The FP64 oracle as it stands on the host cores, on the main workload's
+    own inputs: the GPU result's relative L2 error against it, and its time
+    on all cores and on one core (oracle_check)."""
     import oracle
     import pac_inputs as pin
     c = workload_conv(a, pin)
     x, (h, fs) = pin.make_x(c), pin.make_h(c)
     oracle.build()
-    t0 = time.perf_counter()
-    route = oracle_convolution(c, x, h, fs)
-    dt = time.perf_counter() - t0
-    B = 3 * c.n_total * c.elem_bytes
-    return {"value": B / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"one whole {'x'.join(map(str, c.dims))} {route}, {dt:.2f} s; GB/s = 3*N*S / time"}
+    chk = oracle_check(c, x, h, fs, y_gpu)
+    allc, one = chk["cpu_oracle"]["all_cores"], chk["cpu_oracle"]["one_core"]
+    base = {"value": allc["GBps"], "unit": UNIT, "cores": allc["cores"], "kind": "oracle",
+            "sample": f"{'x'.join(map(str, c.dims))}: {allc['route']}, {allc['s']:.2f} s on {allc['cores']} "
+                      "cores; GB/s = 3*N*S of the computed outputs / time",
+            "one_core": one}
+    return {"rel_l2_vs_oracle": chk["rel_l2_vs_oracle"], "tolerance": chk["tolerance"],
+            "oracle_route": chk["oracle_route"], "cpu_baseline": base}
 
 
 def reference_arm(a):
@@ -321,7 +561,9 @@ def reference_arm(a):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": tot / a.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(a), "dims": list(c.dims), "radix": c.radix},
+            "config": {"workload": workload_name(a), "dims": list(c.dims), "radix": c.radix,
+                       "inputs": "the workload's seeded inputs rounded once to its precision, promoted to FP64 "
+                                 "for the oracle"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -332,15 +574,15 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
     """Every single-convolution workload: 1-D 2^10 FP64 radix 2; 3-D 128^3
     radix 2/4/8 FP32 and FP64; 2-D 2187^2 radix 3 and 3125^2 radix 5, FP32
     and FP64; mixed radix (2^a 3^b 5^c) 2-D 1000^2 and 6000^2 and 3-D 120^3,
-    FP32; the anisotropic 2^24 x 2 and 2^22 x 2 x 2, FP32.  Each: GB/s of 3 N S, the permuted form and cuFFT on the same
-    GPU, launches per convolution and the pass schedule (autotuned unless
-    --no-tune).  Inputs of each workload's recipe, generated on the device
-    from a seed (x: re, im N(0,1) or U[-1,1]; the workload's filter)."""
+    FP32; the anisotropic 2^24 x 2 and 2^22 x 2 x 2, FP32.  Each: GB/s of
+    3 N S and its HBM fraction, the ALU fraction of the algorithmic flops, the
+    permuted form and cuFFT on the same GPU, launches per convolution and the
+    pass schedule (autotuned unless --no-tune), the relative L2 error against
+    the FP64 oracle and the oracle's time on all host cores and on one core.
+    Inputs are each workload's seeded recipe (pac_inputs), made on the host
+    (x: re, im N(0,1) or U[-1,1]; the workload's filter)."""
     out = []
-    fma_peak = {dt: pac.pac_measure_fma_peak(dt) for dt in ("c64", "c128")}
-    # algorithmic flops per convolution: 2 c_r N log2 N + 6 N, c_r = 5, 4.25, 4.08 for
-    # radix 2, 4, 8 (the paper's per-transform counts); 5.9 for radix 3 and 5 (estimates)
-    c_r = {2: 5.0, 4: 4.25, 8: 4.08, 3: 5.9, 5: 5.9, 0: 5.0}  # 0: mixed radix, taken as radix 2's
+    probe = {dt: pac.pac_measure_fma_peak(dt) for dt in ("c64", "c128")}
     cases = [(pin.c1(), "1-D n=2^10, radix 2, complex FP64")]
     for dt in ("c64", "c128"):
         for r in (2, 4, 8):
@@ -357,25 +599,13 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
     cases.append((pin.aniso((2 ** 24, 2)), "2-D 2^24 x 2, radix 2, complex FP32 (anisotropic)"))
     cases.append((pin.aniso((2 ** 22, 2, 2)), "3-D 2^22 x 2 x 2, radix 2, complex FP32 (anisotropic)"))
     sh = stream.cuda_stream
+    oracle_cache = {}
     for c, name in cases:
         N, S = c.n_total, c.elem_bytes
         B = 3 * N * S
-        real = torch.float32 if c.dtype == "c64" else torch.float64
-        g = torch.Generator(device=dev)
-        g.manual_seed(c.seed)
-        if c.x_kind == "normal":
-            x = torch.view_as_complex(torch.randn(*c.dims, 2, generator=g, device=dev, dtype=real))
-        else:
-            x = torch.view_as_complex(torch.rand(*c.dims, 2, generator=g, device=dev, dtype=real) * 2 - 1)
-        if c.h_kind == "uniform":
-            h = torch.view_as_complex(torch.rand(*c.dims, 2, generator=g, device=dev, dtype=real) * 2 - 1)
-        else:
-            fs = pin.gaussian_factors(c.dims, c.h_param) if c.h_kind == "gauss" else \
-                pin.exponential_factors(c.dims, c.h_param)
-            h = torch.from_numpy(fs[0]).to(dev)
-            for f in fs[1:]:
-                h = torch.outer(h.reshape(-1), torch.from_numpy(f).to(dev)).reshape(*h.shape, f.shape[0])
-            h = h.to(x.dtype).contiguous()
+        x_np, (h_np, fs) = pin.make_x(c), pin.make_h(c)
+        x = torch.from_numpy(x_np).to(dev)
+        h = torch.from_numpy(h_np).to(dev)
         y = torch.empty_like(x)
         tuned_us = None
         if not a.no_tune:
@@ -406,40 +636,44 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
         stream.synchronize()
         diff = float(torch.linalg.vector_norm(y - yc) / torch.linalg.vector_norm(yc))
         t, tp, tc = (statistics.median(v) for v in (ms, msp, msc))
-        out.append({"workload": name, "dims": list(c.dims), "radix": c.radix, "dtype": c.dtype,
-                    "ms": t, "GBps": B / (t * 1e-3) / 1e9, "pct_hbm_roofline": B / (t * 1e-3) / 1e9 / peak,
-                    "permuted_GBps": B / (tp * 1e-3) / 1e9, "speedup_vs_permuted": tp / t,
-                    "cufft_GBps": B / (tc * 1e-3) / 1e9, "speedup_vs_cufft": tc / t,
-                    "launches": plan.query(pac.Q_LAUNCHES_CONVOLVE), "groups": plan.query(pac.Q_GROUPS),
-                    "plane_ctas": plan.query(pac.Q_PLANE), "group_cap": plan.query(pac.Q_GROUP_CAP),
-                    "tuned_us": tuned_us, "rel_l2_vs_cufft": diff,
-                    "transform": {"unordered_us": statistics.median(msu) * 1e3,
-                                  "ordered_us": statistics.median(mso) * 1e3,
-                                  "permutation_share_of_ordered": per.get("permute", 0.0) / sum(per.values())}})
-        flops = 2 * c_r[c.radix] * N * math.log2(N) + 6 * N
-        out[-1]["alu"] = {"flops_per_conv": flops, "achieved_gflops": flops / (t * 1e-3) / 1e9,
-                          "peak_gflops": fma_peak[c.dtype],
-                          "frac": flops / (t * 1e-3) / 1e9 / fma_peak[c.dtype],
-                          "peak_kind": "measured FMA probe (pac_measure_fma_peak)"}
+        flops = alg_flops(c.dims)
+        ent = {"workload": name, "dims": list(c.dims), "radix": c.radix, "dtype": c.dtype,
+               "ms": t, "GBps": B / (t * 1e-3) / 1e9, "pct_hbm_roofline": B / (t * 1e-3) / 1e9 / peak,
+               "permuted_GBps": B / (tp * 1e-3) / 1e9, "speedup_vs_permuted": tp / t,
+               "cufft_GBps": B / (tc * 1e-3) / 1e9, "speedup_vs_cufft": tc / t,
+               "launches": plan.query(pac.Q_LAUNCHES_CONVOLVE), "groups": plan.query(pac.Q_GROUPS),
+               "plane_ctas": plan.query(pac.Q_PLANE), "group_cap": plan.query(pac.Q_GROUP_CAP),
+               "tuned_us": tuned_us, "rel_l2_vs_cufft": diff,
+               "transform": {"unordered_us": statistics.median(msu) * 1e3,
+                             "ordered_us": statistics.median(mso) * 1e3,
+                             "permutation_share_of_ordered": per.get("permute", 0.0) / sum(per.values())},
+               "alu": {"flops_per_conv": flops, "c_r": c_r_of(c.dims), "achieved_gflops": flops / (t * 1e-3) / 1e9,
+                       "peak_gflops": ALU_PEAK_GFLOPS[c.dtype], "probe_gflops": probe[c.dtype],
+                       "frac": flops / (t * 1e-3) / 1e9 / ALU_PEAK_GFLOPS[c.dtype]}}
+        y_host = y.cpu().numpy()
         plan.close()
         del x, y, h, yc, Hn
         torch.cuda.empty_cache()
-    out.append(prime_factor_entry(torch, pac, dev, stream, flush, peak))
+        if not a.no_cpu:
+            ent.update(oracle_check(c, x_np, h_np, fs, y_host, cache=oracle_cache))
+        out.append(ent)
+    out.append(prime_factor_entry(a, torch, pac, pin, dev, stream, flush, peak))
     return out
 
 
-def prime_factor_entry(torch, pac, dev, stream, flush, peak):
+def prime_factor_entry(a, torch, pac, pin, dev, stream, flush, peak):
     """The prime factor form (Section 7.2) of a 1-D length n = 2^10 3^5 5^3
     (FP32): three permutations around the 3-D convolution of shape
     (1024, 243, 125), against the permutation-free mixed-radix 1-D plan of
     the same n and cuFFT; the two per-call permutations' share of the prime
-    factor form's time.  x: re, im U[-1,1]; h: re, im U[-1,1] (seeded)."""
+    factor form's time; both results against the FP64 oracle at seeded
+    points.  x: re, im U[-1,1]; h: re, im U[-1,1] (seeded)."""
     n = 2 ** 10 * 3 ** 5 * 5 ** 3
     B = 3 * n * 8
-    g = torch.Generator(device=dev)
-    g.manual_seed(7)
-    x = torch.view_as_complex(torch.rand(n, 2, generator=g, device=dev) * 2 - 1)
-    h = torch.view_as_complex(torch.rand(n, 2, generator=g, device=dev) * 2 - 1)
+    c = pin.Conv((n,), 0, "c64", "uniform", "uniform", seed=7, h_seed=107)
+    x_np, (h_np, _) = pin.make_x(c), pin.make_h(c)
+    x = torch.from_numpy(x_np).to(dev)
+    h = torch.from_numpy(h_np).to(dev)
     y = torch.empty_like(x)
     sh = stream.cuda_stream
     pfa = pac.Pfa(n, "c64")
@@ -455,8 +689,21 @@ def prime_factor_entry(torch, pac, dev, stream, flush, peak):
         Hn = torch.fft.fft(h)
         ms_cufft = time_steps(torch, lambda: torch.fft.ifft(torch.fft.fft(x) * Hn, out=xt), 10, 3, flush, stream)
         t_pfa, t_inner, t_ct, t_cu = (statistics.median(v) for v in (ms_pfa, ms_inner, ms_ct, ms_cufft))
-        return {"workload": "1-D n=2^10 3^5 5^3 (31.1 M), complex FP32: prime factor form (Section 7.2) "
-                            "against the mixed-radix plan",
+        chk = {}
+        if not a.no_cpu:
+            pac.pac_pfa_convolve(pfa.handle, x, y, sh)
+            stream.synchronize()
+            y_pfa = y.cpu().numpy()
+            pac.pac_convolve(plan.handle, x, y, sh)
+            stream.synchronize()
+            chk = oracle_check(c, x_np, h_np, None, y.cpu().numpy())
+            pts = pin_sample(n, 256, 4242)
+            import oracle
+            ref = oracle.conv_direct_points(h_np, x_np, pts)
+            chk["prime_factor_rel_l2_vs_oracle"] = oracle.rel_l2(y_pfa.reshape(-1)[pts], ref)
+            chk["prime_factor_oracle_route"] = "direct definition at 256 seeded output points (oracle route O1)"
+        return {**chk, "workload": "1-D n=2^10 3^5 5^3 (31.1 M), complex FP32: prime factor form (Section 7.2) "
+                                   "against the mixed-radix plan",
                 "dims": [n], "radix": 0, "dtype": "c64", "ms": t_ct, "GBps": B / (t_ct * 1e-3) / 1e9,
                 "pct_hbm_roofline": B / (t_ct * 1e-3) / 1e9 / peak,
                 "launches": plan.query(pac.Q_LAUNCHES_CONVOLVE), "groups": plan.query(pac.Q_GROUPS),
@@ -693,40 +940,8 @@ def main(argv=None):
             "launches_per_step": launches}
 
     if not a.quick:
-        # per-kernel times inside the same kind of step (events around each launch)
-        per = {}
-        with torch.cuda.stream(stream):
-            for k in range(max(5, min(a.steps, 50))):
-                flush()
-                for name, t in pac.pac_convolve_timed(plan.handle, 0, x, y, sh):
-                    per.setdefault(name, []).append(t)
-        # group launches by kernel instantiation (what ncu lists): the DIF and
-        # DIT passes of the outer axes are one kernel (rows case), the fused
-        # pass of the contiguous axis another (lines case)
-        vname = "float2" if c.dtype == "c64" else "double2"
-        m0 = math.prod(plan.stages(0))  # axis-0 group size (one group per axis in these workloads)
-        ml = math.prod(plan.stages(len(c.dims) - 1))
-        kern = {"dif_pass": f"pass_kernel<{vname},{m0},rows>", "dit_pass": f"pass_kernel<{vname},{m0},rows>",
-                "fused_dif_mul_dit_pass": f"pass_kernel<{vname},{ml},lines>",
-                "plane_pass": f"plane_kernel<{vname},{m0 if len(c.dims) == 2 else math.prod(plan.stages(1))},{ml}>"}
-        byk = {}
-        for name, v in per.items():
-            byk.setdefault(kern.get(name, name), []).extend(v)
-        reps = max(5, min(a.steps, 50))
-        dom = max(byk, key=lambda k: sum(byk[k]))
-        nlaunch = len(byk[dom]) / reps
-        avg_ms = sum(byk[dom]) / len(byk[dom])
-        alg_bytes = (3 if dom.endswith("lines>") or dom.startswith("plane") else 2) * N * S
-        achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
-        line["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                            "frac": achieved / peak, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
-                            "traffic": ncu_traffic(dom, {"conv2d-r5": "conv2d_3125"}.get(a.workload, a.workload)),
-                            "alg_bytes_per_launch": alg_bytes,
-                            "alg_bytes_rule": "2*N*S per rows pass (read+write the array); 3*N*S per fused or "
-                                              "plane pass (read x, read the spectrum, write y)",
-                            "avg_launch_ms": avg_ms, "launches_per_step": nlaunch,
-                            "time_share": sum(byk[dom]) / sum(sum(v) for v in byk.values())}
-        line["kernel_ms_per_step"] = {k: sum(v) / reps for k, v in per.items()}
+        line["roofline"], line["kernel_ms_per_step"] = roofline_block(a, torch, pac, plan, c, x, y, stream, flush,
+                                                                      ms_per_step, peak, peak_kind)
 
         # the permuted form on the same GPU, same bytes B
         msp = time_steps(torch, lambda: pac.pac_convolve_permuted(plan.handle, x, y, sh), a.steps, a.warmup, flush,
@@ -758,11 +973,13 @@ def main(argv=None):
         line["e2e"] = {"value": world * ke * B / (te * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": N * S,
                        "d2h_bytes_per_step": N * S, "ms_per_step": te / ke,
                        "call": "pac_convolve_host (pinned host x -> device -> convolve -> host y)"}
-        ref = None
+        y_main = None
         if rank == 0:
+            pac.pac_convolve(plan.handle, x, y, sh)  # y was reused by the comparison legs
+            stream.synchronize()
+            y_main = y.cpu().numpy()
             ref = yc.cpu().numpy()
-            err = float(np.linalg.norm(y.cpu().numpy() - ref) / np.linalg.norm(ref))
-            line["check_vs_cufft_rel_l2"] = err
+            line["check_vs_cufft_rel_l2"] = float(np.linalg.norm(y_main - ref) / np.linalg.norm(ref))
 
     if sampler:
         sampler.stop()
@@ -776,7 +993,11 @@ def main(argv=None):
     if extra and "served" in a.legs:
         line["served"] = served_leg(a, torch, pac, pin, dev)
     if rank == 0 and world == 1 and not a.no_cpu and not a.quick:
-        line["cpu_baseline"] = cpu_baseline_leg(a)
+        chk = cpu_baseline_leg(a, y_main)
+        line["rel_l2_vs_oracle"] = chk["rel_l2_vs_oracle"]
+        line["tolerance"] = chk["tolerance"]
+        line["oracle_route"] = chk["oracle_route"]
+        line["cpu_baseline"] = chk["cpu_baseline"]
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
