@@ -361,6 +361,23 @@ int pac_measure_fma_peak(int dtype, double* gflops);
 int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int flags, int cap, int* axis,
                     int* size, int* rounds, int* count);
 
+/*
+ * Host only (no device): the twiddle table `which` of group `group` of the
+ * schedule pac_plan_groups gives for this problem (same flags and cap),
+ * exactly the values a plan of that problem uploads: each root
+ * w_L^e = exp(-2 pi i e / L) (Section 2, twiddles of Eq. 25) computed in
+ * FP64 with the exponent reduced in integers to the first eighth turn, then
+ * rounded once to the plan's precision.  which 0: the round twiddles w_M^u,
+ * u < M; 1: the external factor's low table w_L^u, u < T; 2: its high table
+ * w_L^{T v}, v < ceil(L/T) (tables 1 and 2 are empty when the group has no
+ * external factor).  out (may be NULL): *count interleaved complex values of
+ * the dtype; *count in: room (entries), out: the table's length.  L, T (may
+ * be NULL): the table's root order and the two-level split.  PAC_ERR_ARG for
+ * a bad group or table or too little room; size errors as pac_plan_create.
+ */
+int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int flags, int cap, int group,
+                      int which, void* out, int64_t* count, int64_t* L, int64_t* T);
+
 /* Host-only helpers (no device needed): the stage list of pac_plan_create
  * (radix 0 included) and the reversal table of a stage list. */
 int pac_stage_list(int64_t n, int radix, int* radices, int* count);

@@ -72,6 +72,8 @@ _SIGS = {
     "pac_plan_groups": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _i32, ctypes.POINTER(_i32),
                                ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "pac_reverse_table": (_i32, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "pac_plan_twiddles": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _i32, _i32, _i32, _vp,
+                                 ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "pac_version": (ctypes.c_char_p, []),
     "pac_pfa_create": (_i32, [_i64, _i32, ctypes.POINTER(_vp)]),
     "pac_pfa_destroy": (_i32, [_vp]),
@@ -159,6 +161,21 @@ def pac_plan_groups(dims, radix: int, dtype: int = 0, mixed: bool = False, cap: 
     _check(load().pac_plan_groups(len(vals), d, int(radix), int(dtype), 1 if mixed else 0, int(cap), ax, sz, rr,
                                   ctypes.byref(cnt)))
     return [(ax[g], sz[g], [r for r in rr[8 * g:8 * g + 8] if r]) for g in range(cnt.value)]
+
+
+def pac_plan_twiddles(dims, radix: int, dtype: int, group: int, which: int, mixed: bool = False, cap: int = 0):
+    """Host only: twiddle table `which` (0 round, 1 external low, 2 external high) of group `group`
+    of the schedule pac_plan_groups gives, as uploaded by a plan; returns (values, L, T) with values a
+    numpy complex64 / complex128 array."""
+    import numpy as np
+    vals = [int(v) for v in dims]
+    d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
+    cnt, L, T = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    args = (len(vals), d, int(radix), int(dtype), 1 if mixed else 0, int(cap), int(group), int(which))
+    _check(load().pac_plan_twiddles(*args, None, ctypes.byref(cnt), ctypes.byref(L), ctypes.byref(T)))
+    out = np.zeros(max(1, cnt.value), np.complex64 if int(dtype) == C64 else np.complex128)
+    _check(load().pac_plan_twiddles(*args, out.ctypes.data, ctypes.byref(cnt), None, None))
+    return out[: cnt.value], L.value, T.value
 
 
 def pac_stage_list(n: int, radix: int) -> list[int]:

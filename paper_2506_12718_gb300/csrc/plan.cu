@@ -335,6 +335,27 @@ void put_root(std::vector<unsigned char>& blob, size_t off, int64_t idx, int64_t
 
 size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
 
+// Twiddle table `which` of group g (0: round twiddles w_M^u, u < M; 1: the
+// external factor's low table w_L^u, u < T; 2: its high table w_L^{T v},
+// v < ceil(L/T)), each root computed in FP64 (root_fp64) and rounded once to
+// the plan's precision, written at dst.  The plan builder and the host hook
+// pac_plan_twiddles both call this, so the hook returns the uploaded values.
+int64_t twiddle_count(const GroupPlan& g, int which) {
+    if (which == 0) return g.M;
+    if (!g.has_ext) return 0;
+    return which == 1 ? g.tw_T : (g.L + g.tw_T - 1) / g.tw_T;
+}
+
+void fill_twiddles(const GroupPlan& g, int esize, int which, std::vector<unsigned char>& blob, size_t off) {
+    const int64_t n = twiddle_count(g, which);
+    for (int64_t u = 0; u < n; ++u) {
+        const int64_t e = which == 2 ? u * g.tw_T : u;
+        const int64_t L = which == 0 ? g.M : g.L;
+        if (esize == 8) put_root<float2, float>(blob, off, u, e, L);
+        else put_root<double2, double>(blob, off, u, e, L);
+    }
+}
+
 }  // namespace
 
 // Device copies of plan tables (twiddles and placement tables), shared by
@@ -468,6 +489,39 @@ extern "C" int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dty
                     rounds[8 * g + i] = i < nr ? (p.mix_nr > 0 ? p.mix_r[i] : round_radix(p.M, esize, i)) : 0;
             }
         }
+    }
+    *count = n;
+    return PAC_OK;
+}
+
+extern "C" int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int flags, int cap,
+                                 int group, int which, void* out, int64_t* count, int64_t* L, int64_t* T) {
+    if (ndim < 1 || ndim > 3 || !dims || !count) return fail(PAC_ERR_ARG, "bad arguments");
+    if (dtype != PAC_C64 && dtype != PAC_C128) return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
+    if (radix != 0 && prime_of(radix) == 0) return fail(PAC_ERR_ARG, "radix %d not in {0,2,3,4,5,8}", radix);
+    if (which < 0 || which > 2) return fail(PAC_ERR_ARG, "table %d not in {0,1,2}", which);
+    std::vector<std::vector<int>> st(ndim);
+    for (int a = 0; a < ndim; ++a) {
+        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
+            return fail(PAC_ERR_SIZE, "dimension %lld out of range", (long long)dims[a]);
+        if (int rc = stage_list(dims[a], radix, st[a])) return rc;
+    }
+    Schedule sch;
+    sch.cap = cap;
+    sch.mixed = (flags & 1) != 0;
+    std::vector<GroupPlan> gr;
+    const int esize = dtype == PAC_C64 ? 8 : 16;
+    if (int rc = form_groups(ndim, dims, st, esize, sch, gr)) return rc;
+    if (group < 0 || group >= (int)gr.size()) return fail(PAC_ERR_ARG, "group %d of %d", group, (int)gr.size());
+    const GroupPlan& g = gr[group];
+    const int64_t n = twiddle_count(g, which);
+    if (L) *L = which == 0 ? g.M : g.L;
+    if (T) *T = g.tw_T;
+    if (out) {
+        if (*count < n) return fail(PAC_ERR_ARG, "room for %lld entries, %lld needed", (long long)*count, (long long)n);
+        std::vector<unsigned char> blob((size_t)std::max<int64_t>(n, 1) * esize);
+        fill_twiddles(g, esize, which, blob, 0);
+        std::memcpy(out, blob.data(), (size_t)n * esize);
     }
     *count = n;
     return PAC_OK;
@@ -678,20 +732,10 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     // host blob of every table
     std::vector<unsigned char> blob(std::max<size_t>(off, 16), 0);
     for (const GroupPlan& g : pl->groups) {
-        for (int64_t u = 0; u < g.M; ++u) {
-            if (pl->esize == 8) put_root<float2, float>(blob, g.off_twi, u, u, g.M);
-            else put_root<double2, double>(blob, g.off_twi, u, u, g.M);
-        }
+        fill_twiddles(g, pl->esize, 0, blob, g.off_twi);
         if (g.has_ext) {
-            const int64_t nhi = (g.L + g.tw_T - 1) / g.tw_T;
-            for (int64_t u = 0; u < g.tw_T; ++u) {
-                if (pl->esize == 8) put_root<float2, float>(blob, g.off_lo, u, u, g.L);
-                else put_root<double2, double>(blob, g.off_lo, u, u, g.L);
-            }
-            for (int64_t v = 0; v < nhi; ++v) {
-                if (pl->esize == 8) put_root<float2, float>(blob, g.off_hi, v, v * g.tw_T, g.L);
-                else put_root<double2, double>(blob, g.off_hi, v, v * g.tw_T, g.L);
-            }
+            fill_twiddles(g, pl->esize, 1, blob, g.off_lo);
+            fill_twiddles(g, pl->esize, 2, blob, g.off_hi);
         }
         // frequency at each global row: digit reversal over the group's stages
         std::vector<int64_t> f(g.M);
