@@ -278,6 +278,21 @@ int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, vo
                        float* launch_ms, int* kernel_ids, int* n_launches);
 
 /*
+ * Test hook of the bounded device waits (no counterpart in the paper): runs
+ * the plan's convolution as the single-launch cooperative kernel (the passes
+ * as phases separated by grid-wide barriers), with every barrier waiting for
+ * one arrival more than the grid can make and each wait limited to
+ * spin_limit polls (1 .. 2^20).  Every wait therefore runs out: the CTA
+ * records 1 in the device error word (read and cleared by
+ * pac_plan_query(PAC_Q_DEVICE_ERROR)) and goes on, so the kernel ends
+ * without a hang and the device stays usable.  y_dev receives passes run
+ * without synchronisation between them, not the convolution.  Needs a plan
+ * whose passes all have one group size and no plane pass (e.g. 1-D 2^16,
+ * radix 2), else PAC_ERR_ARG.  Asynchronous on `stream`.
+ */
+int pac_test_barrier_timeout(pac_plan p, const void* x_dev, void* y_dev, void* stream, int spin_limit);
+
+/*
  * Allocation-free form of pac_convolve_permuted, for callers that cannot
  * allocate device memory: processes whose GPU memory is owned by another
  * allocator that reserved nearly all of it up front, services under a hard

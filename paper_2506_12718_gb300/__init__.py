@@ -72,6 +72,7 @@ _SIGS = {
     "pac_plan_groups": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _i32, ctypes.POINTER(_i32),
                                ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "pac_reverse_table": (_i32, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "pac_test_barrier_timeout": (_i32, [_vp, _vp, _vp, _vp, _i32]),
     "pac_plan_twiddles": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _i32, _i32, _i32, _vp,
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "pac_version": (ctypes.c_char_p, []),
@@ -260,6 +261,11 @@ def pac_fft(plan: int, in_dev, out_dev, inverse: bool = False, stream=None) -> N
 
 def pac_convolve_permuted(plan: int, x_dev, y_dev, stream=None) -> None:
     _check(load().pac_convolve_permuted(plan, _ptr(x_dev), _ptr(y_dev), _stream(stream)))
+
+
+def pac_test_barrier_timeout(plan: int, x_dev, y_dev, spin_limit: int, stream=None) -> None:
+    """Test hook: the convolution as one cooperative launch whose bounded barrier waits all run out."""
+    _check(load().pac_test_barrier_timeout(plan, _ptr(x_dev), _ptr(y_dev), _stream(stream), int(spin_limit)))
 
 
 def pac_convolve_permuted_noalloc(plan: int, x_dev, y_dev, stream=None) -> None:

@@ -876,8 +876,10 @@ __global__ void __launch_bounds__(PlaneShape<V, M1, M2, K>::NT, plane_min_blocks
 
 // Grid-wide barrier for the cooperative convolution kernel (all CTAs are
 // co-resident).  The arrival counter only grows; barrier k of a launch waits
-// for base + (k+1) * gridDim.x arrivals.  The wait is bounded: after the
-// limit the CTA records the failure in *error and goes on (no hang).
+// for base + (k+1) * gridDim.x arrivals (plus target_bias, which only the
+// timeout test hook sets, to a target no launch reaches).  The wait is
+// bounded: after spin_limit polls (default kBarrierSpinLimit) the CTA
+// records the failure in *error and goes on (no hang).
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
 
 __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
@@ -889,12 +891,13 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 __device__ __forceinline__ void grid_barrier(const ConvArgs& args, unsigned k) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned target = args.base + (k + 1) * gridDim.x;
+        const unsigned target = args.base + (k + 1) * gridDim.x + args.target_bias;
+        const unsigned limit = args.spin_limit ? args.spin_limit : kBarrierSpinLimit;
         __threadfence();
         atomicAdd(args.barrier, 1u);
         unsigned spins = 0;
         while ((int)(ld_acquire_gpu(args.barrier) - target) < 0) {
-            if (++spins > kBarrierSpinLimit) {
+            if (++spins > limit) {
                 atomicExch(args.error, 1u);
                 break;
             }

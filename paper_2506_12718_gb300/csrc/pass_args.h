@@ -70,6 +70,8 @@ struct ConvArgs {
     unsigned* barrier;  // arrival counter (monotonic; never reset)
     unsigned base;      // its value when this launch starts
     unsigned* error;    // set to 1 if a barrier wait gave up
+    unsigned target_bias;  // added to every barrier's target (0; > 0 only from the timeout test hook)
+    unsigned spin_limit;   // polls before a wait gives up (0: kBarrierSpinLimit)
 };
 
 }  // namespace pac

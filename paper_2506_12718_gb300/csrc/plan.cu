@@ -925,6 +925,29 @@ int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* ds
 }
 
 
+// A pass sequence as one cooperative launch (every group of size uniform_m,
+// no plane pass); target_bias and spin_limit as in ConvArgs (0 and 0 except
+// from the timeout test hook).
+static int run_single(pac_plan p, const std::vector<Step>& steps, int grid, unsigned target_bias, unsigned spin_limit,
+                      cudaStream_t s) {
+    const int n = (int)steps.size();
+    ConvArgs args;
+    args.npasses = n;
+    for (int i = 0; i < n; ++i) {
+        const Step& st = steps[i];
+        args.pass[i] = make_pass(p, p->groups[st.group], st.mode, st.src, st.dst, st.scale);
+    }
+    int rc = barrier_slot(p->device, &args.barrier, &args.base, (unsigned)((n - 1) * grid), &args.error);
+    if (rc) return rc;
+    args.target_bias = target_bias;
+    args.spin_limit = spin_limit;
+    timer_mark(s, 5, true);
+    cudaError_t e = launch_conv(p->esize, p->uniform_m, args, grid, s);
+    timer_mark(s, 5, false);
+    if (e != cudaSuccess) return cuda_fail(e, "convolution kernel launch");
+    return PAC_OK;
+}
+
 // Run a pass sequence: as one cooperative launch when every group has the
 // same size M and single launches are allowed, else one launch per pass.
 static int run_steps(pac_plan p, const std::vector<Step>& steps, cudaStream_t s, bool allow_single) {
@@ -935,21 +958,7 @@ static int run_steps(pac_plan p, const std::vector<Step>& steps, cudaStream_t s,
         grid = conv_grid(p->esize, p->uniform_m, p->device);
         single = grid > 0;
     }
-    if (single) {
-        ConvArgs args;
-        args.npasses = n;
-        for (int i = 0; i < n; ++i) {
-            const Step& st = steps[i];
-            args.pass[i] = make_pass(p, p->groups[st.group], st.mode, st.src, st.dst, st.scale);
-        }
-        int rc = barrier_slot(p->device, &args.barrier, &args.base, (unsigned)((n - 1) * grid), &args.error);
-        if (rc) return rc;
-        timer_mark(s, 5, true);
-        cudaError_t e = launch_conv(p->esize, p->uniform_m, args, grid, s);
-        timer_mark(s, 5, false);
-        if (e != cudaSuccess) return cuda_fail(e, "convolution kernel launch");
-        return PAC_OK;
-    }
+    if (single) return run_single(p, steps, grid, 0u, 0u, s);
     for (const Step& st : steps) {
         int rc = st.mode == kPlane ? run_plane(p, st.src, st.dst, s)
                                    : run_pass(p, p->groups[st.group], st.mode, st.src, st.dst, st.scale, s);
@@ -1018,6 +1027,27 @@ static int check_ptr(const void* ptr, const char* name) {
     if (reinterpret_cast<uintptr_t>(ptr) % 16) return fail(PAC_ERR_ARG, "%s is not 16-byte aligned", name);
     return PAC_OK;
 }
+
+// Test hook of the bounded waits (see pac.h): the convolution's passes as one
+// cooperative launch whose barriers wait for one arrival more than the grid
+// makes, each wait limited to spin_limit polls.
+extern "C" int pac_test_barrier_timeout(pac_plan p, const void* x_dev, void* y_dev, void* stream, int spin_limit) {
+    if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = check_ptr(x_dev, "x_dev")) return rc;
+    if (int rc = check_ptr(y_dev, "y_dev")) return rc;
+    if (!p->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "pac_filter_spectrum was not called for this plan");
+    if (spin_limit < 1 || spin_limit > (1 << 20)) return fail(PAC_ERR_ARG, "spin_limit %d not in [1, 2^20]", spin_limit);
+    const int G = (int)p->groups.size();
+    std::vector<Step> steps;
+    if (G > 0 && !p->plane) convolve_steps(p, x_dev, y_dev, steps);
+    const int n = (int)steps.size();
+    if (n < 2 || n > kMaxPasses || p->uniform_m == 0)
+        return fail(PAC_ERR_ARG, "the plan has no single-launch form (needs >= 2 passes of one group size, no plane pass)");
+    const int grid = conv_grid(p->esize, p->uniform_m, p->device);
+    if (grid <= 0) return fail(PAC_ERR_CUDA, "no co-resident grid for the cooperative kernel");
+    return run_single(p, steps, grid, 1u, (unsigned)spin_limit, static_cast<cudaStream_t>(stream));
+}
+
 
 // Load and set up (module load, shared-memory attribute, occupancy) every
 // kernel the plan's convolution launches, with launches of no work, so that

@@ -10,6 +10,7 @@ far below the tolerances.
 """
 import math
 import os
+import time
 
 import numpy as np
 import pytest
@@ -983,3 +984,41 @@ def test_single_launch_repeatable_and_barrier_clean(dims, radix, dtype, monkeypa
     finally:
         plan.close()
     check(first, oracle.conv_separable(fs, x), dtype, int(np.prod(dims)), "single launch")
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_bounded_barrier_wait_runs_out_and_reports(dtype):
+    """The grid barrier of the single-launch kernel waits with a bound: with a
+    target no launch reaches (one arrival more than the grid makes) and a
+    limit of 64 polls, every wait runs out.  The kernel still ends promptly,
+    the device error word reads 1 (and 0 once read), and the next ordinary
+    convolution on the same context matches the oracle."""
+    pac = pac_mod()
+    dims = (1 << 16,)
+    h = pin.as_dtype(pin.complex_uniform(dims, 31), dtype)
+    x = pin.as_dtype(pin.complex_uniform(dims, 32), dtype)
+    plan = pac.Plan(dims, 2, dtype)
+    try:
+        plan.filter_spectrum(dev(h))
+        xd = dev(x)
+        y = torch.empty_like(xd)
+        assert plan.query(pac.Q_DEVICE_ERROR) == 0
+        t0 = time.perf_counter()
+        pac.pac_test_barrier_timeout(plan.handle, xd, y, 64)
+        torch.cuda.synchronize()
+        assert time.perf_counter() - t0 < 10.0
+        assert plan.query(pac.Q_DEVICE_ERROR) == 1
+        assert plan.query(pac.Q_DEVICE_ERROR) == 0
+        with pytest.raises(pac.PacError) as ei:
+            pac.pac_test_barrier_timeout(plan.handle, xd, y, 0)
+        assert ei.value.status == pac.Status.ERR_ARG
+        plan.convolve(xd, y)
+        torch.cuda.synchronize()
+        got = y.cpu().numpy()
+        assert plan.query(pac.Q_DEVICE_ERROR) == 0
+    finally:
+        plan.close()
+    pts = pin.sample_points(int(np.prod(dims)), 1024, 33)
+    err = oracle.rel_l2(got.reshape(-1)[pts], oracle.conv_direct_points(h, x, pts))
+    tol = 1e-12 if dtype == "c128" else 1e-5 * math.log2(np.prod(dims))
+    assert err <= tol, f"after a timed-out launch: rel_l2 {err:.3e} > {tol:.1e}"
