@@ -44,8 +44,14 @@ constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi 
 // up to 1 KB per row segment, so that its CTAs get enough tasks: with 256
 // bytes a 3-point group would run 32 tasks in a 64-thread CTA (measured on
 // mixed-radix 6000^2: 3.2 -> 1.7 ms; 120^3: 260 -> 130 us).
+// The large complex FP64 groups (2187 and 3125 points) are bound by the FP64
+// pipe, not by HBM: one column per tile (a 16-byte row segment) halves the
+// CTA so that two CTAs share an SM and one computes while the other waits on
+// its loads.
+constexpr int tile_wmin(int m, int esize) { return esize == 16 && m >= 2187 ? 1 : 32 / esize; }
 constexpr int tile_w(int m, int esize) {
-    return clampi(floor_pow2(kTileBytes / (m * esize)), 32 / esize, (round_count(m, esize) == 1 ? 1024 : 256) / esize);
+    return clampi(floor_pow2(kTileBytes / (m * esize)), tile_wmin(m, esize),
+                  (round_count(m, esize) == 1 ? 1024 : 256) / esize);
 }
 
 // Row padding of the shared-memory exchange buffer, in elements.  Chosen per
