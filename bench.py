@@ -63,6 +63,11 @@ def parse_args(argv=None):
     ap.add_argument("--workload", choices=["conv3d", "conv2d-r3", "conv2d-r5", "conv1d"], default="conv2d-r5",
                     help="the main leg's problem (default: the 2-D 3125^2 radix-5 workload)")
     ap.add_argument("--quick", action="store_true", help="main leg only (for profiler runs)")
+    ap.add_argument("--profile-path", choices=["none", "permuted", "single", "mixed", "pfa"], default="none",
+                    help="profiler runs: time one other path instead of the main line and print its times "
+                         "(permuted: the comparator on the main workload; single: the one-launch cooperative "
+                         "form of 3-D 128^3 FP32 radix 4; mixed: 2-D 1000^2 FP32 with groups spanning prime "
+                         "bases; pfa: the prime factor form of 1-D 2^10 3^5 5^3 FP32)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline and the oracle checks")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--legs", default="configs,batched,served",  # "none": the main leg only
@@ -861,6 +866,50 @@ def served_leg(a, torch, pac, pin, dev):
     return out
 
 
+def profile_path_leg(a, torch, pac, pin, dev):
+    """--profile-path: warm-up and timed calls of one other path (for ncu
+    launch lists and captures of its kernels); prints one JSON line of times."""
+    stream = torch.cuda.Stream(device=dev)
+    sh = stream.cuda_stream
+    env = {}
+    if a.profile_path == "permuted":
+        c = workload_conv(a, pin)
+    elif a.profile_path == "single":
+        c = pin.c2(4, "c64", 128)
+        env = {"PAC_SINGLE_LAUNCH": "1", "PAC_PLANE": "0"}
+    elif a.profile_path == "mixed":
+        c = pin.mixed((1000, 1000))
+        env = {"PAC_MIXED": "1"}
+    else:
+        n = 2 ** 10 * 3 ** 5 * 5 ** 3
+        c = pin.Conv((n,), 0, "c64", "uniform", "uniform", seed=7, h_seed=107)
+    x = torch.from_numpy(pin.make_x(c)).to(dev)
+    h = torch.from_numpy(pin.make_h(c)[0]).to(dev)
+    y = torch.empty_like(x)
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        obj = pac.Pfa(c.n_total, c.dtype) if a.profile_path == "pfa" else pac.Plan(c.dims, c.radix, c.dtype)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    obj.filter_spectrum(h)
+    if a.profile_path == "permuted":
+        fn = lambda: pac.pac_convolve_permuted(obj.handle, x, y, sh)  # noqa: E731
+    elif a.profile_path == "pfa":
+        fn = lambda: pac.pac_pfa_convolve(obj.handle, x, y, sh)  # noqa: E731
+    else:
+        fn = lambda: pac.pac_convolve(obj.handle, x, y, sh)  # noqa: E731
+    ms = time_steps(torch, fn, a.steps, a.warmup, lambda: None, stream)
+    print(json.dumps({"profile_path": a.profile_path, "dims": list(c.dims), "dtype": c.dtype,
+                      "launches_per_call": obj.query(pac.Q_LAUNCHES_CONVOLVE), "ms": ms}), flush=True)
+    obj.close()
+    return 0
+
+
 def main(argv=None):
     a = parse_args(argv)
     world, rank, local = dist_env()
@@ -888,6 +937,9 @@ def main(argv=None):
         _build.build()
     barrier(world)
     pac.load()
+
+    if a.profile_path != "none":
+        return profile_path_leg(a, torch, pac, pin, dev)
 
     c = workload_conv(a, pin)
     x_np, (h_np, _) = pin.make_x(c), pin.make_h(c)
