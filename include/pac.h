@@ -353,7 +353,8 @@ enum {
                                      (1: a bounded grid-barrier wait gave up) */
     PAC_Q_GROUPS = 9,             /* stage groups (one pass each) over all axes */
     PAC_Q_PLANE = 10,             /* CTAs per plane of the plane pass, 0 when the plan has none */
-    PAC_Q_GROUP_CAP = 11          /* the schedule's group-exponent cap (0: none) */
+    PAC_Q_GROUP_CAP = 11,         /* the schedule's group-exponent cap (0: none) */
+    PAC_Q_TMA_GROUPS = 12         /* groups whose passes run in the TMA-fed lines kernel */
 };
 
 /*

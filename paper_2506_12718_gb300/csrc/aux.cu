@@ -14,7 +14,7 @@ namespace pac {
 template <typename V>
 __global__ void permute_kernel(int64_t d0, int64_t d1, int64_t d2, const int64_t* __restrict__ t0,
                                const int64_t* __restrict__ t1, const int64_t* __restrict__ t2, const V* src,
-                               V* dst, const V* __restrict__ mul, double scale) {
+                               V* dst, const V* __restrict__ mul, typename Real<V>::T scale, int do_scale) {
     const int64_t rows = d0 * d1;
     for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
         const int64_t i0 = row / d1, i1 = row - (row / d1) * d1;
@@ -26,7 +26,7 @@ __global__ void permute_kernel(int64_t d0, int64_t d1, int64_t d2, const int64_t
              i2 += (int64_t)gridDim.x * blockDim.x) {
             V v = srow[t2 ? __ldg(t2 + i2) : i2];
             if (mul) v = cmul(v, __ldg(mul + row * d2 + i2));
-            if (scale != 1.0) v = cscale(v, (typename Real<V>::T)scale);
+            if (do_scale) v = cscale(v, scale);
             drow[i2] = v;
         }
     }
@@ -38,7 +38,7 @@ __global__ void permute_kernel(int64_t d0, int64_t d1, int64_t d2, const int64_t
 template <typename V>
 __global__ void permute_flat_kernel(uint32_t n, uint32_t d1, uint32_t d2, const int64_t* __restrict__ t0,
                                     const int64_t* __restrict__ t1, const int64_t* __restrict__ t2, const V* src,
-                                    V* dst, const V* __restrict__ mul, double scale) {
+                                    V* dst, const V* __restrict__ mul, typename Real<V>::T scale, int do_scale) {
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const uint32_t row = e / d2, i2 = e - row * d2;
         const uint32_t i0 = row / d1, i1 = row - i0 * d1;
@@ -47,17 +47,18 @@ __global__ void permute_flat_kernel(uint32_t n, uint32_t d1, uint32_t d2, const 
         const uint32_t s2 = t2 ? (uint32_t)__ldg(t2 + i2) : i2;
         V v = src[(s0 * d1 + s1) * d2 + s2];
         if (mul) v = cmul(v, __ldg(mul + e));
-        if (scale != 1.0) v = cscale(v, (typename Real<V>::T)scale);
+        if (do_scale) v = cscale(v, scale);
         dst[e] = v;
     }
 }
 
 template <typename V>
-__global__ void pointwise_kernel(int64_t n, const V* a, const V* __restrict__ b, V* out, double scale) {
+__global__ void pointwise_kernel(int64_t n, const V* a, const V* __restrict__ b, V* out, typename Real<V>::T scale,
+                                 int do_scale) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         V v = a[i];
         if (b) v = cmul(v, __ldg(b + i));
-        if (scale != 1.0) v = cscale(v, (typename Real<V>::T)scale);
+        if (do_scale) v = cscale(v, scale);
         out[i] = v;
     }
 }
@@ -107,11 +108,11 @@ cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64
         if (esize == 8)
             permute_flat_kernel<float2><<<blocks, 256, 0, s>>>((uint32_t)n, (uint32_t)d[1], (uint32_t)d[2], t[0], t[1],
                                                                t[2], (const float2*)src, (float2*)dst,
-                                                               (const float2*)mul, scale);
+                                                               (const float2*)mul, (float)scale, scale != 1.0);
         else
             permute_flat_kernel<double2><<<blocks, 256, 0, s>>>((uint32_t)n, (uint32_t)d[1], (uint32_t)d[2], t[0],
                                                                 t[1], t[2], (const double2*)src, (double2*)dst,
-                                                                (const double2*)mul, scale);
+                                                                (const double2*)mul, scale, scale != 1.0);
         return cudaGetLastError();
     }
     const int threads = (int)std::min<int64_t>(256, ((d[2] + 31) / 32) * 32);
@@ -120,10 +121,10 @@ cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64
     dim3 grid((unsigned)gx, (unsigned)gy);
     if (esize == 8)
         permute_kernel<float2><<<grid, threads, 0, s>>>(d[0], d[1], d[2], t[0], t[1], t[2], (const float2*)src,
-                                                         (float2*)dst, (const float2*)mul, scale);
+                                                         (float2*)dst, (const float2*)mul, (float)scale, scale != 1.0);
     else
         permute_kernel<double2><<<grid, threads, 0, s>>>(d[0], d[1], d[2], t[0], t[1], t[2], (const double2*)src,
-                                                          (double2*)dst, (const double2*)mul, scale);
+                                                          (double2*)dst, (const double2*)mul, scale, scale != 1.0);
     return cudaGetLastError();
 }
 
@@ -133,10 +134,10 @@ cudaError_t launch_pointwise_mul(int esize, int64_t n, const void* a, const void
     const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, 65535);
     if (esize == 8)
         pointwise_kernel<float2><<<(unsigned)blocks, threads, 0, s>>>(n, (const float2*)a, (const float2*)b,
-                                                                     (float2*)out, scale);
+                                                                     (float2*)out, (float)scale, scale != 1.0);
     else
         pointwise_kernel<double2><<<(unsigned)blocks, threads, 0, s>>>(n, (const double2*)a, (const double2*)b,
-                                                                      (double2*)out, scale);
+                                                                      (double2*)out, scale, scale != 1.0);
     return cudaGetLastError();
 }
 

@@ -35,23 +35,62 @@ struct pac_pfa_s {
 
 namespace pac {
 
-// Gamma^T: tensor entry t = (i_0, i_1, i_2) (i_2 fastest) = src[(i_0 e_0 + i_1 e_1 + i_2 e_2) mod n]
+// Gamma^T: tensor entry t = (i_0, i_1, i_2) (i_2 fastest) = src[k], k = (i_0 e_0 + i_1 e_1 + i_2 e_2) mod n.
+// A thread walks t, t + S, t + 2S, ... (S the grid's thread count) and keeps
+// the digits of t and k up to date with 32-bit additions: adding the digits
+// (s_0, s_1, s_2) of S adds delta = (s_0 e_0 + s_1 e_1 + s_2 e_2) mod n to k,
+// and a carry out of digit q adds e_{q-1}, because d_q e_q = 0 mod n (e_q is
+// 0 modulo every other factor and d_q e_q is 0 modulo d_q).  No 64-bit
+// division per element (a 64-bit modulo runs on the FP64 pipe, which is
+// narrow on this GPU).
 template <typename V>
-__global__ void pfa_to_tensor_kernel(uint64_t n, uint64_t d1, uint64_t d2, uint64_t e0, uint64_t e1, uint64_t e2,
+__global__ void pfa_to_tensor_kernel(uint32_t n, uint32_t d1, uint32_t d2, uint32_t e0, uint32_t e1, uint32_t e2,
+                                     uint32_t s0, uint32_t s1, uint32_t s2, uint32_t delta,
                                      const V* __restrict__ src, V* __restrict__ dst) {
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t i2 = t % d2, r = t / d2, i1 = r % d1, i0 = r / d1;
-        const uint64_t k = ((i0 * e0) % n + (i1 * e1) % n + (i2 * e2) % n) % n;
+    const uint32_t S = gridDim.x * blockDim.x;
+    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    uint32_t i2 = t % d2, r = t / d2, i1 = r % d1, i0 = r / d1;
+    uint32_t k = (uint32_t)(((uint64_t)i0 * e0 + (uint64_t)i1 * e1 + (uint64_t)i2 * e2) % n);
+    const auto addmod = [n](uint32_t a, uint32_t b) { const uint32_t c = a + b; return c >= n ? c - n : c; };
+    for (;;) {
         dst[t] = __ldg(src + k);
+        t += S;
+        if (t >= n) break;
+        i2 += s2;
+        const bool c2 = i2 >= d2;
+        if (c2) i2 -= d2;
+        i1 += s1 + (c2 ? 1u : 0u);
+        const bool c1 = i1 >= d1;
+        if (c1) i1 -= d1;
+        i0 += s0 + (c1 ? 1u : 0u);
+        k = addmod(k, delta);
+        if (c2) k = addmod(k, e1);
+        if (c1) k = addmod(k, e0);
     }
 }
 
-// Gamma: dst[k] = tensor entry (k mod d_0, k mod d_1, k mod d_2)
+// Gamma: dst[k] = tensor entry (k mod d_0, k mod d_1, k mod d_2); a thread
+// walks k, k + S, ... keeping the three residues with 32-bit additions of
+// S mod d_q.
 template <typename V>
-__global__ void pfa_from_tensor_kernel(uint64_t n, uint64_t d0, uint64_t d1, uint64_t d2, const V* __restrict__ src,
-                                       V* __restrict__ dst) {
-    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x)
-        dst[k] = __ldg(src + ((k % d0) * d1 + k % d1) * d2 + k % d2);
+__global__ void pfa_from_tensor_kernel(uint32_t n, uint32_t d0, uint32_t d1, uint32_t d2, uint32_t m0, uint32_t m1,
+                                       uint32_t m2, const V* __restrict__ src, V* __restrict__ dst) {
+    const uint32_t S = gridDim.x * blockDim.x;
+    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t r0 = k % d0, r1 = k % d1, r2 = k % d2;
+    for (;;) {
+        dst[k] = __ldg(src + (r0 * d1 + r1) * d2 + r2);
+        k += S;
+        if (k >= n) break;
+        r0 += m0;
+        if (r0 >= d0) r0 -= d0;
+        r1 += m1;
+        if (r1 >= d1) r1 -= d1;
+        r2 += m2;
+        if (r2 >= d2) r2 -= d2;
+    }
 }
 
 static cudaError_t launch_pfa_map(const pac_pfa_s* p, bool to_tensor, const void* src, void* dst, cudaStream_t s) {
@@ -62,23 +101,36 @@ static cudaError_t launch_pfa_map(const pac_pfa_s* p, bool to_tensor, const void
     const int64_t want = (p->n + threads - 1) / threads;
     const int64_t cap = (int64_t)device_sm_count(dev) * 8;
     const unsigned grid = (unsigned)(want < cap ? want : cap);
-    const uint64_t n = (uint64_t)p->n;
-    if (p->esize == 8) {
-        if (to_tensor)
-            pfa_to_tensor_kernel<float2><<<grid, threads, 0, s>>>(n, p->dims[1], p->dims[2], p->crt[0], p->crt[1],
-                                                                  p->crt[2], static_cast<const float2*>(src),
+    const uint64_t n = (uint64_t)p->n;  // < 2^31
+    const uint64_t S = (uint64_t)grid * threads;
+    const uint64_t d0 = (uint64_t)p->dims[0], d1 = (uint64_t)p->dims[1], d2 = (uint64_t)p->dims[2];
+    if (to_tensor) {
+        // digits of the stride S (mod n) in the tensor's mixed radix, and the k increment they give
+        const uint64_t sm = S % n;
+        const uint64_t s2 = sm % d2, s1 = (sm / d2) % d1, s0 = sm / (d1 * d2);
+        const uint64_t delta = (s0 * ((uint64_t)p->crt[0] % n) % n + s1 * ((uint64_t)p->crt[1] % n) % n +
+                                s2 * ((uint64_t)p->crt[2] % n) % n) % n;
+        const uint32_t a[10] = {(uint32_t)n, (uint32_t)d1, (uint32_t)d2, (uint32_t)(p->crt[0] % (int64_t)n),
+                                (uint32_t)(p->crt[1] % (int64_t)n), (uint32_t)(p->crt[2] % (int64_t)n),
+                                (uint32_t)s0, (uint32_t)s1, (uint32_t)s2, (uint32_t)delta};
+        if (p->esize == 8)
+            pfa_to_tensor_kernel<float2><<<grid, threads, 0, s>>>(a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8],
+                                                                  a[9], static_cast<const float2*>(src),
                                                                   static_cast<float2*>(dst));
         else
-            pfa_from_tensor_kernel<float2><<<grid, threads, 0, s>>>(n, p->dims[0], p->dims[1], p->dims[2],
+            pfa_to_tensor_kernel<double2><<<grid, threads, 0, s>>>(a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8],
+                                                                   a[9], static_cast<const double2*>(src),
+                                                                   static_cast<double2*>(dst));
+    } else {
+        const uint32_t m0 = (uint32_t)(S % d0), m1 = (uint32_t)(S % d1), m2 = (uint32_t)(S % d2);
+        if (p->esize == 8)
+            pfa_from_tensor_kernel<float2><<<grid, threads, 0, s>>>((uint32_t)n, (uint32_t)d0, (uint32_t)d1,
+                                                                    (uint32_t)d2, m0, m1, m2,
                                                                     static_cast<const float2*>(src),
                                                                     static_cast<float2*>(dst));
-    } else {
-        if (to_tensor)
-            pfa_to_tensor_kernel<double2><<<grid, threads, 0, s>>>(n, p->dims[1], p->dims[2], p->crt[0], p->crt[1],
-                                                                   p->crt[2], static_cast<const double2*>(src),
-                                                                   static_cast<double2*>(dst));
         else
-            pfa_from_tensor_kernel<double2><<<grid, threads, 0, s>>>(n, p->dims[0], p->dims[1], p->dims[2],
+            pfa_from_tensor_kernel<double2><<<grid, threads, 0, s>>>((uint32_t)n, (uint32_t)d0, (uint32_t)d1,
+                                                                     (uint32_t)d2, m0, m1, m2,
                                                                      static_cast<const double2*>(src),
                                                                      static_cast<double2*>(dst));
     }
