@@ -33,8 +33,6 @@ namespace {
 struct MultiLaunch {
     int esize, M;
     bool lines;
-    bool tma;            // lines passes of the TMA-fed kernel
-    bool fused;          // some pass of the launch is a fused pass (its spectrum tiles are staged)
     int M2;              // > 0: a plane launch (groups M x M2), arguments are PlaneArgs
     int K;               // plane launch: CTAs per plane
     int n;               // passes in the launch
@@ -72,8 +70,7 @@ ShapeKey shape_key(pac_plan p, const Step& st) {
     if (st.mode == kPlane)
         return ShapeKey(p->esize, p->groups[p->plane_g1].M, p->plane_k, p->groups[p->plane_g1 + 1].M);
     const GroupPlan& g = p->groups[st.group];
-    // -M: a mixed group; lines 2: a lines group of the TMA-fed kernel
-    return ShapeKey(p->esize, g.mix_nr > 0 ? -g.M : g.M, g.C == 1 ? (g.tma ? 2 : 1) : 0, 0);
+    return ShapeKey(p->esize, g.mix_nr > 0 ? -g.M : g.M, g.C == 1 ? 1 : 0, 0);  // -M: a mixed group
 }
 
 // Append one merged launch (arguments, then tile starts) to the host image.
@@ -83,11 +80,6 @@ int add_launch(std::vector<unsigned char>& blob, const ShapeKey& key, const void
     int lines;
     std::tie(m.esize, m.M, lines, m.M2) = key;
     m.lines = m.M2 == 0 && lines != 0;
-    m.tma = m.M2 == 0 && lines == 2;
-    m.fused = false;
-    if (m.M2 == 0)
-        for (size_t k = 0; k < tiles.size(); ++k)
-            if (static_cast<const PassArgs*>(args)[k].mode == kFused) m.fused = true;
     m.K = m.M2 > 0 ? lines : 1;
     m.n = (int)tiles.size();
     m.off_args = align_up(blob.size(), 64);
@@ -166,9 +158,6 @@ cudaError_t enqueue_launch(const BatchEntry* e, const MultiLaunch& m, cudaStream
     if (m.M2 > 0)
         return launch_plane_multi(m.esize, m.M, m.M2, m.K, reinterpret_cast<const PlaneArgs*>(b + m.off_args),
                                   starts, m.n, m.tiles, s);
-    if (m.tma)
-        return launch_lines_tma_multi(m.esize, m.M, reinterpret_cast<const PassArgs*>(b + m.off_args), starts, m.n,
-                                      m.tiles, m.fused ? 1 : 0, s);
     return launch_multi(m.esize, m.M, m.lines, reinterpret_cast<const PassArgs*>(b + m.off_args), starts, m.n,
                         m.tiles, s);
 }
@@ -176,7 +165,6 @@ cudaError_t enqueue_launch(const BatchEntry* e, const MultiLaunch& m, cudaStream
 // per-kernel set-up (shared-memory attribute, occupancy): a launch with no work
 cudaError_t prepare_launch(const MultiLaunch& m, cudaStream_t s) {
     if (m.M2 > 0) return launch_plane_multi(m.esize, m.M, m.M2, m.K, nullptr, nullptr, 0, 0, s);
-    if (m.tma) return launch_lines_tma_multi(m.esize, m.M, nullptr, nullptr, 0, 0, m.fused ? 1 : 0, s);
     return launch_multi(m.esize, m.M, m.lines, nullptr, nullptr, 0, 0, s);
 }
 

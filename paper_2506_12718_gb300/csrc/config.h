@@ -115,39 +115,6 @@ constexpr int min_blocks(int m, int esize) {
     return clampi(65536 / (pass_threads(m, esize) * reg_target(m, esize)), 1, 8);
 }
 
-// ------------------------------------------------------- TMA-staged lines
-// Lines passes of large one-base groups (the contiguous axis: a tile of W
-// lines is one contiguous stretch of the array) run in a persistent kernel
-// that stages each tile in shared memory with bulk asynchronous copies (TMA,
-// cp.async.bulk) one tile ahead, into two buffers, and the fused pass' filter
-// spectrum tile (also contiguous, in slot order) into two more.  The tile
-// width is the largest power of two <= tile_w whose four buffers fit
-// kTmaSmemMax; the first round reads the staged tile in place.
-constexpr int kTmaSmemMax = 200 * 1024;
-constexpr int kTmaMinBytes = 8192;  // groups whose line is at least this many bytes
-constexpr int tma_w(int m, int esize) {
-    return clampi(floor_pow2(kTmaSmemMax / (4 * m * esize)), 1, tile_w(m, esize));
-}
-// exchange-buffer pitch of the staged tile (the ordinary lines pitch when the width is unchanged)
-constexpr int tma_pitch(int m, int esize) {
-    return tma_w(m, esize) == tile_w(m, esize) ? tile_pitch(m, esize, true) : tma_w(m, esize);
-}
-// one thread per task of the first round: the staged round reads every value before writing any
-constexpr int tma_threads(int m, int esize) {
-    return clampi(((tma_w(m, esize) * (m / round_radix(m, esize, 0)) + 31) / 32) * 32, 64, 1024);
-}
-// elements of one staged tile buffer: the staged lines [w][g] and, in place, the exchange layout [g][pitch]
-constexpr int tma_buf(int m, int esize) {
-    return m * tma_pitch(m, esize) > m * tma_w(m, esize) ? m * tma_pitch(m, esize) : m * tma_w(m, esize);
-}
-constexpr int tma_smem_bytes(int m, int esize, bool spec) {
-    return 128 + (2 * tma_buf(m, esize) + (spec ? 2 * m * tma_w(m, esize) : 0)) * esize;
-}
-constexpr bool tma_group(int m, int esize) {
-    return esize == 8 && base_of(m) > 1 && ipow(base_of(m), ilog(m, base_of(m))) == m && m * esize >= kTmaMinBytes &&
-           m <= group_mmax(base_of(m), esize) && tma_smem_bytes(m, esize, true) <= 227 * 1024;
-}
-
 // ------------------------------------------------------------ mixed groups
 // A group whose stages have more than one prime base (mixed radix, Section
 // 7.1) runs in the runtime-radix kernel (mix.cuh): the tile is copied into

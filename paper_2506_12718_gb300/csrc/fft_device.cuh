@@ -305,8 +305,6 @@ template <typename V> struct TileCtx {
     typename Real<V>::T scale;
     int wofs;          // column offset of this CTA's columns in the buffer (split rows)
     uint32_t sk[4];    // split rows: the buffer of each CTA of the cluster (shared::cluster addresses)
-    const V* stage;    // staged lines tile (line w, global row g at w * M + g), the TMA-fed kernel
-    const V* sstage;   // staged spectrum tile (slot u * TASKS + tau), or null: read from global
 };
 
 // Loads and stores of distributed shared memory (a CTA of the cluster,
@@ -372,7 +370,7 @@ template <typename GEO> __device__ __forceinline__ void round_sync() {
         __syncthreads();
 }
 
-enum : int { kFromSmem = 0, kFromNatural = 1, kFromPlaced = 2, kFromStageNatural = 3, kFromStagePlaced = 4 };
+enum : int { kFromSmem = 0, kFromNatural = 1, kFromPlaced = 2 };
 enum : int { kToSmem = 0, kToNatural = 1, kToPlaced = 2 };
 
 // Global position of a task's column: offset of its row 0, external-twiddle
@@ -480,60 +478,9 @@ __device__ __forceinline__ void load_spec(const TileCtx<typename GEO::V>& c, int
     using V = typename GEO::V;
     using G = RoundGeom<GEO::M, GEO::ES, RI>;
     constexpr int TASKS = TT::TASKS;
-    if (c.sstage) {  // the TMA-fed kernel staged this tile's slots in shared memory
-#pragma unroll
-        for (int u = 0; u < G::R; ++u) hs[u] = col.valid ? c.sstage[u * TASKS + tau] : V{0, 0};
-        return;
-    }
     const V* spec = reinterpret_cast<const V*>(c.a->spec) + (size_t)c.t * (GEO::W * GEO::M) + tau;
 #pragma unroll
     for (int u = 0; u < G::R; ++u) hs[u] = col.valid ? __ldg(spec + u * TASKS) : V{0, 0};
-}
-
-// The first round of a staged lines tile: the tile's W lines sit in shared
-// memory as staged (line w at w * M), and the round's output goes to the
-// exchange layout of the same buffer, so every thread reads the values of
-// all its tasks (ITER of them, held in registers) before any thread writes.
-// Tasks in line-fastest order, so a warp reads consecutive elements of one
-// line.
-template <typename GEO, int RI, bool INV, int SRC, int DST, bool MUL>
-__device__ __forceinline__ void round_staged(const TileCtx<typename GEO::V>& c) {
-    using V = typename GEO::V;
-    constexpr int M = GEO::M;
-    using G = RoundGeom<M, GEO::ES, RI>;
-    constexpr int R = G::R;
-    using T = Task<M, GEO::ES, GEO::W, RI, !MUL>;
-    constexpr int ITER = (T::TASKS + GEO::NT - 1) / GEO::NT;
-    static_assert(ITER * R <= 32, "the staged round holds every task's values in registers");
-    static_assert(SRC == kFromStageNatural || SRC == kFromStagePlaced, "a staged source");
-    V v[ITER][R];
-    V hs[ITER][MUL ? R : 1];
-#pragma unroll
-    for (int it = 0; it < ITER; ++it) {
-        const int tau = (int)threadIdx.x + it * GEO::NT;
-        if (tau < T::TASKS) {
-            const T t(tau);
-            const TaskCol col = task_col<true, M>(c, t.w);
-#pragma unroll
-            for (int u = 0; u < R; ++u) {
-                const int row = t.row0 + G::SP * u;
-                const int g = SRC == kFromStagePlaced ? __ldg(c.a->r2g + row) : row;
-                v[it][u] = col.valid ? c.stage[t.w * M + g] : V{0, 0};
-            }
-            if constexpr (MUL) load_spec<GEO, RI, T>(c, tau, col, hs[it]);
-        }
-    }
-    __syncthreads();  // the staged layout is read in full before the exchange layout overwrites it
-#pragma unroll
-    for (int it = 0; it < ITER; ++it) {
-        const int tau = (int)threadIdx.x + it * GEO::NT;
-        if (tau < T::TASKS) {
-            const T t(tau);
-            const TaskCol col = task_col<true, M>(c, t.w);
-            task_body<GEO, true, RI, INV, SRC == kFromStagePlaced ? kFromPlaced : kFromNatural, DST, MUL>(c, t, col,
-                                                                                                        v[it], hs[it]);
-        }
-    }
 }
 
 // One round of a tile.  SRC: shared memory, natural global rows, or global
@@ -679,51 +626,6 @@ __device__ __forceinline__ void tile_fused(const TileCtx<typename GEO::V>& c) {
     }
 }
 
-// Staged forms of the tile functions (TMA-fed lines kernel): the first
-// round reads the staged tile, the others as in tile_forward / tile_inverse /
-// tile_fused.
-template <typename GEO>
-__device__ __forceinline__ void tile_forward_staged(const TileCtx<typename GEO::V>& c) {
-    constexpr int NR = GEO::NR;
-    if constexpr (NR == 1) {
-        round_staged<GEO, 0, false, kFromStageNatural, kToPlaced, false>(c);
-    } else {
-        round_staged<GEO, 0, false, kFromStageNatural, kToSmem, false>(c);
-        round_sync<GEO>();
-        fwd_middle<GEO, true, 1>(c);
-        round_exec<GEO, true, NR - 1, false, kFromSmem, kToPlaced, false>(c);
-    }
-}
-
-template <typename GEO>
-__device__ __forceinline__ void tile_inverse_staged(const TileCtx<typename GEO::V>& c) {
-    constexpr int NR = GEO::NR;
-    if constexpr (NR == 1) {
-        round_staged<GEO, 0, true, kFromStagePlaced, kToNatural, false>(c);
-    } else {
-        round_staged<GEO, NR - 1, true, kFromStagePlaced, kToSmem, false>(c);
-        round_sync<GEO>();
-        inv_middle<GEO, true, NR - 2>(c);
-        round_exec<GEO, true, 0, true, kFromSmem, kToNatural, false>(c);
-    }
-}
-
-template <typename GEO>
-__device__ __forceinline__ void tile_fused_staged(const TileCtx<typename GEO::V>& c) {
-    constexpr int NR = GEO::NR;
-    if constexpr (NR == 1) {
-        round_staged<GEO, 0, false, kFromStageNatural, kToNatural, true>(c);
-    } else {
-        round_staged<GEO, 0, false, kFromStageNatural, kToSmem, false>(c);
-        round_sync<GEO>();
-        fwd_middle<GEO, true, 1>(c);
-        round_exec<GEO, true, NR - 1, false, kFromSmem, kToSmem, true>(c);
-        round_sync<GEO>();
-        inv_middle<GEO, true, NR - 2>(c);
-        round_exec<GEO, true, 0, true, kFromSmem, kToNatural, false>(c);
-    }
-}
-
 // Programmatic dependent launch: let the next pass in the stream be scheduled
 // now; wait here until the previous pass' writes are visible.
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
@@ -770,8 +672,6 @@ template <typename V> __device__ __forceinline__ void ctx_init(TileCtx<V>& c, co
     c.scale = (typename Real<V>::T)a.scale;
     c.wofs = 0;
     for (int k = 0; k < 4; ++k) c.sk[k] = 0;
-    c.stage = nullptr;
-    c.sstage = nullptr;
 }
 
 // One pass over all tiles, CTAs walking tiles blockIdx.x, +gridDim.x, ...

@@ -23,7 +23,6 @@ cudaError_t launch_mix_multi(int esize, int M, bool lines, const PassArgs* list,
 
 cudaError_t launch_pass(int esize, int M, const PassArgs& a, cudaStream_t s) {
     if (a.mix_nr > 0) return launch_mix(esize, a.C == 1, a, s);
-    if (a.tma) return launch_lines_tma(esize, M, a, s);
     if (esize == 8) return (M % 2 == 0) ? launch_pass_c64_p2(M, a, s) : launch_pass_c64_p35(M, a, s);
     return (M % 2 == 0) ? launch_pass_c128_p2(M, a, s) : launch_pass_c128_p35(M, a, s);
 }

@@ -27,23 +27,19 @@ struct GroupPlan {
     int64_t Q = 1;          // columns = N / M
     int tw_T = 1, tw_shift = 0;
     bool has_ext = false;
-    bool tma = false;       // a lines group run by the TMA-fed kernel (its tile width is tma_w)
     int mix_nr = 0;         // > 0: a mixed group (several prime bases), rounds mix_r of the runtime-radix kernel
     int mix_r[kMixMaxRounds] = {0};
     size_t off_twi = 0, off_lo = 0, off_hi = 0, off_rowmap = 0, off_freq = 0, off_r2g = 0, off_r2f = 0;  // in tables
 };
 
 // tile width of a group's pass
-inline int group_w(const GroupPlan& g, int esize) {
-    return g.mix_nr > 0 ? mix_w(g.M, esize) : (g.tma ? tma_w(g.M, esize) : tile_w(g.M, esize));
-}
+inline int group_w(const GroupPlan& g, int esize) { return g.mix_nr > 0 ? mix_w(g.M, esize) : tile_w(g.M, esize); }
 
 // A pass schedule: the largest group exponent per pass (0: the largest a CTA
 // takes) and whether the last two axes may run as a plane pass.
 struct Schedule {
     int cap = 0;
     bool plane = true;
-    bool tma = true;     // large contiguous-axis groups run in the TMA-fed lines kernel (tile width tma_w)
     bool mixed = false;  // stage lists of several prime bases: groups may span bases (runtime-radix kernel)
 };
 int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out);
@@ -73,14 +69,6 @@ cudaError_t launch_plane(int esize, int M1, int M2, int K, const PlaneArgs& pa, 
 cudaError_t launch_plane_multi(int esize, int M1, int M2, int K, const PlaneArgs* list, const uint32_t* starts, int n,
                                int64_t total, cudaStream_t s);
 PlaneArgs make_plane(pac_plan p, const void* src, void* dst);
-
-// TMA-fed lines kernel (kern_lines_tma.cu): supported group sizes, one pass, n passes of one shape
-int tma_lines_supported(int M, int esize);
-cudaError_t launch_lines_tma(int esize, int M, const PassArgs& a, cudaStream_t s);
-cudaError_t launch_lines_tma_multi(int esize, int M, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
-                                   int stage_spec, cudaStream_t s);
-// the library's device error word (runtime.cu), created with the barrier pool
-int device_error_word(int device, unsigned** error);
 
 // n passes of one shape in one launch; list and starts in device memory (starts has n + 1 entries)
 cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,

@@ -32,7 +32,6 @@ struct PassArgs {
     // mixed group (stages of several prime bases, the runtime-radix kernel):
     // mix_nr rounds of radices mix_r (0: a one-base group), group size mix_m,
     // tile width mix_w
-    int tma;                // 1: a lines pass of the TMA-fed kernel (tile width tma_w)
     int mix_nr;
     int mix_m;
     int mix_w;

@@ -722,22 +722,11 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
                                         pl->N / ((int64_t)pl->groups[G - 2].M * pl->groups[G - 1].M), dev);
         }
     }
-    // TMA-fed lines kernel for the contiguous axis' large one-base group (not when it is part of the
-    // plane pass); PAC_TMA=0 in the environment keeps the ordinary lines kernel
-    const char* te = std::getenv("PAC_TMA");
-    if (sch.tma && !(te && te[0] == '0')) {
-        const int G = (int)pl->groups.size();
-        for (int gi = 0; gi < G; ++gi) {
-            GroupPlan& g = pl->groups[gi];
-            if (g.C == 1 && g.mix_nr == 0 && !(pl->plane && gi == G - 1) && tma_lines_supported(g.M, pl->esize))
-                g.tma = true;
-        }
-    }
     pl->uniform_m = 0;
     if (!pl->groups.empty()) {
         pl->uniform_m = pl->groups[0].M;
         for (const GroupPlan& g : pl->groups)
-            if (g.M != pl->uniform_m || g.mix_nr > 0 || g.tma) pl->uniform_m = 0;  // single launch: ordinary passes only
+            if (g.M != pl->uniform_m || g.mix_nr > 0) pl->uniform_m = 0;
     }
 
     // host blob of every table
@@ -778,16 +767,6 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
         return cuda_fail(e, "cudaGetDevice");
     }
     pl->tables_bytes = blob.size();
-    for (const GroupPlan& g : pl->groups) {
-        if (g.tma) {  // the TMA kernel's error word exists before any launch (none is made during a capture)
-            unsigned* w = nullptr;
-            if (int rc = device_error_word(pl->device, &w)) {
-                delete pl;
-                return rc;
-            }
-            break;
-        }
-    }
     if (int rc = acquire_tables(pl->device, blob, &pl->d_tables)) {
         free_plan(pl);
         return rc;
@@ -911,7 +890,6 @@ PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, vo
     a.mode = mode;
     a.has_ext = g.has_ext ? 1 : 0;
     a.scale = scale;
-    a.tma = g.tma ? 1 : 0;
     a.mix_nr = g.mix_nr;
     a.mix_m = g.M;
     a.mix_w = W;
@@ -1389,12 +1367,6 @@ extern "C" int pac_plan_query(pac_plan p, int key, int64_t* value) {
         case PAC_Q_GROUPS: *value = G; break;
         case PAC_Q_PLANE: *value = p->plane ? p->plane_k : 0; break;
         case PAC_Q_GROUP_CAP: *value = p->schedule.cap; break;
-        case PAC_Q_TMA_GROUPS: {
-            int64_t n = 0;
-            for (const GroupPlan& g : p->groups) n += g.tma ? 1 : 0;
-            *value = n;
-            break;
-        }
         default: return fail(PAC_ERR_ARG, "unknown query key %d", key);
     }
     return PAC_OK;

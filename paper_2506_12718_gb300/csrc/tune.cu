@@ -9,11 +9,9 @@
 // timed with CUDA events, and the fastest is remembered per
 // (dims, radix, dtype).  For stage lists of several prime bases (radix 0)
 // the candidates also include one-base groups only against groups spanning
-// bases, and the tile shape of the contiguous axis' large groups: W lines per
-// tile of the TMA-fed kernel (tma_w) against the ordinary lines kernel's W.
-// With PAC_TUNE_FILE set, schedules persist in that file as lines
+// bases.  With PAC_TUNE_FILE set, schedules persist in that file as lines
 // "ndim n0 n1 n2 radix dtype cap flags us", flags bit 0 = plane pass allowed,
-// bit 1 = groups may not span bases, bit 2 = no TMA-fed lines kernel.
+// bit 1 = groups may not span bases.
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -78,7 +76,6 @@ void load_file_locked() {
         t.sch.cap = cap;
         t.sch.plane = (plane & 1) != 0;
         t.sch.mixed = (plane & 2) == 0;
-        t.sch.tma = (plane & 4) == 0;
         t.us = us;
         g_tuned[k] = t;  // later lines win
     }
@@ -91,8 +88,7 @@ void append_file(const Key& k, const Tuned& t) {
     FILE* f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f, "%d %lld %lld %lld %d %d %d %d %.3f\n", k.ndim, (long long)k.d[0], (long long)k.d[1],
-                 (long long)k.d[2], k.radix, k.dtype, t.sch.cap,
-                 (t.sch.plane ? 1 : 0) | (t.sch.mixed ? 0 : 2) | (t.sch.tma ? 0 : 4), t.us);
+                 (long long)k.d[2], k.radix, k.dtype, t.sch.cap, (t.sch.plane ? 1 : 0) | (t.sch.mixed ? 0 : 2), t.us);
     std::fclose(f);
 }
 
@@ -149,30 +145,25 @@ bool tuned_schedule(int ndim, const int64_t* dims, int radix, pac_dtype dtype, S
 extern "C" int pac_tune(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int reps, double* best_us) {
     if (ndim < 1 || ndim > 3 || !dims || reps < 1) return fail(PAC_ERR_ARG, "bad arguments");
     // candidates: every group cap that changes the split, plane on and off,
-    // groups spanning prime bases or not, the TMA-fed lines kernel (its tile
-    // width) or the ordinary one
+    // groups spanning prime bases or not
     std::vector<Schedule> cands;
     std::vector<std::vector<int>> seen;
-    for (int tma = 1; tma >= 0; --tma) {
-        for (int mixed = 1; mixed >= 0; --mixed) {
-            for (int cap = 12; cap >= 1; --cap) {
-                for (int plane = 1; plane >= 0; --plane) {
-                    Schedule sch;
-                    sch.cap = cap;
-                    sch.plane = plane != 0;
-                    sch.mixed = mixed != 0;
-                    sch.tma = tma != 0;
-                    pac_plan p = nullptr;
-                    if (plan_build(ndim, dims, radix, dtype, sch, &p) != PAC_OK) continue;
-                    std::vector<int> sig;  // the resulting pass structure and tile shapes
-                    for (const GroupPlan& g : p->groups)
-                        sig.push_back(g.mix_nr > 0 ? -g.M : (g.tma ? g.M + (1 << 20) : g.M));
-                    sig.push_back(p->plane ? -p->plane_k : 0);
-                    pac_plan_destroy(p);
-                    if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
-                    seen.push_back(sig);
-                    cands.push_back(sch);
-                }
+    for (int mixed = 1; mixed >= 0; --mixed) {
+        for (int cap = 12; cap >= 1; --cap) {
+            for (int plane = 1; plane >= 0; --plane) {
+                Schedule sch;
+                sch.cap = cap;
+                sch.plane = plane != 0;
+                sch.mixed = mixed != 0;
+                pac_plan p = nullptr;
+                if (plan_build(ndim, dims, radix, dtype, sch, &p) != PAC_OK) continue;
+                std::vector<int> sig;  // the resulting pass structure
+                for (const GroupPlan& g : p->groups) sig.push_back(g.mix_nr > 0 ? -g.M : g.M);
+                sig.push_back(p->plane ? -p->plane_k : 0);
+                pac_plan_destroy(p);
+                if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+                seen.push_back(sig);
+                cands.push_back(sch);
             }
         }
     }

@@ -1023,42 +1023,3 @@ def test_bounded_barrier_wait_runs_out_and_reports(dtype):
     tol = 1e-12 if dtype == "c128" else 1e-5 * math.log2(np.prod(dims))
     assert err <= tol, f"after a timed-out launch: rel_l2 {err:.3e} > {tol:.1e}"
 
-
-TMA_SHAPES = [((3125, 3125), 5), ((2187, 2187), 3), ((4096,), 2), ((1024, 1024), 2), ((6, 2048), 0),
-              ((5, 3125), 5), ((4, 4096), 2), ((2187,), 3), ((3, 3, 2187), 3)]
-
-
-@pytest.mark.parametrize("dims,radix", TMA_SHAPES)
-def test_tma_lines_kernel_matches_oracle(dims, radix, monkeypatch):
-    """Complex FP32 plans whose contiguous axis is a large one-base group run
-    that axis in the TMA-fed lines kernel (bulk copies of whole tiles, one
-    tile ahead; tiles whose stretch is not 16-byte sized are copied by the
-    threads).  The convolution matches the oracle, the same plan without the
-    TMA-fed kernel (PAC_TMA=0) to rounding, and the unordered forward
-    transform (the kernel's forward mode) matches the plain one exactly in
-    layout and to rounding in value."""
-    pac = pac_mod()
-    fs, h, x = separable_case(dims, "c64", seed=71)
-    n = int(np.prod(dims))
-    plan = pac.Plan(dims, radix, "c64")
-    monkeypatch.setenv("PAC_TMA", "0")
-    plain = pac.Plan(dims, radix, "c64")
-    monkeypatch.delenv("PAC_TMA")
-    try:
-        assert plan.query(pac.Q_TMA_GROUPS) >= 1
-        assert plain.query(pac.Q_TMA_GROUPS) == 0
-        hd, xd = dev(h), dev(x)
-        plan.filter_spectrum(hd)
-        plain.filter_spectrum(hd)
-        y = plan.convolve(xd)
-        y0 = plain.convolve(xd)
-        f = plan.forward_unordered(xd)
-        f0 = plain.forward_unordered(xd)
-        torch.cuda.synchronize()
-        y, y0, f, f0 = (t.cpu().numpy() for t in (y, y0, f, f0))
-    finally:
-        plan.close()
-        plain.close()
-    check(y, oracle.conv_separable(fs, x), "c64", n, f"TMA-fed {dims}")
-    assert oracle.rel_l2(y, y0) <= tol("c64", n)
-    assert oracle.rel_l2(f, f0) <= tol("c64", n)
