@@ -75,6 +75,7 @@ def parse_args(argv=None):
                          "with its permuted form and cuFFT), batched (4096 mixed convolutions in one call), "
                          "served (Poisson request stream through the queue)")
     ap.add_argument("--max-inflight", type=int, default=16, help="served leg: requests running at once")
+    ap.add_argument("--serve-repeats", type=int, default=5, help="served leg: times the request stream is served")
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default pass schedules)")
     ap.add_argument("--flush-mb", type=int, default=FLUSH_BYTES >> 20,
@@ -819,48 +820,67 @@ def served_leg(a, torch, pac, pin, dev):
         pac.pac_convolve(p.handle, xbuf[(dims, dtype)], ybuf[(dims, dtype)][0])
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
-    q = pac.pac_queue_create(budget, max_inflight)
-    tickets, nbytes = [], 0
-    t0 = time.perf_counter()
-    for r in reqs:
-        c = r.conv
-        while time.perf_counter() - t0 < r.t_arrive:
-            pass
-        sk = (c.dims, c.dtype)
-        y = ybuf[sk][rr[sk] % K]
-        rr[sk] += 1
-        tickets.append(pac.pac_submit(q, plans[(c.dims, c.radix, c.dtype, r.filter_id)].handle, xbuf[sk], y))
-        nbytes += 3 * c.n_total * c.elem_bytes
-    pac.pac_queue_drain(q, 600000)
-    t_end = time.perf_counter()
-    lats, by_class = [], {}
-    for tk, r in zip(tickets, reqs):
-        st, lat = pac.pac_poll(q, tk)
-        lats.append(lat)
-        small = 2 * r.conv.n_total * r.conv.elem_bytes <= (8 << 20)  # the queue's small-request class
-        by_class.setdefault(f"{'small' if small else 'large'} {'FP32' if r.conv.dtype == 'c64' else 'FP64'}",
-                            []).append(lat)
-    pac.pac_queue_destroy(q)
+
+    def pct_of(v, p):
+        v = sorted(v)
+        return v[min(len(v) - 1, max(0, math.ceil(p / 100 * len(v)) - 1))]
+
+    def one_run():
+        q = pac.pac_queue_create(budget, max_inflight)
+        tickets, nbytes = [], 0
+        t0 = time.perf_counter()
+        for r in reqs:
+            c = r.conv
+            while time.perf_counter() - t0 < r.t_arrive:
+                pass
+            sk = (c.dims, c.dtype)
+            y = ybuf[sk][rr[sk] % K]
+            rr[sk] += 1
+            tickets.append(pac.pac_submit(q, plans[(c.dims, c.radix, c.dtype, r.filter_id)].handle, xbuf[sk], y))
+            nbytes += 3 * c.n_total * c.elem_bytes
+        pac.pac_queue_drain(q, 600000)
+        t_end = time.perf_counter()
+        lats, by_class = [], {}
+        for tk, r in zip(tickets, reqs):
+            st, lat = pac.pac_poll(q, tk)
+            lats.append(lat)
+            small = 2 * r.conv.n_total * r.conv.elem_bytes <= (8 << 20)  # the queue's small-request class
+            by_class.setdefault(f"{'small' if small else 'large'} {'FP32' if r.conv.dtype == 'c64' else 'FP64'}",
+                                []).append(lat)
+        pac.pac_queue_destroy(q)
+        span = t_end - t0
+        return {"p50_us": pct_of(lats, 50), "p99_us": pct_of(lats, 99), "mean_us": sum(lats) / len(lats),
+                "GBps": nbytes / span / 1e9, "span_s": span, "offered_GBps": nbytes / a.serve_seconds / 1e9,
+                "by_class": {k: {"n": len(v), "p50_us": pct_of(v, 50), "p99_us": pct_of(v, 99)}
+                             for k, v in sorted(by_class.items())}}
+
+    runs = [one_run() for _ in range(max(1, a.serve_repeats))]
     for p in plans.values():
         p.close()
-    lats.sort()
 
-    def pct(p):
-        return lats[min(len(lats) - 1, int(math.ceil(p / 100 * len(lats))) - 1)]
+    def spread(vals):
+        med = statistics.median(vals)
+        return {"median": med, "min": min(vals), "max": max(vals),
+                "max_rel_dev": max(abs(v - med) for v in vals) / med if med else 0.0}
 
-    span = t_end - t0
-
-    def pcts(v):
-        v = sorted(v)
-        return {"n": len(v), "p50_us": v[min(len(v) - 1, max(0, math.ceil(0.5 * len(v)) - 1))],
-                "p99_us": v[min(len(v) - 1, max(0, math.ceil(0.99 * len(v)) - 1))]}
+    classes = sorted({k for r in runs for k in r["by_class"]})
     out = {"workload": f"Poisson {len(reqs) / a.serve_seconds:.0f} req/s for {a.serve_seconds:g} s: 1-D/2-D/3-D, "
                        "radix 2/3, 70% FP32 / 30% FP64, 32 resident filters",
-           "requests": len(reqs), "p50_us": pct(50), "p99_us": pct(99), "mean_us": sum(lats) / len(lats),
-           "value": nbytes / span / 1e9, "unit": "GB/s", "offered_GBps": nbytes / a.serve_seconds / 1e9,
-           "span_s": span, "max_inflight": max_inflight, "hbm_budget_bytes": budget, "plans": len(plans),
-           "by_class": {k: pcts(v) for k, v in sorted(by_class.items())},
-           "by_class_note": "small = at most 8 MiB of device bytes (2 N S): high-priority streams, reserved slots",
+           "requests": len(reqs), "repeats": len(runs),
+           "p50_us": statistics.median(r["p50_us"] for r in runs),
+           "p99_us": statistics.median(r["p99_us"] for r in runs),
+           "value": statistics.median(r["GBps"] for r in runs), "unit": "GB/s",
+           "offered_GBps": runs[0]["offered_GBps"],
+           "spread": {"p50_us": spread([r["p50_us"] for r in runs]), "p99_us": spread([r["p99_us"] for r in runs])},
+           "by_class": {k: {"p50_us": spread([r["by_class"][k]["p50_us"] for r in runs if k in r["by_class"]]),
+                            "p99_us": spread([r["by_class"][k]["p99_us"] for r in runs if k in r["by_class"]]),
+                            "n": runs[0]["by_class"].get(k, {}).get("n", 0)} for k in classes},
+           "runs": [{k: v for k, v in r.items() if k != "by_class"} for r in runs],
+           "max_inflight": max_inflight, "hbm_budget_bytes": budget, "plans": len(plans),
+           "by_class_note": "small = at most 8 MiB of device bytes (2 N S): high-priority streams, reserved slots; "
+                            "at most two large FP64 requests run at once",
+           "note": f"the same seeded request stream served {len(runs)} times; medians over the runs, "
+                   "max_rel_dev = largest deviation of a run from the median, relative",
            "setup_s": setup_s}
     torch.cuda.empty_cache()
     return out

@@ -191,8 +191,12 @@ int pac_pfa_plan(pac_pfa p, pac_plan* inner);
  * A request queue with continuous batching.  Requests (plan, x_dev, y_dev)
  * are admitted in arrival order while (a) fewer than max_inflight are
  * running and (b) the device bytes of running requests (2 * N * elem size
- * each) stay within hbm_budget_bytes and cudaMemGetInfo's free memory; a
- * request that does not fit waits (it is never dropped).  Admitted requests
+ * each) stay within the admission budget: hbm_budget_bytes, or the device
+ * memory cudaMemGetInfo reports free when the queue is created if that is
+ * less (a request larger than the budget runs alone); a request that does
+ * not fit waits (it is never dropped).  At most two large complex FP64
+ * requests (FP64-pipe bound, milliseconds each) run at once
+ * (PAC_QUEUE_FP64_LARGE in the environment overrides).  Admitted requests
  * run on a pool of streams so their kernels overlap on the device.  Plans
  * and spectra stay resident; the queue does not own them.  Requests of at
  * most 8 MiB of device bytes are "small": they run on high-priority streams
@@ -353,8 +357,7 @@ enum {
                                      (1: a bounded grid-barrier wait gave up) */
     PAC_Q_GROUPS = 9,             /* stage groups (one pass each) over all axes */
     PAC_Q_PLANE = 10,             /* CTAs per plane of the plane pass, 0 when the plan has none */
-    PAC_Q_GROUP_CAP = 11,         /* the schedule's group-exponent cap (0: none) */
-    PAC_Q_TMA_GROUPS = 12         /* groups whose passes run in the TMA-fed lines kernel */
+    PAC_Q_GROUP_CAP = 11          /* the schedule's group-exponent cap (0: none) */
 };
 
 /*

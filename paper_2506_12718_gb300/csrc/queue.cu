@@ -14,7 +14,11 @@
 // block scheduler starts their CTAs before those of large requests as SMs
 // free up) and a quarter of the slots is kept for them, so a burst of large
 // requests cannot hold every slot while small ones wait; within each class
-// admission stays in arrival order.
+// admission stays in arrival order.  Large complex FP64 requests are bound by
+// the FP64 pipe (on GB300 a fraction of the FP32 rate) and take milliseconds
+// each: at most two of them run at once (PAC_QUEUE_FP64_LARGE overrides), so
+// that a burst of them cannot fill the SMs for long stretches while smaller
+// requests wait behind their CTAs.
 //
 // Fault injection (host side only, no device fault): the environment
 // variable PAC_FAULT=launch:K makes the K-th admitted request (1-based) fail
@@ -52,6 +56,7 @@ struct Request {
     int status = PAC_PENDING;
     int slot = -1;
     bool small = false;
+    bool fp64 = false;
     std::atomic<bool> gpu_done{false};
     pac_queue owner = nullptr;
 };
@@ -69,6 +74,8 @@ struct pac_queue_s {
     std::deque<Request*> waiting_small;  // small requests, arrival order
     std::vector<Request*> running;
     int running_large = 0;
+    int running_large_fp64 = 0;
+    int max_large_fp64 = 2;              // large complex FP64 requests running at once
     int reserve_small = 1;               // slots large requests may not take
     std::vector<int> slot_small;         // slot's stream has high priority
     std::unordered_map<uint64_t, Request*> by_ticket;
@@ -100,6 +107,7 @@ static void CUDART_CB on_request_done(void* arg) {
 static bool fits(pac_queue q, const Request* r) {
     if ((int)q->running.size() >= q->max_inflight) return false;
     if (!r->small && q->running_large >= q->max_inflight - q->reserve_small) return false;
+    if (!r->small && r->fp64 && q->running_large_fp64 >= q->max_large_fp64) return false;
     if (q->running.empty()) return true;
     return q->running_bytes + r->bytes <= q->budget;
 }
@@ -127,6 +135,7 @@ static void scheduler(pac_queue q) {
                 r->status = PAC_OK;
                 q->running_bytes -= r->bytes;
                 if (!r->small) --q->running_large;
+                if (!r->small && r->fp64) --q->running_large_fp64;
                 q->slot_busy[r->slot] = 0;
                 q->running[i] = q->running.back();
                 q->running.pop_back();
@@ -168,6 +177,7 @@ static void scheduler(pac_queue q) {
             q->slot_busy[slot] = 1;
             q->running_bytes += r->bytes;
             if (!r->small) ++q->running_large;
+            if (!r->small && r->fp64) ++q->running_large_fp64;
             q->running.push_back(r);
             progress = true;
         }
@@ -191,6 +201,13 @@ extern "C" int pac_queue_create(size_t hbm_budget_bytes, int max_inflight, pac_q
         delete q;
         return cuda_fail(e, "cudaGetDevice");
     }
+    size_t free_b = 0, total_b = 0;  // the admission budget is at most the device memory free now
+    e = cudaMemGetInfo(&free_b, &total_b);
+    if (e != cudaSuccess) {
+        delete q;
+        return cuda_fail(e, "cudaMemGetInfo");
+    }
+    if (free_b < q->budget) q->budget = free_b;
     q->streams.resize(max_inflight);
     q->slot_busy.assign(max_inflight, 0);
     q->reserve_small = max_inflight >= 4 ? max_inflight / 4 : (max_inflight > 1 ? 1 : 0);
@@ -205,6 +222,10 @@ extern "C" int pac_queue_create(size_t hbm_budget_bytes, int max_inflight, pac_q
             delete q;
             return cuda_fail(e, "cudaStreamCreate");
         }
+    }
+    if (const char* f = std::getenv("PAC_QUEUE_FP64_LARGE")) {
+        const int v = std::atoi(f);
+        if (v >= 1) q->max_large_fp64 = v;
     }
     if (const char* f = std::getenv("PAC_FAULT")) {
         if (std::strncmp(f, "launch:", 7) == 0) q->fault_launch = std::atoll(f + 7);
@@ -224,6 +245,7 @@ extern "C" int pac_submit(pac_queue q, pac_plan p, const void* x_dev, void* y_de
     r->y = y_dev;
     r->bytes = 2 * (size_t)p->bytes();
     r->small = r->bytes <= kSmallBytes;
+    r->fp64 = p->dtype == PAC_C128;
     r->owner = q;
     r->t_submit = Clock::now();
     {
