@@ -728,7 +728,8 @@ def prime_factor_entry(a, torch, pac, pin, dev, stream, flush, peak):
 def batched_leg(a, torch, pac, pin, dev, stream, flush):
     """4096 independent complex FP32 convolutions, sizes from 20 classes
     (1-D 2^8..2^16 and 3^5..3^10, 2-D (2^6..2^10)^2), 64 filter ids, in one
-    pac_convolve_many call (merged launches, replayed as a CUDA graph).
+    pac_convolve_many call (one persistent launch replayed as a CUDA graph),
+    next to the merged-launch form (one launch per level and shape).
     Inputs are drawn on the device from seeded generators (x: re, im
     N(0,1); filters: re, im U[-1,1] per filter id and shape)."""
     insts = pin.c4_instances(a.batch)
@@ -761,6 +762,15 @@ def batched_leg(a, torch, pac, pin, dev, stream, flush):
     ms = time_steps(torch, lambda: pac.pac_convolve_many(handles, xs, ys, sh), steps, max(3, a.warmup // 3),
                     flush, stream)
     t = sum(ms) / steps
+    # the merged-launch form of the same batch (one launch per level and shape, a captured graph)
+    os.environ["PAC_BATCH"] = "graph"
+    try:
+        launches_g = pac.pac_convolve_many_launches(handles)
+        msg = time_steps(torch, lambda: pac.pac_convolve_many(handles, xs, ys, sh), steps, max(3, a.warmup // 3),
+                         flush, stream)
+    finally:
+        os.environ.pop("PAC_BATCH", None)
+    tg = sum(msg) / steps
     # the same instances one call each (no merging, no graph), for comparison
     ms1 = time_steps(torch, lambda: [pac.pac_convolve(hd, x, y, sh) for hd, x, y in zip(handles, xs, ys)],
                      3, 1, flush, stream)
@@ -768,6 +778,8 @@ def batched_leg(a, torch, pac, pin, dev, stream, flush):
     out = {"workload": f"{len(insts)} complex FP32 convolutions, 20 size classes, 64 filter ids",
            "value": total / (t * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": t, "bytes_per_step": total,
            "launches_per_step": launches, "plans": len(plans),
+           "form": "one persistent launch (graph of one kernel)" if launches == 1 else "merged launches per level",
+           "merged_launches": {"value": total / (tg * 1e-3) / 1e9, "ms_per_step": tg, "launches_per_step": launches_g},
            "one_call_each": {"value": total / (t1 * 1e-3) / 1e9, "ms_per_step": t1},
            "setup_s": setup_s, "inputs": "device-generated, seeded (torch Philox)",
            "schedules": "autotuned per size class" if not a.no_tune else "default"}

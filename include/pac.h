@@ -297,6 +297,21 @@ int pac_convolve_timed(pac_plan p, int which, const void* x_dev, void* y_dev, vo
 int pac_test_barrier_timeout(pac_plan p, const void* x_dev, void* y_dev, void* stream, int spin_limit);
 
 /*
+ * Test hook of the persistent batched kernel's bounded waits (no
+ * counterpart in the paper): runs the batch as one launch of the persistent
+ * kernel (as pac_convolve_many does), with every pass' wait for the pass
+ * before it in its instance set one finished tile beyond what that pass has,
+ * and each wait limited to about wait_us microseconds (1 .. 10^6).  Every
+ * such wait runs out: the unit records 1 in the device error word (read and
+ * cleared by pac_plan_query(PAC_Q_DEVICE_ERROR)) and goes on, so the launch
+ * ends and the device stays usable; y receives passes run out of order, not
+ * the convolutions.  Synchronises `stream`.  PAC_ERR_ARG when the batch has
+ * no form of the persistent kernel or no instance of more than one pass.
+ */
+int pac_test_batch_timeout(int count, const pac_plan* plans, const void* const* x_dev, void* const* y_dev,
+                           void* stream, int wait_us);
+
+/*
  * Allocation-free form of pac_convolve_permuted, for callers that cannot
  * allocate device memory: processes whose GPU memory is owned by another
  * allocator that reserved nearly all of it up front, services under a hard

@@ -73,6 +73,7 @@ _SIGS = {
                                ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "pac_reverse_table": (_i32, [_i32, ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "pac_test_barrier_timeout": (_i32, [_vp, _vp, _vp, _vp, _i32]),
+    "pac_test_batch_timeout": (_i32, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _i32]),
     "pac_plan_twiddles": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _i32, _i32, _i32, _vp,
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "pac_version": (ctypes.c_char_p, []),
@@ -240,6 +241,15 @@ def pac_convolve_many(plans, xs, ys, stream=None) -> None:
     X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
     Y = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
     _check(load().pac_convolve_many(n, P, X, Y, _stream(stream)))
+
+
+def pac_test_batch_timeout(plans, xs, ys, wait_us: int, stream=None) -> None:
+    """Test hook: the batch as one persistent launch whose dependency waits all run out."""
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*plans)
+    X = (ctypes.c_void_p * n)(*[_ptr(x) for x in xs])
+    Y = (ctypes.c_void_p * n)(*[_ptr(y) for y in ys])
+    _check(load().pac_test_batch_timeout(n, P, X, Y, _stream(stream), int(wait_us)))
 
 
 def pac_convolve_many_launches(plans) -> int:

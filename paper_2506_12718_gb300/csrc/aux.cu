@@ -10,22 +10,24 @@
 
 namespace pac {
 
-// out[i0,i1,i2] = in[t0[i0], t1[i1], t2[i2]] (* mul[i0,i1,i2]) (* scale); a null table is the identity
+// out[i0,i1,i2] = in[t0[i0], t1[i1], t2[i2]] (* mul[i0,i1,i2]) (* scale); a null table is the identity.
+// 32-bit index arithmetic (a plan keeps N < 2^31): a 64-bit division would
+// run on the FP64 pipe, which is narrow on this GPU.
 template <typename V>
-__global__ void permute_kernel(int64_t d0, int64_t d1, int64_t d2, const int64_t* __restrict__ t0,
+__global__ void permute_kernel(uint32_t d0, uint32_t d1, uint32_t d2, const int64_t* __restrict__ t0,
                                const int64_t* __restrict__ t1, const int64_t* __restrict__ t2, const V* src,
                                V* dst, const V* __restrict__ mul, typename Real<V>::T scale, int do_scale) {
-    const int64_t rows = d0 * d1;
-    for (int64_t row = blockIdx.y; row < rows; row += gridDim.y) {
-        const int64_t i0 = row / d1, i1 = row - (row / d1) * d1;
-        const int64_t s0 = t0 ? __ldg(t0 + i0) : i0;
-        const int64_t s1 = t1 ? __ldg(t1 + i1) : i1;
-        const V* srow = src + (s0 * d1 + s1) * d2;
-        V* drow = dst + row * d2;
-        for (int64_t i2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i2 < d2;
-             i2 += (int64_t)gridDim.x * blockDim.x) {
-            V v = srow[t2 ? __ldg(t2 + i2) : i2];
-            if (mul) v = cmul(v, __ldg(mul + row * d2 + i2));
+    const uint32_t rows = d0 * d1;
+    for (uint32_t row = blockIdx.y; row < rows; row += gridDim.y) {
+        const uint32_t i0 = row / d1, i1 = row - i0 * d1;
+        const uint32_t s0 = t0 ? (uint32_t)__ldg(t0 + i0) : i0;
+        const uint32_t s1 = t1 ? (uint32_t)__ldg(t1 + i1) : i1;
+        const V* srow = src + (size_t)(s0 * d1 + s1) * d2;
+        V* drow = dst + (size_t)row * d2;
+        const V* mrow = mul ? mul + (size_t)row * d2 : nullptr;
+        for (uint32_t i2 = blockIdx.x * blockDim.x + threadIdx.x; i2 < d2; i2 += gridDim.x * blockDim.x) {
+            V v = srow[t2 ? (uint32_t)__ldg(t2 + i2) : i2];
+            if (mrow) v = cmul(v, __ldg(mrow + i2));
             if (do_scale) v = cscale(v, scale);
             drow[i2] = v;
         }
@@ -120,11 +122,13 @@ cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64
     const int64_t gy = std::min<int64_t>(rows, 65535);
     dim3 grid((unsigned)gx, (unsigned)gy);
     if (esize == 8)
-        permute_kernel<float2><<<grid, threads, 0, s>>>(d[0], d[1], d[2], t[0], t[1], t[2], (const float2*)src,
-                                                         (float2*)dst, (const float2*)mul, (float)scale, scale != 1.0);
+        permute_kernel<float2><<<grid, threads, 0, s>>>((uint32_t)d[0], (uint32_t)d[1], (uint32_t)d[2], t[0], t[1],
+                                                         t[2], (const float2*)src, (float2*)dst, (const float2*)mul,
+                                                         (float)scale, scale != 1.0);
     else
-        permute_kernel<double2><<<grid, threads, 0, s>>>(d[0], d[1], d[2], t[0], t[1], t[2], (const double2*)src,
-                                                          (double2*)dst, (const double2*)mul, scale, scale != 1.0);
+        permute_kernel<double2><<<grid, threads, 0, s>>>((uint32_t)d[0], (uint32_t)d[1], (uint32_t)d[2], t[0], t[1],
+                                                          t[2], (const double2*)src, (double2*)dst,
+                                                          (const double2*)mul, scale, scale != 1.0);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 // the graph's pass arguments live in one device buffer owned by the cache
 // entry.  Destroying a plan drops every cached batch that uses it.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <list>
 #include <map>
@@ -21,9 +22,12 @@
 #include <tuple>
 
 #include "pac_internal.h"
+#include "persist.h"
 
 namespace pac {
 int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s);
+int persist_grid(int dev, int smem);
+cudaError_t launch_persist(const PersistArgs& A, int grid, int smem, cudaStream_t s);
 }
 
 using namespace pac;
@@ -44,11 +48,41 @@ struct MultiLaunch {
 struct BatchEntry {
     std::vector<const void*> key;  // plans, x and y pointers
     int device = 0;
+    bool persistent = false;       // the whole batch is one launch of the persistent kernel
     void* d_buf = nullptr;
     std::vector<std::vector<MultiLaunch>> levels;
+    PersistArgs pargs = {};        // persistent form: arguments (in d_buf), grid, shared memory
+    int pgrid = 0, psmem = 0;
     std::vector<int> pointwise;    // instances with N = 1 (no pass: a plain product)
     cudaGraphExec_t exec = nullptr;
 };
+
+// PAC_BATCH=graph in the environment keeps merged launches per level (a
+// captured graph of several launches) even where the persistent kernel
+// applies; PAC_BATCH=persistent (the default) uses the persistent kernel
+// whenever every pass of the batch has a shape it carries.
+bool persistent_wanted() {
+    const char* v = std::getenv("PAC_BATCH");
+    return !(v && std::strcmp(v, "graph") == 0);
+}
+
+// index in kPersistShapes of a step's shape (-1: the persistent kernel does not carry it)
+int persist_shape_of(pac_plan p, const Step& st) {
+    if (p->esize != 8) return -1;
+    if (st.mode == kPlane) {
+        if (p->plane_k != 1) return -1;
+        const int m1 = p->groups[p->plane_g1].M, m2 = p->groups[p->plane_g1 + 1].M;
+        for (int i = 0; i < kPersistShapeCount; ++i)
+            if (kPersistShapes[i].m2 == m2 && kPersistShapes[i].m == m1) return i;
+        return -1;
+    }
+    const GroupPlan& g = p->groups[st.group];
+    if (g.mix_nr > 0) return -1;
+    const int lines = g.C == 1 ? 1 : 0;
+    for (int i = 0; i < kPersistShapeCount; ++i)
+        if (kPersistShapes[i].m2 == 0 && kPersistShapes[i].m == g.M && kPersistShapes[i].lines == lines) return i;
+    return -1;
+}
 
 constexpr size_t kCacheEntries = 8;
 std::mutex g_mu;
@@ -152,6 +186,121 @@ int build_entry(int count, const pac_plan* plans, const void* const* x, void* co
     return PAC_OK;
 }
 
+// The persistent form of a batch: every pass of every instance as tiles of
+// one launch of the persistent kernel.  Returns 1 when the batch does not
+// qualify (an element type, group or plane the kernel does not carry, or an
+// instance whose quarter-unit pass would precede a whole-CTA pass: the
+// kernel runs all whole-CTA tiles before any quarter tile).
+constexpr long long kPersistWaitCycles = 4000000000LL;  // about two seconds
+
+int build_persistent(int count, const pac_plan* plans, const void* const* x, void* const* y, unsigned bias,
+                     long long wait_cycles, BatchEntry* e) {
+    struct Rec {
+        PersistPass pp;
+        int inst, level, tiles;
+        bool quarter;
+    };
+    std::vector<Rec> recs;
+    std::vector<std::vector<int>> of(count);  // per instance: its records in level order
+    for (int i = 0; i < count; ++i) {
+        if (plans[i]->groups.empty()) {  // N = 1: a plain product outside the launch
+            e->pointwise.push_back(i);
+            continue;
+        }
+        std::vector<Step> seq;
+        convolve_steps(plans[i], x[i], y[i], seq);
+        bool seen_quarter = false;
+        for (size_t l = 0; l < seq.size(); ++l) {
+            const Step& st = seq[l];
+            const int sh = persist_shape_of(plans[i], st);
+            if (sh < 0) return 1;
+            Rec r = {};
+            r.pp.shape = sh;
+            r.inst = i;
+            r.level = (int)l;
+            r.quarter = persist_quarter(sh);
+            if (!r.quarter && seen_quarter) return 1;
+            seen_quarter = seen_quarter || r.quarter;
+            if (st.mode == kPlane) {
+                r.pp.pa = make_plane(plans[i], st.src, st.dst);
+                r.tiles = (int)r.pp.pa.planes;
+            } else {
+                r.pp.pa.a1 = make_pass(plans[i], plans[i]->groups[st.group], st.mode, st.src, st.dst, st.scale);
+                r.tiles = (int)r.pp.pa.a1.tiles;
+            }
+            of[i].push_back((int)recs.size());
+            recs.push_back(r);
+        }
+    }
+    // order: whole-CTA passes by level, then quarter passes by level (instances in order within a level)
+    std::vector<int> order(recs.size());
+    for (size_t k = 0; k < recs.size(); ++k) order[k] = (int)k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (recs[a].quarter != recs[b].quarter) return !recs[a].quarter;
+        return recs[a].level < recs[b].level;
+    });
+    std::vector<int> pos(recs.size());
+    for (size_t k = 0; k < order.size(); ++k) pos[order[k]] = (int)k;
+    const int npass = (int)order.size();
+    int nfull = 0;
+    int smem_full = 0;
+    bool any_quarter = false;
+    std::vector<PersistPass> passes(npass);
+    std::vector<uint32_t> starts(npass + 1, 0);
+    int64_t acc = 0;
+    for (int k = 0; k < npass; ++k) {
+        const Rec& r = recs[order[k]];
+        PersistPass pp = r.pp;
+        pp.dep = -1;
+        pp.dep_tiles = 0;
+        if (r.level > 0) {
+            const int prev = of[r.inst][r.level - 1];
+            pp.dep = pos[prev];
+            pp.dep_tiles = (uint32_t)recs[prev].tiles;
+        }
+        passes[k] = pp;
+        starts[k] = (uint32_t)acc;
+        acc += r.tiles;
+        if (acc > 0x7fffffffLL) return 1;
+        if (!r.quarter) {
+            nfull = k + 1;
+            smem_full = std::max(smem_full, persist_smem(r.pp.shape));
+        } else {
+            any_quarter = true;
+        }
+    }
+    starts[npass] = (uint32_t)acc;
+    if (npass == 0) return 1;
+    const int smem = std::max(smem_full, any_quarter ? 4 * kPersistQuarterSmem : 0);
+    const int grid = persist_grid(e->device, smem);
+    if (grid <= 0) return 1;
+    // one device image: passes, tile starts, counters (zeroed; the kernel leaves them zeroed)
+    const size_t off_starts = align_up((size_t)npass * sizeof(PersistPass), 64);
+    const size_t off_ctr = align_up(off_starts + (size_t)(npass + 1) * sizeof(uint32_t), 128);
+    const size_t bytes = off_ctr + (size_t)(3 + npass) * sizeof(unsigned);
+    std::vector<unsigned char> blob(bytes, 0);
+    std::memcpy(blob.data(), passes.data(), (size_t)npass * sizeof(PersistPass));
+    std::memcpy(blob.data() + off_starts, starts.data(), (size_t)(npass + 1) * sizeof(uint32_t));
+    cudaError_t ce = cudaMalloc(&e->d_buf, bytes);
+    if (ce != cudaSuccess) return fail(PAC_ERR_NOMEM, "batch arguments: %s", cudaGetErrorString(ce));
+    ce = cudaMemcpy(e->d_buf, blob.data(), bytes, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_fail(ce, "copy batch arguments");
+    unsigned char* b = static_cast<unsigned char*>(e->d_buf);
+    PersistArgs& A = e->pargs;
+    A.passes = reinterpret_cast<const PersistPass*>(b);
+    A.starts = reinterpret_cast<const uint32_t*>(b + off_starts);
+    A.nfull = nfull;
+    A.npass = npass;
+    A.ctr = reinterpret_cast<unsigned*>(b + off_ctr);
+    if (int rc = device_error_word(e->device, &A.error)) return rc;
+    A.bias = bias;
+    A.wait_cycles = wait_cycles;
+    e->pgrid = grid;
+    e->psmem = smem;
+    e->persistent = true;
+    return PAC_OK;
+}
+
 cudaError_t enqueue_launch(const BatchEntry* e, const MultiLaunch& m, cudaStream_t s) {
     const unsigned char* b = static_cast<const unsigned char*>(e->d_buf);
     const uint32_t* starts = reinterpret_cast<const uint32_t*>(b + m.off_starts);
@@ -168,9 +317,24 @@ cudaError_t prepare_launch(const MultiLaunch& m, cudaStream_t s) {
     return launch_multi(m.esize, m.M, m.lines, nullptr, nullptr, 0, 0, s);
 }
 
-// Capture the batch's launches into a graph: per level a fork over the
-// level's launches (one stream each) and a join.
+// Capture the batch's launches into a graph: the one persistent launch, or
+// per level a fork over the level's launches (one stream each) and a join.
 int capture(BatchEntry* e) {
+    if (e->persistent) {
+        cudaStream_t st = nullptr;
+        cudaError_t ce = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        cudaGraph_t graph = nullptr;
+        if (ce == cudaSuccess) ce = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            const cudaError_t le = launch_persist(e->pargs, e->pgrid, e->psmem, st);
+            ce = cudaStreamEndCapture(st, &graph);
+            if (le != cudaSuccess) ce = le;
+        }
+        if (ce == cudaSuccess) ce = cudaGraphInstantiate(&e->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (st) cudaStreamDestroy(st);
+        return ce == cudaSuccess ? PAC_OK : cuda_fail(ce, "batch graph capture");
+    }
     size_t width = 1;
     for (const auto& lv : e->levels) width = std::max(width, lv.size());
     std::vector<cudaStream_t> st(width, nullptr);
@@ -249,12 +413,13 @@ extern "C" int pac_convolve_many(int count, const pac_plan* plans, const void* c
     if (count == 0) return PAC_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<const void*> key;
-    key.reserve(3 * (size_t)count);
+    key.reserve(3 * (size_t)count + 1);
     for (int i = 0; i < count; ++i) {
         key.push_back(plans[i]);
         key.push_back(x_dev[i]);
         key.push_back(y_dev[i]);
     }
+    key.push_back(reinterpret_cast<const void*>(uintptr_t(persistent_wanted() ? 1 : 2)));  // the batch form
     std::lock_guard<std::mutex> lk(g_mu);
     BatchEntry* e = nullptr;
     for (auto it = g_cache.begin(); it != g_cache.end(); ++it) {
@@ -269,7 +434,12 @@ extern "C" int pac_convolve_many(int count, const pac_plan* plans, const void* c
         if (!e) return fail(PAC_ERR_NOMEM, "host allocation failed");
         e->key = key;
         e->device = dev;
-        int rc = build_entry(count, plans, x_dev, y_dev, e);
+        int rc = 1;
+        if (persistent_wanted()) {
+            rc = build_persistent(count, plans, x_dev, y_dev, 0u, kPersistWaitCycles, e);
+            if (rc == 1) e->pointwise.clear();  // not applicable: merged launches instead
+        }
+        if (rc == 1) rc = build_entry(count, plans, x_dev, y_dev, e);
         if (rc == PAC_OK) rc = capture(e);
         if (rc != PAC_OK) {
             free_entry(e);
@@ -290,8 +460,36 @@ extern "C" int pac_convolve_many(int count, const pac_plan* plans, const void* c
     return PAC_OK;
 }
 
+// whether the persistent kernel carries every pass of the batch (host only; the
+// same rules as build_persistent)
+static bool persist_applies(int count, const pac_plan* plans) {
+    bool any = false;
+    for (int i = 0; i < count; ++i) {
+        if (plans[i]->groups.empty()) continue;
+        std::vector<Step> seq;
+        convolve_steps(plans[i], nullptr, nullptr, seq);
+        bool seen_quarter = false;
+        for (const Step& st : seq) {
+            const int sh = persist_shape_of(plans[i], st);
+            if (sh < 0) return false;
+            if (!persist_quarter(sh) && seen_quarter) return false;
+            seen_quarter = seen_quarter || persist_quarter(sh);
+            any = true;
+        }
+    }
+    return any;
+}
+
 extern "C" int pac_convolve_many_launches(int count, const pac_plan* plans, int* launches) {
     if (count < 0 || !launches || (count > 0 && !plans)) return fail(PAC_ERR_ARG, "bad arguments");
+    for (int i = 0; i < count; ++i)
+        if (!plans[i]) return fail(PAC_ERR_ARG, "null plan %d", i);
+    if (persistent_wanted() && persist_applies(count, plans)) {
+        int n = 1;
+        for (int i = 0; i < count; ++i) n += plans[i]->groups.empty() ? 1 : 0;
+        *launches = n;
+        return PAC_OK;
+    }
     std::vector<std::map<ShapeKey, int>> by_level;
     int pointwise = 0;
     for (int i = 0; i < count; ++i) {
@@ -311,3 +509,34 @@ extern "C" int pac_convolve_many_launches(int count, const pac_plan* plans, int*
     return PAC_OK;
 }
 
+
+extern "C" int pac_test_batch_timeout(int count, const pac_plan* plans, const void* const* x_dev, void* const* y_dev,
+                                      void* stream, int wait_us) {
+    if (count < 1 || !plans || !x_dev || !y_dev) return fail(PAC_ERR_ARG, "bad arguments");
+    if (wait_us < 1 || wait_us > 1000000) return fail(PAC_ERR_ARG, "wait_us %d not in [1, 10^6]", wait_us);
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i] || !x_dev[i] || !y_dev[i]) return fail(PAC_ERR_ARG, "null entry %d", i);
+        if (!plans[i]->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "instance %d: plan has no spectrum", i);
+    }
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGetDevice");
+    BatchEntry e;
+    e.device = dev;
+    // every dependency target one tile beyond what its pass has: each dependent wait runs out
+    int rc = build_persistent(count, plans, x_dev, y_dev, 1u, (long long)wait_us * 2070, &e);
+    if (rc == 1) rc = fail(PAC_ERR_ARG, "the batch has no form of the persistent kernel");
+    if (rc == PAC_OK) {
+        bool dep = false;
+        for (int i = 0; i < count; ++i) dep = dep || plans[i]->groups.size() > 1;
+        if (!dep) rc = fail(PAC_ERR_ARG, "no instance of the batch has a pass that waits for another");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (rc == PAC_OK) {
+        ce = launch_persist(e.pargs, e.pgrid, e.psmem, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        if (ce != cudaSuccess) rc = cuda_fail(ce, "persistent kernel");
+    }
+    if (e.d_buf) cudaFree(e.d_buf);
+    return rc;
+}

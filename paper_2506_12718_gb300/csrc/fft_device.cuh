@@ -214,11 +214,18 @@ template <typename V, int M, bool LINES = false> struct Shape {
 // KS > 1: the M rows are split over the KS CTAs of a thread-block cluster
 // (rows [k M/KS, (k+1) M/KS) in CTA k's buffer, reached through distributed
 // shared memory), and rounds synchronise the whole cluster.
-template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int KS_ = 1> struct Geo {
+// SPLIT: the CTA is several independent units of NT threads (the persistent
+// batched kernel), each running its own tile: task numbering uses the
+// thread's index within its unit, and rounds synchronise the unit with a
+// named barrier instead of the whole CTA.
+template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int KS_ = 1, bool SPLIT_ = false>
+struct Geo {
     using V = V_;
     static constexpr int M = M_, W = W_, NT = NT_, RS = RS_, WS = WS_, ES = (int)sizeof(V_), KS = KS_;
     static constexpr int NR = round_count(M_, ES);
     static constexpr bool PF = PF_;
+    static constexpr bool SPLIT = SPLIT_;
+    __device__ __forceinline__ static int tid() { return SPLIT_ ? (int)(threadIdx.x % NT_) : (int)threadIdx.x; }
 };
 // the pass kernels' geometry: a tile of W columns, buffer [row][w] of pitch
 // P; several CTAs per SM hide latency, so registers are not spent on prefetch
@@ -362,10 +369,20 @@ __device__ __forceinline__ void cluster_sync_all() {
                  "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
+// barrier of the NT-thread unit this thread belongs to (units of 256 threads
+// use named barriers 1-2, units of 128 threads 3-6; 0 is the CTA's)
+template <int NT> __device__ __forceinline__ void unit_sync() {
+    static_assert(NT == 128 || NT == 256, "units of 128 or 256 threads");
+    const unsigned id = (NT == 256 ? 1u : 3u) + threadIdx.x / NT;
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(NT) : "memory");
+}
+
 // synchronisation between two rounds of a geometry
 template <typename GEO> __device__ __forceinline__ void round_sync() {
     if constexpr (GEO::KS > 1)
         cluster_sync_all();
+    else if constexpr (GEO::SPLIT)
+        unit_sync<GEO::NT>();
     else
         __syncthreads();
 }
@@ -509,7 +526,7 @@ __device__ __forceinline__ void round_exec(const TileCtx<typename GEO::V>& c) {
         V pre[ITER][R];
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
-            const int tau = (int)threadIdx.x + it * GEO::NT;
+            const int tau = GEO::tid() + it * GEO::NT;
             if (tau < T::TASKS) {
                 const T t(tau);
                 const TaskCol col = task_col<LINES, M>(c, t.w);
@@ -521,7 +538,7 @@ __device__ __forceinline__ void round_exec(const TileCtx<typename GEO::V>& c) {
         }
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
-            const int tau = (int)threadIdx.x + it * GEO::NT;
+            const int tau = GEO::tid() + it * GEO::NT;
             if (tau < T::TASKS) {
                 const T t(tau);
                 const TaskCol col = task_col<LINES, M>(c, t.w);
@@ -544,7 +561,7 @@ __device__ __forceinline__ void round_exec(const TileCtx<typename GEO::V>& c) {
         }
     } else {
 #pragma unroll 1
-        for (int tau = threadIdx.x; tau < T::TASKS; tau += GEO::NT) {
+        for (int tau = GEO::tid(); tau < T::TASKS; tau += GEO::NT) {
             const T t(tau);
             const TaskCol col = task_col<LINES, M>(c, t.w);
             V v[R];
@@ -752,6 +769,17 @@ template <typename V, int M1, int M2, int K> struct PlaneShape {
     static_assert(M1 % K == 0 && M2 % K == 0, "the plane must split evenly");
 };
 
+// A plane geometry of NT threads (the persistent batched kernel: its
+// whole-CTA items, or with SPLIT its units of NT threads).
+template <typename V, int M1, int M2, int NT_, bool SPLIT = false> struct PlaneShapeNT {
+    static constexpr int ES = sizeof(V);
+    static constexpr int P2 = plane_pitch(M1, M2, ES);
+    static constexpr int NT = NT_;
+    static constexpr int SMEM = plane_smem_bytes(M1, M2, ES);
+    using G2 = Geo<V, M2, M1, NT, 1, P2, true, 1, SPLIT>;
+    using G1 = Geo<V, M1, M2, NT, P2, 1, true, 1, SPLIT>;
+};
+
 // forward rounds 0..NR-1, the first from global (natural rows), all results in shared memory
 template <typename GEO, bool LINES>
 __device__ __forceinline__ void fwd_all_to_smem(const TileCtx<typename GEO::V>& c) {
@@ -809,9 +837,10 @@ template <typename V> __device__ __forceinline__ uint32_t map_cluster(V* p, unsi
     return out;
 }
 
-template <typename V, int M1, int M2, int K>
+// PS: the plane geometry (PlaneShape, or a whole-CTA geometry of another
+// thread count for the persistent batched kernel)
+template <typename V, int M1, int M2, int K, typename PS = PlaneShape<V, M1, M2, K>>
 __device__ __forceinline__ void plane_run(const PlaneArgs& pa, uint32_t plane, unsigned rank, V* s) {
-    using PS = PlaneShape<V, M1, M2, K>;
     TileCtx<V> c2, c1;
     ctx_init(c2, pa.a2, s);
     c2.t = plane;

@@ -89,6 +89,8 @@ void batch_forget_plan(pac_plan p);
 // Barrier counters of single-launch convolutions: a device pool of slots,
 // handed out round robin; *base receives the slot's counter value at launch.
 int barrier_slot(int device, unsigned** counter, unsigned* base, unsigned arrivals, unsigned** error);
+// The library's device error word (created with the barrier pool), for kernels that report a wait that gave up.
+int device_error_word(int device, unsigned** error);
 // Device error word of the library (barrier timeouts); returns and clears it.
 int take_device_error(int device, unsigned* value);
 

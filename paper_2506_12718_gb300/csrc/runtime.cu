@@ -56,6 +56,15 @@ int barrier_slot(int device, unsigned** counter, unsigned* base, unsigned arriva
     return PAC_OK;
 }
 
+int device_error_word(int device, unsigned** error) {
+    if (device < 0 || device >= 64) return fail(PAC_ERR_ARG, "device %d out of range", device);
+    Pool& P = g_pool[device];
+    std::lock_guard<std::mutex> lk(P.mu);
+    if (int rc = ensure_pool(device, P)) return rc;
+    *error = P.d + (size_t)kSlots * kStride;
+    return PAC_OK;
+}
+
 int take_device_error(int device, unsigned* value) {
     *value = 0;
     if (device < 0 || device >= 64) return fail(PAC_ERR_ARG, "device %d out of range", device);

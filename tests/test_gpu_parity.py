@@ -1023,3 +1023,85 @@ def test_bounded_barrier_wait_runs_out_and_reports(dtype):
     tol = 1e-12 if dtype == "c128" else 1e-5 * math.log2(np.prod(dims))
     assert err <= tol, f"after a timed-out launch: rel_l2 {err:.3e} > {tol:.1e}"
 
+
+
+PERSIST_CASES = [((4096,), 2, 1), ((27, 81), 3, 2), ((64, 64), 8, 3), ((3125,), 5, 4), ((32, 32, 32), 4, 5),
+                 ((128, 128), 2, 6), ((1 << 16,), 2, 7), ((2187,), 3, 8), ((1024, 1024), 2, 9), ((729, 9), 3, 10)]
+
+
+def test_persistent_batch_is_one_launch_and_matches_the_merged_form(monkeypatch):
+    """A batch whose passes all have shapes the persistent kernel carries runs
+    as one launch (replayed from a graph): every instance matches the oracle,
+    the same batch in the merged-launch form (PAC_BATCH=graph) to rounding,
+    and a second call (the replay, counters reset by the kernel) gives the
+    same result bit for bit."""
+    pac = pac_mod()
+    plans, xs, refs = [], [], []
+    try:
+        for dims, radix, seed in PERSIST_CASES:
+            fs, h, x = separable_case(dims, "c64", seed)
+            p = pac.Plan(dims, radix, "c64")
+            p.filter_spectrum(dev(h))
+            plans.append(p)
+            xs.append(dev(x))
+            refs.append(oracle.conv_separable(fs, x))
+        handles = [p.handle for p in plans] * 2
+        xs2 = xs * 2
+        assert pac.pac_convolve_many_launches(handles) == 1
+        ys = [torch.full_like(x, float("nan")) for x in xs2]
+        pac.pac_convolve_many(handles, xs2, ys)
+        torch.cuda.synchronize()
+        first = [y.cpu().numpy() for y in ys]
+        pac.pac_convolve_many(handles, xs2, ys)  # replay
+        torch.cuda.synchronize()
+        for k, y in enumerate(ys):
+            assert np.array_equal(y.cpu().numpy(), first[k])
+        monkeypatch.setenv("PAC_BATCH", "graph")
+        assert pac.pac_convolve_many_launches(handles) > 1
+        yg = [torch.empty_like(x) for x in xs2]
+        pac.pac_convolve_many(handles, xs2, yg)
+        torch.cuda.synchronize()
+        monkeypatch.delenv("PAC_BATCH")
+        for k in range(len(handles)):
+            dims = PERSIST_CASES[k % len(PERSIST_CASES)][0]
+            n = int(np.prod(dims))
+            check(first[k], refs[k % len(PERSIST_CASES)], "c64", n, f"persistent {dims}")
+            assert oracle.rel_l2(first[k], yg[k].cpu().numpy()) <= tol("c64", n)
+        assert plans[0].query(pac.Q_DEVICE_ERROR) == 0
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_persistent_batch_bounded_wait_runs_out_and_reports():
+    """The persistent kernel's dependency waits are bounded: with every
+    target one tile beyond what the pass before has and a limit of about
+    200 us, each dependent wait runs out; the launch ends, the device error
+    word reads 1 (then 0), and the next ordinary batch matches the oracle."""
+    pac = pac_mod()
+    cases = [((1 << 16,), 2, 21), ((32, 32, 32), 4, 22), ((27, 81), 3, 23)]
+    plans, xs, refs = [], [], []
+    try:
+        for dims, radix, seed in cases:
+            fs, h, x = separable_case(dims, "c64", seed)
+            p = pac.Plan(dims, radix, "c64")
+            p.filter_spectrum(dev(h))
+            plans.append(p)
+            xs.append(dev(x))
+            refs.append(oracle.conv_separable(fs, x))
+        handles = [p.handle for p in plans]
+        ys = [torch.empty_like(x) for x in xs]
+        assert plans[0].query(pac.Q_DEVICE_ERROR) == 0
+        t0 = time.perf_counter()
+        pac.pac_test_batch_timeout(handles, xs, ys, 200)
+        assert time.perf_counter() - t0 < 30.0
+        assert plans[0].query(pac.Q_DEVICE_ERROR) == 1
+        assert plans[0].query(pac.Q_DEVICE_ERROR) == 0
+        pac.pac_convolve_many(handles, xs, ys)
+        torch.cuda.synchronize()
+        for y, ref, (dims, _, _) in zip(ys, refs, cases):
+            check(y.cpu().numpy(), ref, "c64", int(np.prod(dims)), f"after timeouts {dims}")
+        assert plans[0].query(pac.Q_DEVICE_ERROR) == 0
+    finally:
+        for p in plans:
+            p.close()
