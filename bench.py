@@ -63,11 +63,12 @@ def parse_args(argv=None):
     ap.add_argument("--workload", choices=["conv3d", "conv2d-r3", "conv2d-r5", "conv1d"], default="conv2d-r5",
                     help="the main leg's problem (default: the 2-D 3125^2 radix-5 workload)")
     ap.add_argument("--quick", action="store_true", help="main leg only (for profiler runs)")
-    ap.add_argument("--profile-path", choices=["none", "permuted", "single", "mixed", "pfa"], default="none",
+    ap.add_argument("--profile-path", choices=["none", "permuted", "single", "mixed", "pfa", "batched"], default="none",
                     help="profiler runs: time one other path instead of the main line and print its times "
                          "(permuted: the comparator on the main workload; single: the one-launch cooperative "
                          "form of 3-D 128^3 FP32 radix 4; mixed: 2-D 1000^2 FP32 with groups spanning prime "
-                         "bases; pfa: the prime factor form of 1-D 2^10 3^5 5^3 FP32)")
+                         "bases; pfa: the prime factor form of 1-D 2^10 3^5 5^3 FP32; batched: --batch instances of "
+                         "the batched workload in one pac_convolve_many call)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline and the oracle checks")
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--legs", default="configs,batched,served",  # "none": the main leg only
@@ -903,6 +904,25 @@ def profile_path_leg(a, torch, pac, pin, dev):
     launch lists and captures of its kernels); prints one JSON line of times."""
     stream = torch.cuda.Stream(device=dev)
     sh = stream.cuda_stream
+    if a.profile_path == "batched":
+        insts = pin.c4_instances(a.batch)
+        plans, handles, xs, ys = {}, [], [], []
+        for c in insts:
+            key = (c.dims, c.radix, c.h_seed)
+            if key not in plans:
+                p = pac.Plan(c.dims, c.radix, "c64")
+                p.filter_spectrum(torch.from_numpy(pin.make_h(c)[0]).to(dev))
+                plans[key] = p
+            handles.append(plans[key].handle)
+            xs.append(torch.from_numpy(pin.make_x(c)).to(dev))
+            ys.append(torch.empty_like(xs[-1]))
+        ms = time_steps(torch, lambda: pac.pac_convolve_many(handles, xs, ys, sh), a.steps, a.warmup, lambda: None,
+                        stream)
+        print(json.dumps({"profile_path": "batched", "instances": len(insts),
+                          "launches_per_call": pac.pac_convolve_many_launches(handles), "ms": ms}), flush=True)
+        for p in plans.values():
+            p.close()
+        return 0
     env = {}
     if a.profile_path == "permuted":
         c = workload_conv(a, pin)

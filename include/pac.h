@@ -134,18 +134,27 @@ int pac_convolve_host(pac_plan p, const void* x_host, void* y_host, void* stream
 
 /*
  * Many independent convolutions in one call: plans[i] applied to x_dev[i] ->
- * y_dev[i] for i < count.  Work of all instances is merged into one launch
- * per pass level (instances grouped by kernel shape), so a batch of any mix
- * of shapes costs a handful of launches; the launch sequence is recorded once
- * per distinct batch and replayed as a CUDA graph.  Plans may repeat.  Each
- * plan needs its spectrum.  Asynchronous on `stream`.
+ * y_dev[i] for i < count (the batching pattern; the paper has one
+ * convolution per call).  When every plan is complex FP32 and every pass has
+ * a shape the persistent kernel carries (one-base groups up to 4096 / 2187 /
+ * 3125 points, square planes), the whole batch is ONE launch of a persistent
+ * kernel: resident CTAs pull the tiles of all instances' passes from a
+ * device work list, and each pass of an instance waits (bounded, on device
+ * counters) for the pass before it.  Otherwise (or with PAC_BATCH=graph in
+ * the environment) the work is merged into one launch per pass level and
+ * kernel shape.  Either way the launch sequence is recorded once per
+ * distinct batch (plans, x and y pointers) and replayed as a CUDA graph.
+ * Plans may repeat.  Each plan needs its spectrum.  Asynchronous on
+ * `stream`; calls for the same batch must not overlap on the device (the
+ * persistent form keeps its work counters per batch).
  */
 int pac_convolve_many(int count, const pac_plan* plans, const void* const* x_dev, void* const* y_dev,
                       void* stream);
 
 /*
- * Kernel launches one pac_convolve_many call over these plans makes (the
- * merged launches of its captured graph, plus one per N = 1 plan).  Host
+ * Kernel launches one pac_convolve_many call over these plans makes (1 for
+ * the persistent form, else the merged launches of its captured graph; plus
+ * one per N = 1 plan).  Host
  * only; no device work.
  */
 int pac_convolve_many_launches(int count, const pac_plan* plans, int* launches);

@@ -276,11 +276,15 @@ int build_persistent(int count, const pac_plan* plans, const void* const* x, voi
     if (grid <= 0) return 1;
     // one device image: passes, tile starts, counters (zeroed; the kernel leaves them zeroed)
     const size_t off_starts = align_up((size_t)npass * sizeof(PersistPass), 64);
-    const size_t off_ctr = align_up(off_starts + (size_t)(npass + 1) * sizeof(uint32_t), 128);
+    const size_t off_pass_of = align_up(off_starts + (size_t)(npass + 1) * sizeof(uint32_t), 64);
+    const size_t off_ctr = align_up(off_pass_of + (size_t)acc * sizeof(uint32_t), 128);
     const size_t bytes = off_ctr + (size_t)(3 + npass) * sizeof(unsigned);
     std::vector<unsigned char> blob(bytes, 0);
     std::memcpy(blob.data(), passes.data(), (size_t)npass * sizeof(PersistPass));
     std::memcpy(blob.data() + off_starts, starts.data(), (size_t)(npass + 1) * sizeof(uint32_t));
+    uint32_t* po = reinterpret_cast<uint32_t*>(blob.data() + off_pass_of);  // tile -> pass, one load per tile
+    for (int k = 0; k < npass; ++k)
+        for (uint32_t g = starts[k]; g < starts[k + 1]; ++g) po[g] = (uint32_t)k;
     cudaError_t ce = cudaMalloc(&e->d_buf, bytes);
     if (ce != cudaSuccess) return fail(PAC_ERR_NOMEM, "batch arguments: %s", cudaGetErrorString(ce));
     ce = cudaMemcpy(e->d_buf, blob.data(), bytes, cudaMemcpyHostToDevice);
@@ -289,6 +293,7 @@ int build_persistent(int count, const pac_plan* plans, const void* const* x, voi
     PersistArgs& A = e->pargs;
     A.passes = reinterpret_cast<const PersistPass*>(b);
     A.starts = reinterpret_cast<const uint32_t*>(b + off_starts);
+    A.pass_of = reinterpret_cast<const uint32_t*>(b + off_pass_of);
     A.nfull = nfull;
     A.npass = npass;
     A.ctr = reinterpret_cast<unsigned*>(b + off_ctr);

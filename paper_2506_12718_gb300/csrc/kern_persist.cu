@@ -9,10 +9,12 @@
 // with its own named barrier.  Within each list the passes are in level
 // order.  A tile of pass p may start only when every tile of the pass before
 // it in the same instance is done: per-pass counters of finished tiles,
-// incremented after a tile's stores (fence, then atomic add) and read with
+// incremented after a tile's stores (a release-ordered add) and read with
 // acquire loads by the unit's first thread before it starts.  Because tiles
-// are handed out in level order and a unit holding a tile keeps running, a
-// wait only ever depends on tiles held by running units, so it ends; it is
+// are handed out in level order and a unit takes its tiles in the order it
+// got them (it fetches the next index while it runs the current tile), a
+// wait only ever depends on tiles handed out earlier to running units, so it
+// ends; it is
 // still bounded (wait_cycles), after which the unit records 1 in the
 // library's device error word and goes on.  The last CTA to finish resets
 // the counters, so the same launch can be replayed (a captured graph).
@@ -26,22 +28,16 @@ namespace pac {
 
 namespace {
 
+// completion of a tile: one release-ordered add (the unit's stores, ordered by
+// the unit's barrier before it, are visible to whoever acquires the count)
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
-}
-
-// the pass holding global tile g among passes [lo, hi] (starts ascending)
-__device__ __forceinline__ int find_pass(const uint32_t* starts, int lo, int hi, uint32_t g) {
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(starts + mid) <= g)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
 }
 
 // wait (first thread of the unit) until pass p's dependency is complete
@@ -126,50 +122,55 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const __gri
     float2* s = reinterpret_cast<float2*>(smem_raw);
     __shared__ uint32_t s_item[4];
     __shared__ int s_last;
-    // whole-CTA items
+    // whole-CTA items; the next index is fetched while the current item runs
+    // (items are still taken in order, so every wait is on an earlier item)
     const uint32_t nfull_tiles = __ldg(A.starts + A.nfull);
+    uint32_t next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(A.ctr + 0, 1u);
     for (;;) {
-        if (threadIdx.x == 0) s_item[0] = atomicAdd(A.ctr + 0, 1u);
+        if (threadIdx.x == 0) s_item[0] = next;
         __syncthreads();
         const uint32_t g = s_item[0];
         if (g >= nfull_tiles) break;
-        const int p = find_pass(A.starts, 0, A.nfull - 1, g);
+        if (threadIdx.x == 0) next = atomicAdd(A.ctr + 0, 1u);
+        const int p = (int)__ldg(A.pass_of + g);
         const PersistPass& pp = A.passes[p];
         if (threadIdx.x == 0) wait_dep(A, pp);
         __syncthreads();
         run_shape<false>(pp.shape, pp, g - __ldg(A.starts + p), s);
-        __syncthreads();  // the tile's stores, and the next item's s_item write after every read
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicAdd(A.ctr + 3 + p, 1u);
-        }
+        __syncthreads();  // the tile's stores, and every read of s_item before the next write
+        if (threadIdx.x == 0) red_release_add(A.ctr + 3 + p, 1u);
     }
+    __syncthreads();  // every thread has read the last whole-CTA index before the units reuse s_item
     // quarter units
     if (A.npass > A.nfull) {
         const int unit = (int)(threadIdx.x / kPersistUnit);
         const bool lead = threadIdx.x % kPersistUnit == 0;
         float2* su = s + (size_t)unit * (kPersistQuarterSmem / sizeof(float2));
         const uint32_t q0 = __ldg(A.starts + A.nfull), qend = __ldg(A.starts + A.npass);
+        uint32_t qnext = 0;
+        if (lead) qnext = q0 + atomicAdd(A.ctr + 1, 1u);
         for (;;) {
-            if (lead) s_item[unit] = q0 + atomicAdd(A.ctr + 1, 1u);
+            if (lead) s_item[unit] = qnext;
             unit_sync<kPersistUnit>();
             const uint32_t g = s_item[unit];
             if (g >= qend) break;
-            const int p = find_pass(A.starts, A.nfull, A.npass - 1, g);
+            if (lead) qnext = q0 + atomicAdd(A.ctr + 1, 1u);
+            const int p = (int)__ldg(A.pass_of + g);
             const PersistPass& pp = A.passes[p];
             if (lead) wait_dep(A, pp);
             unit_sync<kPersistUnit>();
             run_shape<true>(pp.shape, pp, g - __ldg(A.starts + p), su);
             unit_sync<kPersistUnit>();
-            if (lead) {
-                __threadfence();
-                atomicAdd(A.ctr + 3 + p, 1u);
-            }
+            if (lead) red_release_add(A.ctr + 3 + p, 1u);
         }
     }
     // the last CTA out resets the counters for the next launch
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(A.ctr + 2, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) {
+        __threadfence();  // this CTA's completion adds are performed before it counts itself out
+        s_last = atomicAdd(A.ctr + 2, 1u) == gridDim.x - 1;
+    }
     __syncthreads();
     if (s_last) {
         __threadfence();

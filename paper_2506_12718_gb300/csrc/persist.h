@@ -54,6 +54,7 @@ struct PersistPass {
 struct PersistArgs {
     const PersistPass* passes;
     const uint32_t* starts;  // [npass + 1]: first global tile of each pass (full tiles, then quarter tiles)
+    const uint32_t* pass_of; // [starts[npass]]: the pass of each global tile
     int nfull, npass;
     unsigned* ctr;           // [0] next full tile, [1] next quarter tile, [2] CTAs done, [3 + p] tiles done of pass p
     unsigned* error;         // device error word: 1 when a dependency wait gave up
