@@ -232,12 +232,14 @@ int build_persistent(int count, const pac_plan* plans, const void* const* x, voi
             recs.push_back(r);
         }
     }
-    // order: whole-CTA passes by level, then quarter passes by level (instances in order within a level)
+    // order: whole-CTA passes by level, then quarter passes by level; within a level passes of one
+    // shape together (units that take neighbouring tiles then run the same code), instances in order
     std::vector<int> order(recs.size());
     for (size_t k = 0; k < recs.size(); ++k) order[k] = (int)k;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         if (recs[a].quarter != recs[b].quarter) return !recs[a].quarter;
-        return recs[a].level < recs[b].level;
+        if (recs[a].level != recs[b].level) return recs[a].level < recs[b].level;
+        return recs[a].pp.shape < recs[b].pp.shape;
     });
     std::vector<int> pos(recs.size());
     for (size_t k = 0; k < order.size(); ++k) pos[order[k]] = (int)k;
@@ -271,7 +273,7 @@ int build_persistent(int count, const pac_plan* plans, const void* const* x, voi
     }
     starts[npass] = (uint32_t)acc;
     if (npass == 0) return 1;
-    const int smem = std::max(smem_full, any_quarter ? 4 * kPersistQuarterSmem : 0);
+    const int smem = std::max(smem_full, any_quarter ? kPersistUnits * kPersistQuarterSmem : 0);
     const int grid = persist_grid(e->device, smem);
     if (grid <= 0) return 1;
     // one device image: passes, tile starts, counters (zeroed; the kernel leaves them zeroed)

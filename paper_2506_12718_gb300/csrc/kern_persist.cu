@@ -85,7 +85,7 @@ __device__ __forceinline__ void group_tile(const PassArgs& a, uint32_t t, float2
 }
 
 template <int M, bool LINES, int NT, bool SPLIT>
-using PGeo = Geo<float2, M, tile_w(M, 8), NT, tile_pitch(M, 8, LINES), 1, SPLIT, 1, SPLIT>;
+using PGeo = Geo<float2, M, tile_w(M, 8), NT, tile_pitch(M, 8, LINES), 1, SPLIT && kPersistPrefetch, 1, SPLIT>;
 
 // one item of shape I, compiled as a function of its own (the kernel calls
 // it; keeping the shapes out of one inlined body bounds compile time)

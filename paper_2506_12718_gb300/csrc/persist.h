@@ -9,12 +9,17 @@
 namespace pac {
 
 // A CTA of the persistent kernel has kPersistThreads threads.  Items whose
-// tile or plane fits a quarter of the shared memory run in quarter units
-// (four independent units of kPersistUnit threads per CTA, each on its own
-// item); larger ones run on the whole CTA.
+// tile or plane fits a unit's share of the shared memory run in units
+// (kPersistUnits independent units of kPersistUnit threads per CTA, each on
+// its own item; "quarter" below for short); larger ones run on the whole
+// CTA.
 constexpr int kPersistThreads = 512;
 constexpr int kPersistUnit = 128;
-constexpr int kPersistQuarterSmem = 56 * 1024;
+constexpr int kPersistUnits = kPersistThreads / kPersistUnit;
+// shared memory of one unit: an equal share of what one CTA may take, in whole 128-byte lines
+constexpr int kPersistQuarterSmem = ((227 * 1024 - 1024) / kPersistUnits) / 128 * 128;
+// units of 256 threads match the pass kernels' own CTAs; smaller units load several tasks at once
+constexpr bool kPersistPrefetch = kPersistUnit < 256;
 
 // One shape the kernel carries: a one-base group pass of size m (rows or
 // lines) or, with m2 > 0, a plane pass of m x m2 (K = 1).  Complex FP32.
