@@ -56,6 +56,14 @@ __device__ __forceinline__ void wait_dep(const PersistArgs& A, const PersistPass
     }
 }
 
+// copy a pass record to shared memory with n threads (i = this thread's index among them)
+__device__ __forceinline__ void copy_pass(const PersistPass* src, PersistPass* dst, int i, int n) {
+    static_assert(sizeof(PersistPass) % 16 == 0, "whole 16-byte words");
+    const int4* s4 = reinterpret_cast<const int4*>(src);
+    int4* d4 = reinterpret_cast<int4*>(dst);
+    for (int k = i; k < (int)(sizeof(PersistPass) / 16); k += n) d4[k] = __ldg(s4 + k);
+}
+
 // one tile of a group pass with geometry GEO (GEO::tid() is the thread's index in its unit)
 template <typename GEO, bool LINES>
 __device__ __forceinline__ void group_tile(const PassArgs& a, uint32_t t, float2* s) {
@@ -87,10 +95,9 @@ __device__ __forceinline__ void group_tile(const PassArgs& a, uint32_t t, float2
 template <int M, bool LINES, int NT, bool SPLIT>
 using PGeo = Geo<float2, M, tile_w(M, 8), NT, tile_pitch(M, 8, LINES), 1, SPLIT && kPersistPrefetch, 1, SPLIT>;
 
-// one item of shape I, compiled as a function of its own (the kernel calls
-// it; keeping the shapes out of one inlined body bounds compile time)
+// one item of shape I
 template <int I>
-__device__ __noinline__ void shape_item(const PersistPass& pp, uint32_t t, float2* s) {
+__device__ __forceinline__ void shape_body(const PersistPass& pp, uint32_t t, float2* s) {
     constexpr PersistShape S = kPersistShapes[I];
     if constexpr (S.m2 > 0 && persist_quarter(I)) {
         plane_run<float2, S.m, S.m2, 1, PlaneShapeNT<float2, S.m, S.m2, kPersistUnit, true>>(pp.pa, t, 0u, s);
@@ -103,13 +110,29 @@ __device__ __noinline__ void shape_item(const PersistPass& pp, uint32_t t, float
     }
 }
 
+// Most shapes are compiled as functions of their own, which the kernel
+// calls (one inlined body of every shape takes minutes to compile); the
+// groups of 512 and 1024 points, the bulk of a batch of mixed sizes, are
+// inlined into the kernel (no call: no registers saved across it).
+constexpr bool persist_inlined(int i) {
+    return kPersistShapes[i].m2 == 0 && (kPersistShapes[i].m == 512 || kPersistShapes[i].m == 1024);
+}
+
+template <int I>
+__device__ __noinline__ void shape_item(const PersistPass& pp, uint32_t t, float2* s) {
+    shape_body<I>(pp, t, s);
+}
+
 // the item of shape `shape` (whole CTA when !QUARTER, a quarter unit otherwise)
 template <bool QUARTER, int I = 0>
 __device__ __forceinline__ void run_shape(int shape, const PersistPass& pp, uint32_t t, float2* s) {
     if constexpr (I < kPersistShapeCount) {
         if constexpr (persist_quarter(I) == QUARTER) {
             if (shape == I) {
-                shape_item<I>(pp, t, s);
+                if constexpr (persist_inlined(I))
+                    shape_body<I>(pp, t, s);
+                else
+                    shape_item<I>(pp, t, s);
                 return;
             }
         }
@@ -120,8 +143,11 @@ __device__ __forceinline__ void run_shape(int shape, const PersistPass& pp, uint
 __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const __grid_constant__ PersistArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float2* s = reinterpret_cast<float2*>(smem_raw);
-    __shared__ uint32_t s_item[4];
+    __shared__ uint32_t s_item[kPersistUnits];
     __shared__ int s_last;
+    // the current item's pass record, copied into shared memory by its unit (or the whole CTA), so
+    // that the tile code's many reads of its arguments hit shared memory, not a cold cache line
+    __shared__ __align__(16) PersistPass s_pp[kPersistUnits];
     // whole-CTA items; the next index is fetched while the current item runs
     // (items are still taken in order, so every wait is on an earlier item)
     const uint32_t nfull_tiles = __ldg(A.starts + A.nfull);
@@ -134,9 +160,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const __gri
         if (g >= nfull_tiles) break;
         if (threadIdx.x == 0) next = atomicAdd(A.ctr + 0, 1u);
         const int p = (int)__ldg(A.pass_of + g);
-        const PersistPass& pp = A.passes[p];
-        if (threadIdx.x == 0) wait_dep(A, pp);
+        copy_pass(A.passes + p, s_pp + 0, (int)threadIdx.x, kPersistThreads);
+        if (threadIdx.x == 0) wait_dep(A, A.passes[p]);
         __syncthreads();
+        const PersistPass& pp = s_pp[0];
         run_shape<false>(pp.shape, pp, g - __ldg(A.starts + p), s);
         __syncthreads();  // the tile's stores, and every read of s_item before the next write
         if (threadIdx.x == 0) red_release_add(A.ctr + 3 + p, 1u);
@@ -157,9 +184,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const __gri
             if (g >= qend) break;
             if (lead) qnext = q0 + atomicAdd(A.ctr + 1, 1u);
             const int p = (int)__ldg(A.pass_of + g);
-            const PersistPass& pp = A.passes[p];
-            if (lead) wait_dep(A, pp);
+            copy_pass(A.passes + p, s_pp + unit, (int)(threadIdx.x % kPersistUnit), kPersistUnit);
+            if (lead) wait_dep(A, A.passes[p]);
             unit_sync<kPersistUnit>();
+            const PersistPass& pp = s_pp[unit];
             run_shape<true>(pp.shape, pp, g - __ldg(A.starts + p), su);
             unit_sync<kPersistUnit>();
             if (lead) red_release_add(A.ctr + 3 + p, 1u);

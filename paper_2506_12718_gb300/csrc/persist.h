@@ -13,11 +13,12 @@ namespace pac {
 // (kPersistUnits independent units of kPersistUnit threads per CTA, each on
 // its own item; "quarter" below for short); larger ones run on the whole
 // CTA.
-constexpr int kPersistThreads = 512;
-constexpr int kPersistUnit = 128;
+constexpr int kPersistThreads = 1024;
+constexpr int kPersistUnit = 256;
 constexpr int kPersistUnits = kPersistThreads / kPersistUnit;
-// shared memory of one unit: an equal share of what one CTA may take, in whole 128-byte lines
-constexpr int kPersistQuarterSmem = ((227 * 1024 - 1024) / kPersistUnits) / 128 * 128;
+// shared memory of one unit: an equal share of what one CTA may take (less 4 KB for the
+// kernel's own variables), in whole 128-byte lines
+constexpr int kPersistQuarterSmem = ((227 * 1024 - 4096) / kPersistUnits) / 128 * 128;
 // units of 256 threads match the pass kernels' own CTAs; smaller units load several tasks at once
 constexpr bool kPersistPrefetch = kPersistUnit < 256;
 
@@ -46,7 +47,7 @@ constexpr int persist_smem(int i) {
 constexpr bool persist_quarter(int i) { return persist_smem(i) <= kPersistQuarterSmem; }
 
 // One pass of one instance.
-struct PersistPass {
+struct alignas(16) PersistPass {
     PlaneArgs pa;        // a plane pass uses all of it; a group pass uses pa.a1
     int shape;           // index into kPersistShapes
     int dep;             // the pass whose tiles must all be done first (-1: none)
