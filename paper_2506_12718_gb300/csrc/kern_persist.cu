@@ -210,17 +210,32 @@ __global__ void __launch_bounds__(kPersistThreads, 1) persist_kernel(const __gri
 
 // CTAs of the persistent kernel resident at once (one per SM at most; 0: none fits)
 int persist_grid(int dev, int smem) {
-    static std::atomic<int> attr_set[64];
+    static std::atomic<int> dyn_max[64];  // per device: the dynamic shared memory the kernel may take
     if (dev < 0 || dev >= 64) return 0;
-    if (!attr_set[dev].load(std::memory_order_relaxed)) {
-        if (cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 64) !=
-            cudaSuccess)
+    int lim = dyn_max[dev].load(std::memory_order_relaxed);
+    if (lim == 0) {
+        // what a CTA may take in all, less the kernel's static shared memory
+        cudaFuncAttributes fa;
+        int optin = 0;
+        if (cudaFuncGetAttributes(&fa, persist_kernel) != cudaSuccess ||
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+            cudaGetLastError();  // leave no error for a later launch check to find
             return 0;
-        attr_set[dev].store(1, std::memory_order_relaxed);
+        }
+        lim = optin - (int)fa.sharedSizeBytes;
+        if (lim <= 0 || cudaFuncSetAttribute(persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) !=
+                            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        dyn_max[dev].store(lim, std::memory_order_relaxed);
     }
+    if (smem > lim) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persist_kernel, kPersistThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persist_kernel, kPersistThreads, smem) != cudaSuccess) {
+        cudaGetLastError();
         return 0;
+    }
     return nb > 0 ? device_sm_count(dev) : 0;
 }
 
