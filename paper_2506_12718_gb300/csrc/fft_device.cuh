@@ -43,70 +43,134 @@ template <typename V> __device__ __forceinline__ V mul_mi(V a) { return V{a.y, -
 template <typename V> __device__ __forceinline__ V mul_pi(V a) { return V{-a.y, a.x}; }
 template <typename V> __device__ __forceinline__ V cscale(V a, typename Real<V>::T s) { return V{a.x * s, a.y * s}; }
 
-// the root w_R^e = exp(-2 pi i e / R) (conjugated when INV) from the constant tables
-template <typename V> __device__ __forceinline__ V root_const(int off);
-template <> __device__ __forceinline__ float2 root_const<float2>(int off) { return c_roots32[off]; }
-template <> __device__ __forceinline__ double2 root_const<double2>(int off) { return c_roots64[off]; }
+// Constants of the in-register DFTs (roots.h, generated): tau of the factored
+// twiddles and the stage-2 butterfly constants, FP64 or FP64 rounded once.
+template <typename V> __device__ __forceinline__ typename Real<V>::T tau_const(int off);
+template <> __device__ __forceinline__ float tau_const<float2>(int off) { return c_tau32[off]; }
+template <> __device__ __forceinline__ double tau_const<double2>(int off) { return c_tau64[off]; }
+template <typename V> __device__ __forceinline__ typename Real<V>::T bfly_const(int off);
+template <> __device__ __forceinline__ float bfly_const<float2>(int off) { return c_bfly32[off]; }
+template <> __device__ __forceinline__ double bfly_const<double2>(int off) { return c_bfly64[off]; }
 
-__host__ __device__ constexpr int root_off(int r) {
-    return r == 3 ? PAC_ROOT_OFF_3
-         : r == 5 ? PAC_ROOT_OFF_5
-         : r == 9 ? PAC_ROOT_OFF_9
-         : r == 16 ? PAC_ROOT_OFF_16
-         : r == 25 ? PAC_ROOT_OFF_25
-         : r == 27 ? PAC_ROOT_OFF_27
-         : r == 32 ? PAC_ROOT_OFF_32
+__host__ __device__ constexpr int tau_off(int r) {
+    return r == 3 ? PAC_TAU_OFF_3
+         : r == 5 ? PAC_TAU_OFF_5
+         : r == 8 ? PAC_TAU_OFF_8
+         : r == 9 ? PAC_TAU_OFF_9
+         : r == 16 ? PAC_TAU_OFF_16
+         : r == 25 ? PAC_TAU_OFF_25
+         : r == 27 ? PAC_TAU_OFF_27
+         : r == 32 ? PAC_TAU_OFF_32
                    : -1;
 }
+__host__ __device__ constexpr int bfly_off(int r) {
+    return r == 3 ? PAC_BFLY_OFF_3
+         : r == 5 ? PAC_BFLY_OFF_5
+         : r == 8 ? PAC_BFLY_OFF_8
+         : r == 9 ? PAC_BFLY_OFF_9
+         : r == 16 ? PAC_BFLY_OFF_16
+         : r == 25 ? PAC_BFLY_OFF_25
+         : r == 27 ? PAC_BFLY_OFF_27
+         : r == 32 ? PAC_BFLY_OFF_32
+                   : -1;
+}
+// constants per stage-2 butterfly of radix B
+__host__ __device__ constexpr int bfly_nc(int b) { return b == 2 ? 1 : b == 3 ? 4 : b == 4 ? 3 : 12; }
 
-// z * w_R^e (forward) or z * conj(w_R^e) (inverse).  e and R are compile-time
-// constants after unrolling, so the special cases fold away.
-template <int R, bool INV, typename V> __device__ __forceinline__ V twiddle_const(V z, int e) {
-    using T = typename Real<V>::T;
-    e %= R;
-    if (e == 0) return z;
-    if ((8 * e) % R == 0) {
-        const int o = (8 * e) / R;  // eighth turns
-        const T h = T(0.70710678118654752440);
-        V r;
-        switch (INV ? (8 - o) : o) {  // multiply by exp(-2 pi i o / 8)
-            case 1: r = V{(z.x + z.y) * h, (z.y - z.x) * h}; break;
-            case 2: r = mul_mi(z); break;
-            case 3: r = V{(z.y - z.x) * h, -(z.x + z.y) * h}; break;
-            case 4: r = V{-z.x, -z.y}; break;
-            case 5: r = V{-(z.x + z.y) * h, (z.x - z.y) * h}; break;
-            case 6: r = mul_pi(z); break;
-            default: r = V{(z.x - z.y) * h, (z.x + z.y) * h}; break;
-        }
-        return r;
-    }
-    const V w = root_const<V>(root_off(R) + e);
-    return INV ? cmulc(z, w) : cmul(z, w);
+// Stage-2 radix of an in-register split R = A x B (B in 2, 3, 4, 5; A may be composite).
+constexpr int small_factor(int r) { return r % 4 == 0 && r > 4 ? 4 : (r % 2 == 0 ? 2 : (r % 3 == 0 ? 3 : 5)); }
+
+// |cos| >= |sin| for the angle 2 pi e / r (exact integer test)
+__host__ __device__ constexpr bool form_c(int e, int r) {
+    return (8 * e) % (4 * r) <= r || (8 * e) % (4 * r) >= 3 * r;
 }
 
-constexpr int small_factor(int r) { return r % 4 == 0 && r > 4 ? 4 : (r % 2 == 0 ? 2 : (r % 3 == 0 ? 3 : 5)); }
+// Factored twiddle.  w = w_R^e (its conjugate when INV) is sigma (1 + i tau)
+// when |cos| >= |sin| and sigma (tau + i) otherwise, |tau| <= 1; this returns
+// u = w z / sigma (two fused multiply-adds, none for quarter turns), and the
+// real sigma is folded into the constants of the stage-2 butterfly that
+// consumes u.  e and R are compile-time constants after unrolling.
+template <int R, bool INV, typename V> __device__ __forceinline__ V tw_factored(V z, int e) {
+    using T = typename Real<V>::T;
+    e %= R;
+    if ((4 * e) % R == 0) return (2 * e) % R == 0 ? z : mul_pi(z);  // w = sigma or sigma i
+    const T t0 = tau_const<V>(tau_off(R) + e);
+    const T t = INV ? -t0 : t0;
+    if (form_c(e, R)) return V{z.x - t * z.y, z.y + t * z.x};
+    return V{t * z.x - z.y, t * z.y + z.x};
+}
+
+// DFT_B (B = 2, 3, 4, 5) of inputs sigma_b u_b, sigma_0 = 1, in place on
+// u[0..B): the sigma_b are folded into the constants at bfly_const(off ...),
+// so the butterfly costs what the plain one does.  Forward w = exp(-2 pi i / B),
+// conjugate when INV; natural order in and out, no scaling.
+template <int B, bool INV, typename V> __device__ __forceinline__ void dft_sc(V* v, int off) {
+    using T = typename Real<V>::T;
+    if constexpr (B == 2) {
+        const T s1 = bfly_const<V>(off);
+        const V a = v[0], b = v[1];
+        v[0] = V{a.x + s1 * b.x, a.y + s1 * b.y};
+        v[1] = V{a.x - s1 * b.x, a.y - s1 * b.y};
+    } else if constexpr (B == 3) {
+        const T rho = bfly_const<V>(off), s1 = bfly_const<V>(off + 1);
+        const T cs = bfly_const<V>(off + 2), g = bfly_const<V>(off + 3);
+        const V a = v[0];
+        const V t = V{v[1].x + rho * v[2].x, v[1].y + rho * v[2].y};
+        const V d = V{v[1].x - rho * v[2].x, v[1].y - rho * v[2].y};
+        const V m = V{a.x + cs * t.x, a.y + cs * t.y};
+        v[0] = V{a.x + s1 * t.x, a.y + s1 * t.y};
+        v[1] = V{m.x - g * d.y, m.y + g * d.x};  // m + i g d
+        v[2] = V{m.x + g * d.y, m.y - g * d.x};  // m - i g d
+    } else if constexpr (B == 4) {
+        const T s2 = bfly_const<V>(off), rho = bfly_const<V>(off + 1), s1 = bfly_const<V>(off + 2);
+        const V a = v[0];
+        const V s0 = V{a.x + s2 * v[2].x, a.y + s2 * v[2].y};
+        const V d0 = V{a.x - s2 * v[2].x, a.y - s2 * v[2].y};
+        const V t1 = V{v[1].x + rho * v[3].x, v[1].y + rho * v[3].y};
+        const V d1 = V{v[1].x - rho * v[3].x, v[1].y - rho * v[3].y};
+        v[0] = V{s0.x + s1 * t1.x, s0.y + s1 * t1.y};
+        v[2] = V{s0.x - s1 * t1.x, s0.y - s1 * t1.y};
+        // forward: v1 = d0 - i s1 d1, v3 = d0 + i s1 d1 (signs swapped when INV)
+        const T f = INV ? -s1 : s1;
+        v[1] = V{d0.x + f * d1.y, d0.y - f * d1.x};
+        v[3] = V{d0.x - f * d1.y, d0.y + f * d1.x};
+    } else {
+        static_assert(B == 5, "stage-2 radices are 2, 3, 4, 5");
+        const T r14 = bfly_const<V>(off), r23 = bfly_const<V>(off + 1);
+        const T s1 = bfly_const<V>(off + 2), s2 = bfly_const<V>(off + 3);
+        const T c11 = bfly_const<V>(off + 4), c22 = bfly_const<V>(off + 5);
+        const T c21 = bfly_const<V>(off + 6), c12 = bfly_const<V>(off + 7);
+        const T ra = bfly_const<V>(off + 8), g1 = bfly_const<V>(off + 9);
+        const T rb = bfly_const<V>(off + 10), g2 = bfly_const<V>(off + 11);
+        const V a = v[0];
+        const V t1 = V{v[1].x + r14 * v[4].x, v[1].y + r14 * v[4].y};
+        const V d1 = V{v[1].x - r14 * v[4].x, v[1].y - r14 * v[4].y};
+        const V t2 = V{v[2].x + r23 * v[3].x, v[2].y + r23 * v[3].y};
+        const V d2 = V{v[2].x - r23 * v[3].x, v[2].y - r23 * v[3].y};
+        const V m1 = V{a.x + c11 * t1.x + c22 * t2.x, a.y + c11 * t1.y + c22 * t2.y};
+        const V m2 = V{a.x + c21 * t1.x + c12 * t2.x, a.y + c21 * t1.y + c12 * t2.y};
+        const V e1 = V{d1.x + ra * d2.x, d1.y + ra * d2.y};
+        const V e2 = V{d1.x - rb * d2.x, d1.y - rb * d2.y};
+        v[0] = V{a.x + s1 * t1.x + s2 * t2.x, a.y + s1 * t1.y + s2 * t2.y};
+        v[1] = V{m1.x + g1 * e1.y, m1.y - g1 * e1.x};  // m1 - i g1 e1
+        v[4] = V{m1.x - g1 * e1.y, m1.y + g1 * e1.x};  // m1 + i g1 e1
+        v[2] = V{m2.x + g2 * e2.y, m2.y - g2 * e2.x};  // m2 - i g2 e2
+        v[3] = V{m2.x - g2 * e2.y, m2.y + g2 * e2.x};  // m2 + i g2 e2
+    }
+}
 
 // In-register DFT of size R, natural order in and out: v[k] = sum_j v[j] w^{jk}
 // with w = exp(-2 pi i / R), or its conjugate (no scaling) when INV.
+// Composite R = A x B (B = small_factor(R)), decimation in frequency: B DFT_A
+// over stride B, the twiddles w_R^{b k1} in factored form, then A stage-2
+// DFT_B with the twiddles' real factors in their constants.
 template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V* v) {
-    using T = typename Real<V>::T;
     if constexpr (R == 1) {
         return;
     } else if constexpr (R == 2) {
         const V a = v[0], b = v[1];
         v[0] = cadd(a, b);
         v[1] = csub(a, b);
-    } else if constexpr (R == 3) {
-        const V w1 = root_const<V>(PAC_ROOT_OFF_3 + 1);  // (-1/2, -sqrt(3)/2)
-        const V t = cadd(v[1], v[2]);
-        const V d = csub(v[1], v[2]);
-        const V m = V{v[0].x + w1.x * t.x, v[0].y + w1.x * t.y};
-        // u = i * Im(w1) * d : forward Im(w1) = -sqrt(3)/2
-        const T s = INV ? -w1.y : w1.y;
-        const V u = V{-s * d.y, s * d.x};
-        v[0] = cadd(v[0], t);
-        v[1] = cadd(m, u);
-        v[2] = csub(m, u);
     } else if constexpr (R == 4) {
         const V a = v[0], b = v[1], c = v[2], d = v[3];
         const V s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = csub(b, d);
@@ -115,28 +179,12 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V* v)
         v[2] = csub(s0, s1);
         v[1] = cadd(d0, r1);
         v[3] = csub(d0, r1);
-    } else if constexpr (R == 5) {
-        const V w1 = root_const<V>(PAC_ROOT_OFF_5 + 1);  // (cos 2pi/5, -sin 2pi/5)
-        const V w2 = root_const<V>(PAC_ROOT_OFF_5 + 2);  // (cos 4pi/5, -sin 4pi/5)
-        const T c1 = w1.x, c2 = w2.x;
-        const T s1 = INV ? w1.y : -w1.y, s2 = INV ? w2.y : -w2.y;  // forward: +sin
-        const V a = v[0];
-        const V t1 = cadd(v[1], v[4]), t2 = cadd(v[2], v[3]);
-        const V d1 = csub(v[1], v[4]), d2 = csub(v[2], v[3]);
-        const V m1 = V{a.x + c1 * t1.x + c2 * t2.x, a.y + c1 * t1.y + c2 * t2.y};
-        const V m2 = V{a.x + c2 * t1.x + c1 * t2.x, a.y + c2 * t1.y + c1 * t2.y};
-        // e1 = s1 d1 + s2 d2, e2 = s2 d1 - s1 d2; outputs m -/+ i e
-        const V e1 = V{s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y};
-        const V e2 = V{s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y};
-        v[0] = cadd(a, cadd(t1, t2));
-        v[1] = cadd(m1, mul_mi(e1));
-        v[4] = cadd(m1, mul_pi(e1));
-        v[2] = cadd(m2, mul_mi(e2));
-        v[3] = cadd(m2, mul_pi(e2));
+    } else if constexpr (R == 3 || R == 5) {
+        dft_sc<R, INV>(v, bfly_off(R) + (INV ? bfly_nc(R) : 0));
     } else {
-        // Cooley-Tukey in registers: R = A * B, decimation in frequency.
-        constexpr int A = small_factor(R);
-        constexpr int B = R / A;
+        constexpr int B = small_factor(R);
+        constexpr int A = R / B;
+        static_assert(bfly_off(R) >= 0 && tau_off(R) >= 0, "in-register size without constants");
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             V z[A];
@@ -144,10 +192,10 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V* v)
             for (int a = 0; a < A; ++a) z[a] = v[b + B * a];
             dft<A, INV>(z);
 #pragma unroll
-            for (int k1 = 0; k1 < A; ++k1) v[b + B * k1] = twiddle_const<R, INV>(z[k1], b * k1);
+            for (int k1 = 0; k1 < A; ++k1) v[b + B * k1] = tw_factored<R, INV>(z[k1], b * k1);
         }
 #pragma unroll
-        for (int k1 = 0; k1 < A; ++k1) dft<B, INV>(v + B * k1);
+        for (int k1 = 0; k1 < A; ++k1) dft_sc<B, INV>(v + B * k1, bfly_off(R) + ((INV ? A : 0) + k1) * bfly_nc(B));
         V t[R];
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1)

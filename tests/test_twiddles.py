@@ -1,6 +1,5 @@
-"""CPU tests of the twiddle tables (no GPU): every root a plan uploads and
-every constant of the in-register DFT kernels is exp(-2 pi i e / L) computed
-in FP64 and rounded once to the plan's precision.
+"""CPU tests of the twiddle tables (no GPU): every root a plan uploads is
+exp(-2 pi i e / L) computed in FP64 and rounded once to the plan's precision.
 
 * Against the exact value (mpmath, 60 digits): an FP32 entry is within half
   an FP32 ulp of it, plus the few FP64 ulps of the FP64 value it was rounded
@@ -10,7 +9,12 @@ in FP64 and rounded once to the plan's precision.
   cos and sin by at most 3 u a, plus one ulp of the C library's cos / sin.
 * Rounded once: the FP32 table of a problem equals its FP64 table rounded to
   FP32 entry by entry (no second computation in FP32).
-* roots.h is exactly what gen_roots.py writes.
+* The in-register DFT constants (roots.h: the factored twiddles' tau and the
+  stage-2 butterfly constants with the twiddles' real factors folded in)
+  are the exact values rounded once to FP64 (within half an FP64 ulp of the
+  60-digit value), the FP32 tables are the FP64 tables rounded once, and a
+  numpy model of the kernels' in-register DFT built from those constants
+  is the DFT; roots.h is exactly what gen_roots.py writes.
 """
 import math
 import os
@@ -138,14 +142,19 @@ def test_plan_twiddles_rejects_bad_arguments():
 
 
 def parse_roots_h(text):
-    offs = {int(r): int(o) for r, o in re.findall(r"#define PAC_ROOT_OFF_(\d+) (\d+)", text)}
-    body64 = text.split("c_roots64[PAC_ROOT_COUNT] = {")[1].split("};")[0]
-    body32 = text.split("c_roots32[PAC_ROOT_COUNT] = {")[1].split("};")[0]
-    pairs64 = re.findall(r"\{(\S+), (\S+)\}", body64)
-    pairs32 = re.findall(r"\{(\S+)f, (\S+)f\}", body32)
-    r64 = np.array([complex(float.fromhex(a), float.fromhex(b)) for a, b in pairs64])
-    r32 = np.array([complex(float.fromhex(a), float.fromhex(b)) for a, b in pairs32])
-    return offs, r64, r32
+    """offsets and FP64 / FP32 arrays of the generated header"""
+    def arr(name):
+        body = text.split(name)[1].split("= {")[1].split("};")[0]
+        return np.array([float.fromhex(x.strip().rstrip("f")) for x in body.split(",") if x.strip()])
+    toff = {int(r): int(o) for r, o in re.findall(r"#define PAC_TAU_OFF_(\d+) (\d+)", text)}
+    boff = {int(r): int(o) for r, o in re.findall(r"#define PAC_BFLY_OFF_(\d+) (\d+)", text)}
+    return (toff, arr("c_tau64[PAC_TAU_COUNT]"), arr("c_tau32[PAC_TAU_COUNT]"),
+            boff, arr("c_bfly64[PAC_BFLY_COUNT]"), arr("c_bfly32[PAC_BFLY_COUNT]"))
+
+
+def header():
+    with open(os.path.join(CSRC, "roots.h")) as f:
+        return parse_roots_h(f.read())
 
 
 def test_roots_header_is_what_the_generator_writes():
@@ -155,17 +164,176 @@ def test_roots_header_is_what_the_generator_writes():
         assert f.read() == out
 
 
-def test_roots_header_constants_are_fp64_roots_rounded_once():
-    with open(os.path.join(CSRC, "roots.h")) as f:
-        offs, r64, r32 = parse_roots_h(f.read())
-    assert len(r64) == len(r32) and len(r64) > 0
-    radices = sorted(offs)
-    for i, R in enumerate(radices):
-        end = offs[radices[i + 1]] if i + 1 < len(radices) else len(r64)
-        assert end - offs[R] == R
-        exps = np.arange(R)
-        check_entries(r64[offs[R]:end], exps, R, "c128")
-        check_entries(r32[offs[R]:end], exps, R, "c64")
-        # the FP32 constants are the FP64 constants rounded once
-        assert np.array_equal(r32[offs[R]:end].astype(np.complex64), r64[offs[R]:end].astype(np.complex64))
-        assert np.array_equal(r32[offs[R]:end], r64[offs[R]:end].astype(np.complex64).astype(np.complex128))
+# ---- the factored twiddles and stage-2 butterfly constants, against mpmath
+
+
+def stage2_radix(R):
+    return 4 if R % 4 == 0 and R > 4 else (2 if R % 2 == 0 else (3 if R % 3 == 0 else 5))
+
+
+def exact_factored(e, R, inv):
+    """(sigma, tau) of w = w_R^e (conjugate when inv) as mpf: w = sigma (1 + i tau) when |cos| >= |sin|,
+    else sigma (tau + i); quarter turns give tau = 0."""
+    c, im = exact_root(e, R)
+    if inv:
+        im = -im
+    e %= R
+    if (4 * e) % R == 0:
+        return ((mpmath.nint(c), mpmath.mpf(0)) if (2 * e) % R == 0 else (mpmath.nint(im), mpmath.mpf(0)))
+    if form_c(e, R):  # |cos| >= |sin|, decided in integers (ties at the eighth turns go to the cosine form)
+        assert abs(c) >= abs(im) - mpmath.mpf(10) ** -50
+        return c, im / c
+    assert abs(im) > abs(c)
+    return im, c / im
+
+
+def exact_bfly(B, sig, inv):
+    """The constants a stage-2 DFT_B with input scales sig reads, in the kernels' order, as mpf."""
+    if B == 2:
+        return [sig[1]]
+    if B == 4:
+        return [sig[2], sig[3] / sig[1], sig[1]]
+    c1, im1 = exact_root(1, B)          # w_B = c1 + i im1 (forward)
+    if B == 3:
+        sb = -im1 if inv else im1
+        return [sig[2] / sig[1], sig[1], c1 * sig[1], sb * sig[1]]
+    c2, im2 = exact_root(2, 5)
+    s1 = im1 if inv else -im1           # forward: +sin(2 pi / 5)
+    s2 = im2 if inv else -im2
+    g1, g2 = s1 * sig[1], s2 * sig[1]
+    return [sig[4] / sig[1], sig[3] / sig[2], sig[1], sig[2], c1 * sig[1], c2 * sig[2], c2 * sig[1], c1 * sig[2],
+            s2 * sig[2] / g1, g1, s1 * sig[2] / g2, g2]
+
+
+def bfly_layout(R):
+    """(B, A) of the entries at PAC_BFLY_OFF_R: fwd then inv, A stage-1 frequencies each"""
+    B = R if R in (3, 5) else stage2_radix(R)
+    return B, R // B
+
+
+NC = {2: 1, 3: 4, 4: 3, 5: 12}
+
+
+def within_half_ulp(got64, want):
+    """FP64 entry = the exact value rounded once (0.5 ulp, plus the reference's 1e-50)"""
+    err = abs(mpmath.mpf(float(got64)) - want)
+    return err <= 0.5 * float(np.spacing(abs(float(want)))) + mpmath.mpf(10) ** -50
+
+
+def test_tau_table_is_exact_and_rounded_once():
+    toff, t64, t32, _, _, _ = header()
+    assert len(t64) == len(t32) and sorted(toff) == [3, 5, 8, 9, 16, 25, 27, 32]
+    for R, off in toff.items():
+        for e in range(R):
+            _, tau = exact_factored(e, R, False)
+            assert within_half_ulp(t64[off + e], tau), (R, e, t64[off + e], float(tau))
+            assert abs(t64[off + e]) <= 1.0
+            # the conjugate root has -tau: one table serves both directions
+            assert exact_factored(e, R, True)[1] == -tau
+    assert np.array_equal(t32, t64.astype(np.float32).astype(np.float64))
+
+
+def test_bfly_table_is_exact_and_rounded_once():
+    _, _, _, boff, b64, b32 = header()
+    n = 0
+    for R, off in boff.items():
+        B, A = bfly_layout(R)
+        for d, inv in enumerate((False, True)):
+            for k1 in range(A):
+                sig = [exact_factored(b * k1, R, inv)[0] for b in range(B)]
+                want = exact_bfly(B, sig, inv)
+                base = off + (d * A + k1) * NC[B]
+                for i, w in enumerate(want):
+                    assert within_half_ulp(b64[base + i], w), (R, inv, k1, i, b64[base + i], float(w))
+                n += len(want)
+    assert n == len(b64)
+    assert np.array_equal(b32, b64.astype(np.float32).astype(np.float64))
+
+
+# ---- a numpy model of the kernels' in-register DFT (fft_device.cuh: dft, dft_sc, tw_factored)
+
+
+def form_c(e, R):
+    f = (8 * e) % (4 * R)
+    return f <= R or f >= 3 * R
+
+
+def model_dft(v, R, inv, tabs, dt):
+    """The kernels' in-register DFT_R of the vector v, step for step, with the table constants"""
+    toff, t, boff, b = tabs
+    if R == 1:
+        return v.copy()
+    if R == 2:
+        return np.array([v[0] + v[1], v[0] - v[1]])
+    if R == 4:
+        s0, d0, s1, d1 = v[0] + v[2], v[0] - v[2], v[1] + v[3], v[1] - v[3]
+        r1 = 1j * d1 if inv else -1j * d1
+        return np.array([s0 + s1, d0 + r1, s0 - s1, d0 - r1])
+    if R in (3, 5):
+        return model_dft_sc(v, R, inv, b, boff[R] + (NC[R] if inv else 0), dt)
+    B = stage2_radix(R)
+    A = R // B
+    w = np.empty(R, dtype=v.dtype)
+    for bb in range(B):
+        z = model_dft(v[bb::B][:A], A, inv, tabs, dt)
+        for k1 in range(A):
+            e = (bb * k1) % R
+            if (4 * e) % R == 0:
+                u = z[k1] if (2 * e) % R == 0 else 1j * z[k1]
+            else:
+                tau = dt(-t[toff[R] + e] if inv else t[toff[R] + e])
+                u = z[k1] * (1 + 1j * tau) if form_c(e, R) else z[k1] * (tau + 1j)
+            w[bb + B * k1] = u
+    out = np.empty(R, dtype=v.dtype)
+    for k1 in range(A):
+        y = model_dft_sc(w[B * k1:B * k1 + B], B, inv, b, boff[R] + ((A if inv else 0) + k1) * NC[B], dt)
+        for k2 in range(B):
+            out[k1 + A * k2] = y[k2]
+    return out
+
+
+def model_dft_sc(u, B, inv, b, off, dt):
+    c = [dt(x) for x in b[off:off + NC[B]]]
+    if B == 2:
+        return np.array([u[0] + c[0] * u[1], u[0] - c[0] * u[1]])
+    if B == 3:
+        rho, s1, cs, g = c
+        t, d = u[1] + rho * u[2], u[1] - rho * u[2]
+        m = u[0] + cs * t
+        return np.array([u[0] + s1 * t, m + 1j * g * d, m - 1j * g * d])
+    if B == 4:
+        s2, rho, s1 = c
+        s0, d0 = u[0] + s2 * u[2], u[0] - s2 * u[2]
+        t1, d1 = u[1] + rho * u[3], u[1] - rho * u[3]
+        f = -s1 if inv else s1
+        return np.array([s0 + s1 * t1, d0 - 1j * f * d1, s0 - s1 * t1, d0 + 1j * f * d1])
+    r14, r23, s1, s2, c11, c22, c21, c12, ra, g1, rb, g2 = c
+    t1, d1 = u[1] + r14 * u[4], u[1] - r14 * u[4]
+    t2, d2 = u[2] + r23 * u[3], u[2] - r23 * u[3]
+    m1 = u[0] + c11 * t1 + c22 * t2
+    m2 = u[0] + c21 * t1 + c12 * t2
+    e1, e2 = d1 + ra * d2, d1 - rb * d2
+    return np.array([u[0] + s1 * t1 + s2 * t2, m1 - 1j * g1 * e1, m2 - 1j * g2 * e2, m2 + 1j * g2 * e2,
+                     m1 + 1j * g1 * e1])
+
+
+@pytest.mark.parametrize("R", [3, 4, 5, 8, 9, 16, 25, 27, 32])
+@pytest.mark.parametrize("inv", [False, True])
+def test_in_register_dft_model_is_the_dft(R, inv):
+    toff, t64, t32, boff, b64, b32 = header()
+    rng = np.random.default_rng(R + 100 * inv)
+    j = np.arange(R)
+    F = np.exp((2j if inv else -2j) * np.pi * np.outer(j, j) / R)  # the DFT matrix (conjugate when inv)
+    for tabs, dt, cdt, tol in (((toff, t64, boff, b64), np.float64, np.complex128, 4e-15),
+                               ((toff, t32, boff, b32), np.float32, np.complex64, 2.5e-6)):
+        for _ in range(4):
+            x = (rng.standard_normal(R) + 1j * rng.standard_normal(R)).astype(cdt)
+            got = model_dft(x, R, inv, tabs, dt)
+            want = F @ x.astype(np.complex128)
+            assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want) * np.log2(R), (R, inv, dt)
+        # every basis vector: a wrong constant anywhere shows
+        for k in range(R):
+            x = np.zeros(R, dtype=cdt)
+            x[k] = 1
+            got = model_dft(x, R, inv, tabs, dt)
+            assert np.allclose(got, F[:, k], atol=tol * 8 * R), (R, inv, k)
