@@ -66,29 +66,30 @@ __global__ void pointwise_kernel(int64_t n, const V* a, const V* __restrict__ b,
 }
 
 // Between the plain index-reversed order of a spectrum and its storage order
-// (see SpecOrder): to_kernel ? dst[slot(e)] = src[e] : dst[e] = src[slot(e)].
+// (see SpecOrder): to_kernel ? dst[slot(e)] = src[e] : dst[e] = src[slot(e)],
+// times `scale` (the filter spectrum's 1/N, applied here once).
 template <typename V>
 __global__ void spec_order_kernel(const SpecOrder o, uint32_t n, const V* __restrict__ src, V* __restrict__ dst,
-                                  int to_kernel) {
+                                  int to_kernel, typename Real<V>::T scale) {
     for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         const uint32_t k = spec_slot(o, e);
         if (to_kernel)
-            dst[k] = src[e];
+            dst[k] = cscale(src[e], scale);
         else
-            dst[e] = src[k];
+            dst[e] = cscale(src[k], scale);
     }
 }
 
 cudaError_t launch_spec_order(int esize, const SpecOrder& o, int64_t n, const void* src, void* dst, bool to_kernel,
-                              cudaStream_t s) {
+                              cudaStream_t s, double scale) {
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, 8192);
     if (esize == 8)
         spec_order_kernel<float2><<<(unsigned)blocks, threads, 0, s>>>(o, (uint32_t)n, (const float2*)src,
-                                                                      (float2*)dst, to_kernel ? 1 : 0);
+                                                                      (float2*)dst, to_kernel ? 1 : 0, (float)scale);
     else
         spec_order_kernel<double2><<<(unsigned)blocks, threads, 0, s>>>(o, (uint32_t)n, (const double2*)src,
-                                                                       (double2*)dst, to_kernel ? 1 : 0);
+                                                                       (double2*)dst, to_kernel ? 1 : 0, scale);
     return cudaGetLastError();
 }
 

@@ -156,8 +156,7 @@ int build_entry(int count, const pac_plan* plans, const void* const* x, void* co
             if (st.mode == kPlane)
                 planes_by_level[l][k].push_back(make_plane(plans[i], st.src, st.dst));
             else
-                by_level[l][k].push_back(make_pass(plans[i], plans[i]->groups[st.group], st.mode, st.src, st.dst,
-                                                   st.scale));
+                by_level[l][k].push_back(make_pass(plans[i], plans[i]->groups[st.group], st.mode, st.src, st.dst));
         }
     }
     // one host image of every launch's arguments and tile starts
@@ -225,7 +224,7 @@ int build_persistent(int count, const pac_plan* plans, const void* const* x, voi
                 r.pp.pa = make_plane(plans[i], st.src, st.dst);
                 r.tiles = (int)r.pp.pa.planes;
             } else {
-                r.pp.pa.a1 = make_pass(plans[i], plans[i]->groups[st.group], st.mode, st.src, st.dst, st.scale);
+                r.pp.pa.a1 = make_pass(plans[i], plans[i]->groups[st.group], st.mode, st.src, st.dst);
                 r.tiles = (int)r.pp.pa.a1.tiles;
             }
             of[i].push_back((int)recs.size());

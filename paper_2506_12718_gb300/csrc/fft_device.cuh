@@ -266,13 +266,21 @@ template <typename V, int M, bool LINES = false> struct Shape {
 // batched kernel), each running its own tile: task numbering uses the
 // thread's index within its unit, and rounds synchronise the unit with a
 // named barrier instead of the whole CTA.
-template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int KS_ = 1, bool SPLIT_ = false>
+// SWZ: the buffer is an XOR-swizzled plane (plane_swizzle in config.h): the
+// element at (line i1, position i2) of a plane sits at i1 * P + (i2 ^ g(i1)),
+// g(i1) = ((i1 & 1) << 3) | ((i1 >> 1) & 7), a permutation inside each aligned
+// group of 16 elements; for axis d-1 (RS = 1) the row is i2 and the column i1,
+// for axis d-2 the row is i1 and the column i2.
+template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int KS_ = 1, bool SPLIT_ = false,
+          bool SWZ_ = false>
 struct Geo {
     using V = V_;
     static constexpr int M = M_, W = W_, NT = NT_, RS = RS_, WS = WS_, ES = (int)sizeof(V_), KS = KS_;
     static constexpr int NR = round_count(M_, ES);
     static constexpr bool PF = PF_;
     static constexpr bool SPLIT = SPLIT_;
+    static constexpr bool SWZ = SWZ_;
+    static_assert(!SWZ_ || KS_ == 1, "swizzled planes are single-CTA");
     __device__ __forceinline__ static int tid() { return SPLIT_ ? (int)(threadIdx.x % NT_) : (int)threadIdx.x; }
 };
 // the pass kernels' geometry: a tile of W columns, buffer [row][w] of pitch
@@ -342,6 +350,9 @@ __device__ __forceinline__ uint32_t spec_slot(const SpecOrder& o, uint32_t e) {
     return t * o.W * o.M + u * o.tasks + w + o.W * b;
 }
 
+// CTAs of a thread-block cluster a split plane may use (the portable maximum).
+constexpr int kMaxClusterCtas = 8;
+
 // Per-tile facts.  Rows case (C > 1): a thread's column w = tid mod W is
 // fixed, so its global offset and external-twiddle column are computed once
 // per tile.  Offsets are 32-bit element offsets (plans keep N < 2^31).
@@ -356,10 +367,8 @@ template <typename V> struct TileCtx {
     uint32_t base;     // rows case: global offset of row 0 of this thread's column
     uint32_t j;        // rows case: external twiddle column j = (q mod C) / I
     bool valid;        // rows case: this thread's column exists (q < Q)
-    bool do_scale;     // kFwd: multiply by `scale` on store (decided once, not per element)
-    typename Real<V>::T scale;
     int wofs;          // column offset of this CTA's columns in the buffer (split rows)
-    uint32_t sk[4];    // split rows: the buffer of each CTA of the cluster (shared::cluster addresses)
+    uint32_t sk[kMaxClusterCtas];  // split planes: the buffer of each CTA of the cluster (shared::cluster addresses)
 };
 
 // Loads and stores of distributed shared memory (a CTA of the cluster,
@@ -388,24 +397,36 @@ template <typename GEO>
 __device__ __forceinline__ uint32_t dsmem_addr(const TileCtx<typename GEO::V>& c, int row, int w) {
     constexpr int H = GEO::M / GEO::KS;
     const int part = row / H;
+    static_assert(GEO::KS <= kMaxClusterCtas, "cluster larger than the address table");
     uint32_t b = c.sk[0];
 #pragma unroll
     for (int k = 1; k < GEO::KS; ++k) b = part == k ? c.sk[k] : b;
     return b + (uint32_t)(((row - part * H) * GEO::RS + (w + c.wofs) * GEO::WS) * GEO::ES);
 }
 
+// buffer index of element (row, w) of a single-CTA geometry
+__device__ __forceinline__ int swz_g(int i) { return ((i & 1) << 3) | ((i >> 1) & 7); }
+template <typename GEO> __device__ __forceinline__ int sidx(int row, int w) {
+    if constexpr (!GEO::SWZ)
+        return row * GEO::RS + w * GEO::WS;
+    else if constexpr (GEO::RS == 1)
+        return w * GEO::WS + (row ^ swz_g(w));
+    else
+        return row * GEO::RS + (w ^ swz_g(row));
+}
+
 // Element (row, w) of a round's exchange buffer.
 template <typename GEO>
 __device__ __forceinline__ typename GEO::V sld(const TileCtx<typename GEO::V>& c, int row, int w) {
     if constexpr (GEO::KS == 1)
-        return c.s[row * GEO::RS + w * GEO::WS];
+        return c.s[sidx<GEO>(row, w)];
     else
         return ld_dsmem(dsmem_addr<GEO>(c, row, w), static_cast<typename GEO::V*>(nullptr));
 }
 template <typename GEO>
 __device__ __forceinline__ void sst(const TileCtx<typename GEO::V>& c, int row, int w, typename GEO::V v) {
     if constexpr (GEO::KS == 1)
-        c.s[row * GEO::RS + w * GEO::WS] = v;
+        c.s[sidx<GEO>(row, w)] = v;
     else
         st_dsmem(dsmem_addr<GEO>(c, row, w), v);
 }
@@ -510,7 +531,6 @@ __device__ __forceinline__ void task_body(const TileCtx<typename GEO::V>& c, con
                 if constexpr (!LINES) {
                     if (a.has_ext && col.j != 0) o = cmul(o, ext_twiddle<V>(a, (int64_t)col.j * __ldg(a.r2f + row)));
                 }
-                if (c.do_scale) o = cscale(o, c.scale);
                 dst[col.base + (uint32_t)__ldg(a.r2g + row) * stride] = o;
             }
         }
@@ -554,7 +574,7 @@ __device__ __forceinline__ void load_spec(const TileCtx<typename GEO::V>& c, int
 // Inverse (adjoint): conj twiddles, then the conjugate DFT.  MUL (the last
 // forward round of a fused pass): DFT, product with the filter spectrum at
 // the same global position, conjugate DFT.  DST as SRC; a placed store also
-// applies w_L^{j k'} and the scale, a placed load (first inverse round) the
+// applies w_L^{j k'}, a placed load (first inverse round) the
 // conjugate w_L^{j k'}.  When a thread has a few tasks in the round and the
 // round reads global memory, every global load of all its tasks is issued
 // before the first task is computed, so their latencies overlap.
@@ -646,7 +666,7 @@ __device__ __forceinline__ void inv_middle(const TileCtx<typename GEO::V>& c) {
     }
 }
 
-// kFwd: natural rows in, placed rows out (with w_L^{j k'} and the scale).
+// kFwd: natural rows in, placed rows out (with w_L^{j k'}).
 template <typename GEO, bool LINES>
 __device__ __forceinline__ void tile_forward(const TileCtx<typename GEO::V>& c) {
     constexpr int NR = GEO::NR;
@@ -733,10 +753,8 @@ template <typename V> __device__ __forceinline__ void ctx_init(TileCtx<V>& c, co
     c.twi = reinterpret_cast<const V*>(a.tw_int);
     c.Q = (uint32_t)a.Q;
     c.C = (uint32_t)a.C;
-    c.do_scale = a.mode == kFwd && a.scale != 1.0;
-    c.scale = (typename Real<V>::T)a.scale;
     c.wofs = 0;
-    for (int k = 0; k < 4; ++k) c.sk[k] = 0;
+    for (int k = 0; k < kMaxClusterCtas; ++k) c.sk[k] = 0;
 }
 
 // One pass over all tiles, CTAs walking tiles blockIdx.x, +gridDim.x, ...
@@ -808,24 +826,27 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, size
 // for axis d-2, transforming columns [k n2/K, (k+1) n2/K) over all rows.
 template <typename V, int M1, int M2, int K> struct PlaneShape {
     static constexpr int ES = sizeof(V);
-    static constexpr int P2 = plane_pitch(M1, M2, ES);
+    static constexpr bool SWZ = plane_swizzle(M1, M2, ES, K);
+    static constexpr int P2 = plane_pitch_k(M1, M2, ES, K);
     static constexpr int NT = plane_threads(M1, M2, ES, K);
-    static constexpr int SMEM = plane_smem_bytes(M1 / K, M2, ES);
-    using G2 = Geo<V, M2, M1 / K, NT, 1, P2, true, 1>;  // axis d-1: rows i2, columns = local lines
-    using G1 = Geo<V, M1, M2 / K, NT, P2, 1, true, K>;  // axis d-2: rows i1 (split), columns i2
+    static constexpr int SMEM = (M1 / K) * P2 * ES;
+    using G2 = Geo<V, M2, M1 / K, NT, 1, P2, true, 1, false, SWZ>;  // axis d-1: rows i2, columns = local lines
+    using G1 = Geo<V, M1, M2 / K, NT, P2, 1, true, K, false, SWZ>;  // axis d-2: rows i1 (split), columns i2
     static_assert(SMEM <= kPlaneSmemMax, "plane too large for one CTA");
     static_assert(M1 % K == 0 && M2 % K == 0, "the plane must split evenly");
+    static_assert(K >= 1 && K <= kMaxClusterCtas, "CTAs per plane beyond the cluster address table");
 };
 
 // A plane geometry of NT threads (the persistent batched kernel: its
 // whole-CTA items, or with SPLIT its units of NT threads).
 template <typename V, int M1, int M2, int NT_, bool SPLIT = false> struct PlaneShapeNT {
     static constexpr int ES = sizeof(V);
-    static constexpr int P2 = plane_pitch(M1, M2, ES);
+    static constexpr bool SWZ = plane_swizzle(M1, M2, ES, 1);
+    static constexpr int P2 = plane_pitch_k(M1, M2, ES, 1);
     static constexpr int NT = NT_;
-    static constexpr int SMEM = plane_smem_bytes(M1, M2, ES);
-    using G2 = Geo<V, M2, M1, NT, 1, P2, true, 1, SPLIT>;
-    using G1 = Geo<V, M1, M2, NT, P2, 1, true, 1, SPLIT>;
+    static constexpr int SMEM = M1 * P2 * ES;
+    using G2 = Geo<V, M2, M1, NT, 1, P2, true, 1, SPLIT, SWZ>;
+    using G1 = Geo<V, M1, M2, NT, P2, 1, true, 1, SPLIT, SWZ>;
 };
 
 // forward rounds 0..NR-1, the first from global (natural rows), all results in shared memory

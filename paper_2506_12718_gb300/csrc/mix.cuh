@@ -7,8 +7,8 @@
 // radices come with the launch (a switch over the radices a round can have
 // selects the in-register DFT), and copied out.  The copy-in and copy-out
 // carry what the first and last rounds of the one-base kernels do in
-// registers: the placement of frequencies (rowmap), the external factor
-// w_L^{j k'} and the scale.  Round i has block length S_i = M / (R_0 ... R_{i-1})
+// registers: the placement of frequencies (rowmap) and the external factor
+// w_L^{j k'}.  Round i has block length S_i = M / (R_0 ... R_{i-1})
 // and applies w_{S_i}^{jp k} after its forward DFT, as in round_exec.
 #pragma once
 
@@ -171,14 +171,12 @@ __device__ __forceinline__ void mix_load(const MixCtx<V>& c, bool placed) {
 }
 
 // Copy-out.  Placed rows (forward output): global row g takes in-tile row
-// rowmap[g], times w_L^{j freq[g]} and the scale; natural rows otherwise.
+// rowmap[g], times w_L^{j freq[g]}; natural rows otherwise.
 template <typename V, bool LINES>
 __device__ __forceinline__ void mix_store(const MixCtx<V>& c, bool placed) {
     const PassArgs& a = *c.a;
     V* dst = reinterpret_cast<V*>(a.dst);
     const int NT = blockDim.x;
-    const bool do_scale = placed && a.mode == kFwd && a.scale != 1.0;
-    const typename Real<V>::T scale = (typename Real<V>::T)a.scale;
     if constexpr (LINES) {
         const uint32_t n = mix_line_elems(c), base = c.q0 * (uint32_t)c.M;
 #pragma unroll 4
@@ -186,7 +184,6 @@ __device__ __forceinline__ void mix_store(const MixCtx<V>& c, bool placed) {
             const int w = (int)(e / (uint32_t)c.M), g = (int)e - w * c.M;
             const int row = placed ? __ldg(a.rowmap + g) : g;
             V v = c.s[row * c.P + w];
-            if (do_scale) v = cscale(v, scale);
             dst[base + e] = v;
         }
     } else {
@@ -200,8 +197,7 @@ __device__ __forceinline__ void mix_store(const MixCtx<V>& c, bool placed) {
             V v = c.s[row * c.P + w];
             if (placed) {
                 if (k.j != 0) v = cmul(v, ext_twiddle<V>(a, (int64_t)k.j * __ldg(a.freq + g)));
-                if (do_scale) v = cscale(v, scale);
-            }
+                }
             dst[k.base + (uint32_t)g * C] = v;
         }
     }

@@ -30,7 +30,7 @@
 #include "pac_internal.h"
 
 namespace pac {
-int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale, cudaStream_t s);
+int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, cudaStream_t s);
 }
 
 using namespace pac;
@@ -168,7 +168,7 @@ extern "C" int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void
     }
     // FFT2 = permute o uFFT2 (Algorithm 5): DIF passes one launch per group
     for (int i = 0; i < G; ++i) {
-        int rc = run_pass(p, p->groups[i], kFwd, i == 0 ? x_dev : y_dev, y_dev, 1.0, s);
+        int rc = run_pass(p, p->groups[i], kFwd, i == 0 ? x_dev : y_dev, y_dev, s);
         if (rc) return rc;
     }
     // natural order with the product (spectrum gathered at the same positions), into the static scratch
@@ -181,7 +181,7 @@ extern "C" int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void
                       : launch_digits<double2>(dp, false, scratch, y_dev, nullptr, so, p->N, s);
     if (e != cudaSuccess) return cuda_fail(e, "permute kernel");
     for (int i = G - 1; i >= 0; --i) {
-        int rc = run_pass(p, p->groups[i], kInv, y_dev, y_dev, 1.0, s);
+        int rc = run_pass(p, p->groups[i], kInv, y_dev, y_dev, s);
         if (rc) return rc;
     }
     return PAC_OK;

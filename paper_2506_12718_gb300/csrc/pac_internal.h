@@ -79,10 +79,9 @@ struct Step {
     int group, mode;
     const void* src;
     void* dst;
-    double scale;
 };
 void convolve_steps(pac_plan p, const void* x, void* y, std::vector<Step>& out);
-PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale);
+PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst);
 // forget every cached batch that uses plan p (batch.cu); called by pac_plan_destroy
 void batch_forget_plan(pac_plan p);
 
@@ -97,8 +96,9 @@ int take_device_error(int device, unsigned* value);
 // auxiliary kernels (aux.cu)
 cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64_t* const* idx_dev,
                            const void* src, void* dst, const void* mul, cudaStream_t s, double scale = 1.0);
+// to_kernel: dst[slot(e)] = src[e] * scale; else dst[e] = src[slot(e)] * scale
 cudaError_t launch_spec_order(int esize, const SpecOrder& o, int64_t n, const void* src, void* dst, bool to_kernel,
-                              cudaStream_t s);
+                              cudaStream_t s, double scale = 1.0);
 cudaError_t launch_pointwise_mul(int esize, int64_t n, const void* a, const void* b, void* out, double scale,
                                  cudaStream_t s);
 

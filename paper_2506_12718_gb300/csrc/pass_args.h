@@ -28,7 +28,6 @@ struct PassArgs {
     int tw_shift;           // log2(tw_T) when tw_T is a power of two, else -1
     int mode;               // PassMode
     int has_ext;            // apply w_L^{j k'} (L' > 1)
-    double scale;           // applied on store in kFwd (filter spectrum 1/N); 1 = none
     // mixed group (stages of several prime bases, the runtime-radix kernel):
     // mix_nr rounds of radices mix_r (0: a one-base group), group size mix_m,
     // tile width mix_w

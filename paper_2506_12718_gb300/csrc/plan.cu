@@ -867,7 +867,7 @@ SpecOrder spec_order_of(pac_plan p) {
     return o;
 }
 
-PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale) {
+PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst) {
     PassArgs a;
     const unsigned char* t = static_cast<const unsigned char*>(p->d_tables);
     a.src = src;
@@ -889,7 +889,6 @@ PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, vo
     a.tw_shift = g.tw_shift;
     a.mode = mode;
     a.has_ext = g.has_ext ? 1 : 0;
-    a.scale = scale;
     a.mix_nr = g.mix_nr;
     a.mix_m = g.M;
     a.mix_w = W;
@@ -899,8 +898,8 @@ PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, vo
 
 PlaneArgs make_plane(pac_plan p, const void* src, void* dst) {
     PlaneArgs pa;
-    pa.a1 = make_pass(p, p->groups[p->plane_g1], kPlane, src, dst, 1.0);
-    pa.a2 = make_pass(p, p->groups[p->plane_g1 + 1], kPlane, src, dst, 1.0);
+    pa.a1 = make_pass(p, p->groups[p->plane_g1], kPlane, src, dst);
+    pa.a2 = make_pass(p, p->groups[p->plane_g1 + 1], kPlane, src, dst);
     pa.planes = p->N / ((int64_t)p->groups[p->plane_g1].M * p->groups[p->plane_g1 + 1].M);
     return pa;
 }
@@ -914,8 +913,8 @@ static int run_plane(pac_plan p, const void* src, void* dst, cudaStream_t s) {
     return PAC_OK;
 }
 
-int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, double scale, cudaStream_t s) {
-    const PassArgs a = make_pass(p, g, mode, src, dst, scale);
+int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, cudaStream_t s) {
+    const PassArgs a = make_pass(p, g, mode, src, dst);
     const int kid = mode == kFwd ? 0 : (mode == kFused ? 1 : 2);
     timer_mark(s, kid, true);
     cudaError_t e = launch_pass(p->esize, g.M, a, s);
@@ -935,7 +934,7 @@ static int run_single(pac_plan p, const std::vector<Step>& steps, int grid, unsi
     args.npasses = n;
     for (int i = 0; i < n; ++i) {
         const Step& st = steps[i];
-        args.pass[i] = make_pass(p, p->groups[st.group], st.mode, st.src, st.dst, st.scale);
+        args.pass[i] = make_pass(p, p->groups[st.group], st.mode, st.src, st.dst);
     }
     int rc = barrier_slot(p->device, &args.barrier, &args.base, (unsigned)((n - 1) * grid), &args.error);
     if (rc) return rc;
@@ -961,7 +960,7 @@ static int run_steps(pac_plan p, const std::vector<Step>& steps, cudaStream_t s,
     if (single) return run_single(p, steps, grid, 0u, 0u, s);
     for (const Step& st : steps) {
         int rc = st.mode == kPlane ? run_plane(p, st.src, st.dst, s)
-                                   : run_pass(p, p->groups[st.group], st.mode, st.src, st.dst, st.scale, s);
+                                   : run_pass(p, p->groups[st.group], st.mode, st.src, st.dst, s);
         if (rc) return rc;
     }
     return PAC_OK;
@@ -998,25 +997,25 @@ void convolve_steps(pac_plan p, const void* x, void* y, std::vector<Step>& steps
     steps.clear();
     if (p->plane) {
         const int g1 = p->plane_g1;
-        for (int i = 0; i < g1; ++i) steps.push_back({i, kFwd, i == 0 ? x : y, y, 1.0});
-        steps.push_back({g1, kPlane, g1 == 0 ? x : y, y, 1.0});
-        for (int i = g1 - 1; i >= 0; --i) steps.push_back({i, kInv, y, y, 1.0});
+        for (int i = 0; i < g1; ++i) steps.push_back({i, kFwd, i == 0 ? x : y, y});
+        steps.push_back({g1, kPlane, g1 == 0 ? x : y, y});
+        for (int i = g1 - 1; i >= 0; --i) steps.push_back({i, kInv, y, y});
         return;
     }
-    for (int i = 0; i < G; ++i) steps.push_back({i, i == G - 1 ? kFused : kFwd, i == 0 ? x : y, y, 1.0});
-    for (int i = G - 2; i >= 0; --i) steps.push_back({i, kInv, y, y, 1.0});
+    for (int i = 0; i < G; ++i) steps.push_back({i, i == G - 1 ? kFused : kFwd, i == 0 ? x : y, y});
+    for (int i = G - 2; i >= 0; --i) steps.push_back({i, kInv, y, y});
 }
 
 int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s) { return run_convolve(p, x, y, s, true); }
 
-int run_forward(pac_plan p, const void* x, void* xhat, double scale, cudaStream_t s) {
+int run_forward(pac_plan p, const void* x, void* xhat, cudaStream_t s) {
     const int G = (int)p->groups.size();
     if (G == 0) {
-        cudaError_t e = launch_pointwise_mul(p->esize, p->N, x, nullptr, xhat, scale, s);
+        cudaError_t e = launch_pointwise_mul(p->esize, p->N, x, nullptr, xhat, 1.0, s);
         return e == cudaSuccess ? PAC_OK : cuda_fail(e, "pointwise kernel");
     }
     std::vector<Step> steps;
-    for (int i = 0; i < G; ++i) steps.push_back({i, kFwd, i == 0 ? x : xhat, xhat, i == G - 1 ? scale : 1.0});
+    for (int i = 0; i < G; ++i) steps.push_back({i, kFwd, i == 0 ? x : xhat, xhat});
     return run_steps(p, steps, s, true);
 }
 
@@ -1063,7 +1062,7 @@ static int prepare_convolve(pac_plan p) {
             pa.planes = 0;
             e = launch_plane(p->esize, p->groups[p->plane_g1].M, p->groups[p->plane_g1 + 1].M, p->plane_k, pa, 0);
         } else {
-            PassArgs a = make_pass(p, p->groups[st.group], st.mode, nullptr, nullptr, 1.0);
+            PassArgs a = make_pass(p, p->groups[st.group], st.mode, nullptr, nullptr);
             a.tiles = 0;
             e = launch_pass(p->esize, p->groups[st.group].M, a, 0);
         }
@@ -1084,18 +1083,19 @@ extern "C" int pac_filter_spectrum(pac_plan p, const void* h_dev) {
     int rc;
     void* tmp = nullptr;
     if (p->groups.empty()) {  // N = 1
-        rc = run_forward(p, h_dev, p->d_spec, 1.0 / (double)p->N, s);
+        e = launch_pointwise_mul(p->esize, p->N, h_dev, nullptr, p->d_spec, 1.0 / (double)p->N, s);
+        rc = e == cudaSuccess ? PAC_OK : cuda_fail(e, "pointwise kernel");
     } else {
-        // A^T h / N in the plain index-reversed order, then once into the
-        // order the fused pass reads it
+        // A^T h in the plain index-reversed order, then once into the order
+        // the fused pass reads it, times 1/N (the scale of the inverse)
         e = cudaMalloc(&tmp, (size_t)p->bytes());
         if (e != cudaSuccess) {
             cudaStreamDestroy(s);
             return fail(PAC_ERR_NOMEM, "filter spectrum staging: %s", cudaGetErrorString(e));
         }
-        rc = run_forward(p, h_dev, tmp, 1.0 / (double)p->N, s);
+        rc = run_forward(p, h_dev, tmp, s);
         if (rc == PAC_OK) {
-            e = launch_spec_order(p->esize, spec_order_of(p), p->N, tmp, p->d_spec, true, s);
+            e = launch_spec_order(p->esize, spec_order_of(p), p->N, tmp, p->d_spec, true, s, 1.0 / (double)p->N);
             if (e != cudaSuccess) rc = cuda_fail(e, "spectrum order kernel");
         }
     }
@@ -1125,7 +1125,7 @@ extern "C" int pac_forward_unordered(pac_plan p, const void* x_dev, void* xhat_d
     if (!p) return fail(PAC_ERR_ARG, "null plan");
     if (int rc = check_ptr(x_dev, "x_dev")) return rc;
     if (int rc = check_ptr(xhat_dev, "xhat_dev")) return rc;
-    return run_forward(p, x_dev, xhat_dev, 1.0, static_cast<cudaStream_t>(stream));
+    return run_forward(p, x_dev, xhat_dev, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int pac_convolve_host(pac_plan p, const void* x_host, void* y_host, void* stream) {
@@ -1222,7 +1222,7 @@ extern "C" int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int G = (int)p->groups.size();
     // FFT2 = permute o uFFT2 (Algorithm 5): DIF passes, then reversed -> natural
-    int rc = run_forward(p, x_dev, y_dev, 1.0, s);
+    int rc = run_forward(p, x_dev, y_dev, s);
     if (rc) return rc;
     const int64_t* to_nat[3];
     const int64_t* to_rev[3];
@@ -1239,7 +1239,7 @@ extern "C" int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev,
     e = timed_permute(p, to_rev, p->d_scratch, y_dev, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "permute kernel");
     std::vector<Step> steps;
-    for (int i = G - 1; i >= 0; --i) steps.push_back({i, kInv, y_dev, y_dev, 1.0});
+    for (int i = G - 1; i >= 0; --i) steps.push_back({i, kInv, y_dev, y_dev});
     return run_steps(p, steps, s, true);
 }
 
@@ -1267,7 +1267,7 @@ extern "C" int pac_fft(pac_plan p, const void* in_dev, void* out_dev, int invers
     }
     const int G = (int)p->groups.size();
     if (!inverse) {
-        int rc = run_forward(p, in_dev, p->d_scratch, 1.0, s);  // A^T x, index-reversed
+        int rc = run_forward(p, in_dev, p->d_scratch, s);  // A^T x, index-reversed
         if (rc) return rc;
         cudaError_t e = timed_permute(p, to_nat, p->d_scratch, out_dev, nullptr, s);
         return e == cudaSuccess ? PAC_OK : cuda_fail(e, "permute kernel");
@@ -1283,7 +1283,7 @@ extern "C" int pac_fft(pac_plan p, const void* in_dev, void* out_dev, int invers
         return e == cudaSuccess ? PAC_OK : cuda_fail(e, "copy");
     }
     std::vector<Step> steps;
-    for (int i = G - 1; i >= 0; --i) steps.push_back({i, kInv, i == G - 1 ? (const void*)p->d_scratch : out_dev, out_dev, 1.0});
+    for (int i = G - 1; i >= 0; --i) steps.push_back({i, kInv, i == G - 1 ? (const void*)p->d_scratch : out_dev, out_dev});
     return run_steps(p, steps, s, false);
 }
 
