@@ -16,125 +16,101 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "fft_device.cuh"
 #include "pac_internal.h"
+
+namespace pac {
+
+// The maps in tiles.  Write the tensor as m = d_0 d_1 rows of d_2 elements,
+// row rho(s) = (s mod d_0) d_1 + (s mod d_1) holding the residues of s.
+// Output k has row residue s = k mod m and column c = k mod d_2 (m and d_2
+// coprime), k = (s E_m + c E_2) mod n with the idempotents E_m (1 mod m,
+// 0 mod d_2) and E_2 (0 mod m, 1 mod d_2).  In the sheared coordinates
+// u = s, v = (c - s) mod d_2 a tile is u in [u_0, u_0 + 32), v in
+// [v_0, v_0 + 32); its element (p, q) is
+//   tensor row rho(u_0 + p), column (u_0 + p + v_0 + q) mod d_2, and
+//   output k = K_0 + q E_2 + p (mod n), K_0 = (u_0 E_m + ((u_0 + v_0) mod d_2) E_2) mod n,
+// because adding p to both residues adds p to k.  So for fixed p the tile's
+// tensor elements are consecutive (a row segment), for fixed q its outputs
+// are consecutive: the tile moves through shared memory with 32-element
+// runs on both sides.  K_0 per tile and q E_2 mod n per q come from host
+// tables (no 64-bit division on the device).
+struct PfaMapArgs {
+    uint32_t n, m, d0, d1, d2;
+    uint32_t tiles_v;          // ceil(d_2 / 32)
+    uint32_t tiles;            // ceil(m / 32) * tiles_v
+    const uint32_t* k0;        // [tiles] K_0 of each tile
+    const uint32_t* qe2;       // [32] q E_2 mod n
+};
+}  // namespace pac
 
 struct pac_pfa_s {
     int64_t n = 1;
     int t = 0;                       // number of factors
     int64_t dims[3] = {1, 1, 1};     // tensor shape (n_t, ..., n_1), the last index fastest
-    int64_t crt[3] = {0, 0, 0};      // e_q per tensor axis
     pac_dtype dtype = PAC_C64;
     int esize = 8;
     pac_plan inner = nullptr;        // the t-D convolution
     void* d_scratch = nullptr;       // the gathered tensor, n elements
+    uint32_t* d_maptab = nullptr;    // tables of the tiled maps (pfa_build_map)
+    pac::PfaMapArgs map = {};
     bool has_spec = false;
     std::mutex mu;
 };
 
 namespace pac {
 
-// Gamma^T: tensor entry t = (i_0, i_1, i_2) (i_2 fastest) = src[k], k = (i_0 e_0 + i_1 e_1 + i_2 e_2) mod n.
-// A thread walks t, t + S, t + 2S, ... (S the grid's thread count) and keeps
-// the digits of t and k up to date with 32-bit additions: adding the digits
-// (s_0, s_1, s_2) of S adds delta = (s_0 e_0 + s_1 e_1 + s_2 e_2) mod n to k,
-// and a carry out of digit q adds e_{q-1}, because d_q e_q = 0 mod n (e_q is
-// 0 modulo every other factor and d_q e_q is 0 modulo d_q).  No 64-bit
-// division per element (a 64-bit modulo runs on the FP64 pipe, which is
-// narrow on this GPU).
-template <typename V>
-__global__ void pfa_to_tensor_kernel(uint32_t n, uint32_t d1, uint32_t d2, uint32_t e0, uint32_t e1, uint32_t e2,
-                                     uint32_t s0, uint32_t s1, uint32_t s2, uint32_t delta,
-                                     const V* __restrict__ src, V* __restrict__ dst) {
-    const uint32_t S = gridDim.x * blockDim.x;
-    uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    uint32_t i2 = t % d2, r = t / d2, i1 = r % d1, i0 = r / d1;
-    uint32_t k = (uint32_t)(((uint64_t)i0 * e0 + (uint64_t)i1 * e1 + (uint64_t)i2 * e2) % n);
-    const auto addmod = [n](uint32_t a, uint32_t b) { const uint32_t c = a + b; return c >= n ? c - n : c; };
-    for (;;) {
-        dst[t] = __ldg(src + k);
-        t += S;
-        if (t >= n) break;
-        i2 += s2;
-        const bool c2 = i2 >= d2;
-        if (c2) i2 -= d2;
-        i1 += s1 + (c2 ? 1u : 0u);
-        const bool c1 = i1 >= d1;
-        if (c1) i1 -= d1;
-        i0 += s0 + (c1 ? 1u : 0u);
-        k = addmod(k, delta);
-        if (c2) k = addmod(k, e1);
-        if (c1) k = addmod(k, e0);
-    }
+
+
+
+// tensor offset of element (p, lane) of a tile: row rho(u_0 + p), column (u_0 + p + v_0 + lane) mod d_2
+__device__ __forceinline__ size_t pfa_tensor_off(const PfaMapArgs& a, uint32_t u0, uint32_t v0, int p, int lane) {
+    const uint32_t s = u0 + (uint32_t)p;
+    const uint32_t row = (s % a.d0) * a.d1 + s % a.d1;
+    uint32_t c = (s + v0) % a.d2 + (uint32_t)lane;
+    if (c >= a.d2) c -= a.d2;
+    return (size_t)row * a.d2 + c;
 }
 
-// Gamma: dst[k] = tensor entry (k mod d_0, k mod d_1, k mod d_2); a thread
-// walks k, k + S, ... keeping the three residues with 32-bit additions of
-// S mod d_q.
-template <typename V>
-__global__ void pfa_from_tensor_kernel(uint32_t n, uint32_t d0, uint32_t d1, uint32_t d2, uint32_t m0, uint32_t m1,
-                                       uint32_t m2, const V* __restrict__ src, V* __restrict__ dst) {
-    const uint32_t S = gridDim.x * blockDim.x;
-    uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    uint32_t r0 = k % d0, r1 = k % d1, r2 = k % d2;
-    for (;;) {
-        dst[k] = __ldg(src + (r0 * d1 + r1) * d2 + r2);
-        k += S;
-        if (k >= n) break;
-        r0 += m0;
-        if (r0 >= d0) r0 -= d0;
-        r1 += m1;
-        if (r1 >= d1) r1 -= d1;
-        r2 += m2;
-        if (r2 >= d2) r2 -= d2;
-    }
+// output index of element (lane, q) of a tile: K_0 + q E_2 + lane (mod n)
+__device__ __forceinline__ uint32_t pfa_vector_idx(const PfaMapArgs& a, uint32_t K0, int q, int lane) {
+    uint32_t k = K0 + __ldg(a.qe2 + q);
+    if (k >= a.n) k -= a.n;
+    k += (uint32_t)lane;
+    if (k >= a.n) k -= a.n;
+    return k;
 }
 
-static cudaError_t launch_pfa_map(const pac_pfa_s* p, bool to_tensor, const void* src, void* dst, cudaStream_t s) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    const int threads = 256;
-    const int64_t want = (p->n + threads - 1) / threads;
-    const int64_t cap = (int64_t)device_sm_count(dev) * 8;
-    const unsigned grid = (unsigned)(want < cap ? want : cap);
-    const uint64_t n = (uint64_t)p->n;  // < 2^31
-    const uint64_t S = (uint64_t)grid * threads;
-    const uint64_t d0 = (uint64_t)p->dims[0], d1 = (uint64_t)p->dims[1], d2 = (uint64_t)p->dims[2];
-    if (to_tensor) {
-        // digits of the stride S (mod n) in the tensor's mixed radix, and the k increment they give
-        const uint64_t sm = S % n;
-        const uint64_t s2 = sm % d2, s1 = (sm / d2) % d1, s0 = sm / (d1 * d2);
-        const uint64_t delta = (s0 * ((uint64_t)p->crt[0] % n) % n + s1 * ((uint64_t)p->crt[1] % n) % n +
-                                s2 * ((uint64_t)p->crt[2] % n) % n) % n;
-        const uint32_t a[10] = {(uint32_t)n, (uint32_t)d1, (uint32_t)d2, (uint32_t)(p->crt[0] % (int64_t)n),
-                                (uint32_t)(p->crt[1] % (int64_t)n), (uint32_t)(p->crt[2] % (int64_t)n),
-                                (uint32_t)s0, (uint32_t)s1, (uint32_t)s2, (uint32_t)delta};
-        if (p->esize == 8)
-            pfa_to_tensor_kernel<float2><<<grid, threads, 0, s>>>(a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8],
-                                                                  a[9], static_cast<const float2*>(src),
-                                                                  static_cast<float2*>(dst));
-        else
-            pfa_to_tensor_kernel<double2><<<grid, threads, 0, s>>>(a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8],
-                                                                   a[9], static_cast<const double2*>(src),
-                                                                   static_cast<double2*>(dst));
-    } else {
-        const uint32_t m0 = (uint32_t)(S % d0), m1 = (uint32_t)(S % d1), m2 = (uint32_t)(S % d2);
-        if (p->esize == 8)
-            pfa_from_tensor_kernel<float2><<<grid, threads, 0, s>>>((uint32_t)n, (uint32_t)d0, (uint32_t)d1,
-                                                                    (uint32_t)d2, m0, m1, m2,
-                                                                    static_cast<const float2*>(src),
-                                                                    static_cast<float2*>(dst));
-        else
-            pfa_from_tensor_kernel<double2><<<grid, threads, 0, s>>>((uint32_t)n, (uint32_t)d0, (uint32_t)d1,
-                                                                     (uint32_t)d2, m0, m1, m2,
-                                                                     static_cast<const double2*>(src),
-                                                                     static_cast<double2*>(dst));
+// TO_TENSOR: Gamma^T (tensor entry of k = src[k]); else Gamma (dst[k] = tensor entry of k).
+// Each warp moves row segments (lane = q) on the tensor side and output runs
+// (lane = p) on the vector side; the 32 x 33 buffer keeps both conflict-free.
+template <typename V, bool TO_TENSOR>
+__global__ void __launch_bounds__(256) pfa_map_kernel(const PfaMapArgs a, const V* __restrict__ src,
+                                                      V* __restrict__ dst) {
+    __shared__ V tile[32][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t tix = blockIdx.x; tix < a.tiles; tix += gridDim.x) {
+        const uint32_t tu = tix / a.tiles_v, tv = tix - tu * a.tiles_v;
+        const uint32_t u0 = tu * 32, v0 = tv * 32;
+        const int pn = (int)min(32u, a.m - u0), qn = (int)min(32u, a.d2 - v0);
+        const uint32_t K0 = __ldg(a.k0 + tix);
+        if constexpr (TO_TENSOR) {
+            for (int q = warp; q < qn; q += 8)
+                if (lane < pn) tile[lane][q] = __ldg(src + pfa_vector_idx(a, K0, q, lane));
+            __syncthreads();
+            for (int p = warp; p < pn; p += 8)
+                if (lane < qn) dst[pfa_tensor_off(a, u0, v0, p, lane)] = tile[p][lane];
+        } else {
+            for (int p = warp; p < pn; p += 8)
+                if (lane < qn) tile[p][lane] = __ldg(src + pfa_tensor_off(a, u0, v0, p, lane));
+            __syncthreads();
+            for (int q = warp; q < qn; q += 8)
+                if (lane < pn) dst[pfa_vector_idx(a, K0, q, lane)] = tile[lane][q];
+        }
+        __syncthreads();  // the next tile reuses the buffer
     }
-    return cudaGetLastError();
 }
 
 // a^{-1} mod m (a and m coprime, m >= 1)
@@ -151,6 +127,68 @@ static int64_t inverse_mod(int64_t a, int64_t m) {
     }
     s0 %= m;
     return s0 < 0 ? s0 + m : s0;
+}
+
+// a * b mod n without overflow (a, b < n < 2^31)
+static uint64_t mulmod(uint64_t a, uint64_t b, uint64_t n) { return (a % n) * (b % n) % n; }
+
+// Host tables of the tiled maps: K_0 of every tile and q E_2 mod n (q < 32).
+static int pfa_build_map(pac_pfa_s* p, PfaMapArgs* out, uint32_t** d_tab) {
+    const uint64_t n = (uint64_t)p->n, d0 = (uint64_t)p->dims[0], d1 = (uint64_t)p->dims[1], d2 = (uint64_t)p->dims[2];
+    const uint64_t m = d0 * d1;
+    PfaMapArgs a = {};
+    a.n = (uint32_t)n;
+    a.m = (uint32_t)m;
+    a.d0 = (uint32_t)d0;
+    a.d1 = (uint32_t)d1;
+    a.d2 = (uint32_t)d2;
+    a.tiles_v = (uint32_t)((d2 + 31) / 32);
+    a.tiles = (uint32_t)((m + 31) / 32) * a.tiles_v;
+    // idempotents of the coprime pair (m, d_2)
+    const uint64_t Em = d2 == 1 ? 1 % n : mulmod(d2, (uint64_t)inverse_mod((int64_t)(d2 % m), (int64_t)m), n);
+    const uint64_t E2 = m == 1 ? 1 % n : mulmod(m, (uint64_t)inverse_mod((int64_t)(m % d2), (int64_t)d2), n);
+    std::vector<uint32_t> tab((size_t)a.tiles + 32);
+    for (uint32_t tu = 0, i = 0; tu * 32ull < m; ++tu)
+        for (uint32_t tv = 0; tv < a.tiles_v; ++tv, ++i) {
+            const uint64_t u0 = tu * 32ull, v0 = tv * 32ull;
+            tab[i] = (uint32_t)((mulmod(u0, Em, n) + mulmod((u0 + v0) % d2, E2, n)) % n);
+        }
+    for (uint32_t q = 0; q < 32; ++q) tab[a.tiles + q] = (uint32_t)mulmod(q, E2, n);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(d_tab), tab.size() * sizeof(uint32_t));
+    if (e != cudaSuccess) return fail(PAC_ERR_NOMEM, "prime factor map tables: %s", cudaGetErrorString(e));
+    e = cudaMemcpy(*d_tab, tab.data(), tab.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(*d_tab);
+        *d_tab = nullptr;
+        return cuda_fail(e, "prime factor map tables");
+    }
+    a.k0 = *d_tab;
+    a.qe2 = *d_tab + a.tiles;
+    *out = a;
+    return PAC_OK;
+}
+
+// Gamma^T (to_tensor) or Gamma; a single factor (or n = 1) is the identity: a copy
+static cudaError_t launch_pfa_map(const pac_pfa_s* p, bool to_tensor, const void* src, void* dst, cudaStream_t s) {
+    if (p->t <= 1)
+        return cudaMemcpyAsync(dst, src, (size_t)p->n * p->esize, cudaMemcpyDeviceToDevice, s);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int64_t cap = (int64_t)device_sm_count(dev) * 8;
+    const unsigned grid = (unsigned)std::min<int64_t>(p->map.tiles, cap);
+    if (p->esize == 8) {
+        if (to_tensor)
+            pfa_map_kernel<float2, true><<<grid, 256, 0, s>>>(p->map, (const float2*)src, (float2*)dst);
+        else
+            pfa_map_kernel<float2, false><<<grid, 256, 0, s>>>(p->map, (const float2*)src, (float2*)dst);
+    } else {
+        if (to_tensor)
+            pfa_map_kernel<double2, true><<<grid, 256, 0, s>>>(p->map, (const double2*)src, (double2*)dst);
+        else
+            pfa_map_kernel<double2, false><<<grid, 256, 0, s>>>(p->map, (const double2*)src, (double2*)dst);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace pac
@@ -192,8 +230,6 @@ extern "C" int pac_pfa_create(int64_t n, pac_dtype dtype, pac_pfa* out) {
     for (int a = 0; a < 3; ++a) {
         const int q = 2 - a;  // axis a holds factor n_{q+1} (zero-based f[q])
         p->dims[a] = q < t ? f[q] : 1;
-        const int64_t d = p->dims[a];
-        p->crt[a] = d == 1 ? 0 : (n / d) * inverse_mod((n / d) % d, d) % n;
     }
     const int ndim = t > 0 ? t : 1;
     const int64_t* inner_dims = p->dims + (3 - ndim);
@@ -208,6 +244,15 @@ extern "C" int pac_pfa_create(int64_t n, pac_dtype dtype, pac_pfa* out) {
         delete p;
         return fail(PAC_ERR_NOMEM, "prime factor scratch: %s", cudaGetErrorString(e));
     }
+    if (t >= 2) {
+        rc = pfa_build_map(p, &p->map, &p->d_maptab);
+        if (rc) {
+            cudaFree(p->d_scratch);
+            pac_plan_destroy(p->inner);
+            delete p;
+            return rc;
+        }
+    }
     *out = p;
     return PAC_OK;
 }
@@ -216,6 +261,7 @@ extern "C" int pac_pfa_destroy(pac_pfa p) {
     if (!p) return PAC_OK;
     cudaDeviceSynchronize();
     if (p->d_scratch) cudaFree(p->d_scratch);
+    if (p->d_maptab) cudaFree(p->d_maptab);
     int rc = p->inner ? pac_plan_destroy(p->inner) : PAC_OK;
     delete p;
     return rc;
