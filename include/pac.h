@@ -78,8 +78,12 @@ typedef enum {
  * with radix 8 -> [8,8,2]), the mixed-radix framework of Section 7.1.
  * radix 0 (mixed radix, Section 7.1): each dim is any 2^a 3^b 5^c, with the
  * stage list [4,..,4,(2), 3,..,3, 5,..,5] (the factor 2^a in radix-4 stages,
- * a leftover 2 last, then the 3s and the 5s).  A dim of 1 is allowed (empty
- * stage list).  Builds twiddle tables in FP64, rounds them once to dtype and
+ * a leftover 2 last, then the 3s and the 5s).  Each run of stages of one
+ * base becomes one or more passes; where groups spanning the bases (at most
+ * 2048 points) are fewer and each has a compiled kernel (48, 120 and 1000
+ * points), those run instead (PAC_MIXED=0 / 1 / rt in the environment forces
+ * one-base groups / groups spanning bases / those groups in the runtime-radix
+ * kernel).  A dim of 1 is allowed (empty stage list).  Builds twiddle tables in FP64, rounds them once to dtype and
  * uploads them to the current device.  On success *out owns device memory
  * until pac_plan_destroy.  Errors: PAC_ERR_ARG, PAC_ERR_SIZE, PAC_ERR_NOMEM,
  * PAC_ERR_CUDA.
@@ -96,7 +100,8 @@ int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, p
  * The unordered transform (pac_forward_unordered) leaves frequency
  * k = k_1 + s_1 k_2 + s_1 s_2 k_3 + ... at position
  * sum_i k_i prod_{j>i} s_j of each axis.  Stages of one prime base that are
- * adjacent run in one pass; each change of base starts a new pass.  Such
+ * adjacent run in one pass; each change of base starts a new pass unless
+ * groups spanning bases are formed (the rule of pac_plan_create).  Such
  * plans are not autotuned.  Errors: PAC_ERR_ARG (ndim, null pointers, more
  * than 64 stages), PAC_ERR_SIZE (a stage or product rule broken), as
  * pac_plan_create otherwise.
@@ -350,7 +355,8 @@ int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void* y_dev, vo
  * Autotuner: time the candidate pass schedules of this problem on the current
  * device (the largest group per pass, i.e. how many DIF stages one pass fuses,
  * from the largest a CTA holds down to small groups; and, in 2-D/3-D, the
- * plane pass on or off), `reps` convolutions each after a warm-up, and keep
+ * plane pass on or off and its tile: a whole plane per CTA or a plane split
+ * over a cluster of K CTAs), `reps` convolutions each after a warm-up, and keep
  * the fastest.  Plans created afterwards with the same (dims, radix, dtype)
  * use it.  With PAC_TUNE_FILE set in the environment, tuned schedules are
  * read from that file on first use and appended to it.  Allocates and frees
@@ -360,8 +366,9 @@ int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void* y_dev, vo
  * the first time a plan is made for it.  PAC_LOG=1 makes every plan print
  * its pass schedule (groups, plane pass) to stderr.  For stage lists of
  * several prime bases (radix 0) the candidates include groups spanning bases
- * (the runtime-radix kernel; off by default, PAC_MIXED=1 / 0 in the
- * environment forces them on / off for every plan).
+ * (compiled kernels for 48, 120 and 1000 points, the runtime-radix kernel for
+ * other sizes) and one-base groups; PAC_MIXED in the environment overrides
+ * the choice for every plan (see pac_plan_create).
  */
 int pac_tune(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int reps, double* best_us);
 
@@ -395,7 +402,9 @@ int pac_measure_fma_peak(int dtype, double* gflops);
 /*
  * Host only (no device): the pass groups a plan of this problem gets, in
  * forward order (axis 0 first), without the plane pass.  flags bit 0:
- * groups may span prime bases (as PAC_MIXED=1); cap: a schedule's
+ * groups may span prime bases (as PAC_MIXED=1); bit 1 (bit 0 ignored): the
+ * default rule of pac_plan_create, groups span bases only where every such
+ * group has a compiled kernel (sizes 48, 120, 1000); cap: a schedule's
  * group-exponent cap (0: none).  For group g: axis[g], size[g] (its M) and
  * rounds[8 g .. 8 g + 7] (its in-CTA round radices, 0-padded).  *count: in,
  * the room of the arrays (groups; ignored when all three are NULL); out, the

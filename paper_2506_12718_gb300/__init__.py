@@ -151,8 +151,14 @@ def pac_last_error() -> str:
     return load().pac_last_error().decode(errors="replace")
 
 
-def pac_plan_groups(dims, radix: int, dtype: int = 0, mixed: bool = False, cap: int = 0) -> list:
-    """Host only: the pass groups of a plan, forward order, as (axis, M, rounds)."""
+def _mixed_flags(mixed) -> int:
+    # None: the default rule (groups spanning bases where each has a compiled kernel)
+    return 2 if mixed is None else (1 if mixed else 0)
+
+
+def pac_plan_groups(dims, radix: int, dtype: int = 0, mixed=False, cap: int = 0) -> list:
+    """Host only: the pass groups of a plan, forward order, as (axis, M, rounds).
+    mixed: True / False allow / forbid groups spanning prime bases, None the default rule."""
     vals = [int(v) for v in dims]
     d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
     room = 64
@@ -160,12 +166,12 @@ def pac_plan_groups(dims, radix: int, dtype: int = 0, mixed: bool = False, cap: 
     sz = (ctypes.c_int * room)()
     rr = (ctypes.c_int * (8 * room))()
     cnt = ctypes.c_int(room)
-    _check(load().pac_plan_groups(len(vals), d, int(radix), int(dtype), 1 if mixed else 0, int(cap), ax, sz, rr,
+    _check(load().pac_plan_groups(len(vals), d, int(radix), int(dtype), _mixed_flags(mixed), int(cap), ax, sz, rr,
                                   ctypes.byref(cnt)))
     return [(ax[g], sz[g], [r for r in rr[8 * g:8 * g + 8] if r]) for g in range(cnt.value)]
 
 
-def pac_plan_twiddles(dims, radix: int, dtype: int, group: int, which: int, mixed: bool = False, cap: int = 0):
+def pac_plan_twiddles(dims, radix: int, dtype: int, group: int, which: int, mixed=False, cap: int = 0):
     """Host only: twiddle table `which` (0 round, 1 external low, 2 external high) of group `group`
     of the schedule pac_plan_groups gives, as uploaded by a plan; returns (values, L, T) with values a
     numpy complex64 / complex128 array."""
@@ -173,7 +179,7 @@ def pac_plan_twiddles(dims, radix: int, dtype: int, group: int, which: int, mixe
     vals = [int(v) for v in dims]
     d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
     cnt, L, T = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
-    args = (len(vals), d, int(radix), int(dtype), 1 if mixed else 0, int(cap), int(group), int(which))
+    args = (len(vals), d, int(radix), int(dtype), _mixed_flags(mixed), int(cap), int(group), int(which))
     _check(load().pac_plan_twiddles(*args, None, ctypes.byref(cnt), ctypes.byref(L), ctypes.byref(T)))
     out = np.zeros(max(1, cnt.value), np.complex64 if int(dtype) == C64 else np.complex128)
     _check(load().pac_plan_twiddles(*args, out.ctypes.data, ctypes.byref(cnt), None, None))

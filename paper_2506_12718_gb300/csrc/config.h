@@ -22,17 +22,69 @@ constexpr int group_mmax(int base, int esize) {
     return base == 2 ? (esize == 8 ? 4096 : 2048) : base == 3 ? 2187 : 3125;
 }
 
-// Number of rounds for a column of length m: ceil(log_base m / log_base rmax).
+// ------------------------------------------------------------ mixed groups
+// A group whose stages have more than one prime base (mixed radix, Section
+// 7.1): its rounds are the prime-power parts of M, each split like a one-base
+// group into the fewest rounds of at most mix_rmax (16 for base 2, 9 for base
+// 3, 25 for base 5) with the exponent spread evenly, all sorted larger first
+// (1000 = 25 x 8 x 5, 120 = 8 x 5 x 3, 48 = 16 x 3).  A few sizes have
+// compiled pass kernels (mixed_compiled); the others run in the runtime-radix
+// kernel (mix.cuh).
+constexpr int mix_rmax(int base) { return base == 2 ? 16 : base == 3 ? 9 : 25; }
+constexpr int exponent_of(int m, int p) {
+    int e = 0;
+    while (m > 1 && m % p == 0) {
+        m /= p;
+        ++e;
+    }
+    return e;
+}
+constexpr bool is_mixed(int m) { return m > 1 && (m % 2 == 0) + (m % 3 == 0) + (m % 5 == 0) > 1; }
+constexpr int mixed_round_count(int m) {
+    const int ps[3] = {2, 3, 5};
+    int n = 0;
+    for (int k = 0; k < 3; ++k) {
+        const int e = exponent_of(m, ps[k]), er = ilog(mix_rmax(ps[k]), ps[k]);
+        n += (e + er - 1) / er;
+    }
+    return n;
+}
+constexpr int mixed_round_radix(int m, int i) {
+    const int ps[3] = {2, 3, 5};
+    int r[16] = {};
+    int n = 0;
+    for (int k = 0; k < 3; ++k) {
+        const int p = ps[k], e = exponent_of(m, p), er = ilog(mix_rmax(p), p);
+        const int nr = (e + er - 1) / er;
+        for (int j = 0; j < nr && n < 16; ++j) r[n++] = ipow(p, e / nr + (j < e % nr ? 1 : 0));
+    }
+    for (int a = 1; a < n; ++a)  // larger first
+        for (int b = a; b > 0 && r[b - 1] < r[b]; --b) {
+            const int t = r[b];
+            r[b] = r[b - 1];
+            r[b - 1] = t;
+        }
+    return i < n ? r[i] : 1;
+}
+// mixed group sizes with compiled pass kernels (the groups of 1000, 120 and
+// 6000 = 48 x 125 per axis)
+constexpr bool mixed_compiled(int m) { return m == 48 || m == 120 || m == 1000; }
+
+// Number of rounds for a column of length m: ceil(log_base m / log_base rmax)
+// for one base, the mixed list otherwise.
 constexpr int round_count(int m, int esize) {
     return m <= 1 ? 0
-                  : (ilog(m, base_of(m)) + ilog(round_rmax(base_of(m), esize), base_of(m)) - 1) /
-                        ilog(round_rmax(base_of(m), esize), base_of(m));
+           : is_mixed(m)
+               ? mixed_round_count(m)
+               : (ilog(m, base_of(m)) + ilog(round_rmax(base_of(m), esize), base_of(m)) - 1) /
+                     ilog(round_rmax(base_of(m), esize), base_of(m));
 }
 
 // Radix of round i: the exponent of m is spread evenly, larger rounds first.
 constexpr int round_radix(int m, int esize, int i) {
-    return ipow(base_of(m), ilog(m, base_of(m)) / round_count(m, esize) +
-                                (i < ilog(m, base_of(m)) % round_count(m, esize) ? 1 : 0));
+    return is_mixed(m) ? mixed_round_radix(m, i)
+                       : ipow(base_of(m), ilog(m, base_of(m)) / round_count(m, esize) +
+                                              (i < ilog(m, base_of(m)) % round_count(m, esize) ? 1 : 0));
 }
 
 constexpr int floor_pow2(int v) { return v >= 2 ? 2 * floor_pow2(v / 2) : 1; }
@@ -115,16 +167,13 @@ constexpr int min_blocks(int m, int esize) {
     return clampi(65536 / (pass_threads(m, esize) * reg_target(m, esize)), 1, 8);
 }
 
-// ------------------------------------------------------------ mixed groups
-// A group whose stages have more than one prime base (mixed radix, Section
-// 7.1) runs in the runtime-radix kernel (mix.cuh): the tile is copied into
-// shared memory, transformed by rounds whose radices are the prime-power
-// parts of M (each split like a one-base group: at most 16 for base 2, 9 for
-// base 3, 25 for base 5; larger first), and copied out.
+// ------------------------------------------------- the runtime-radix kernel
+// Mixed groups without a compiled kernel run in the runtime-radix kernel
+// (mix.cuh): the tile is copied into shared memory, transformed by the mixed
+// group's rounds (radices given at launch), and copied out.
 constexpr int kMixThreads = 256;
 constexpr int kMixMaxRounds = 8;
 constexpr int kMixMmax = 2048;  // largest mixed group
-constexpr int mix_rmax(int base) { return base == 2 ? 16 : base == 3 ? 9 : 25; }
 constexpr int mix_w(int m, int esize) { return clampi(floor_pow2(kTileBytes / (m * esize)), 32 / esize, 256 / esize); }
 constexpr int mix_pitch(int m, int esize) { return mix_w(m, esize) + 1; }
 constexpr int mix_smem_bytes(int m, int esize) { return m * mix_pitch(m, esize) * esize; }
@@ -166,4 +215,13 @@ constexpr int plane_min_blocks(int k) { return k > 1 ? 2 : 1; }
 // largest plane the plane pass takes (bytes of shared memory)
 constexpr int kPlaneSmemMax = 200 * 1024;
 
+}  // namespace pac
+
+namespace pac {
+static_assert(mixed_round_count(1000) == 3 && mixed_round_radix(1000, 0) == 25 && mixed_round_radix(1000, 1) == 8 &&
+                  mixed_round_radix(1000, 2) == 5,
+              "1000 = 25 x 8 x 5");
+static_assert(mixed_round_count(120) == 3 && mixed_round_radix(120, 0) == 8 && mixed_round_radix(120, 2) == 3,
+              "120 = 8 x 5 x 3");
+static_assert(mixed_round_count(48) == 2 && mixed_round_radix(48, 0) == 16, "48 = 16 x 3");
 }  // namespace pac

@@ -18,21 +18,27 @@ cudaError_t launch_conv_c128_p2(int M, ConvArgs& args, int grid, cudaStream_t s)
 cudaError_t launch_conv_c128_p35(int M, ConvArgs& args, int grid, cudaStream_t s);
 
 cudaError_t launch_mix(int esize, bool lines, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_pass_mixc(int esize, int M, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_multi_mixc(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+                              int64_t total, cudaStream_t s);
 cudaError_t launch_mix_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
                              int64_t total, cudaStream_t s);
 
 cudaError_t launch_pass(int esize, int M, const PassArgs& a, cudaStream_t s) {
     if (a.mix_nr > 0) return launch_mix(esize, a.C == 1, a, s);
+    if (is_mixed(M)) return launch_pass_mixc(esize, M, a, s);
     if (esize == 8) return (M % 2 == 0) ? launch_pass_c64_p2(M, a, s) : launch_pass_c64_p35(M, a, s);
     return (M % 2 == 0) ? launch_pass_c128_p2(M, a, s) : launch_pass_c128_p35(M, a, s);
 }
 
 int conv_grid(int esize, int M, int dev) {
+    if (is_mixed(M)) return 0;  // no single-launch form of the mixed groups
     if (esize == 8) return (M % 2 == 0) ? conv_grid_c64_p2(M, dev) : conv_grid_c64_p35(M, dev);
     return (M % 2 == 0) ? conv_grid_c128_p2(M, dev) : conv_grid_c128_p35(M, dev);
 }
 
 cudaError_t launch_conv(int esize, int M, ConvArgs& args, int grid, cudaStream_t s) {
+    if (is_mixed(M)) return cudaErrorInvalidValue;
     if (esize == 8) return (M % 2 == 0) ? launch_conv_c64_p2(M, args, grid, s) : launch_conv_c64_p35(M, args, grid, s);
     return (M % 2 == 0) ? launch_conv_c128_p2(M, args, grid, s) : launch_conv_c128_p35(M, args, grid, s);
 }
@@ -49,6 +55,7 @@ cudaError_t launch_multi_c128_p35(int M, bool lines, const PassArgs* list, const
 cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
                          int64_t total, cudaStream_t s) {
     if (M < 0) return launch_mix_multi(esize, -M, lines, list, starts, n, total, s);  // mixed groups of size -M
+    if (is_mixed(M)) return launch_multi_mixc(esize, M, lines, list, starts, n, total, s);
     if (esize == 8)
         return (M % 2 == 0) ? launch_multi_c64_p2(M, lines, list, starts, n, total, s)
                             : launch_multi_c64_p35(M, lines, list, starts, n, total, s);
@@ -57,6 +64,7 @@ cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, con
 }
 
 int pass_kernel_supported(int M, int esize) {
+    if (is_mixed(M)) return mixed_compiled(M) && M <= kMixMmax ? 1 : 0;
     int b = base_of(M);
     if (b == 1 || M < 2) return 0;
     int m = M;

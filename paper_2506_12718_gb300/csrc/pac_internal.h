@@ -40,7 +40,13 @@ inline int group_w(const GroupPlan& g, int esize) { return g.mix_nr > 0 ? mix_w(
 struct Schedule {
     int cap = 0;
     bool plane = true;
-    bool mixed = false;  // stage lists of several prime bases: groups may span bases (runtime-radix kernel)
+    // stage lists of several prime bases: 1 groups may span bases, 0 they may not,
+    // -1 (the default) they do when every group spanning bases has a compiled kernel
+    int mixed = -1;
+    bool mix_runtime = false;  // groups spanning bases always in the runtime-radix kernel
+    // the plane pass' tile: CTAs per plane (1: a whole plane per CTA, K > 1: split over a
+    // K-CTA cluster); 0: the rule of plane_cluster
+    int plane_k = 0;
 };
 int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out);
 // the same from explicit per-axis DIF stage lists (radix: the label the plan reports; -1 = explicit)

@@ -247,7 +247,9 @@ static std::vector<std::pair<int, int>> split_mixed(const std::vector<int>& st) 
 // of the one-base kernels take one base): each maximal run of equal base is
 // split on its own (one run for a uniform radix).  With several bases and
 // sch.mixed, groups spanning bases (split_mixed) are taken instead when they
-// are fewer.
+// are fewer; by default (sch.mixed < 0) only when each of them has a compiled
+// kernel (mixed_compiled), since the runtime-radix kernel costs 2-3x a
+// compiled pass.
 static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st, int esize, const Schedule& sch) {
     std::vector<std::pair<int, int>> out;
     const int T = (int)st.size();
@@ -260,31 +262,27 @@ static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st,
         ++runs;
         i = j;
     }
-    if (runs > 1 && sch.mixed) {
+    if (runs > 1 && sch.mixed != 0) {
         std::vector<std::pair<int, int>> mixed = split_mixed(st);
-        if (mixed.size() < out.size()) return mixed;
+        bool take = mixed.size() < out.size();
+        if (take && sch.mixed < 0) {
+            for (auto [first, cnt] : mixed) {
+                int m = 1;
+                for (int k = 0; k < cnt; ++k) m *= st[first + k];
+                if (is_mixed(m) && (!mixed_compiled(m) || sch.mix_runtime)) take = false;
+            }
+        }
+        if (take) return mixed;
     }
     return out;
 }
 
-// Round radices of a mixed group of size M: each prime-power part of M split
-// into the fewest rounds of at most mix_rmax, evenly, then all sorted larger
-// first.  Returns the round count.
+// Round radices of a mixed group of size M for the runtime-radix kernel (the
+// rule of config.h, the same rounds a compiled mixed kernel runs).  Returns
+// the round count.
 static int mix_round_list(int M, int* r) {
-    int n = 0;
-    for (int p : {2, 3, 5}) {
-        int e = 0, m = M;
-        while (m % p == 0) {
-            m /= p;
-            ++e;
-        }
-        if (e == 0) continue;
-        int er = 0;
-        for (int v = mix_rmax(p); v > 1; v /= p) ++er;
-        const int nr = (e + er - 1) / er;
-        for (int k = 0; k < nr && n < kMixMaxRounds; ++k) r[n++] = ipow(p, e / nr + (k < e % nr ? 1 : 0));
-    }
-    std::sort(r, r + n, [](int x, int y) { return x > y; });
+    const int n = std::min(mixed_round_count(M), kMixMaxRounds);
+    for (int i = 0; i < n; ++i) r[i] = mixed_round_radix(M, i);
     return n;
 }
 
@@ -472,7 +470,7 @@ extern "C" int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dty
     }
     Schedule sch;
     sch.cap = cap;
-    sch.mixed = (flags & 1) != 0;
+    sch.mixed = (flags & 2) ? -1 : (flags & 1) ? 1 : 0;
     std::vector<GroupPlan> gr;
     if (int rc = form_groups(ndim, dims, st, dtype == PAC_C64 ? 8 : 16, sch, gr)) return rc;
     const int n = (int)gr.size();
@@ -508,7 +506,7 @@ extern "C" int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_d
     }
     Schedule sch;
     sch.cap = cap;
-    sch.mixed = (flags & 1) != 0;
+    sch.mixed = (flags & 2) ? -1 : (flags & 1) ? 1 : 0;
     std::vector<GroupPlan> gr;
     const int esize = dtype == PAC_C64 ? 8 : 16;
     if (int rc = form_groups(ndim, dims, st, esize, sch, gr)) return rc;
@@ -577,8 +575,9 @@ static int form_groups(int ndim, const int64_t* dims, const std::vector<std::vec
             for (int i = 1; i < cnt; ++i)
                 if (stage_base(stages[a][first + i]) != stage_base(stages[a][first])) one_base = false;
             if (!one_base) {
-                g.mix_nr = mix_round_list(g.M, g.mix_r);
                 if (g.M > kMixMmax) return fail(PAC_ERR_SIZE, "mixed group size %d above %d", g.M, kMixMmax);
+                // a compiled mixed kernel runs the config.h rounds (mix_nr = 0), else the runtime-radix kernel
+                if (!mixed_compiled(g.M) || sch.mix_runtime) g.mix_nr = mix_round_list(g.M, g.mix_r);
             } else if (!pass_kernel_supported(g.M, esize)) {
                 return fail(PAC_ERR_SIZE, "no pass kernel for group size %d", g.M);
             }
@@ -669,10 +668,15 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     }
 
     // groups, forward order: axis 0 (outermost) first, the contiguous axis last;
-    // PAC_MIXED=1 / 0 in the environment forces groups spanning prime bases on / off
+    // PAC_MIXED=1 / 0 in the environment forces groups spanning prime bases on / off,
+    // PAC_MIXED=rt on and every one of them in the runtime-radix kernel
     Schedule gs = sch;
     const char* me = std::getenv("PAC_MIXED");
-    if (me && (me[0] == '0' || me[0] == '1')) gs.mixed = me[0] == '1';
+    if (me && (me[0] == '0' || me[0] == '1')) gs.mixed = me[0] == '1' ? 1 : 0;
+    if (me && me[0] == 'r' && me[1] == 't') {
+        gs.mixed = 1;
+        gs.mix_runtime = true;
+    }
     if (int rc = form_groups(ndim, dims, pl->stages, pl->esize, gs, pl->groups)) {
         delete pl;
         return rc;
@@ -720,6 +724,8 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
             if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
             pl->plane_k = plane_cluster(pl->groups[G - 2].M, pl->groups[G - 1].M, pl->esize,
                                         pl->N / ((int64_t)pl->groups[G - 2].M * pl->groups[G - 1].M), dev);
+            if (sch.plane_k > 0 && plane_supported_k(pl->groups[G - 2].M, pl->groups[G - 1].M, pl->esize, sch.plane_k))
+                pl->plane_k = sch.plane_k;
         }
     }
     pl->uniform_m = 0;

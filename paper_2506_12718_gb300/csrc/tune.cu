@@ -1,8 +1,9 @@
 // Autotuner of pass schedules (pac_tune).
 //
 // A schedule fixes how many DIF stages one pass fuses (the largest group
-// size, as a cap on its exponent) and whether the last two axes may run as
-// one plane pass.  Large groups mean few passes over HBM but narrow tiles
+// size, as a cap on its exponent), whether the last two axes may run as one
+// plane pass, and the plane pass' tile (a whole plane per CTA or a plane split
+// over a K-CTA cluster).  Large groups mean few passes over HBM but narrow tiles
 // and few resident CTAs; small groups the opposite, so the best choice
 // depends on the shape and the GPU and is measured, not guessed: every
 // candidate that gives a different split is built, run on scratch data and
@@ -11,7 +12,8 @@
 // the candidates also include one-base groups only against groups spanning
 // bases.  With PAC_TUNE_FILE set, schedules persist in that file as lines
 // "ndim n0 n1 n2 radix dtype cap flags us", flags bit 0 = plane pass allowed,
-// bit 1 = groups may not span bases.
+// bit 1 = groups may not span bases, bits 4-7 = CTAs per plane (0: the
+// default rule).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -76,6 +78,7 @@ void load_file_locked() {
         t.sch.cap = cap;
         t.sch.plane = (plane & 1) != 0;
         t.sch.mixed = (plane & 2) == 0;
+        t.sch.plane_k = (plane >> 4) & 15;
         t.us = us;
         g_tuned[k] = t;  // later lines win
     }
@@ -88,7 +91,8 @@ void append_file(const Key& k, const Tuned& t) {
     FILE* f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f, "%d %lld %lld %lld %d %d %d %d %.3f\n", k.ndim, (long long)k.d[0], (long long)k.d[1],
-                 (long long)k.d[2], k.radix, k.dtype, t.sch.cap, (t.sch.plane ? 1 : 0) | (t.sch.mixed ? 0 : 2), t.us);
+                 (long long)k.d[2], k.radix, k.dtype, t.sch.cap,
+                 (t.sch.plane ? 1 : 0) | (t.sch.mixed ? 0 : 2) | ((t.sch.plane_k & 15) << 4), t.us);
     std::fclose(f);
 }
 
@@ -157,13 +161,26 @@ extern "C" int pac_tune(int ndim, const int64_t* dims, int radix, pac_dtype dtyp
                 sch.mixed = mixed != 0;
                 pac_plan p = nullptr;
                 if (plan_build(ndim, dims, radix, dtype, sch, &p) != PAC_OK) continue;
-                std::vector<int> sig;  // the resulting pass structure
-                for (const GroupPlan& g : p->groups) sig.push_back(g.mix_nr > 0 ? -g.M : g.M);
-                sig.push_back(p->plane ? -p->plane_k : 0);
+                // the plane tile: every supported split of the plane (0 = the default rule first)
+                std::vector<int> ks = {0};
+                if (p->plane) {
+                    const int m1 = p->groups[p->plane_g1].M, m2 = p->groups[p->plane_g1 + 1].M;
+                    for (int k = 1; k <= 5; ++k)
+                        if (plane_supported_k(m1, m2, p->esize, k)) ks.push_back(k);
+                }
                 pac_plan_destroy(p);
-                if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
-                seen.push_back(sig);
-                cands.push_back(sch);
+                for (int k : ks) {
+                    Schedule sk = sch;
+                    sk.plane_k = k;
+                    if (plan_build(ndim, dims, radix, dtype, sk, &p) != PAC_OK) continue;
+                    std::vector<int> sig;  // the resulting pass structure
+                    for (const GroupPlan& g : p->groups) sig.push_back(g.mix_nr > 0 ? -g.M : g.M);
+                    sig.push_back(p->plane ? -p->plane_k : 0);
+                    pac_plan_destroy(p);
+                    if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+                    seen.push_back(sig);
+                    cands.push_back(sk);
+                }
             }
         }
     }

@@ -167,12 +167,19 @@ def test_prime_factor_object_rejects_bad_lengths_before_touching_the_device(n, s
     ((1 << 20,), 4, 0, False, 0, [(0, 1024, [16, 8, 8]), (0, 1024, [16, 8, 8])]),
     ((1 << 20,), 4, 0, False, 9, [(0, 64, [8, 8]), (0, 64, [8, 8]), (0, 256, [16, 16])]),  # a schedule's cap
     ((4096,), 2, 1, False, 0, [(0, 64, [8, 8]), (0, 64, [8, 8])]),     # FP64 groups stop at 2048
-    ((1000,), 0, 0, False, 0, [(0, 8, [8]), (0, 125, [25, 5])]),       # one-base groups (default)
+    ((1000,), 0, 0, False, 0, [(0, 8, [8]), (0, 125, [25, 5])]),       # one-base groups (PAC_MIXED=0)
     ((1000,), 0, 0, True, 0, [(0, 1000, [25, 8, 5])]),                 # one group spanning bases
     ((6000,), 0, 0, False, 0, [(0, 16, [16]), (0, 3, [3]), (0, 125, [25, 5])]),
     ((6000,), 0, 0, True, 0, [(0, 48, [16, 3]), (0, 125, [25, 5])]),
     ((2 ** 10 * 3 ** 5 * 5 ** 3,), 0, 0, True, 0,                       # spanning bases would not be fewer
      [(0, 1024, [16, 8, 8]), (0, 243, [27, 9]), (0, 125, [25, 5])]),
+    # the default rule: groups spanning bases where each has a compiled kernel (48, 120, 1000 points)
+    ((1000,), 0, 0, None, 0, [(0, 1000, [25, 8, 5])]),
+    ((1000,), 0, 1, None, 0, [(0, 1000, [25, 8, 5])]),
+    ((6000,), 0, 0, None, 0, [(0, 48, [16, 3]), (0, 125, [25, 5])]),
+    ((120, 120), 0, 0, None, 0, [(0, 120, [8, 5, 3]), (1, 120, [8, 5, 3])]),
+    ((360,), 0, 0, None, 0, [(0, 8, [8]), (0, 9, [9]), (0, 5, [5])]),   # 360 has no compiled kernel
+    ((360,), 0, 0, True, 0, [(0, 360, [9, 8, 5])]),
 ])
 def test_plan_groups(dims, radix, dtype, mixed, cap, want):
     """The pass schedule rules, pinned on the host: one-base runs split evenly
@@ -184,7 +191,7 @@ def test_plan_groups(dims, radix, dtype, mixed, cap, want):
 @pytest.mark.parametrize("dims", [(30,), (360, 360), (12, 20, 30), (6000, 6000), (2 ** 7 * 3 ** 4 * 5 ** 2,), (64, 81, 25),
                                   (2, 3, 5), (1, 1000), (4 * 27 * 125,), (3 ** 7 * 2,)])
 @pytest.mark.parametrize("dtype", [0, 1])
-@pytest.mark.parametrize("mixed", [False, True])
+@pytest.mark.parametrize("mixed", [False, True, None])
 def test_plan_groups_invariants(dims, dtype, mixed):
     """Any 2^a 3^b 5^c shape: per axis the group sizes multiply to the dim,
     each group's rounds multiply to its size and are radices the kernels have,
@@ -202,7 +209,9 @@ def test_plan_groups_invariants(dims, dtype, mixed):
         if len(bases) == 1:
             assert m <= limits[bases.pop()]
         else:
-            assert mixed and m <= 2048
+            assert mixed is not False and m <= 2048
+            if mixed is None:  # the default rule forms only groups with compiled kernels
+                assert m in (48, 120, 1000)
     assert len(groups) <= len(pac.pac_plan_groups(dims, 0, dtype, False))
 
 

@@ -368,7 +368,7 @@ def test_ordered_fft_is_the_dft(dims, radix, dtype):
 MIXED_SHAPES = [((30,), "c128"), ((360,), "c64"), ((1000,), "c128"), ((2700,), "c64"), ((6000,), "c64"),
                 ((12, 20), "c128"), ((60, 90), "c64"), ((100, 120), "c128"), ((250, 48), "c64"), ((1, 45), "c64"),
                 ((6, 10, 15), "c128"), ((12, 20, 30), "c64"), ((40, 36, 50), "c64"), ((96, 2, 2), "c128"),
-                ((1000, 1000), "c64")]
+                ((1000, 1000), "c64"), ((48, 1000), "c128"), ((120, 120, 120), "c64")]
 
 
 @pytest.mark.parametrize("dims,dtype", MIXED_SHAPES, ids=[f"{'x'.join(map(str, d))}-{t}" for d, t in MIXED_SHAPES])
@@ -385,20 +385,22 @@ def test_mixed_radix_plans(dims, dtype):
                          [((1000, 1000), "c64", 3, 7), ((120, 120, 120), "c64", 5, 17), ((60, 90), "c128", 3, 11),
                           ((6000,), "c64", 3, 5), ((30,), "c128", 1, 5), ((72, 75), "c64", 3, 7)])
 def test_mixed_groups_against_one_base_groups(dims, dtype, mixed_launches, onebase_launches, monkeypatch):
-    """Groups spanning prime bases (the runtime-radix kernel, PAC_MIXED=1)
-    against one-base groups (the default, PAC_MIXED=0): fewer launches, the
-    same convolution."""
+    """Groups spanning prime bases (compiled kernels where they exist,
+    PAC_MIXED=1; the runtime-radix kernel for all of them, PAC_MIXED=rt)
+    against one-base groups (PAC_MIXED=0): fewer launches, the same
+    convolution."""
     pac = pac_mod()
     fs, h, x = separable_case(dims, dtype, seed=3 * sum(dims))
     ref = oracle.conv_separable(fs, x)
     n = int(np.prod(dims))
-    monkeypatch.setenv("PAC_MIXED", "1")
-    plan = pac.Plan(dims, 0, dtype)
-    try:
-        assert plan.query(pac.Q_LAUNCHES_CONVOLVE) == mixed_launches
-    finally:
-        plan.close()
-    check(gpu_conv(dims, 0, dtype, h, x), ref, dtype, n, f"mixed groups {dims}")
+    for mode in ("1", "rt"):
+        monkeypatch.setenv("PAC_MIXED", mode)
+        plan = pac.Plan(dims, 0, dtype)
+        try:
+            assert plan.query(pac.Q_LAUNCHES_CONVOLVE) == mixed_launches
+        finally:
+            plan.close()
+        check(gpu_conv(dims, 0, dtype, h, x), ref, dtype, n, f"mixed groups {dims} ({mode})")
     monkeypatch.setenv("PAC_MIXED", "0")
     plan = pac.Plan(dims, 0, dtype)
     try:
@@ -414,7 +416,7 @@ STAGE_ORDERS = [((60,), [[3, 4, 5]], "c128"), ((60,), [[5, 3, 2, 2]], "c128"), (
                 ((64, 48), [[16, 4], [16, 3]], "c64")]
 
 
-@pytest.mark.parametrize("mixed", ["0", "1"])
+@pytest.mark.parametrize("mixed", ["0", "1", "rt"])
 @pytest.mark.parametrize("dims,stages,dtype", STAGE_ORDERS,
                          ids=[f"{'x'.join(map(str, d))}-{'_'.join('.'.join(map(str, s)) for s in st)}-{t}"
                               for d, st, t in STAGE_ORDERS])
@@ -461,10 +463,11 @@ def test_mixed_radix_comparator_and_ordered_fft(dims, dtype):
         plan.close()
 
 
-@pytest.mark.parametrize("mixed", ["0", "1"])
+@pytest.mark.parametrize("mixed", ["0", "1", "rt"])
 def test_mixed_radix_in_a_batch(mixed, monkeypatch):
     """Mixed-radix plans merged with uniform-radix ones in one pac_convolve_many
-    call (with groups spanning bases: the batched runtime-radix kernel)."""
+    call (with groups spanning bases: the batched compiled mixed kernels, or
+    the batched runtime-radix kernel with PAC_MIXED=rt)."""
     monkeypatch.setenv("PAC_MIXED", mixed)
     pac = pac_mod()
     cases = [((60, 90), 0), ((1000,), 0), ((64, 64), 4), ((360,), 0), ((1000,), 0)]
@@ -771,6 +774,43 @@ def test_tune_file_round_trip(tmp_path):
     out = subprocess.run([sys.executable, "-c", code2], env=env, check=True, capture_output=True, text=True,
                          cwd=os.path.dirname(os.path.dirname(__file__)))
     assert int(out.stdout.strip().splitlines()[-1]) == int(line[6])
+
+
+def test_tuner_chooses_the_plane_tile(tmp_path):
+    """The tuner's candidates include the plane pass' tile: a whole 81 x 81
+    plane per CTA or the plane split over a 3-CTA cluster.  The tune file
+    records the split (flags bits 4-7, 0 = the default rule), a later plan
+    uses it, and its convolution matches the oracle."""
+    import subprocess
+    import sys
+    path = tmp_path / "tune.txt"
+    env = dict(os.environ, PAC_TUNE_FILE=str(path))
+    root = os.path.dirname(os.path.dirname(__file__))
+    code1 = ("import paper_2506_12718_gb300 as pac; pac.load(); import torch; torch.cuda.init(); "
+             "print(pac.pac_tune((81, 81), 3, 'c64', 3))")
+    subprocess.run([sys.executable, "-c", code1], env=env, check=True, cwd=root)
+    line = path.read_text().split()
+    assert len(line) == 9 and line[1] == "81"
+    k = (int(line[7]) >> 4) & 15
+    code2 = ("import paper_2506_12718_gb300 as pac; pac.load(); import torch; torch.cuda.init(); "
+             "p = pac.Plan((81, 81), 3, 'c64'); print(p.query(pac.Q_PLANE)); p.close()")
+    out = subprocess.run([sys.executable, "-c", code2], env=env, check=True, capture_output=True, text=True, cwd=root)
+    plane = int(out.stdout.strip().splitlines()[-1])
+    assert plane in (1, 3) and (k == 0 or plane == k)
+    fs, h, x = separable_case((81, 81), "c64", seed=181)
+    ref = oracle.conv_separable(fs, x)
+    pac = pac_mod()
+    for forced in (1, 3):  # both tiles give the convolution
+        os.environ["PAC_PLANE_K"] = str(forced)
+        try:
+            plan = pac.Plan((81, 81), 3, "c64")
+            try:
+                assert plan.query(pac.Q_PLANE) == forced
+            finally:
+                plan.close()
+            check(gpu_conv((81, 81), 3, "c64", h, x), ref, "c64", 81 * 81, f"plane tile {forced}")
+        finally:
+            del os.environ["PAC_PLANE_K"]
 
 
 def test_tune_search_at_plan_creation_and_plan_log():
