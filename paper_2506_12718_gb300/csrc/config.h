@@ -190,18 +190,6 @@ constexpr int plane_pad(int m1, int m2, int esize) {
 }
 constexpr int plane_pitch(int m1, int m2, int esize) { return m2 + plane_pad(m1, m2, esize); }
 constexpr int plane_smem_bytes(int m1, int m2, int esize) { return m1 * plane_pitch(m1, m2, esize) * esize; }
-// Complex FP32 planes of at least 64 x 64 powers of two in one CTA use an
-// XOR-swizzled, unpadded buffer instead: no plain pitch serves both the
-// column-fastest rounds (a half-warp on 16 consecutive lines) and the
-// line-fastest rounds next to global memory (8 consecutive positions of two
-// lines), the swizzle makes both conflict-free (a bank model of every round
-// of these shapes).
-constexpr bool plane_swizzle(int m1, int m2, int esize, int k) {
-    return esize == 8 && k == 1 && base_of(m1) == 2 && base_of(m2) == 2 && m1 >= 64 && m2 >= 64;
-}
-constexpr int plane_pitch_k(int m1, int m2, int esize, int k) {
-    return plane_swizzle(m1, m2, esize, k) ? m2 : plane_pitch(m1, m2, esize);
-}
 // threads of a plane CTA (K CTAs per plane): the larger first-round task count
 constexpr int plane_threads(int m1, int m2, int esize, int k) {
     return clampi((((m1 / k * (m2 / round_radix(m2, esize, 0)) > m2 / k * (m1 / round_radix(m1, esize, 0))

@@ -159,11 +159,44 @@ template <int B, bool INV, typename V> __device__ __forceinline__ void dft_sc(V*
     }
 }
 
+// Complex FP32 power-of-two sizes keep plain twiddles: their pass kernels run
+// at 64 registers a thread, and the factored form's stage-2 constants (kept
+// in registers across a tile's tasks) cost them spills that outweigh the two
+// instructions a twiddle saves (measured on 128^3 FP32: 38 -> 41 us).
+template <typename V, int R> constexpr bool plain_twiddles() {
+    return sizeof(V) == 8 && (R == 8 || R == 16 || R == 32);
+}
+__host__ __device__ constexpr int root32_off(int r) {
+    return r == 8 ? PAC_ROOT32_OFF_8 : r == 16 ? PAC_ROOT32_OFF_16 : r == 32 ? PAC_ROOT32_OFF_32 : -1;
+}
+
+// z * w_R^e (forward) or z * conj(w_R^e) (inverse), complex FP32; e and R are
+// compile-time constants after unrolling, so the special cases fold away.
+template <int R, bool INV> __device__ __forceinline__ float2 twiddle_root32(float2 z, int e) {
+    e %= R;
+    if (e == 0) return z;
+    if ((8 * e) % R == 0) {
+        const float h = 0.70710678118654752440f;
+        switch (INV ? (8 - (8 * e) / R) : (8 * e) / R) {  // multiply by exp(-2 pi i o / 8)
+            case 1: return float2{(z.x + z.y) * h, (z.y - z.x) * h};
+            case 2: return mul_mi(z);
+            case 3: return float2{(z.y - z.x) * h, -(z.x + z.y) * h};
+            case 4: return float2{-z.x, -z.y};
+            case 5: return float2{-(z.x + z.y) * h, (z.x - z.y) * h};
+            case 6: return mul_pi(z);
+            default: return float2{(z.x - z.y) * h, (z.x + z.y) * h};
+        }
+    }
+    const float2 w = c_roots32[root32_off(R) + e];
+    return INV ? cmulc(z, w) : cmul(z, w);
+}
+
 // In-register DFT of size R, natural order in and out: v[k] = sum_j v[j] w^{jk}
 // with w = exp(-2 pi i / R), or its conjugate (no scaling) when INV.
 // Composite R = A x B (B = small_factor(R)), decimation in frequency: B DFT_A
 // over stride B, the twiddles w_R^{b k1} in factored form, then A stage-2
-// DFT_B with the twiddles' real factors in their constants.
+// DFT_B with the twiddles' real factors in their constants.  Complex FP32
+// powers of two: DFT_4 over stride R/4, plain twiddles, then DFT_{R/4}.
 template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V* v) {
     if constexpr (R == 1) {
         return;
@@ -181,6 +214,27 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V* v)
         v[3] = csub(d0, r1);
     } else if constexpr (R == 3 || R == 5) {
         dft_sc<R, INV>(v, bfly_off(R) + (INV ? bfly_nc(R) : 0));
+    } else if constexpr (plain_twiddles<V, R>()) {
+        constexpr int A = 4;
+        constexpr int B = R / A;
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            V z[A];
+#pragma unroll
+            for (int a = 0; a < A; ++a) z[a] = v[b + B * a];
+            dft<A, INV>(z);
+#pragma unroll
+            for (int k1 = 0; k1 < A; ++k1) v[b + B * k1] = twiddle_root32<R, INV>(z[k1], b * k1);
+        }
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) dft<B, INV>(v + B * k1);
+        V t[R];
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1)
+#pragma unroll
+            for (int k2 = 0; k2 < B; ++k2) t[k1 + A * k2] = v[B * k1 + k2];
+#pragma unroll
+        for (int e = 0; e < R; ++e) v[e] = t[e];
     } else {
         constexpr int B = small_factor(R);
         constexpr int A = R / B;
@@ -266,21 +320,13 @@ template <typename V, int M, bool LINES = false> struct Shape {
 // batched kernel), each running its own tile: task numbering uses the
 // thread's index within its unit, and rounds synchronise the unit with a
 // named barrier instead of the whole CTA.
-// SWZ: the buffer is an XOR-swizzled plane (plane_swizzle in config.h): the
-// element at (line i1, position i2) of a plane sits at i1 * P + (i2 ^ g(i1)),
-// g(i1) = ((i1 & 1) << 3) | ((i1 >> 1) & 7), a permutation inside each aligned
-// group of 16 elements; for axis d-1 (RS = 1) the row is i2 and the column i1,
-// for axis d-2 the row is i1 and the column i2.
-template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int KS_ = 1, bool SPLIT_ = false,
-          bool SWZ_ = false>
+template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int KS_ = 1, bool SPLIT_ = false>
 struct Geo {
     using V = V_;
     static constexpr int M = M_, W = W_, NT = NT_, RS = RS_, WS = WS_, ES = (int)sizeof(V_), KS = KS_;
     static constexpr int NR = round_count(M_, ES);
     static constexpr bool PF = PF_;
     static constexpr bool SPLIT = SPLIT_;
-    static constexpr bool SWZ = SWZ_;
-    static_assert(!SWZ_ || KS_ == 1, "swizzled planes are single-CTA");
     __device__ __forceinline__ static int tid() { return SPLIT_ ? (int)(threadIdx.x % NT_) : (int)threadIdx.x; }
 };
 // the pass kernels' geometry: a tile of W columns, buffer [row][w] of pitch
@@ -404,29 +450,18 @@ __device__ __forceinline__ uint32_t dsmem_addr(const TileCtx<typename GEO::V>& c
     return b + (uint32_t)(((row - part * H) * GEO::RS + (w + c.wofs) * GEO::WS) * GEO::ES);
 }
 
-// buffer index of element (row, w) of a single-CTA geometry
-__device__ __forceinline__ int swz_g(int i) { return ((i & 1) << 3) | ((i >> 1) & 7); }
-template <typename GEO> __device__ __forceinline__ int sidx(int row, int w) {
-    if constexpr (!GEO::SWZ)
-        return row * GEO::RS + w * GEO::WS;
-    else if constexpr (GEO::RS == 1)
-        return w * GEO::WS + (row ^ swz_g(w));
-    else
-        return row * GEO::RS + (w ^ swz_g(row));
-}
-
 // Element (row, w) of a round's exchange buffer.
 template <typename GEO>
 __device__ __forceinline__ typename GEO::V sld(const TileCtx<typename GEO::V>& c, int row, int w) {
     if constexpr (GEO::KS == 1)
-        return c.s[sidx<GEO>(row, w)];
+        return c.s[row * GEO::RS + w * GEO::WS];
     else
         return ld_dsmem(dsmem_addr<GEO>(c, row, w), static_cast<typename GEO::V*>(nullptr));
 }
 template <typename GEO>
 __device__ __forceinline__ void sst(const TileCtx<typename GEO::V>& c, int row, int w, typename GEO::V v) {
     if constexpr (GEO::KS == 1)
-        c.s[sidx<GEO>(row, w)] = v;
+        c.s[row * GEO::RS + w * GEO::WS] = v;
     else
         st_dsmem(dsmem_addr<GEO>(c, row, w), v);
 }
@@ -826,12 +861,11 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, size
 // for axis d-2, transforming columns [k n2/K, (k+1) n2/K) over all rows.
 template <typename V, int M1, int M2, int K> struct PlaneShape {
     static constexpr int ES = sizeof(V);
-    static constexpr bool SWZ = plane_swizzle(M1, M2, ES, K);
-    static constexpr int P2 = plane_pitch_k(M1, M2, ES, K);
+    static constexpr int P2 = plane_pitch(M1, M2, ES);
     static constexpr int NT = plane_threads(M1, M2, ES, K);
-    static constexpr int SMEM = (M1 / K) * P2 * ES;
-    using G2 = Geo<V, M2, M1 / K, NT, 1, P2, true, 1, false, SWZ>;  // axis d-1: rows i2, columns = local lines
-    using G1 = Geo<V, M1, M2 / K, NT, P2, 1, true, K, false, SWZ>;  // axis d-2: rows i1 (split), columns i2
+    static constexpr int SMEM = plane_smem_bytes(M1 / K, M2, ES);
+    using G2 = Geo<V, M2, M1 / K, NT, 1, P2, true, 1>;  // axis d-1: rows i2, columns = local lines
+    using G1 = Geo<V, M1, M2 / K, NT, P2, 1, true, K>;  // axis d-2: rows i1 (split), columns i2
     static_assert(SMEM <= kPlaneSmemMax, "plane too large for one CTA");
     static_assert(M1 % K == 0 && M2 % K == 0, "the plane must split evenly");
     static_assert(K >= 1 && K <= kMaxClusterCtas, "CTAs per plane beyond the cluster address table");
@@ -841,12 +875,11 @@ template <typename V, int M1, int M2, int K> struct PlaneShape {
 // whole-CTA items, or with SPLIT its units of NT threads).
 template <typename V, int M1, int M2, int NT_, bool SPLIT = false> struct PlaneShapeNT {
     static constexpr int ES = sizeof(V);
-    static constexpr bool SWZ = plane_swizzle(M1, M2, ES, 1);
-    static constexpr int P2 = plane_pitch_k(M1, M2, ES, 1);
+    static constexpr int P2 = plane_pitch(M1, M2, ES);
     static constexpr int NT = NT_;
-    static constexpr int SMEM = M1 * P2 * ES;
-    using G2 = Geo<V, M2, M1, NT, 1, P2, true, 1, SPLIT, SWZ>;
-    using G1 = Geo<V, M1, M2, NT, P2, 1, true, 1, SPLIT, SWZ>;
+    static constexpr int SMEM = plane_smem_bytes(M1, M2, ES);
+    using G2 = Geo<V, M2, M1, NT, 1, P2, true, 1, SPLIT>;
+    using G1 = Geo<V, M1, M2, NT, P2, 1, true, 1, SPLIT>;
 };
 
 // forward rounds 0..NR-1, the first from global (natural rows), all results in shared memory

@@ -9,6 +9,10 @@
   DFT_B that consumes it.  c_tau
   holds tau of the forward root (the conjugate root has -tau), for every
   e < R of each split size R.
+* c_roots32: w_R^e itself for the complex FP32 power-of-two sizes R = 8, 16,
+  32, whose splits apply plain complex twiddles (the factored form's constant
+  operands cost those register-bound kernels more than the two saved
+  instructions).
 * c_bfly: the constants of each stage-2 DFT_B (B = 2, 3, 4, 5) with its
   inputs' sigma folded in (products and ratios of sigma with cos and sin of
   2 pi / B), per split R, stage-1 frequency k1 and direction; k1 = 0 (all
@@ -25,8 +29,12 @@ import decimal
 import struct
 
 RADICES = [3, 5, 8, 9, 16, 25, 27, 32]
+# FP32 sizes with plain complex twiddles between the stages of their split
+PLAIN32_RADICES = [8, 16, 32]
 # in-register sizes with a stage-1 / stage-2 split, and the plain prime kernels
 BFLY_RADICES = [3, 5, 8, 9, 16, 25, 27, 32]
+# FP32 sizes with plain complex twiddles between the stages of their split
+PLAIN32_RADICES = [8, 16, 32]
 
 D = decimal.Decimal
 CTX = decimal.Context(prec=60)
@@ -154,7 +162,7 @@ def main():
         taus += [factored(e, r, False)[1] for e in range(r)]
     boffs, bvals = bfly_table()
     print("// Generated by gen_roots.py -- do not edit.")
-    print("// Factored twiddles (tau) and stage-2 butterfly constants of the in-register DFT splits,")
+    print("// Factored twiddles (tau), stage-2 butterfly constants and FP32 roots of the in-register DFT splits,")
     print("// computed in 60-digit decimal arithmetic, rounded once to FP64 and FP64 rounded once to FP32.")
     print("#pragma once")
     for r in RADICES:
@@ -163,11 +171,22 @@ def main():
     for r in BFLY_RADICES:
         print(f"#define PAC_BFLY_OFF_{r} {boffs[r]}")
     print(f"#define PAC_BFLY_COUNT {len(bvals)}")
+    roffs, roots = {}, []
+    for r in PLAIN32_RADICES:
+        roffs[r] = len(roots)
+        roots += [cos_sin(e, r) for e in range(r)]
+    for r in PLAIN32_RADICES:
+        print(f"#define PAC_ROOT32_OFF_{r} {roffs[r]}")
+    print(f"#define PAC_ROOT32_COUNT {len(roots)}")
     print("static __constant__ double c_tau64[PAC_TAU_COUNT] = {")
     print(",\n".join(f"    {hexd(t)}" for t in taus))
     print("};")
     print("static __constant__ float c_tau32[PAC_TAU_COUNT] = {")
     print(",\n".join(f"    {f32(float(t)).hex()}f" for t in taus))
+    print("};")
+    # w = cos - i sin, FP64 rounded once to FP32
+    print("static __constant__ float2 c_roots32[PAC_ROOT32_COUNT] = {")
+    print(",\n".join(f"    {{{f32(float(c)).hex()}f, {f32(-float(sn)).hex()}f}}" for c, sn in roots))
     print("};")
     print("static __constant__ double c_bfly64[PAC_BFLY_COUNT] = {")
     print(",\n".join(f"    {hexd(v)}" for v in bvals))

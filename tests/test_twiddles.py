@@ -152,6 +152,26 @@ def parse_roots_h(text):
             boff, arr("c_bfly64[PAC_BFLY_COUNT]"), arr("c_bfly32[PAC_BFLY_COUNT]"))
 
 
+def parse_roots32(text):
+    """offsets and values of the plain FP32 root table (power-of-two splits)"""
+    roff = {int(r): int(o) for r, o in re.findall(r"#define PAC_ROOT32_OFF_(\d+) (\d+)", text)}
+    body = text.split("c_roots32[PAC_ROOT32_COUNT] = {")[1].split("};")[0]
+    pairs = re.findall(r"\{(\S+)f, (\S+)f\}", body)
+    return roff, np.array([complex(float.fromhex(a), float.fromhex(b)) for a, b in pairs])
+
+
+def test_fp32_root_table_is_the_roots_rounded_once():
+    with open(os.path.join(CSRC, "roots.h")) as f:
+        roff, r32 = parse_roots32(f.read())
+    assert sorted(roff) == [8, 16, 32] and len(r32) == 8 + 16 + 32
+    for R, off in roff.items():
+        for e in range(R):
+            c, im = exact_root(e, R)
+            for got, want in ((r32[off + e].real, c), (r32[off + e].imag, im)):
+                # the exact value rounded to FP64, then once to FP32
+                assert got == float(np.float32(float(want))), (R, e, got, float(want))
+
+
 def header():
     with open(os.path.join(CSRC, "roots.h")) as f:
         return parse_roots_h(f.read())
@@ -250,7 +270,8 @@ def test_bfly_table_is_exact_and_rounded_once():
     assert np.array_equal(b32, b64.astype(np.float32).astype(np.float64))
 
 
-# ---- a numpy model of the kernels' in-register DFT (fft_device.cuh: dft, dft_sc, tw_factored)
+# ---- a numpy model of the kernels' in-register DFT (fft_device.cuh: dft, dft_sc, tw_factored,
+# and the plain-twiddle split of complex FP32 powers of two)
 
 
 def form_c(e, R):
@@ -258,9 +279,26 @@ def form_c(e, R):
     return f <= R or f >= 3 * R
 
 
-def model_dft(v, R, inv, tabs, dt):
-    """The kernels' in-register DFT_R of the vector v, step for step, with the table constants"""
+def model_dft(v, R, inv, tabs, dt, roots32=None):
+    """The kernels' in-register DFT_R of the vector v, step for step, with the table constants
+    (complex FP32 powers of two 8, 16, 32: DFT_4 over stride R/4, plain twiddles from roots32)"""
     toff, t, boff, b = tabs
+    if roots32 is not None and R in (8, 16, 32):
+        roff, r32 = roots32
+        A, B = 4, R // 4
+        w = np.empty(R, dtype=v.dtype)
+        for bb in range(B):
+            z = model_dft(v[bb::B][:A], A, inv, tabs, dt, roots32)
+            for k1 in range(A):
+                e = (bb * k1) % R
+                tw = r32[roff[R] + e]
+                w[bb + B * k1] = z[k1] * (np.conj(tw) if inv else tw)
+        out = np.empty(R, dtype=v.dtype)
+        for k1 in range(A):
+            y = model_dft(w[B * k1:B * k1 + B], B, inv, tabs, dt, roots32)
+            for k2 in range(B):
+                out[k1 + A * k2] = y[k2]
+        return out
     if R == 1:
         return v.copy()
     if R == 2:
@@ -275,7 +313,7 @@ def model_dft(v, R, inv, tabs, dt):
     A = R // B
     w = np.empty(R, dtype=v.dtype)
     for bb in range(B):
-        z = model_dft(v[bb::B][:A], A, inv, tabs, dt)
+        z = model_dft(v[bb::B][:A], A, inv, tabs, dt, roots32)
         for k1 in range(A):
             e = (bb * k1) % R
             if (4 * e) % R == 0:
@@ -321,19 +359,22 @@ def model_dft_sc(u, B, inv, b, off, dt):
 @pytest.mark.parametrize("inv", [False, True])
 def test_in_register_dft_model_is_the_dft(R, inv):
     toff, t64, t32, boff, b64, b32 = header()
+    with open(os.path.join(CSRC, "roots.h")) as f:
+        roots32 = parse_roots32(f.read())
     rng = np.random.default_rng(R + 100 * inv)
     j = np.arange(R)
     F = np.exp((2j if inv else -2j) * np.pi * np.outer(j, j) / R)  # the DFT matrix (conjugate when inv)
-    for tabs, dt, cdt, tol in (((toff, t64, boff, b64), np.float64, np.complex128, 4e-15),
-                               ((toff, t32, boff, b32), np.float32, np.complex64, 2.5e-6)):
+    for tabs, dt, cdt, tol, r32 in (((toff, t64, boff, b64), np.float64, np.complex128, 4e-15, None),
+                                    ((toff, t32, boff, b32), np.float32, np.complex64, 2.5e-6, roots32),
+                                    ((toff, t32, boff, b32), np.float32, np.complex64, 2.5e-6, None)):
         for _ in range(4):
             x = (rng.standard_normal(R) + 1j * rng.standard_normal(R)).astype(cdt)
-            got = model_dft(x, R, inv, tabs, dt)
+            got = model_dft(x, R, inv, tabs, dt, r32)
             want = F @ x.astype(np.complex128)
             assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want) * np.log2(R), (R, inv, dt)
         # every basis vector: a wrong constant anywhere shows
         for k in range(R):
             x = np.zeros(R, dtype=cdt)
             x[k] = 1
-            got = model_dft(x, R, inv, tabs, dt)
+            got = model_dft(x, R, inv, tabs, dt, r32)
             assert np.allclose(got, F[:, k], atol=tol * 8 * R), (R, inv, k)
