@@ -134,6 +134,21 @@ constexpr int tile_pad(int m, int esize, bool lines) {
         default: return 0;
     }
 }
+// Row swizzle of the exchange buffer of base-2 groups with tiles of 32 bytes a
+// row (4 FP32 or 2 FP64 columns, M >= 1024 points).  In their last
+// round (block length R, one task per R consecutive rows) a half-warp spans
+// four tasks whose rows lie 32 bytes x R apart, all on the same banks, and no
+// pitch separates them (a bank model of every round: 1.75x the wavefronts for
+// 1024-4096 points); storing row r at r ^ ((r >> log2 R) & 3) puts them on four
+// bank groups and keeps every other round's accesses within aligned groups of
+// four rows.  Returns log2 R, or 0 for no swizzle.
+constexpr int tile_row_swizzle(int m, int esize) {
+    return (!is_mixed(m) && base_of(m) == 2 && round_count(m, esize) >= 2 && tile_w(m, esize) * esize <= 32 &&
+            round_radix(m, esize, round_count(m, esize) - 1) >= 4)
+               ? ilog(round_radix(m, esize, round_count(m, esize) - 1), 2)
+               : 0;
+}
+
 // Row pitch of the exchange buffer in elements.
 constexpr int tile_pitch(int m, int esize, bool lines) { return tile_w(m, esize) + tile_pad(m, esize, lines); }
 constexpr int tile_elems(int m, int esize, bool lines) { return m * tile_pitch(m, esize, lines); }

@@ -320,19 +320,25 @@ template <typename V, int M, bool LINES = false> struct Shape {
 // batched kernel), each running its own tile: task numbering uses the
 // thread's index within its unit, and rounds synchronise the unit with a
 // named barrier instead of the whole CTA.
-template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int KS_ = 1, bool SPLIT_ = false>
+// RSW > 0: rows of the exchange buffer are stored swizzled, row r at
+// r ^ ((r >> RSW) & 3) (tile_row_swizzle in config.h).
+template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int KS_ = 1, bool SPLIT_ = false,
+          int RSW_ = 0>
 struct Geo {
     using V = V_;
     static constexpr int M = M_, W = W_, NT = NT_, RS = RS_, WS = WS_, ES = (int)sizeof(V_), KS = KS_;
     static constexpr int NR = round_count(M_, ES);
     static constexpr bool PF = PF_;
     static constexpr bool SPLIT = SPLIT_;
+    static constexpr int RSW = RSW_;
+    static_assert(RSW_ == 0 || KS_ == 1, "row swizzle in single-CTA tiles only");
     __device__ __forceinline__ static int tid() { return SPLIT_ ? (int)(threadIdx.x % NT_) : (int)threadIdx.x; }
 };
 // the pass kernels' geometry: a tile of W columns, buffer [row][w] of pitch
 // P; several CTAs per SM hide latency, so registers are not spent on prefetch
 template <typename V, int M, bool LINES>
-using PassGeo = Geo<V, M, Shape<V, M, LINES>::W, Shape<V, M, LINES>::NT, Shape<V, M, LINES>::P, 1, false>;
+using PassGeo = Geo<V, M, Shape<V, M, LINES>::W, Shape<V, M, LINES>::NT, Shape<V, M, LINES>::P, 1, false, 1, false,
+                    tile_row_swizzle(M, sizeof(V))>;
 
 // Task tau of round RI: column w of the tile, offset jp inside its block of
 // S rows, first row row0 = block * S + jp; the task transforms rows
@@ -450,18 +456,26 @@ __device__ __forceinline__ uint32_t dsmem_addr(const TileCtx<typename GEO::V>& c
     return b + (uint32_t)(((row - part * H) * GEO::RS + (w + c.wofs) * GEO::WS) * GEO::ES);
 }
 
+// buffer row of tile row `row` (the row swizzle of tile_row_swizzle)
+template <typename GEO> __device__ __forceinline__ int srow(int row) {
+    if constexpr (GEO::RSW > 0)
+        return row ^ ((row >> GEO::RSW) & 3);
+    else
+        return row;
+}
+
 // Element (row, w) of a round's exchange buffer.
 template <typename GEO>
 __device__ __forceinline__ typename GEO::V sld(const TileCtx<typename GEO::V>& c, int row, int w) {
     if constexpr (GEO::KS == 1)
-        return c.s[row * GEO::RS + w * GEO::WS];
+        return c.s[srow<GEO>(row) * GEO::RS + w * GEO::WS];
     else
         return ld_dsmem(dsmem_addr<GEO>(c, row, w), static_cast<typename GEO::V*>(nullptr));
 }
 template <typename GEO>
 __device__ __forceinline__ void sst(const TileCtx<typename GEO::V>& c, int row, int w, typename GEO::V v) {
     if constexpr (GEO::KS == 1)
-        c.s[row * GEO::RS + w * GEO::WS] = v;
+        c.s[srow<GEO>(row) * GEO::RS + w * GEO::WS] = v;
     else
         st_dsmem(dsmem_addr<GEO>(c, row, w), v);
 }

@@ -93,7 +93,8 @@ __device__ __forceinline__ void group_tile(const PassArgs& a, uint32_t t, float2
 }
 
 template <int M, bool LINES, int NT, bool SPLIT>
-using PGeo = Geo<float2, M, tile_w(M, 8), NT, tile_pitch(M, 8, LINES), 1, SPLIT && kPersistPrefetch, 1, SPLIT>;
+using PGeo = Geo<float2, M, tile_w(M, 8), NT, tile_pitch(M, 8, LINES), 1, SPLIT && kPersistPrefetch, 1, SPLIT,
+                 tile_row_swizzle(M, 8)>;
 
 // one item of shape I
 template <int I>
