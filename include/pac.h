@@ -131,9 +131,16 @@ int pac_filter_spectrum(pac_plan p, const void* h_dev);
 int pac_convolve(pac_plan p, const void* x_dev, void* y_dev, void* stream);
 
 /*
- * As pac_convolve, with x and y in HOST memory: copies x to plan-owned
- * device staging, convolves, copies y back, all on `stream`, then
- * synchronises `stream`.  The end-to-end form of the call.
+ * As pac_convolve, with x and y in HOST memory (pinned for asynchronous
+ * copies): copies x to plan-owned device staging, convolves, copies y back,
+ * then synchronises `stream`.  The end-to-end form of the call.  For arrays
+ * of 64 MiB and more whose first pass is a rows pass of axis 0 with enough
+ * tiles (2-D and 3-D plans, 1-D plans of several groups), the copies run in
+ * 8 column blocks of that pass on two plan-owned copy streams: block k + 1
+ * comes in while the first pass works on block k, and block k goes out
+ * while the last pass works on block k + 1 (the plan's device work stays on
+ * `stream`, which waits for the copies in through events).  Errors:
+ * PAC_ERR_ARG, PAC_ERR_NO_SPECTRUM, PAC_ERR_NOMEM, PAC_ERR_CUDA.
  */
 int pac_convolve_host(pac_plan p, const void* x_host, void* y_host, void* stream);
 

@@ -813,7 +813,7 @@ __device__ __forceinline__ void run_phase(const PassArgs& a, V* s) {
     ctx_init(c, a, s);
     const uint32_t tiles = (uint32_t)a.tiles;
     for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        tile_setup<V, M, LINES>(c, a, t);
+        tile_setup<V, M, LINES>(c, a, (uint32_t)a.tile0 + t);
         tile_run<V, M, LINES>(c, a.mode);
         __syncthreads();  // the next tile reuses the exchange buffer
     }

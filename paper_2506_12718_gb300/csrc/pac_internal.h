@@ -142,7 +142,9 @@ struct pac_plan_s {
     void* d_scratch = nullptr;    // N elements
     int64_t* d_perm = nullptr;    // per axis: [pos_to_freq | freq_to_pos], 2 * dims[a] each
     // host-buffer convolution staging, created on first use
-    void* d_stage = nullptr;      // 2 N elements
+    void* d_stage = nullptr;      // N elements
+    cudaStream_t h2d = nullptr, d2h = nullptr;  // copy streams of the pipelined host-buffer call
+    std::vector<cudaEvent_t> chunk_ev;          // its events (2 per column block)
     std::mutex mu;
     size_t device_bytes = 0;
 

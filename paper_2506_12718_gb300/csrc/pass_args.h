@@ -23,7 +23,8 @@ struct PassArgs {
     int64_t Q;              // columns
     int64_t C;              // row stride in elements
     int64_t I;              // inner stride of the axis: column j = (q mod C) / I
-    int64_t tiles;          // ceil(Q / W)
+    int64_t tiles;          // tiles of this launch: ceil(Q / W) for a whole pass
+    int64_t tile0;          // first tile of this launch (0; > 0 when a pass runs in column blocks)
     int tw_T;               // two-level split of the external exponent e = hi * T + lo
     int tw_shift;           // log2(tw_T) when tw_T is a power of two, else -1
     int mode;               // PassMode
