@@ -169,13 +169,16 @@ constexpr int pass_threads(int m, int esize) {
 
 // Register budget per thread the kernel is compiled for: enough for the
 // largest in-register round without spilling, small enough to keep several
-// CTAs resident.
+// CTAs resident.  Complex FP64 3125-point groups fit 168 registers (three
+// 128-thread CTAs per SM; measured 3.38 -> 3.36 ms on 3125^2, a shorter last
+// wave of the 3125 one-column tiles); smaller FP64 groups with 25-point
+// rounds spill at 168.
 constexpr int max_round_radix(int m, int esize) { return round_radix(m, esize, 0); }  // rounds are sorted, largest first
 constexpr int reg_target(int m, int esize) {
     return esize == 8
                ? (max_round_radix(m, esize) >= 25 ? (two_ctas_per_sm(m, esize) ? 128 : 168)
                   : (round_count(m, esize) >= 2 && round_radix(m, esize, 1) >= 16 ? 96 : 64))
-               : (max_round_radix(m, esize) >= 25 ? 255
+               : (max_round_radix(m, esize) >= 25 ? (m >= 3125 ? 168 : 255)
                   : (round_count(m, esize) >= 2 && round_radix(m, esize, 1) >= 16 ? 168 : 128));
 }
 constexpr int min_blocks(int m, int esize) {
