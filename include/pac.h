@@ -79,14 +79,15 @@ typedef enum {
  * radix 0 (mixed radix, Section 7.1): each dim is any 2^a 3^b 5^c, with the
  * stage list [4,..,4,(2), 3,..,3, 5,..,5] (the factor 2^a in radix-4 stages,
  * a leftover 2 last, then the 3s and the 5s).  Each run of stages of one
- * base becomes one or more passes; where groups spanning the bases (at most
- * 2048 points) are fewer and each has a compiled kernel (48, 120 and 1000
- * points), those run instead (PAC_MIXED=0 / 1 / rt in the environment forces
- * one-base groups / groups spanning bases / those groups in the runtime-radix
- * kernel).  A dim of 1 is allowed (empty stage list).  Builds twiddle tables in FP64, rounds them once to dtype and
- * uploads them to the current device.  On success *out owns device memory
- * until pac_plan_destroy.  Errors: PAC_ERR_ARG, PAC_ERR_SIZE, PAC_ERR_NOMEM,
- * PAC_ERR_CUDA.
+ * base becomes one or more passes; where groups spanning the bases are fewer
+ * and each has a compiled kernel (48, 120, 1000 and 6000 points; a whole
+ * axis of 6000 is one group), those run instead (PAC_MIXED=0 / 1 / rt in
+ * the environment forces one-base groups / groups spanning bases / groups of
+ * at most 2048 points in the runtime-radix kernel).  A dim of 1 is allowed
+ * (empty stage list).  Builds twiddle tables in FP64, rounds them once to
+ * dtype and uploads them to the current device.  On success *out owns device
+ * memory until pac_plan_destroy.  Errors: PAC_ERR_ARG, PAC_ERR_SIZE,
+ * PAC_ERR_NOMEM, PAC_ERR_CUDA.
  */
 int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, pac_plan* out);
 
@@ -373,8 +374,8 @@ int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void* y_dev, vo
  * the first time a plan is made for it.  PAC_LOG=1 makes every plan print
  * its pass schedule (groups, plane pass) to stderr.  For stage lists of
  * several prime bases (radix 0) the candidates include groups spanning bases
- * (compiled kernels for 48, 120 and 1000 points, the runtime-radix kernel for
- * other sizes) and one-base groups; PAC_MIXED in the environment overrides
+ * (compiled kernels for 48, 120, 1000 and 6000 points, the runtime-radix
+ * kernel for other sizes) and one-base groups; PAC_MIXED in the environment overrides
  * the choice for every plan (see pac_plan_create).
  */
 int pac_tune(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int reps, double* best_us);
@@ -411,7 +412,7 @@ int pac_measure_fma_peak(int dtype, double* gflops);
  * forward order (axis 0 first), without the plane pass.  flags bit 0:
  * groups may span prime bases (as PAC_MIXED=1); bit 1 (bit 0 ignored): the
  * default rule of pac_plan_create, groups span bases only where every such
- * group has a compiled kernel (sizes 48, 120, 1000); cap: a schedule's
+ * group has a compiled kernel (sizes 48, 120, 1000, 6000); cap: a schedule's
  * group-exponent cap (0: none).  For group g: axis[g], size[g] (its M) and
  * rounds[8 g .. 8 g + 7] (its in-CTA round radices, 0-padded).  *count: in,
  * the room of the arrays (groups; ignored when all three are NULL); out, the

@@ -66,9 +66,11 @@ constexpr int mixed_round_radix(int m, int i) {
         }
     return i < n ? r[i] : 1;
 }
-// mixed group sizes with compiled pass kernels (the groups of 1000, 120 and
-// 6000 = 48 x 125 per axis)
-constexpr bool mixed_compiled(int m) { return m == 48 || m == 120 || m == 1000; }
+// mixed group sizes with compiled pass kernels: whole axes of 1000, 120 and
+// 6000 points (a 6000-point tile of 4 FP32 or 2 FP64 columns is 192 KB of
+// shared memory, one CTA per SM), and 48 (6000 = 48 x 125 when the runtime
+// form's 2048-point limit applies)
+constexpr bool mixed_compiled(int m) { return m == 48 || m == 120 || m == 1000 || m == 6000; }
 
 // Number of rounds for a column of length m: ceil(log_base m / log_base rmax)
 // for one base, the mixed list otherwise.

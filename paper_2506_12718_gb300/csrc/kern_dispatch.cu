@@ -64,7 +64,7 @@ cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, con
 }
 
 int pass_kernel_supported(int M, int esize) {
-    if (is_mixed(M)) return mixed_compiled(M) && M <= kMixMmax ? 1 : 0;
+    if (is_mixed(M)) return mixed_compiled(M) ? 1 : 0;
     int b = base_of(M);
     if (b == 1 || M < 2) return 0;
     int m = M;

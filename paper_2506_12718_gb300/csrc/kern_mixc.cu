@@ -11,6 +11,7 @@ cudaError_t launch_pass_mixc(int esize, int M, const PassArgs& a, cudaStream_t s
             case 48: return launch_M<float2, 48>(a, s);
             case 120: return launch_M<float2, 120>(a, s);
             case 1000: return launch_M<float2, 1000>(a, s);
+            case 6000: return launch_M<float2, 6000>(a, s);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -18,6 +19,7 @@ cudaError_t launch_pass_mixc(int esize, int M, const PassArgs& a, cudaStream_t s
         case 48: return launch_M<double2, 48>(a, s);
         case 120: return launch_M<double2, 120>(a, s);
         case 1000: return launch_M<double2, 1000>(a, s);
+        case 6000: return launch_M<double2, 6000>(a, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -29,6 +31,7 @@ cudaError_t launch_multi_mixc(int esize, int M, bool lines, const PassArgs* list
             case 48: return launch_multi_M<float2, 48>(lines, list, starts, n, total, s);
             case 120: return launch_multi_M<float2, 120>(lines, list, starts, n, total, s);
             case 1000: return launch_multi_M<float2, 1000>(lines, list, starts, n, total, s);
+            case 6000: return launch_multi_M<float2, 6000>(lines, list, starts, n, total, s);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -36,6 +39,7 @@ cudaError_t launch_multi_mixc(int esize, int M, bool lines, const PassArgs* list
         case 48: return launch_multi_M<double2, 48>(lines, list, starts, n, total, s);
         case 120: return launch_multi_M<double2, 120>(lines, list, starts, n, total, s);
         case 1000: return launch_multi_M<double2, 1000>(lines, list, starts, n, total, s);
+        case 6000: return launch_multi_M<double2, 6000>(lines, list, starts, n, total, s);
         default: return cudaErrorInvalidValue;
     }
 }

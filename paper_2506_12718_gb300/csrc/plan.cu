@@ -262,6 +262,12 @@ static std::vector<std::pair<int, int>> split_groups(const std::vector<int>& st,
         ++runs;
         i = j;
     }
+    if (runs > 1 && sch.mixed != 0 && !sch.mix_runtime && (sch.cap == 0 || sch.cap >= 12)) {
+        // the whole axis as one group when a compiled kernel takes it (6000 = 2^4 3 5^3)
+        int64_t n = 1;
+        for (int k = 0; k < T; ++k) n *= st[k];
+        if (mixed_compiled((int)n) && n > kMixMmax) return {{0, T}};
+    }
     if (runs > 1 && sch.mixed != 0) {
         std::vector<std::pair<int, int>> mixed = split_mixed(st);
         bool take = mixed.size() < out.size();
@@ -578,7 +584,8 @@ static int form_groups(int ndim, const int64_t* dims, const std::vector<std::vec
             for (int i = 1; i < cnt; ++i)
                 if (stage_base(stages[a][first + i]) != stage_base(stages[a][first])) one_base = false;
             if (!one_base) {
-                if (g.M > kMixMmax) return fail(PAC_ERR_SIZE, "mixed group size %d above %d", g.M, kMixMmax);
+                if (g.M > kMixMmax && !mixed_compiled(g.M))
+                    return fail(PAC_ERR_SIZE, "mixed group size %d above %d", g.M, kMixMmax);
                 // a compiled mixed kernel runs the config.h rounds (mix_nr = 0), else the runtime-radix kernel
                 if (!mixed_compiled(g.M) || sch.mix_runtime) g.mix_nr = mix_round_list(g.M, g.mix_r);
             } else if (!pass_kernel_supported(g.M, esize)) {

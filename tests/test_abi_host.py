@@ -170,13 +170,14 @@ def test_prime_factor_object_rejects_bad_lengths_before_touching_the_device(n, s
     ((1000,), 0, 0, False, 0, [(0, 8, [8]), (0, 125, [25, 5])]),       # one-base groups (PAC_MIXED=0)
     ((1000,), 0, 0, True, 0, [(0, 1000, [25, 8, 5])]),                 # one group spanning bases
     ((6000,), 0, 0, False, 0, [(0, 16, [16]), (0, 3, [3]), (0, 125, [25, 5])]),
-    ((6000,), 0, 0, True, 0, [(0, 48, [16, 3]), (0, 125, [25, 5])]),
+    ((6000,), 0, 0, True, 0, [(0, 6000, [25, 16, 5, 3])]),             # the whole axis: a compiled group
     ((2 ** 10 * 3 ** 5 * 5 ** 3,), 0, 0, True, 0,                       # spanning bases would not be fewer
      [(0, 1024, [16, 8, 8]), (0, 243, [27, 9]), (0, 125, [25, 5])]),
     # the default rule: groups spanning bases where each has a compiled kernel (48, 120, 1000 points)
     ((1000,), 0, 0, None, 0, [(0, 1000, [25, 8, 5])]),
     ((1000,), 0, 1, None, 0, [(0, 1000, [25, 8, 5])]),
-    ((6000,), 0, 0, None, 0, [(0, 48, [16, 3]), (0, 125, [25, 5])]),
+    ((6000,), 0, 0, None, 0, [(0, 6000, [25, 16, 5, 3])]),
+    ((6000,), 0, 0, True, 9, [(0, 48, [16, 3]), (0, 125, [25, 5])]),  # a cap: groups of at most 2048
     ((120, 120), 0, 0, None, 0, [(0, 120, [8, 5, 3]), (1, 120, [8, 5, 3])]),
     ((360,), 0, 0, None, 0, [(0, 8, [8]), (0, 9, [9]), (0, 5, [5])]),   # 360 has no compiled kernel
     ((360,), 0, 0, True, 0, [(0, 360, [9, 8, 5])]),
@@ -209,9 +210,9 @@ def test_plan_groups_invariants(dims, dtype, mixed):
         if len(bases) == 1:
             assert m <= limits[bases.pop()]
         else:
-            assert mixed is not False and m <= 2048
+            assert mixed is not False and (m <= 2048 or m == 6000)  # 6000: a compiled whole axis
             if mixed is None:  # the default rule forms only groups with compiled kernels
-                assert m in (48, 120, 1000)
+                assert m in (48, 120, 1000, 6000)
     assert len(groups) <= len(pac.pac_plan_groups(dims, 0, dtype, False))
 
 
@@ -240,6 +241,6 @@ def test_header_is_c_and_the_library_links_from_c():
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.splitlines()
     assert out[0] == "stages 4 2 5 5 5"
     assert out[1] == "reverse " + " ".join(str(v) for v in pf.pos_to_freq([4, 4, 2])[[0, 1, 31]])
-    assert out[2] == "groups 2 48 125"
+    assert out[2] == "groups 1 6000"  # the whole 6000-point axis as one compiled group
     assert out[3] == f"error {int(pac.Status.ERR_SIZE)} message"
     assert out[4].startswith("version ") and "sm_103a" in out[4]

@@ -383,21 +383,23 @@ def test_mixed_radix_plans(dims, dtype):
 
 @pytest.mark.parametrize("dims,dtype,mixed_launches,onebase_launches",
                          [((1000, 1000), "c64", 3, 7), ((120, 120, 120), "c64", 5, 17), ((60, 90), "c128", 3, 11),
-                          ((6000,), "c64", 3, 5), ((30,), "c128", 1, 5), ((72, 75), "c64", 3, 7)])
+                          ((6000,), "c64", (1, 3), 5), ((6000, 6), "c128", (3, 5), 9), ((30,), "c128", 1, 5),
+                          ((72, 75), "c64", 3, 7)])
 def test_mixed_groups_against_one_base_groups(dims, dtype, mixed_launches, onebase_launches, monkeypatch):
     """Groups spanning prime bases (compiled kernels where they exist,
-    PAC_MIXED=1; the runtime-radix kernel for all of them, PAC_MIXED=rt)
-    against one-base groups (PAC_MIXED=0): fewer launches, the same
-    convolution."""
+    PAC_MIXED=1, a 6000-point axis as one compiled group; the runtime-radix
+    kernel for all of them, PAC_MIXED=rt, which stops at 2048 points) against
+    one-base groups (PAC_MIXED=0): fewer launches, the same convolution."""
     pac = pac_mod()
     fs, h, x = separable_case(dims, dtype, seed=3 * sum(dims))
     ref = oracle.conv_separable(fs, x)
     n = int(np.prod(dims))
-    for mode in ("1", "rt"):
+    for k, mode in enumerate(("1", "rt")):
         monkeypatch.setenv("PAC_MIXED", mode)
         plan = pac.Plan(dims, 0, dtype)
+        want = mixed_launches[k] if isinstance(mixed_launches, tuple) else mixed_launches
         try:
-            assert plan.query(pac.Q_LAUNCHES_CONVOLVE) == mixed_launches
+            assert plan.query(pac.Q_LAUNCHES_CONVOLVE) == want
         finally:
             plan.close()
         check(gpu_conv(dims, 0, dtype, h, x), ref, dtype, n, f"mixed groups {dims} ({mode})")
