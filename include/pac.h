@@ -83,7 +83,8 @@ typedef enum {
  * and each has a compiled kernel (48, 120, 1000 and 6000 points; a whole
  * axis of 6000 is one group), those run instead (PAC_MIXED=0 / 1 / rt in
  * the environment forces one-base groups / groups spanning bases / groups of
- * at most 2048 points in the runtime-radix kernel).  A dim of 1 is allowed
+ * at most 2048 points in the runtime-radix kernel; PAC_NARROW=1 / 0 forces
+ * the narrow tile of the group passes on / off, see pac_tune).  A dim of 1 is allowed
  * (empty stage list).  Builds twiddle tables in FP64, rounds them once to
  * dtype and uploads them to the current device.  On success *out owns device
  * memory until pac_plan_destroy.  Errors: PAC_ERR_ARG, PAC_ERR_SIZE,
@@ -364,7 +365,9 @@ int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void* y_dev, vo
  * device (the largest group per pass, i.e. how many DIF stages one pass fuses,
  * from the largest a CTA holds down to small groups; and, in 2-D/3-D, the
  * plane pass on or off and its tile: a whole plane per CTA or a plane split
- * over a cluster of K CTAs), `reps` convolutions each after a warm-up, and keep
+ * over a cluster of K CTAs; and the tile of the group passes: the default
+ * width or, for groups whose tile rows span 256 bytes or more, the narrow tile
+ * of half the columns, twice the CTAs), `reps` convolutions each after a warm-up, and keep
  * the fastest.  Plans created afterwards with the same (dims, radix, dtype)
  * use it.  With PAC_TUNE_FILE set in the environment, tuned schedules are
  * read from that file on first use and appended to it.  Allocates and frees
@@ -396,7 +399,8 @@ enum {
                                      (1: a bounded grid-barrier wait gave up) */
     PAC_Q_GROUPS = 9,             /* stage groups (one pass each) over all axes */
     PAC_Q_PLANE = 10,             /* CTAs per plane of the plane pass, 0 when the plan has none */
-    PAC_Q_GROUP_CAP = 11          /* the schedule's group-exponent cap (0: none) */
+    PAC_Q_GROUP_CAP = 11,         /* the schedule's group-exponent cap (0: none) */
+    PAC_Q_NARROW = 12             /* group passes that take the narrow tile (half the columns) */
 };
 
 /*

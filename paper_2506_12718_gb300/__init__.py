@@ -37,7 +37,7 @@ class Status(enum.IntEnum):
 
 
 Q_NDIM, Q_N_TOTAL, Q_ELEM_BYTES, Q_LAUNCHES_CONVOLVE, Q_LAUNCHES_PERMUTED, Q_LAUNCHES_FORWARD, \
-    Q_DEVICE_BYTES, Q_HAS_SPECTRUM, Q_DEVICE_ERROR, Q_GROUPS, Q_PLANE, Q_GROUP_CAP = range(12)
+    Q_DEVICE_BYTES, Q_HAS_SPECTRUM, Q_DEVICE_ERROR, Q_GROUPS, Q_PLANE, Q_GROUP_CAP, Q_NARROW = range(13)
 
 # every entry point of include/pac.h: name -> (restype, argtypes)
 _vp, _i64, _i32, _u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64

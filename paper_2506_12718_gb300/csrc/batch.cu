@@ -37,6 +37,7 @@ namespace {
 struct MultiLaunch {
     int esize, M;
     bool lines;
+    int nv = 0;          // the narrow tile variant of the group
     int M2;              // > 0: a plane launch (groups M x M2), arguments are PlaneArgs
     int K;               // plane launch: CTAs per plane
     int n;               // passes in the launch
@@ -78,6 +79,9 @@ int persist_shape_of(pac_plan p, const Step& st) {
     }
     const GroupPlan& g = p->groups[st.group];
     if (g.mix_nr > 0) return -1;
+    // a narrow tile of a forward or inverse pass is dropped (the kernel has its own tiles); the
+    // fused pass' tile width fixes the layout of the stored spectrum, so a narrow one stays out
+    if (g.nv && st.mode == kFused) return -1;
     const int lines = g.C == 1 ? 1 : 0;
     for (int i = 0; i < kPersistShapeCount; ++i)
         if (kPersistShapes[i].m2 == 0 && kPersistShapes[i].m == g.M && kPersistShapes[i].lines == lines) return i;
@@ -97,14 +101,15 @@ void free_entry(BatchEntry* e) {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Kernel shape of a step: element size, group size, rows/lines (for a plane
-// step: CTAs per plane), and for a plane step the second group size.
+// step: CTAs per plane; else bit 0 lines, bit 1 the narrow tile variant),
+// and for a plane step the second group size.
 using ShapeKey = std::tuple<int, int, int, int>;
 
 ShapeKey shape_key(pac_plan p, const Step& st) {
     if (st.mode == kPlane)
         return ShapeKey(p->esize, p->groups[p->plane_g1].M, p->plane_k, p->groups[p->plane_g1 + 1].M);
     const GroupPlan& g = p->groups[st.group];
-    return ShapeKey(p->esize, g.mix_nr > 0 ? -g.M : g.M, g.C == 1 ? 1 : 0, 0);  // -M: a mixed group
+    return ShapeKey(p->esize, g.mix_nr > 0 ? -g.M : g.M, (g.C == 1 ? 1 : 0) | (g.nv ? 2 : 0), 0);  // -M: a mixed group
 }
 
 // Append one merged launch (arguments, then tile starts) to the host image.
@@ -113,7 +118,8 @@ int add_launch(std::vector<unsigned char>& blob, const ShapeKey& key, const void
     MultiLaunch m;
     int lines;
     std::tie(m.esize, m.M, lines, m.M2) = key;
-    m.lines = m.M2 == 0 && lines != 0;
+    m.lines = m.M2 == 0 && (lines & 1) != 0;
+    m.nv = m.M2 == 0 && (lines & 2) != 0 ? 1 : 0;
     m.K = m.M2 > 0 ? lines : 1;
     m.n = (int)tiles.size();
     m.off_args = align_up(blob.size(), 64);
@@ -224,7 +230,9 @@ int build_persistent(int count, const pac_plan* plans, const void* const* x, voi
                 r.pp.pa = make_plane(plans[i], st.src, st.dst);
                 r.tiles = (int)r.pp.pa.planes;
             } else {
-                r.pp.pa.a1 = make_pass(plans[i], plans[i]->groups[st.group], st.mode, st.src, st.dst);
+                GroupPlan g = plans[i]->groups[st.group];
+                g.nv = 0;  // the persistent kernel's tiles are the default ones
+                r.pp.pa.a1 = make_pass(plans[i], g, st.mode, st.src, st.dst);
                 r.tiles = (int)r.pp.pa.a1.tiles;
             }
             of[i].push_back((int)recs.size());
@@ -313,14 +321,14 @@ cudaError_t enqueue_launch(const BatchEntry* e, const MultiLaunch& m, cudaStream
     if (m.M2 > 0)
         return launch_plane_multi(m.esize, m.M, m.M2, m.K, reinterpret_cast<const PlaneArgs*>(b + m.off_args),
                                   starts, m.n, m.tiles, s);
-    return launch_multi(m.esize, m.M, m.lines, reinterpret_cast<const PassArgs*>(b + m.off_args), starts, m.n,
+    return launch_multi(m.esize, m.M, m.lines, m.nv, reinterpret_cast<const PassArgs*>(b + m.off_args), starts, m.n,
                         m.tiles, s);
 }
 
 // per-kernel set-up (shared-memory attribute, occupancy): a launch with no work
 cudaError_t prepare_launch(const MultiLaunch& m, cudaStream_t s) {
     if (m.M2 > 0) return launch_plane_multi(m.esize, m.M, m.M2, m.K, nullptr, nullptr, 0, 0, s);
-    return launch_multi(m.esize, m.M, m.lines, nullptr, nullptr, 0, 0, s);
+    return launch_multi(m.esize, m.M, m.lines, m.nv, nullptr, nullptr, 0, 0, s);
 }
 
 // Capture the batch's launches into a graph: the one persistent launch, or

@@ -103,9 +103,18 @@ constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi 
 // CTA so that two CTAs share an SM and one computes while the other waits on
 // its loads.
 constexpr int tile_wmin(int m, int esize) { return esize == 16 && m >= 2187 ? 1 : 32 / esize; }
-constexpr int tile_w(int m, int esize) {
+constexpr int tile_w0(int m, int esize) {
     return clampi(floor_pow2(kTileBytes / (m * esize)), tile_wmin(m, esize),
                   (round_count(m, esize) == 1 ? 1024 : 256) / esize);
+}
+// The narrow tile variant (nv = 1), one of the autotuner's candidates: half
+// the columns, for one-base groups whose half-width rows still span at least
+// 128 bytes (one 32-byte sector per 8-byte lane of a quarter warp, and the
+// bank model finds every round of these shapes conflict-free with the pads
+// below).
+constexpr bool has_narrow(int m, int esize) { return !is_mixed(m) && (tile_w0(m, esize) / 2) * esize >= 128; }
+constexpr int tile_w(int m, int esize, int nv = 0) {
+    return nv && has_narrow(m, esize) ? tile_w0(m, esize) / 2 : tile_w0(m, esize);
 }
 
 // Row padding of the shared-memory exchange buffer, in elements.  Chosen per
@@ -116,8 +125,8 @@ constexpr int tile_w(int m, int esize) {
 // global memory run in-line-fastest order when the tile is at least 8 lines
 // wide, which wants the padding below; narrower tiles keep column-fastest
 // order and no padding.
-constexpr int tile_pad(int m, int esize, bool lines) {
-    if (!lines || tile_w(m, esize) < 8) return 0;
+constexpr int tile_pad(int m, int esize, bool lines, int nv = 0) {
+    if (!lines || tile_w(m, esize, nv) < 8) return 0;
     if (esize == 8) {
         switch (m) {
             case 32: return 4;
@@ -152,10 +161,10 @@ constexpr int tile_row_swizzle(int m, int esize) {
 }
 
 // Row pitch of the exchange buffer in elements.
-constexpr int tile_pitch(int m, int esize, bool lines) { return tile_w(m, esize) + tile_pad(m, esize, lines); }
-constexpr int tile_elems(int m, int esize, bool lines) { return m * tile_pitch(m, esize, lines); }
-// tasks of a lines-case round that reads or writes global memory run in-line-fastest order
-constexpr bool lines_jfast(int m, int esize) { return tile_w(m, esize) >= 8; }
+constexpr int tile_pitch(int m, int esize, bool lines, int nv = 0) {
+    return tile_w(m, esize, nv) + tile_pad(m, esize, lines, nv);
+}
+constexpr int tile_elems(int m, int esize, bool lines, int nv = 0) { return m * tile_pitch(m, esize, lines, nv); }
 
 // Threads per CTA: one per task of the first (largest) round, rounded up to
 // whole warps, within [64, 512].  A multiple of 32, hence of the tile width,
@@ -164,8 +173,8 @@ constexpr bool lines_jfast(int m, int esize) { return tile_w(m, esize) >= 8; }
 // registers so that two CTAs share an SM (measured 2187^2: 121 -> 108 us);
 // for base 2 and 5 the 512-thread form measured faster.
 constexpr bool two_ctas_per_sm(int m, int esize) { return esize == 8 && base_of(m) == 3 && m >= 729; }
-constexpr int pass_threads(int m, int esize) {
-    return clampi(((tile_w(m, esize) * (m / round_radix(m, esize, 0)) + 31) / 32) * 32, 64,
+constexpr int pass_threads(int m, int esize, int nv = 0) {
+    return clampi(((tile_w(m, esize, nv) * (m / round_radix(m, esize, 0)) + 31) / 32) * 32, 64,
                   two_ctas_per_sm(m, esize) ? 256 : 512);
 }
 
@@ -183,8 +192,8 @@ constexpr int reg_target(int m, int esize) {
                : (max_round_radix(m, esize) >= 25 ? (m >= 3125 ? 168 : 255)
                   : (round_count(m, esize) >= 2 && round_radix(m, esize, 1) >= 16 ? 168 : 128));
 }
-constexpr int min_blocks(int m, int esize) {
-    return clampi(65536 / (pass_threads(m, esize) * reg_target(m, esize)), 1, 8);
+constexpr int min_blocks(int m, int esize, int nv = 0) {
+    return clampi(65536 / (pass_threads(m, esize, nv) * reg_target(m, esize)), 1, 8);
 }
 
 // ------------------------------------------------- the runtime-radix kernel

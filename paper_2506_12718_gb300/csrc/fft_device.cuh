@@ -298,12 +298,13 @@ template <int M, int ES> struct RoundGeom<M, ES, -1> {
     static constexpr int R = 1, S = M * 1, SP = M;
 };
 
-template <typename V, int M, bool LINES = false> struct Shape {
+// NV = 1: the narrow tile variant (has_narrow in config.h)
+template <typename V, int M, bool LINES = false, int NV = 0> struct Shape {
     static constexpr int ES = sizeof(V);
-    static constexpr int W = tile_w(M, ES);
-    static constexpr int P = tile_pitch(M, ES, LINES);
+    static constexpr int W = tile_w(M, ES, NV);
+    static constexpr int P = tile_pitch(M, ES, LINES, NV);
     static constexpr int NR = round_count(M, ES);
-    static constexpr int NT = pass_threads(M, ES);
+    static constexpr int NT = pass_threads(M, ES, NV);
     static constexpr int TILE = M * P;
     static_assert(NT % W == 0, "a thread's tasks must share one column in the rows case");
 };
@@ -336,9 +337,9 @@ struct Geo {
 };
 // the pass kernels' geometry: a tile of W columns, buffer [row][w] of pitch
 // P; several CTAs per SM hide latency, so registers are not spent on prefetch
-template <typename V, int M, bool LINES>
-using PassGeo = Geo<V, M, Shape<V, M, LINES>::W, Shape<V, M, LINES>::NT, Shape<V, M, LINES>::P, 1, false, 1, false,
-                    tile_row_swizzle(M, sizeof(V))>;
+template <typename V, int M, bool LINES, int NV = 0>
+using PassGeo = Geo<V, M, Shape<V, M, LINES, NV>::W, Shape<V, M, LINES, NV>::NT, Shape<V, M, LINES, NV>::P, 1, false,
+                    1, false, tile_row_swizzle(M, sizeof(V))>;
 
 // Task tau of round RI: column w of the tile, offset jp inside its block of
 // S rows, first row row0 = block * S + jp; the task transforms rows
@@ -766,9 +767,9 @@ __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepc
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 
 // Set up the per-tile facts of tile t.
-template <typename V, int M, bool LINES>
+template <typename V, int M, bool LINES, int NV = 0>
 __device__ __forceinline__ void tile_setup(TileCtx<V>& c, const PassArgs& a, uint32_t t) {
-    using SH = Shape<V, M>;
+    using SH = Shape<V, M, false, NV>;
     c.t = t;
     c.q0 = t * SH::W;
     c.valid = false;
@@ -785,9 +786,9 @@ __device__ __forceinline__ void tile_setup(TileCtx<V>& c, const PassArgs& a, uin
     }
 }
 
-template <typename V, int M, bool LINES>
+template <typename V, int M, bool LINES, int NV = 0>
 __device__ __forceinline__ void tile_run(const TileCtx<V>& c, int mode) {
-    using GEO = PassGeo<V, M, LINES>;
+    using GEO = PassGeo<V, M, LINES, NV>;
     if (mode == kFwd)
         tile_forward<GEO, LINES>(c);
     else if (mode == kFused)
@@ -807,37 +808,37 @@ template <typename V> __device__ __forceinline__ void ctx_init(TileCtx<V>& c, co
 }
 
 // One pass over all tiles, CTAs walking tiles blockIdx.x, +gridDim.x, ...
-template <typename V, int M, bool LINES>
+template <typename V, int M, bool LINES, int NV = 0>
 __device__ __forceinline__ void run_phase(const PassArgs& a, V* s) {
     TileCtx<V> c;
     ctx_init(c, a, s);
     const uint32_t tiles = (uint32_t)a.tiles;
     for (uint32_t t = blockIdx.x; t < tiles; t += gridDim.x) {
-        tile_setup<V, M, LINES>(c, a, (uint32_t)a.tile0 + t);
-        tile_run<V, M, LINES>(c, a.mode);
+        tile_setup<V, M, LINES, NV>(c, a, (uint32_t)a.tile0 + t);
+        tile_run<V, M, LINES, NV>(c, a.mode);
         __syncthreads();  // the next tile reuses the exchange buffer
     }
 }
 
-template <typename V, int M> constexpr int pass_smem_bytes(bool lines) {
-    return (lines ? Shape<V, M, true>::TILE : Shape<V, M, false>::TILE) * (int)sizeof(V);
+template <typename V, int M, int NV = 0> constexpr int pass_smem_bytes(bool lines) {
+    return (lines ? Shape<V, M, true, NV>::TILE : Shape<V, M, false, NV>::TILE) * (int)sizeof(V);
 }
 
 // Generic pass kernel: one pass of a convolution (see run_phase).
-template <typename V, int M, bool LINES>
-__global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, sizeof(V)))
+template <typename V, int M, bool LINES, int NV = 0>
+__global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), min_blocks(M, sizeof(V), NV))
     pass_kernel(const __grid_constant__ PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_launch_dependents();
     pdl_wait();
-    run_phase<V, M, LINES>(a, reinterpret_cast<V*>(smem_raw));
+    run_phase<V, M, LINES, NV>(a, reinterpret_cast<V*>(smem_raw));
 }
 
 // Many passes of one kernel shape in one launch (batched convolutions): the
 // tiles of passes list[0..n) are numbered consecutively, pass i owning global
 // tiles [tile_start[i], tile_start[i+1]); CTAs walk the global tiles.
-template <typename V, int M, bool LINES>
-__global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, sizeof(V)))
+template <typename V, int M, bool LINES, int NV = 0>
+__global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), min_blocks(M, sizeof(V), NV))
     pass_multi_kernel(const PassArgs* __restrict__ list, const uint32_t* __restrict__ tile_start, int n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* s = reinterpret_cast<V*>(smem_raw);
@@ -854,8 +855,8 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V)), min_blocks(M, size
         const PassArgs& a = list[lo];
         TileCtx<V> c;
         ctx_init(c, a, s);
-        tile_setup<V, M, LINES>(c, a, t - __ldg(tile_start + lo));
-        tile_run<V, M, LINES>(c, a.mode);
+        tile_setup<V, M, LINES, NV>(c, a, t - __ldg(tile_start + lo));
+        tile_run<V, M, LINES, NV>(c, a.mode);
         __syncthreads();
     }
 }

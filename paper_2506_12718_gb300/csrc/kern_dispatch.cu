@@ -19,8 +19,8 @@ cudaError_t launch_conv_c128_p35(int M, ConvArgs& args, int grid, cudaStream_t s
 
 cudaError_t launch_mix(int esize, bool lines, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_pass_mixc(int esize, int M, const PassArgs& a, cudaStream_t s);
-cudaError_t launch_multi_mixc(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
-                              int64_t total, cudaStream_t s);
+cudaError_t launch_multi_mixc(int esize, int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts,
+                              int n, int64_t total, cudaStream_t s);
 cudaError_t launch_mix_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
                              int64_t total, cudaStream_t s);
 
@@ -43,24 +43,24 @@ cudaError_t launch_conv(int esize, int M, ConvArgs& args, int grid, cudaStream_t
     return (M % 2 == 0) ? launch_conv_c128_p2(M, args, grid, s) : launch_conv_c128_p35(M, args, grid, s);
 }
 
-cudaError_t launch_multi_c64_p2(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
+cudaError_t launch_multi_c64_p2(int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
                                cudaStream_t s);
-cudaError_t launch_multi_c64_p35(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
+cudaError_t launch_multi_c64_p35(int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
                                 cudaStream_t s);
-cudaError_t launch_multi_c128_p2(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
+cudaError_t launch_multi_c128_p2(int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts, int n, int64_t total,
                                 cudaStream_t s);
-cudaError_t launch_multi_c128_p35(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+cudaError_t launch_multi_c128_p35(int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts, int n,
                                  int64_t total, cudaStream_t s);
 
-cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+cudaError_t launch_multi(int esize, int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts, int n,
                          int64_t total, cudaStream_t s) {
     if (M < 0) return launch_mix_multi(esize, -M, lines, list, starts, n, total, s);  // mixed groups of size -M
-    if (is_mixed(M)) return launch_multi_mixc(esize, M, lines, list, starts, n, total, s);
+    if (is_mixed(M)) return launch_multi_mixc(esize, M, lines, nv, list, starts, n, total, s);
     if (esize == 8)
-        return (M % 2 == 0) ? launch_multi_c64_p2(M, lines, list, starts, n, total, s)
-                            : launch_multi_c64_p35(M, lines, list, starts, n, total, s);
-    return (M % 2 == 0) ? launch_multi_c128_p2(M, lines, list, starts, n, total, s)
-                        : launch_multi_c128_p35(M, lines, list, starts, n, total, s);
+        return (M % 2 == 0) ? launch_multi_c64_p2(M, lines, nv, list, starts, n, total, s)
+                            : launch_multi_c64_p35(M, lines, nv, list, starts, n, total, s);
+    return (M % 2 == 0) ? launch_multi_c128_p2(M, lines, nv, list, starts, n, total, s)
+                        : launch_multi_c128_p35(M, lines, nv, list, starts, n, total, s);
 }
 
 int pass_kernel_supported(int M, int esize) {

@@ -24,22 +24,22 @@ cudaError_t launch_pass_mixc(int esize, int M, const PassArgs& a, cudaStream_t s
     }
 }
 
-cudaError_t launch_multi_mixc(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+cudaError_t launch_multi_mixc(int esize, int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts, int n,
                               int64_t total, cudaStream_t s) {
     if (esize == 8) {
         switch (M) {
-            case 48: return launch_multi_M<float2, 48>(lines, list, starts, n, total, s);
-            case 120: return launch_multi_M<float2, 120>(lines, list, starts, n, total, s);
-            case 1000: return launch_multi_M<float2, 1000>(lines, list, starts, n, total, s);
-            case 6000: return launch_multi_M<float2, 6000>(lines, list, starts, n, total, s);
+            case 48: return launch_multi_M<float2, 48>(lines, nv, list, starts, n, total, s);
+            case 120: return launch_multi_M<float2, 120>(lines, nv, list, starts, n, total, s);
+            case 1000: return launch_multi_M<float2, 1000>(lines, nv, list, starts, n, total, s);
+            case 6000: return launch_multi_M<float2, 6000>(lines, nv, list, starts, n, total, s);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (M) {
-        case 48: return launch_multi_M<double2, 48>(lines, list, starts, n, total, s);
-        case 120: return launch_multi_M<double2, 120>(lines, list, starts, n, total, s);
-        case 1000: return launch_multi_M<double2, 1000>(lines, list, starts, n, total, s);
-        case 6000: return launch_multi_M<double2, 6000>(lines, list, starts, n, total, s);
+        case 48: return launch_multi_M<double2, 48>(lines, nv, list, starts, n, total, s);
+        case 120: return launch_multi_M<double2, 120>(lines, nv, list, starts, n, total, s);
+        case 1000: return launch_multi_M<double2, 1000>(lines, nv, list, starts, n, total, s);
+        case 6000: return launch_multi_M<double2, 6000>(lines, nv, list, starts, n, total, s);
         default: return cudaErrorInvalidValue;
     }
 }

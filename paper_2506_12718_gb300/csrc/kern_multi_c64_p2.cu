@@ -3,21 +3,21 @@
 
 namespace pac {
 
-cudaError_t launch_multi_c64_p2(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+cudaError_t launch_multi_c64_p2(int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts, int n,
                                  int64_t total, cudaStream_t s) {
     switch (M) {
-        case 2: return launch_multi_M<float2, 2>(lines, list, starts, n, total, s);
-        case 4: return launch_multi_M<float2, 4>(lines, list, starts, n, total, s);
-        case 8: return launch_multi_M<float2, 8>(lines, list, starts, n, total, s);
-        case 16: return launch_multi_M<float2, 16>(lines, list, starts, n, total, s);
-        case 32: return launch_multi_M<float2, 32>(lines, list, starts, n, total, s);
-        case 64: return launch_multi_M<float2, 64>(lines, list, starts, n, total, s);
-        case 128: return launch_multi_M<float2, 128>(lines, list, starts, n, total, s);
-        case 256: return launch_multi_M<float2, 256>(lines, list, starts, n, total, s);
-        case 512: return launch_multi_M<float2, 512>(lines, list, starts, n, total, s);
-        case 1024: return launch_multi_M<float2, 1024>(lines, list, starts, n, total, s);
-        case 2048: return launch_multi_M<float2, 2048>(lines, list, starts, n, total, s);
-        case 4096: return launch_multi_M<float2, 4096>(lines, list, starts, n, total, s);
+        case 2: return launch_multi_M<float2, 2>(lines, nv, list, starts, n, total, s);
+        case 4: return launch_multi_M<float2, 4>(lines, nv, list, starts, n, total, s);
+        case 8: return launch_multi_M<float2, 8>(lines, nv, list, starts, n, total, s);
+        case 16: return launch_multi_M<float2, 16>(lines, nv, list, starts, n, total, s);
+        case 32: return launch_multi_M<float2, 32>(lines, nv, list, starts, n, total, s);
+        case 64: return launch_multi_M<float2, 64>(lines, nv, list, starts, n, total, s);
+        case 128: return launch_multi_M<float2, 128>(lines, nv, list, starts, n, total, s);
+        case 256: return launch_multi_M<float2, 256>(lines, nv, list, starts, n, total, s);
+        case 512: return launch_multi_M<float2, 512>(lines, nv, list, starts, n, total, s);
+        case 1024: return launch_multi_M<float2, 1024>(lines, nv, list, starts, n, total, s);
+        case 2048: return launch_multi_M<float2, 2048>(lines, nv, list, starts, n, total, s);
+        case 4096: return launch_multi_M<float2, 4096>(lines, nv, list, starts, n, total, s);
         default: return cudaErrorInvalidValue;
     }
 }

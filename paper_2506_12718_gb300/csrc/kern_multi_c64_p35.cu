@@ -3,21 +3,21 @@
 
 namespace pac {
 
-cudaError_t launch_multi_c64_p35(int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+cudaError_t launch_multi_c64_p35(int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts, int n,
                                  int64_t total, cudaStream_t s) {
     switch (M) {
-        case 3: return launch_multi_M<float2, 3>(lines, list, starts, n, total, s);
-        case 9: return launch_multi_M<float2, 9>(lines, list, starts, n, total, s);
-        case 27: return launch_multi_M<float2, 27>(lines, list, starts, n, total, s);
-        case 81: return launch_multi_M<float2, 81>(lines, list, starts, n, total, s);
-        case 243: return launch_multi_M<float2, 243>(lines, list, starts, n, total, s);
-        case 729: return launch_multi_M<float2, 729>(lines, list, starts, n, total, s);
-        case 2187: return launch_multi_M<float2, 2187>(lines, list, starts, n, total, s);
-        case 5: return launch_multi_M<float2, 5>(lines, list, starts, n, total, s);
-        case 25: return launch_multi_M<float2, 25>(lines, list, starts, n, total, s);
-        case 125: return launch_multi_M<float2, 125>(lines, list, starts, n, total, s);
-        case 625: return launch_multi_M<float2, 625>(lines, list, starts, n, total, s);
-        case 3125: return launch_multi_M<float2, 3125>(lines, list, starts, n, total, s);
+        case 3: return launch_multi_M<float2, 3>(lines, nv, list, starts, n, total, s);
+        case 9: return launch_multi_M<float2, 9>(lines, nv, list, starts, n, total, s);
+        case 27: return launch_multi_M<float2, 27>(lines, nv, list, starts, n, total, s);
+        case 81: return launch_multi_M<float2, 81>(lines, nv, list, starts, n, total, s);
+        case 243: return launch_multi_M<float2, 243>(lines, nv, list, starts, n, total, s);
+        case 729: return launch_multi_M<float2, 729>(lines, nv, list, starts, n, total, s);
+        case 2187: return launch_multi_M<float2, 2187>(lines, nv, list, starts, n, total, s);
+        case 5: return launch_multi_M<float2, 5>(lines, nv, list, starts, n, total, s);
+        case 25: return launch_multi_M<float2, 25>(lines, nv, list, starts, n, total, s);
+        case 125: return launch_multi_M<float2, 125>(lines, nv, list, starts, n, total, s);
+        case 625: return launch_multi_M<float2, 625>(lines, nv, list, starts, n, total, s);
+        case 3125: return launch_multi_M<float2, 3125>(lines, nv, list, starts, n, total, s);
         default: return cudaErrorInvalidValue;
     }
 }

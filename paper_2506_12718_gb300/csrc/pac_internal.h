@@ -28,12 +28,15 @@ struct GroupPlan {
     int tw_T = 1, tw_shift = 0;
     bool has_ext = false;
     int mix_nr = 0;         // > 0: a mixed group (several prime bases), rounds mix_r of the runtime-radix kernel
+    int nv = 0;             // 1: the narrow tile variant (has_narrow in config.h)
     int mix_r[kMixMaxRounds] = {0};
     size_t off_twi = 0, off_lo = 0, off_hi = 0, off_rowmap = 0, off_freq = 0, off_r2g = 0, off_r2f = 0;  // in tables
 };
 
 // tile width of a group's pass
-inline int group_w(const GroupPlan& g, int esize) { return g.mix_nr > 0 ? mix_w(g.M, esize) : tile_w(g.M, esize); }
+inline int group_w(const GroupPlan& g, int esize) {
+    return g.mix_nr > 0 ? mix_w(g.M, esize) : tile_w(g.M, esize, g.nv);
+}
 
 // A pass schedule: the largest group exponent per pass (0: the largest a CTA
 // takes) and whether the last two axes may run as a plane pass.
@@ -47,6 +50,8 @@ struct Schedule {
     // the plane pass' tile: CTAs per plane (1: a whole plane per CTA, K > 1: split over a
     // K-CTA cluster); 0: the rule of plane_cluster
     int plane_k = 0;
+    // 1: the passes' tiles take the narrow variant (half the columns) where the group has one
+    int nv = 0;
 };
 int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const Schedule& sch, pac_plan* out);
 // the same from explicit per-axis DIF stage lists (radix: the label the plan reports; -1 = explicit)
@@ -77,7 +82,7 @@ cudaError_t launch_plane_multi(int esize, int M1, int M2, int K, const PlaneArgs
 PlaneArgs make_plane(pac_plan p, const void* src, void* dst);
 
 // n passes of one shape in one launch; list and starts in device memory (starts has n + 1 entries)
-cudaError_t launch_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
+cudaError_t launch_multi(int esize, int M, bool lines, int nv, const PassArgs* list, const uint32_t* starts, int n,
                          int64_t total, cudaStream_t s);
 
 // pass sequence of a convolution (plan.cu): group, mode, source, destination, scale

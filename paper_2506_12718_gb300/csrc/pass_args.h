@@ -29,6 +29,7 @@ struct PassArgs {
     int tw_shift;           // log2(tw_T) when tw_T is a power of two, else -1
     int mode;               // PassMode
     int has_ext;            // apply w_L^{j k'} (L' > 1)
+    int nv;                 // 1: the narrow tile variant of the group (has_narrow), 0: the default tile
     // mixed group (stages of several prime bases, the runtime-radix kernel):
     // mix_nr rounds of radices mix_r (0: a one-base group), group size mix_m,
     // tile width mix_w

@@ -441,7 +441,8 @@ static void log_plan(const pac_plan p) {
     for (int a = 0; a < p->ndim; ++a) std::fprintf(stderr, " %lld", (long long)p->dims[a]);
     std::fprintf(stderr, " radix %d %s cap %d:", p->radix, p->esize == 8 ? "c64" : "c128", p->schedule.cap);
     for (const GroupPlan& g : p->groups)
-        std::fprintf(stderr, " [axis %d M %d C %lld%s]", g.axis, g.M, (long long)g.C, g.mix_nr > 0 ? " mixed" : "");
+        std::fprintf(stderr, " [axis %d M %d C %lld%s]", g.axis, g.M, (long long)g.C,
+                     g.mix_nr > 0 ? " mixed" : (g.nv ? " narrow" : ""));
     if (p->plane) std::fprintf(stderr, " plane %dx%d K=%d", p->groups[p->plane_g1].M, p->groups[p->plane_g1 + 1].M,
                                p->plane_k);
     std::fprintf(stderr, "\n");
@@ -738,11 +739,21 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
                 pl->plane_k = sch.plane_k;
         }
     }
+    // narrow tile variant of the group passes (not the plane pass' groups);
+    // PAC_NARROW=1 / 0 in the environment forces it on / off
+    int nv = sch.nv;
+    const char* ne = std::getenv("PAC_NARROW");
+    if (ne && (ne[0] == '0' || ne[0] == '1')) nv = ne[0] == '1' ? 1 : 0;
+    for (int i = 0; i < (int)pl->groups.size(); ++i) {
+        GroupPlan& g = pl->groups[i];
+        const bool in_plane = pl->plane && i >= pl->plane_g1;
+        g.nv = nv && !in_plane && g.mix_nr == 0 && has_narrow(g.M, pl->esize) ? 1 : 0;
+    }
     pl->uniform_m = 0;
     if (!pl->groups.empty()) {
         pl->uniform_m = pl->groups[0].M;
         for (const GroupPlan& g : pl->groups)
-            if (g.M != pl->uniform_m || g.mix_nr > 0) pl->uniform_m = 0;
+            if (g.M != pl->uniform_m || g.mix_nr > 0 || g.nv) pl->uniform_m = 0;
     }
 
     // host blob of every table
@@ -906,6 +917,7 @@ PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, vo
     a.tw_shift = g.tw_shift;
     a.mode = mode;
     a.has_ext = g.has_ext ? 1 : 0;
+    a.nv = g.nv;
     a.mix_nr = g.mix_nr;
     a.mix_m = g.M;
     a.mix_w = W;
@@ -1474,6 +1486,12 @@ extern "C" int pac_plan_query(pac_plan p, int key, int64_t* value) {
         case PAC_Q_GROUPS: *value = G; break;
         case PAC_Q_PLANE: *value = p->plane ? p->plane_k : 0; break;
         case PAC_Q_GROUP_CAP: *value = p->schedule.cap; break;
+        case PAC_Q_NARROW: {
+            int64_t k = 0;
+            for (const GroupPlan& g : p->groups) k += g.nv;
+            *value = k;
+            break;
+        }
         default: return fail(PAC_ERR_ARG, "unknown query key %d", key);
     }
     return PAC_OK;

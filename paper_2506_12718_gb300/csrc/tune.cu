@@ -79,6 +79,7 @@ void load_file_locked() {
         t.sch.plane = (plane & 1) != 0;
         t.sch.mixed = (plane & 2) == 0;
         t.sch.plane_k = (plane >> 4) & 15;
+        t.sch.nv = (plane >> 2) & 1;
         t.us = us;
         g_tuned[k] = t;  // later lines win
     }
@@ -92,7 +93,8 @@ void append_file(const Key& k, const Tuned& t) {
     if (!f) return;
     std::fprintf(f, "%d %lld %lld %lld %d %d %d %d %.3f\n", k.ndim, (long long)k.d[0], (long long)k.d[1],
                  (long long)k.d[2], k.radix, k.dtype, t.sch.cap,
-                 (t.sch.plane ? 1 : 0) | (t.sch.mixed ? 0 : 2) | ((t.sch.plane_k & 15) << 4), t.us);
+                 (t.sch.plane ? 1 : 0) | (t.sch.mixed ? 0 : 2) | (t.sch.nv ? 4 : 0) | ((t.sch.plane_k & 15) << 4),
+                 t.us);
     std::fclose(f);
 }
 
@@ -149,7 +151,8 @@ bool tuned_schedule(int ndim, const int64_t* dims, int radix, pac_dtype dtype, S
 extern "C" int pac_tune(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int reps, double* best_us) {
     if (ndim < 1 || ndim > 3 || !dims || reps < 1) return fail(PAC_ERR_ARG, "bad arguments");
     // candidates: every group cap that changes the split, plane on and off,
-    // groups spanning prime bases or not
+    // groups spanning prime bases or not, the plane tile, the default or the
+    // narrow tile of the group passes
     std::vector<Schedule> cands;
     std::vector<std::vector<int>> seen;
     for (int mixed = 1; mixed >= 0; --mixed) {
@@ -170,16 +173,20 @@ extern "C" int pac_tune(int ndim, const int64_t* dims, int radix, pac_dtype dtyp
                 }
                 pac_plan_destroy(p);
                 for (int k : ks) {
-                    Schedule sk = sch;
-                    sk.plane_k = k;
-                    if (plan_build(ndim, dims, radix, dtype, sk, &p) != PAC_OK) continue;
-                    std::vector<int> sig;  // the resulting pass structure
-                    for (const GroupPlan& g : p->groups) sig.push_back(g.mix_nr > 0 ? -g.M : g.M);
-                    sig.push_back(p->plane ? -p->plane_k : 0);
-                    pac_plan_destroy(p);
-                    if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
-                    seen.push_back(sig);
-                    cands.push_back(sk);
+                    for (int nv = 0; nv <= 1; ++nv) {
+                        Schedule sk = sch;
+                        sk.plane_k = k;
+                        sk.nv = nv;
+                        if (plan_build(ndim, dims, radix, dtype, sk, &p) != PAC_OK) continue;
+                        std::vector<int> sig;  // the resulting pass structure
+                        for (const GroupPlan& g : p->groups)
+                            sig.push_back(g.mix_nr > 0 ? -2 * g.M : 2 * g.M + g.nv);
+                        sig.push_back(p->plane ? -p->plane_k : 0);
+                        pac_plan_destroy(p);
+                        if (std::find(seen.begin(), seen.end(), sig) != seen.end()) continue;
+                        seen.push_back(sig);
+                        cands.push_back(sk);
+                    }
                 }
             }
         }

@@ -815,8 +815,9 @@ def test_tune_file_round_trip(tmp_path):
 def test_tuner_chooses_the_plane_tile(tmp_path):
     """The tuner's candidates include the plane pass' tile: a whole 81 x 81
     plane per CTA or the plane split over a 3-CTA cluster.  The tune file
-    records the split (flags bits 4-7, 0 = the default rule), a later plan
-    uses it, and its convolution matches the oracle."""
+    records the winner (flags bit 0 the plane pass, bits 4-7 its split, 0 =
+    the default rule), a later plan uses it, and both tiles' convolutions
+    match the oracle."""
     import subprocess
     import sys
     path = tmp_path / "tune.txt"
@@ -832,7 +833,10 @@ def test_tuner_chooses_the_plane_tile(tmp_path):
              "p = pac.Plan((81, 81), 3, 'c64'); print(p.query(pac.Q_PLANE)); p.close()")
     out = subprocess.run([sys.executable, "-c", code2], env=env, check=True, capture_output=True, text=True, cwd=root)
     plane = int(out.stdout.strip().splitlines()[-1])
-    assert plane in (1, 3) and (k == 0 or plane == k)
+    if int(line[7]) & 1:  # the winner has the plane pass: the tile it recorded
+        assert plane in (1, 3) and (k == 0 or plane == k)
+    else:  # per-axis passes won (e.g. with narrow tiles)
+        assert plane == 0
     fs, h, x = separable_case((81, 81), "c64", seed=181)
     ref = oracle.conv_separable(fs, x)
     pac = pac_mod()
@@ -847,6 +851,110 @@ def test_tuner_chooses_the_plane_tile(tmp_path):
             check(gpu_conv((81, 81), 3, "c64", h, x), ref, "c64", 81 * 81, f"plane tile {forced}")
         finally:
             del os.environ["PAC_PLANE_K"]
+
+
+NARROW_SHAPES = [((128, 128, 128), 4, "c64", "1"), ((128, 128, 128), 4, "c64", "0"), ((64, 64), 2, "c128", "0"),
+                 ((16, 4096), 2, "c64", "0"), ((25, 25, 25), 5, "c128", "0"), ((27, 81), 3, "c64", "0"),
+                 ((8, 32, 32), 8, "c64", "0")]
+
+
+@pytest.mark.parametrize("dims,radix,dtype,plane", NARROW_SHAPES,
+                         ids=[f"{'x'.join(map(str, d))}-r{r}-{t}-plane{p}" for d, r, t, p in NARROW_SHAPES])
+def test_narrow_tile_matches_oracle(dims, radix, dtype, plane, monkeypatch):
+    """The narrow tile of the group passes (half the columns, PAC_NARROW=1),
+    rows and lines layouts, with and without the plane pass: the plan takes
+    it for at least one group and the convolution matches the oracle and
+    the default tile."""
+    pac = pac_mod()
+    fs, h, x = separable_case(dims, dtype, seed=7 + dims[-1])
+    ref = oracle.conv_separable(fs, x)
+    monkeypatch.setenv("PAC_PLANE", plane)
+    monkeypatch.setenv("PAC_NARROW", "1")
+    plan = pac.Plan(dims, radix, dtype)
+    try:
+        assert plan.query(pac.Q_NARROW) >= 1
+    finally:
+        plan.close()
+    y = gpu_conv(dims, radix, dtype, h, x)
+    check(y, ref, dtype, int(np.prod(dims)), f"narrow {dims}")
+    monkeypatch.setenv("PAC_NARROW", "0")
+    y0 = gpu_conv(dims, radix, dtype, h, x)
+    check(y0, ref, dtype, int(np.prod(dims)), f"default tile {dims}")
+    assert oracle.rel_l2(y, y0) <= tol(dtype, int(np.prod(dims)))
+
+
+def test_narrow_tile_in_a_batch(monkeypatch):
+    """Plans with narrow tiles in pac_convolve_many: merged per-level launches
+    of the narrow kernels (PAC_BATCH=graph), and the persistent kernel, which
+    runs the same passes in its own default tiles."""
+    pac = pac_mod()
+    monkeypatch.setenv("PAC_NARROW", "1")
+    monkeypatch.setenv("PAC_PLANE", "0")
+    cases = [((128, 128), 2, 11), ((64, 64), 8, 12), ((4096,), 2, 13), ((27, 81), 3, 14)]
+    plans, xs, ys, refs = [], [], [], []
+    try:
+        for dims, radix, seed in cases:
+            fs, h, x = separable_case(dims, "c64", seed)
+            p = pac.Plan(dims, radix, "c64")
+            p.filter_spectrum(dev(h))
+            plans.append(p)
+            xs.append(dev(x))
+            ys.append(torch.empty_like(xs[-1]))
+            refs.append(oracle.conv_separable(fs, x))
+        assert sum(p.query(pac.Q_NARROW) for p in plans) >= 1
+        for batch in ("graph", "persistent"):
+            monkeypatch.setenv("PAC_BATCH", batch)
+            for rep in range(2):
+                for y in ys:
+                    y.fill_(float("nan"))
+                pac.pac_convolve_many([p.handle for p in plans], xs, ys)
+                torch.cuda.synchronize()
+                for y, ref, (dims, _, _) in zip(ys, refs, cases):
+                    check(y.cpu().numpy(), ref, "c64", int(np.prod(dims)), f"many narrow {batch} {dims} rep {rep}")
+        # a narrow forward / inverse pass (axis 0) with a default-tile fused pass: the persistent
+        # kernel takes the batch (one launch) in its own tiles
+        dims = (128, 512)
+        fs, h, x = separable_case(dims, "c64", 15)
+        p = pac.Plan(dims, 2, "c64")
+        plans.append(p)
+        p.filter_spectrum(dev(h))
+        assert p.query(pac.Q_NARROW) == 1
+        assert pac.pac_convolve_many_launches([p.handle, p.handle]) == 1
+        xd = dev(x)
+        yd = [torch.full_like(xd, float("nan")) for _ in range(2)]
+        pac.pac_convolve_many([p.handle, p.handle], [xd, xd], yd)
+        torch.cuda.synchronize()
+        ref = oracle.conv_separable(fs, x)
+        for y in yd:
+            check(y.cpu().numpy(), ref, "c64", int(np.prod(dims)), "persistent, narrow axis-0 passes")
+    finally:
+        for p in plans:
+            p.close()
+
+
+def test_tune_file_narrow_flag(tmp_path):
+    """A tune-file line with flags bit 2 set makes later plans of that problem
+    take the narrow tile; the tuner's own run on the same problem records a
+    valid line, and its schedule matches the oracle."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(__file__))
+    path = tmp_path / "tune.txt"
+    # ndim n0 n1 n2 radix dtype cap flags us: 128^3 radix 4 c64, cap 0 (none), plane on, narrow
+    path.write_text("3 128 128 128 4 0 0 5 1.0\n")
+    env = dict(os.environ, PAC_TUNE_FILE=str(path))
+    code = ("import paper_2506_12718_gb300 as pac; pac.load(); import torch; torch.cuda.init(); "
+            "p = pac.Plan((128, 128, 128), 4, 'c64'); print(p.query(pac.Q_NARROW), p.query(pac.Q_PLANE)); p.close()")
+    out = subprocess.run([sys.executable, "-c", code], env=env, check=True, capture_output=True, text=True, cwd=root)
+    nv, plane = map(int, out.stdout.strip().splitlines()[-1].split())
+    assert nv >= 1 and plane >= 1
+    path2 = tmp_path / "tune2.txt"
+    env2 = dict(os.environ, PAC_TUNE_FILE=str(path2))
+    code1 = ("import paper_2506_12718_gb300 as pac; pac.load(); import torch; torch.cuda.init(); "
+             "print(pac.pac_tune((64, 64, 64), 4, 'c64', 3))")
+    subprocess.run([sys.executable, "-c", code1], env=env2, check=True, cwd=root)
+    line = path2.read_text().split()
+    assert len(line) == 9 and line[1] == "64" and int(line[7]) & ~0xF7 == 0
 
 
 def test_tune_search_at_plan_creation_and_plan_log():
@@ -1110,8 +1218,11 @@ def test_persistent_batch_is_one_launch_and_matches_the_merged_form(monkeypatch)
     as one launch (replayed from a graph): every instance matches the oracle,
     the same batch in the merged-launch form (PAC_BATCH=graph) to rounding,
     and a second call (the replay, counters reset by the kernel) gives the
-    same result bit for bit."""
+    same result bit for bit.  (The default tiles: a schedule tuned earlier in
+    the process may otherwise give a fused pass the narrow tile, which the
+    persistent kernel does not carry.)"""
     pac = pac_mod()
+    monkeypatch.setenv("PAC_NARROW", "0")
     plans, xs, refs = [], [], []
     try:
         for dims, radix, seed in PERSIST_CASES:
