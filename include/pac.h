@@ -22,7 +22,8 @@
  *  - Arrays are complex, interleaved (re, im), row-major with the last index
  *    fastest (the row-major vec of Section 4), dense, 16-byte aligned.
  *    dtype PAC_C64 = complex float (8 bytes/element), PAC_C128 = complex
- *    double (16 bytes/element).
+ *    double (16 bytes/element), PAC_C128_DF = complex double arrays
+ *    computed in double-float arithmetic (see pac_plan_create).
  *  - Pointers named *_dev are device pointers on the current CUDA device;
  *    pointers named *_host are host pointers (pinned memory gives the fastest
  *    copies).  The caller owns every array it passes; the library owns plans,
@@ -51,7 +52,7 @@ typedef struct pac_plan_s* pac_plan;   /* opaque, library-owned */
 typedef struct pac_queue_s* pac_queue; /* opaque, library-owned */
 typedef struct pac_pfa_s* pac_pfa;     /* opaque, library-owned */
 
-typedef enum { PAC_C64 = 0, PAC_C128 = 1 } pac_dtype;
+typedef enum { PAC_C64 = 0, PAC_C128 = 1, PAC_C128_DF = 2 } pac_dtype;
 
 typedef enum {
     PAC_OK = 0,
@@ -89,6 +90,17 @@ typedef enum {
  * dtype and uploads them to the current device.  On success *out owns device
  * memory until pac_plan_destroy.  Errors: PAC_ERR_ARG, PAC_ERR_SIZE,
  * PAC_ERR_NOMEM, PAC_ERR_CUDA.
+ *
+ * PAC_C128_DF: the same complex FP64 arrays in and out as PAC_C128 (h, x,
+ * y), the same stage groups, but every butterfly, twiddle and product in
+ * double-float arithmetic (a value as the unevaluated sum of two FP32
+ * numbers, about 48 significant bits) on the FP32 pipes, which GB300 runs at
+ * 64 times its FP64 rate; the twiddles are the FP64 tables split once into
+ * two FP32 parts.  The relative L2 error stays within the FP64 tolerance
+ * (1e-12) for magnitudes within FP32's range (about 1e-38 to 3e38; smaller
+ * values flush to 0).  One-base stage groups only (no plane pass, no groups
+ * spanning prime bases); pac_convolve, pac_convolve_host, pac_submit and
+ * pac_tune take such plans, the other entry points return PAC_ERR_ARG.
  */
 int pac_plan_create(int ndim, const int64_t* dims, int radix, pac_dtype dtype, pac_plan* out);
 

@@ -49,13 +49,14 @@ def complex_normal(shape, seed: int) -> np.ndarray:
 def as_dtype(a: np.ndarray, dtype: str) -> np.ndarray:
     """Round a complex128 array once to the working precision.
 
-    ``dtype`` is "c64" (complex FP32) or "c128" (complex FP64).  The oracle is
+    ``dtype`` is "c64" (complex FP32), or "c128" / "c128df" (complex FP64
+    arrays, computed in FP64 or in double-float arithmetic).  The oracle is
     then run on the rounded values promoted back to FP64, so an error measure
     reflects the algorithm only, not the input rounding.
     """
     if dtype == "c64":
         return a.astype(np.complex64)
-    if dtype == "c128":
+    if dtype in ("c128", "c128df"):
         return a.astype(np.complex128)
     raise ValueError(f"unknown dtype {dtype!r}")
 

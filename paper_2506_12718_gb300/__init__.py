@@ -20,7 +20,18 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpac.so")
 _lib = None
 
-C64, C128 = 0, 1
+C64, C128, C128_DF = 0, 1, 2
+# dtype names: "c64" complex FP32, "c128" complex FP64, "c128df" complex FP64
+# arrays computed in double-float arithmetic (PAC_C128_DF)
+_DTYPE_CODES = {"c64": C64, "c128": C128, "c128df": C128_DF}
+
+
+def _dtype_code(dtype) -> int:
+    if isinstance(dtype, str):
+        if dtype not in _DTYPE_CODES:
+            raise ValueError(f"dtype must be one of {sorted(_DTYPE_CODES)}, not {dtype!r}")
+        return _DTYPE_CODES[dtype]
+    return int(dtype)
 
 
 class Status(enum.IntEnum):
@@ -328,7 +339,7 @@ def pac_tune(dims, radix: int, dtype: str = "c64", reps: int = 5) -> float:
     vals = [int(v) for v in dims]
     d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
     us = ctypes.c_double(0.0)
-    _check(load().pac_tune(len(vals), d, int(radix), C64 if dtype == "c64" else C128, int(reps), ctypes.byref(us)))
+    _check(load().pac_tune(len(vals), d, int(radix), _dtype_code(dtype), int(reps), ctypes.byref(us)))
     return us.value
 
 
@@ -406,7 +417,8 @@ def pac_queue_destroy(queue: int) -> None:
 
 
 class Plan:
-    """A convolution plan bound to torch tensors (complex64 / complex128, on CUDA)."""
+    """A convolution plan bound to torch tensors (complex64 for "c64",
+    complex128 for "c128" and "c128df", on CUDA)."""
 
     def __init__(self, dims, radix: int, dtype: str = "c64", stages=None):
         """radix in {2,3,4,5,8}, or 0 for mixed radix (dims 2^a 3^b 5^c); or
@@ -414,7 +426,7 @@ class Plan:
         self.dims = tuple(int(d) for d in dims)
         self.radix = int(radix) if stages is None else -1
         self.dtype = dtype
-        code = C64 if dtype == "c64" else C128
+        code = _dtype_code(dtype)
         if stages is None:
             self.handle = pac_plan_create(len(self.dims), self.dims, self.radix, code)
         else:

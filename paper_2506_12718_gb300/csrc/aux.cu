@@ -80,6 +80,17 @@ __global__ void spec_order_kernel(const SpecOrder o, uint32_t n, const V* __rest
     }
 }
 
+cudaError_t launch_spec_order_df(const SpecOrder& o, int64_t n, const void* src, void* dst, cudaStream_t s,
+                                 double scale) {
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((n + threads - 1) / threads, 8192);
+    const float hi = (float)scale;
+    const dfloat sc(hi, (float)(scale - (double)hi));
+    spec_order_kernel<dfloat2><<<(unsigned)blocks, threads, 0, s>>>(o, (uint32_t)n, (const dfloat2*)src, (dfloat2*)dst,
+                                                                    1, sc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spec_order(int esize, const SpecOrder& o, int64_t n, const void* src, void* dst, bool to_kernel,
                               cudaStream_t s, double scale) {
     const int threads = 256;

@@ -423,6 +423,7 @@ extern "C" int pac_convolve_many(int count, const pac_plan* plans, const void* c
             return fail(PAC_ERR_ARG, "instance %d: arrays must be 16-byte aligned", i);
         if (!plans[i]->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "instance %d: plan has no spectrum", i);
         if (plans[i]->device != dev) return fail(PAC_ERR_ARG, "instance %d: plan belongs to another device", i);
+        if (int rc = df_unsupported(plans[i], "pac_convolve_many")) return rc;
     }
     if (count == 0) return PAC_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -496,8 +497,10 @@ static bool persist_applies(int count, const pac_plan* plans) {
 
 extern "C" int pac_convolve_many_launches(int count, const pac_plan* plans, int* launches) {
     if (count < 0 || !launches || (count > 0 && !plans)) return fail(PAC_ERR_ARG, "bad arguments");
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
         if (!plans[i]) return fail(PAC_ERR_ARG, "null plan %d", i);
+        if (int rc = df_unsupported(plans[i], "pac_convolve_many_launches")) return rc;
+    }
     if (persistent_wanted() && persist_applies(count, plans)) {
         int n = 1;
         for (int i = 0; i < count; ++i) n += plans[i]->groups.empty() ? 1 : 0;
@@ -531,6 +534,7 @@ extern "C" int pac_test_batch_timeout(int count, const pac_plan* plans, const vo
     for (int i = 0; i < count; ++i) {
         if (!plans[i] || !x_dev[i] || !y_dev[i]) return fail(PAC_ERR_ARG, "null entry %d", i);
         if (!plans[i]->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "instance %d: plan has no spectrum", i);
+        if (int rc = df_unsupported(plans[i], "a batch")) return rc;
     }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);

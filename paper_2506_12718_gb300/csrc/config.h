@@ -195,6 +195,13 @@ constexpr int reg_target(int m, int esize) {
 constexpr int min_blocks(int m, int esize, int nv = 0) {
     return clampi(65536 / (pass_threads(m, esize, nv) * reg_target(m, esize)), 1, 8);
 }
+// The double-float kernels (16-byte elements like complex FP64, so the same
+// tiles and rounds): a double-float value takes two registers like an FP64
+// one, but each operation keeps a few FP32 temporaries live.
+constexpr int reg_target_df(int m) {
+    return max_round_radix(m, 16) >= 25 ? 255 : (max_round_radix(m, 16) >= 16 ? 168 : 128);
+}
+constexpr int min_blocks_df(int m) { return clampi(65536 / (pass_threads(m, 16) * reg_target_df(m)), 1, 8); }
 
 // ------------------------------------------------- the runtime-radix kernel
 // Mixed groups without a compiled kernel run in the runtime-radix kernel

@@ -17,7 +17,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "config.h"
+#include "df.cuh"
 #include "pass_args.h"
 #include "roots.h"
 
@@ -28,6 +31,7 @@ namespace pac {
 template <typename V> struct Real;
 template <> struct Real<float2> { using T = float; };
 template <> struct Real<double2> { using T = double; };
+template <> struct Real<dfloat2> { using T = dfloat; };  // double-float (df.cuh)
 
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return V{a.x + b.x, a.y + b.y}; }
 template <typename V> __device__ __forceinline__ V csub(V a, V b) { return V{a.x - b.x, a.y - b.y}; }
@@ -48,9 +52,17 @@ template <typename V> __device__ __forceinline__ V cscale(V a, typename Real<V>:
 template <typename V> __device__ __forceinline__ typename Real<V>::T tau_const(int off);
 template <> __device__ __forceinline__ float tau_const<float2>(int off) { return c_tau32[off]; }
 template <> __device__ __forceinline__ double tau_const<double2>(int off) { return c_tau64[off]; }
+template <> __device__ __forceinline__ dfloat tau_const<dfloat2>(int off) {
+    const float2 f = c_taudf[off];
+    return dfloat(f.x, f.y);
+}
 template <typename V> __device__ __forceinline__ typename Real<V>::T bfly_const(int off);
 template <> __device__ __forceinline__ float bfly_const<float2>(int off) { return c_bfly32[off]; }
 template <> __device__ __forceinline__ double bfly_const<double2>(int off) { return c_bfly64[off]; }
+template <> __device__ __forceinline__ dfloat bfly_const<dfloat2>(int off) {
+    const float2 f = c_bflydf[off];
+    return dfloat(f.x, f.y);
+}
 
 __host__ __device__ constexpr int tau_off(int r) {
     return r == 3 ? PAC_TAU_OFF_3
@@ -271,8 +283,33 @@ template <int R, bool INV, typename V> __device__ __forceinline__ void dft(V* v)
 // write per element, plus one shared-memory write and read per round
 // boundary; there is no separate copy-in or copy-out of the tile.
 
+// read-only loads of a complex element (double-float: one 16-byte load)
+template <typename V> __device__ __forceinline__ V ldg_v(const V* p) { return __ldg(p); }
+template <> __device__ __forceinline__ dfloat2 ldg_v<dfloat2>(const dfloat2* p) {
+    const float4 f = __ldg(reinterpret_cast<const float4*>(p));
+    return dfloat2{dfloat(f.x, f.y), dfloat(f.z, f.w)};
+}
+
+// Loads and stores of the arrays a pass reads and writes.  The double-float
+// passes keep their intermediate arrays as double-float pairs (16 bytes an
+// element, like complex FP64) and read the caller's input / write the
+// caller's output as complex FP64 (PassArgs::df bits kDfSrc64 / kDfDst64).
+template <typename V> __device__ __forceinline__ V gload(const PassArgs&, const V* p, uint32_t i) { return p[i]; }
+template <> __device__ __forceinline__ dfloat2 gload<dfloat2>(const PassArgs& a, const dfloat2* p, uint32_t i) {
+    if (a.df & kDfSrc64) return df2_from_double2(reinterpret_cast<const double2*>(p)[i]);
+    const float4 f = reinterpret_cast<const float4*>(p)[i];
+    return dfloat2{dfloat(f.x, f.y), dfloat(f.z, f.w)};
+}
+template <typename V> __device__ __forceinline__ void gstore(const PassArgs&, V* p, uint32_t i, V v) { p[i] = v; }
+template <> __device__ __forceinline__ void gstore<dfloat2>(const PassArgs& a, dfloat2* p, uint32_t i, dfloat2 v) {
+    if (a.df & kDfDst64)
+        reinterpret_cast<double2*>(p)[i] = df2_to_double2(v);
+    else
+        reinterpret_cast<float4*>(p)[i] = float4{v.x.hi, v.x.lo, v.y.hi, v.y.lo};
+}
+
 template <typename V> __device__ __forceinline__ V ld_tw(const void* p, int64_t i) {
-    return __ldg(reinterpret_cast<const V*>(p) + i);
+    return ldg_v(reinterpret_cast<const V*>(p) + i);
 }
 
 // external factor w_L^e, e < L, from the two-level table
@@ -570,7 +607,7 @@ __device__ __forceinline__ void task_body(const TileCtx<typename GEO::V>& c, con
     } else if constexpr (DST == kToNatural) {
         if (col.valid) {
 #pragma unroll
-            for (int u = 0; u < R; ++u) dst[col.base + (uint32_t)(t.row0 + SP * u) * stride] = v[u];
+            for (int u = 0; u < R; ++u) gstore(a, dst, col.base + (uint32_t)(t.row0 + SP * u) * stride, v[u]);
         }
     } else {
         if (col.valid) {
@@ -581,7 +618,7 @@ __device__ __forceinline__ void task_body(const TileCtx<typename GEO::V>& c, con
                 if constexpr (!LINES) {
                     if (a.has_ext && col.j != 0) o = cmul(o, ext_twiddle<V>(a, (int64_t)col.j * __ldg(a.r2f + row)));
                 }
-                dst[col.base + (uint32_t)__ldg(a.r2g + row) * stride] = o;
+                gstore(a, dst, col.base + (uint32_t)__ldg(a.r2g + row) * stride, o);
             }
         }
     }
@@ -600,7 +637,7 @@ __device__ __forceinline__ void load_src(const TileCtx<typename GEO::V>& c, cons
     for (int u = 0; u < G::R; ++u) {
         const int row = t.row0 + G::SP * u;
         const uint32_t g = SRC == kFromNatural ? (uint32_t)row : (uint32_t)__ldg(a.r2g + row);
-        v[u] = col.valid ? src[col.base + g * stride] : V{0, 0};
+        v[u] = col.valid ? gload(a, src, col.base + g * stride) : V{0, 0};
     }
 }
 
@@ -615,7 +652,7 @@ __device__ __forceinline__ void load_spec(const TileCtx<typename GEO::V>& c, int
     constexpr int TASKS = TT::TASKS;
     const V* spec = reinterpret_cast<const V*>(c.a->spec) + (size_t)c.t * (GEO::W * GEO::M) + tau;
 #pragma unroll
-    for (int u = 0; u < G::R; ++u) hs[u] = col.valid ? __ldg(spec + u * TASKS) : V{0, 0};
+    for (int u = 0; u < G::R; ++u) hs[u] = col.valid ? ldg_v(spec + u * TASKS) : V{0, 0};
 }
 
 // One round of a tile.  SRC: shared memory, natural global rows, or global
@@ -824,9 +861,14 @@ template <typename V, int M, int NV = 0> constexpr int pass_smem_bytes(bool line
     return (lines ? Shape<V, M, true, NV>::TILE : Shape<V, M, false, NV>::TILE) * (int)sizeof(V);
 }
 
+// CTAs per SM the pass kernels are compiled for (the register budget)
+template <typename V, int M, int NV> constexpr int pass_min_blocks() {
+    return std::is_same<V, dfloat2>::value ? min_blocks_df(M) : min_blocks(M, sizeof(V), NV);
+}
+
 // Generic pass kernel: one pass of a convolution (see run_phase).
 template <typename V, int M, bool LINES, int NV = 0>
-__global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), min_blocks(M, sizeof(V), NV))
+__global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), (pass_min_blocks<V, M, NV>()))
     pass_kernel(const __grid_constant__ PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_launch_dependents();
@@ -838,7 +880,7 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), min_blocks(M, 
 // tiles of passes list[0..n) are numbered consecutively, pass i owning global
 // tiles [tile_start[i], tile_start[i+1]); CTAs walk the global tiles.
 template <typename V, int M, bool LINES, int NV = 0>
-__global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), min_blocks(M, sizeof(V), NV))
+__global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), (pass_min_blocks<V, M, NV>()))
     pass_multi_kernel(const PassArgs* __restrict__ list, const uint32_t* __restrict__ tile_start, int n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* s = reinterpret_cast<V*>(smem_raw);

@@ -21,6 +21,9 @@
   angle (pi by Machin's formula, sin and cos by their Taylor series after an
   exact reduction to at most an eighth turn), rounded once to FP64, and the
   FP32 table is the FP64 table rounded once.
+* c_taudf, c_bflydf: the same constants as double-float pairs {hi, lo} for
+  the double-float kernels: hi the decimal value rounded to FP32, lo the
+  remainder rounded to FP32 (about 48 significant bits in all).
 
 Literals are written as C hex floats, so the tables hold exactly these
 values.  Run: python gen_roots.py > roots.h
@@ -155,6 +158,13 @@ def hexd(v):
     return float(v).hex()
 
 
+def df_pair(v):
+    """{hi, lo} float literals: v (decimal) rounded to FP32, then the remainder rounded to FP32"""
+    hi = f32(float(v))
+    lo = f32(float(CTX.subtract(v, D(hi))))
+    return f"{{{hi.hex()}f, {lo.hex()}f}}"
+
+
 def main():
     offs, taus = {}, []
     for r in RADICES:
@@ -163,7 +173,8 @@ def main():
     boffs, bvals = bfly_table()
     print("// Generated by gen_roots.py -- do not edit.")
     print("// Factored twiddles (tau), stage-2 butterfly constants and FP32 roots of the in-register DFT splits,")
-    print("// computed in 60-digit decimal arithmetic, rounded once to FP64 and FP64 rounded once to FP32.")
+    print("// computed in 60-digit decimal arithmetic, rounded once to FP64 and FP64 rounded once to FP32;")
+    print("// double-float pairs {hi, lo} of the same decimal values.")
     print("#pragma once")
     for r in RADICES:
         print(f"#define PAC_TAU_OFF_{r} {offs[r]}")
@@ -193,6 +204,12 @@ def main():
     print("};")
     print("static __constant__ float c_bfly32[PAC_BFLY_COUNT] = {")
     print(",\n".join(f"    {f32(float(v)).hex()}f" for v in bvals))
+    print("};")
+    print("static __constant__ float2 c_taudf[PAC_TAU_COUNT] = {")
+    print(",\n".join(f"    {df_pair(t)}" for t in taus))
+    print("};")
+    print("static __constant__ float2 c_bflydf[PAC_BFLY_COUNT] = {")
+    print(",\n".join(f"    {df_pair(v)}" for v in bvals))
     print("};")
 
 

@@ -24,7 +24,16 @@ cudaError_t launch_multi_mixc(int esize, int M, bool lines, int nv, const PassAr
 cudaError_t launch_mix_multi(int esize, int M, bool lines, const PassArgs* list, const uint32_t* starts, int n,
                              int64_t total, cudaStream_t s);
 
+cudaError_t launch_pass_df_p2(int M, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_pass_df_p3(int M, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_pass_df_p5(int M, const PassArgs& a, cudaStream_t s);
+
 cudaError_t launch_pass(int esize, int M, const PassArgs& a, cudaStream_t s) {
+    if (a.df & kDfKernel) {  // double-float plans: one-base groups only
+        if (a.mix_nr > 0 || is_mixed(M)) return cudaErrorInvalidValue;
+        return (M % 2 == 0) ? launch_pass_df_p2(M, a, s)
+                            : (M % 3 == 0 ? launch_pass_df_p3(M, a, s) : launch_pass_df_p5(M, a, s));
+    }
     if (a.mix_nr > 0) return launch_mix(esize, a.C == 1, a, s);
     if (is_mixed(M)) return launch_pass_mixc(esize, M, a, s);
     if (esize == 8) return (M % 2 == 0) ? launch_pass_c64_p2(M, a, s) : launch_pass_c64_p35(M, a, s);

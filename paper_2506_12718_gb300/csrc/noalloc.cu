@@ -29,10 +29,6 @@
 #include "fft_device.cuh"
 #include "pac_internal.h"
 
-namespace pac {
-int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, cudaStream_t s);
-}
-
 using namespace pac;
 
 #define PAC_NOALLOC_SCRATCH_BYTES (8u << 20)
@@ -133,6 +129,7 @@ extern "C" int pac_convolve_permuted_noalloc(pac_plan p, const void* x_dev, void
     if (reinterpret_cast<uintptr_t>(x_dev) % 16 || reinterpret_cast<uintptr_t>(y_dev) % 16)
         return fail(PAC_ERR_ARG, "arrays must be 16-byte aligned");
     if (!p->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "pac_filter_spectrum was not called for this plan");
+    if (int rc = df_unsupported(p, "pac_convolve_permuted_noalloc")) return rc;
     const uint64_t need = (uint64_t)p->N * (uint64_t)p->esize;
     if (need > PAC_NOALLOC_SCRATCH_BYTES)
         return fail(PAC_ERR_SIZE,

@@ -90,9 +90,13 @@ struct Step {
     int group, mode;
     const void* src;
     void* dst;
+    int io = 0;  // double-float plans: kDfSrc64 / kDfDst64 (the caller's FP64 arrays)
 };
 void convolve_steps(pac_plan p, const void* x, void* y, std::vector<Step>& out);
-PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst);
+PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, int io = 0);
+int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, cudaStream_t s, int io = 0);
+// PAC_ERR_ARG for an entry point that does not take double-float plans (PAC_OK otherwise)
+int df_unsupported(pac_plan p, const char* what);
 // forget every cached batch that uses plan p (batch.cu); called by pac_plan_destroy
 void batch_forget_plan(pac_plan p);
 
@@ -108,6 +112,9 @@ int take_device_error(int device, unsigned* value);
 cudaError_t launch_permute(int esize, int ndim, const int64_t* dims, const int64_t* const* idx_dev,
                            const void* src, void* dst, const void* mul, cudaStream_t s, double scale = 1.0);
 // to_kernel: dst[slot(e)] = src[e] * scale; else dst[e] = src[slot(e)] * scale
+// double-float spectra (df): 16-byte elements of two double-float parts, the scale applied in double-float
+cudaError_t launch_spec_order_df(const SpecOrder& o, int64_t n, const void* src, void* dst, cudaStream_t s,
+                                 double scale);
 cudaError_t launch_spec_order(int esize, const SpecOrder& o, int64_t n, const void* src, void* dst, bool to_kernel,
                               cudaStream_t s, double scale = 1.0);
 cudaError_t launch_pointwise_mul(int esize, int64_t n, const void* a, const void* b, void* out, double scale,
@@ -126,6 +133,7 @@ struct pac_plan_s {
     int radix = 2;
     pac_dtype dtype = PAC_C64;
     int esize = 8;
+    bool df = false;  // PAC_C128_DF: double-float passes (kDf* bits in PassArgs::df)
     int64_t N = 1;
     int uniform_m = 0;  // group size shared by every pass (0: sizes differ)
     bool plane = false;  // the last two axes run as one plane pass (groups plane_g1, plane_g1 + 1)

@@ -6,6 +6,11 @@ namespace pac {
 
 enum PassMode : int { kFwd = 0, kInv = 1, kFused = 2, kPlane = 3 };
 
+// PassArgs::df bits of a double-float plan's passes: the pass runs the
+// double-float kernels; its source / destination holds complex FP64 (the
+// caller's arrays) instead of double-float pairs (the intermediate arrays).
+enum : int { kDfKernel = 1, kDfSrc64 = 2, kDfDst64 = 4 };
+
 // One pass over the array, viewed as [beta][m][c]: m in [0, M) is the group
 // axis (row stride C elements); column q = beta * C + c, Q = N / M columns.
 // Element (row g, column q) sits at (q - q mod C) * M + q mod C + g * C.
@@ -30,6 +35,7 @@ struct PassArgs {
     int mode;               // PassMode
     int has_ext;            // apply w_L^{j k'} (L' > 1)
     int nv;                 // 1: the narrow tile variant of the group (has_narrow), 0: the default tile
+    int df;                 // double-float plans: kDf* bits; 0 otherwise
     // mixed group (stages of several prime bases, the runtime-radix kernel):
     // mix_nr rounds of radices mix_r (0: a one-base group), group size mix_m,
     // tile width mix_w

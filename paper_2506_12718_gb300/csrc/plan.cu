@@ -350,6 +350,18 @@ int64_t twiddle_count(const GroupPlan& g, int which) {
     return which == 1 ? g.tw_T : (g.L + g.tw_T - 1) / g.tw_T;
 }
 
+// FP64 complex values [off, off + 16 n) of the blob as double-float pairs in
+// the same bytes: each double d becomes hi = d rounded to FP32, lo = d - hi
+// rounded to FP32
+void df_split(std::vector<unsigned char>& blob, size_t off, size_t n) {
+    for (size_t i = 0; i < 2 * n; ++i) {
+        double d;
+        std::memcpy(&d, blob.data() + off + 8 * i, 8);
+        const float hl[2] = {(float)d, (float)(d - (double)(float)d)};
+        std::memcpy(blob.data() + off + 8 * i, hl, 8);
+    }
+}
+
 void fill_twiddles(const GroupPlan& g, int esize, int which, std::vector<unsigned char>& blob, size_t off) {
     const int64_t n = twiddle_count(g, which);
     for (int64_t u = 0; u < n; ++u) {
@@ -636,7 +648,8 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     if (!out) return fail(PAC_ERR_ARG, "null out");
     *out = nullptr;
     if (ndim < 1 || ndim > 3 || !dims || (int)stages.size() != ndim) return fail(PAC_ERR_ARG, "ndim must be 1, 2 or 3");
-    if (dtype != PAC_C64 && dtype != PAC_C128) return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
+    if (dtype != PAC_C64 && dtype != PAC_C128 && dtype != PAC_C128_DF)
+        return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
     for (int a = 0; a < ndim; ++a) {
         if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
             return fail(PAC_ERR_SIZE, "dimension %lld out of range", (long long)dims[a]);
@@ -669,6 +682,7 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     pl->radix = radix;
     pl->dtype = dtype;
     pl->esize = dtype == PAC_C64 ? 8 : 16;
+    pl->df = dtype == PAC_C128_DF;
     pl->N = n_total;
     for (int a = 0; a < ndim; ++a) pl->dims[a] = dims[a];
     pl->stages = stages;
@@ -687,6 +701,10 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     if (me && me[0] == 'r' && me[1] == 't') {
         gs.mixed = 1;
         gs.mix_runtime = true;
+    }
+    if (pl->df) {  // the double-float kernels are compiled for one-base groups only
+        gs.mixed = 0;
+        gs.mix_runtime = false;
     }
     if (int rc = form_groups(ndim, dims, pl->stages, pl->esize, gs, pl->groups)) {
         delete pl;
@@ -715,11 +733,11 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     // single-launch (cooperative) form of the pass sequence: opt-in per plan,
     // PAC_SINGLE_LAUNCH=1 in the environment when the plan is created
     const char* sl = std::getenv("PAC_SINGLE_LAUNCH");
-    pl->single_launch = sl && sl[0] == '1';
+    pl->single_launch = sl && sl[0] == '1' && !pl->df;
     // plane pass: axis d-1 one group, a supported shape of (last group of axis d-2) x (axis d-1);
     // PAC_PLANE=0 in the environment keeps per-axis passes instead
     const char* pe = std::getenv("PAC_PLANE");
-    if (ndim >= 2 && sch.plane && !(pe && pe[0] == '0')) {
+    if (ndim >= 2 && sch.plane && !pl->df && !(pe && pe[0] == '0')) {
         int g_last = 0, g_prev = 0;
         for (const GroupPlan& g : pl->groups) {
             if (g.axis == ndim - 1) ++g_last;
@@ -744,6 +762,7 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     int nv = sch.nv;
     const char* ne = std::getenv("PAC_NARROW");
     if (ne && (ne[0] == '0' || ne[0] == '1')) nv = ne[0] == '1' ? 1 : 0;
+    if (pl->df) nv = 0;
     for (int i = 0; i < (int)pl->groups.size(); ++i) {
         GroupPlan& g = pl->groups[i];
         const bool in_plane = pl->plane && i >= pl->plane_g1;
@@ -754,6 +773,7 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
         pl->uniform_m = pl->groups[0].M;
         for (const GroupPlan& g : pl->groups)
             if (g.M != pl->uniform_m || g.mix_nr > 0 || g.nv) pl->uniform_m = 0;
+        if (pl->df) pl->uniform_m = 0;  // no single-launch kernel of the double-float type
     }
 
     // host blob of every table
@@ -785,6 +805,13 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
             rowmap[gg] = f2r[f[gg]];
             r2g[rowmap[gg]] = gg;
             r2f[rowmap[gg]] = (int)f[gg];
+        }
+        if (pl->df) {  // twiddles as double-float pairs: each FP64 value split once into hi + lo
+            df_split(blob, g.off_twi, (size_t)g.M);
+            if (g.has_ext) {
+                df_split(blob, g.off_lo, (size_t)g.tw_T);
+                df_split(blob, g.off_hi, (size_t)((g.L + g.tw_T - 1) / g.tw_T));
+            }
         }
     }
 
@@ -894,7 +921,7 @@ SpecOrder spec_order_of(pac_plan p) {
     return o;
 }
 
-PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst) {
+PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, int io) {
     PassArgs a;
     const unsigned char* t = static_cast<const unsigned char*>(p->d_tables);
     a.src = src;
@@ -918,6 +945,7 @@ PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, vo
     a.mode = mode;
     a.has_ext = g.has_ext ? 1 : 0;
     a.nv = g.nv;
+    a.df = p->df ? (kDfKernel | io) : 0;
     a.mix_nr = g.mix_nr;
     a.mix_m = g.M;
     a.mix_w = W;
@@ -942,8 +970,8 @@ static int run_plane(pac_plan p, const void* src, void* dst, cudaStream_t s) {
     return PAC_OK;
 }
 
-int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, cudaStream_t s) {
-    const PassArgs a = make_pass(p, g, mode, src, dst);
+int run_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, cudaStream_t s, int io) {
+    const PassArgs a = make_pass(p, g, mode, src, dst, io);
     const int kid = mode == kFwd ? 0 : (mode == kFused ? 1 : 2);
     timer_mark(s, kid, true);
     cudaError_t e = launch_pass(p->esize, g.M, a, s);
@@ -989,7 +1017,7 @@ static int run_steps(pac_plan p, const std::vector<Step>& steps, cudaStream_t s,
     if (single) return run_single(p, steps, grid, 0u, 0u, s);
     for (const Step& st : steps) {
         int rc = st.mode == kPlane ? run_plane(p, st.src, st.dst, s)
-                                   : run_pass(p, p->groups[st.group], st.mode, st.src, st.dst, s);
+                                   : run_pass(p, p->groups[st.group], st.mode, st.src, st.dst, s, st.io);
         if (rc) return rc;
     }
     return PAC_OK;
@@ -1033,6 +1061,10 @@ void convolve_steps(pac_plan p, const void* x, void* y, std::vector<Step>& steps
     }
     for (int i = 0; i < G; ++i) steps.push_back({i, i == G - 1 ? kFused : kFwd, i == 0 ? x : y, y});
     for (int i = G - 2; i >= 0; --i) steps.push_back({i, kInv, y, y});
+    if (!steps.empty()) {  // double-float plans: the caller's x and y are complex FP64
+        steps.front().io |= kDfSrc64;
+        steps.back().io |= kDfDst64;
+    }
 }
 
 int run_convolve(pac_plan p, const void* x, void* y, cudaStream_t s) { return run_convolve(p, x, y, s, true); }
@@ -1045,9 +1077,16 @@ int run_forward(pac_plan p, const void* x, void* xhat, cudaStream_t s) {
     }
     std::vector<Step> steps;
     for (int i = 0; i < G; ++i) steps.push_back({i, kFwd, i == 0 ? x : xhat, xhat});
+    steps.front().io |= kDfSrc64;  // double-float plans: x is complex FP64, xhat double-float pairs
     return run_steps(p, steps, s, true);
 }
 
+}  // namespace pac
+
+namespace pac {
+int df_unsupported(pac_plan p, const char* what) {
+    return p && p->df ? fail(PAC_ERR_ARG, "%s does not take double-float (PAC_C128_DF) plans", what) : PAC_OK;
+}
 }  // namespace pac
 
 static int check_ptr(const void* ptr, const char* name) {
@@ -1061,6 +1100,7 @@ static int check_ptr(const void* ptr, const char* name) {
 // makes, each wait limited to spin_limit polls.
 extern "C" int pac_test_barrier_timeout(pac_plan p, const void* x_dev, void* y_dev, void* stream, int spin_limit) {
     if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = df_unsupported(p, "pac_test_barrier_timeout")) return rc;
     if (int rc = check_ptr(x_dev, "x_dev")) return rc;
     if (int rc = check_ptr(y_dev, "y_dev")) return rc;
     if (!p->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "pac_filter_spectrum was not called for this plan");
@@ -1124,7 +1164,8 @@ extern "C" int pac_filter_spectrum(pac_plan p, const void* h_dev) {
         }
         rc = run_forward(p, h_dev, tmp, s);
         if (rc == PAC_OK) {
-            e = launch_spec_order(p->esize, spec_order_of(p), p->N, tmp, p->d_spec, true, s, 1.0 / (double)p->N);
+            e = p->df ? launch_spec_order_df(spec_order_of(p), p->N, tmp, p->d_spec, s, 1.0 / (double)p->N)
+                      : launch_spec_order(p->esize, spec_order_of(p), p->N, tmp, p->d_spec, true, s, 1.0 / (double)p->N);
             if (e != cudaSuccess) rc = cuda_fail(e, "spectrum order kernel");
         }
     }
@@ -1152,6 +1193,7 @@ extern "C" int pac_convolve(pac_plan p, const void* x_dev, void* y_dev, void* st
 
 extern "C" int pac_forward_unordered(pac_plan p, const void* x_dev, void* xhat_dev, void* stream) {
     if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = df_unsupported(p, "pac_forward_unordered")) return rc;
     if (int rc = check_ptr(x_dev, "x_dev")) return rc;
     if (int rc = check_ptr(xhat_dev, "xhat_dev")) return rc;
     return run_forward(p, x_dev, xhat_dev, static_cast<cudaStream_t>(stream));
@@ -1189,9 +1231,8 @@ static int ensure_host_pipeline(pac_plan p) {
 }
 
 // One pass over tiles [t0, t0 + nt) of group g.
-static int run_pass_tiles(pac_plan p, const GroupPlan& g, int mode, const void* src, void* dst, int64_t t0, int64_t nt,
-                          cudaStream_t s) {
-    PassArgs a = make_pass(p, g, mode, src, dst);
+static int run_pass_tiles(pac_plan p, const GroupPlan& g, const Step& st, int64_t t0, int64_t nt, cudaStream_t s) {
+    PassArgs a = make_pass(p, g, st.mode, st.src, st.dst, st.io);
     a.tile0 = t0;
     a.tiles = nt;
     cudaError_t e = launch_pass(p->esize, g.M, a, s);
@@ -1221,8 +1262,7 @@ static int convolve_host_pipelined(pac_plan p, const void* x_host, void* y_host,
         if (e == cudaSuccess) e = cudaEventRecord(ev[k], p->h2d);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev[k], 0);
         if (e != cudaSuccess) return cuda_fail(e, "copy x to device");
-        const Step& st = steps.front();
-        if (int rc = run_pass_tiles(p, g, st.mode, st.src, st.dst, t0, t1 - t0, s)) return rc;
+        if (int rc = run_pass_tiles(p, g, steps.front(), t0, t1 - t0, s)) return rc;
     }
     // the middle passes on the whole array
     std::vector<Step> mid(steps.begin() + 1, steps.end() - 1);
@@ -1232,8 +1272,7 @@ static int convolve_host_pipelined(pac_plan p, const void* x_host, void* y_host,
         const int64_t t0 = k * per, t1 = std::min(tiles, t0 + per);
         if (t0 >= t1) break;
         const int64_t q0 = t0 * W, q1 = std::min<int64_t>(g.Q, t1 * W);
-        const Step& st = steps.back();
-        if (int rc = run_pass_tiles(p, g, st.mode, st.src, st.dst, t0, t1 - t0, s)) return rc;
+        if (int rc = run_pass_tiles(p, g, steps.back(), t0, t1 - t0, s)) return rc;
         e = cudaEventRecord(ev[kHostBlocks + k], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->d2h, ev[kHostBlocks + k], 0);
         if (e == cudaSuccess)
@@ -1331,6 +1370,7 @@ static int ensure_permuted_state(pac_plan p) {
 
 extern "C" int pac_convolve_permuted(pac_plan p, const void* x_dev, void* y_dev, void* stream) {
     if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = df_unsupported(p, "pac_convolve_permuted")) return rc;
     if (int rc = check_ptr(x_dev, "x_dev")) return rc;
     if (int rc = check_ptr(y_dev, "y_dev")) return rc;
     if (!p->has_spec) return fail(PAC_ERR_NO_SPECTRUM, "pac_filter_spectrum was not called for this plan");
@@ -1369,6 +1409,7 @@ static int ensure_perm_tables(pac_plan p);
 
 extern "C" int pac_fft(pac_plan p, const void* in_dev, void* out_dev, int inverse, void* stream) {
     if (!p) return fail(PAC_ERR_ARG, "null plan");
+    if (int rc = df_unsupported(p, "pac_fft")) return rc;
     if (int rc = check_ptr(in_dev, "in_dev")) return rc;
     if (int rc = check_ptr(out_dev, "out_dev")) return rc;
     {

@@ -245,7 +245,7 @@ extern "C" int pac_submit(pac_queue q, pac_plan p, const void* x_dev, void* y_de
     r->y = y_dev;
     r->bytes = 2 * (size_t)p->bytes();
     r->small = r->bytes <= kSmallBytes;
-    r->fp64 = p->dtype == PAC_C128;
+    r->fp64 = p->dtype != PAC_C64;  // complex FP64 arrays (either arithmetic)
     r->owner = q;
     r->t_submit = Clock::now();
     {

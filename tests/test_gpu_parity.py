@@ -40,7 +40,8 @@ def pac_mod():
 
 
 def tol(dtype, n):
-    return 1e-12 if dtype == "c128" else 1e-5 * max(1.0, math.log2(n))
+    # complex FP64 arrays, computed in FP64 ("c128") or double-float arithmetic ("c128df"): the FP64 bound
+    return 1e-12 if dtype in ("c128", "c128df") else 1e-5 * max(1.0, math.log2(n))
 
 
 def dev(a):
@@ -84,7 +85,7 @@ def test_c1_full_definition():
     check(y, oracle.conv_direct(h, x), c.dtype, c.n_total, "c1")
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("dtype", ["c64", "c128", "c128df"])
 @pytest.mark.parametrize("radix", [2, 4, 8])
 def test_c2_128_cubed_gaussian(radix, dtype):
     """3-D 128^3 periodic convolution with the sigma=4 Gaussian, full array (O2)."""
@@ -106,7 +107,7 @@ def _c2_ref(dtype):
     return _C2_CACHE[dtype]
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("dtype", ["c64", "c128", "c128df"])
 @pytest.mark.parametrize("radix", [3, 5])
 def test_c3_large_2d_exponential(radix, dtype):
     """2-D 2187^2 (radix 3) and 3125^2 (radix 5) with the separable exponential (O2)."""
@@ -130,7 +131,7 @@ SHAPES = [
 ]
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("dtype", ["c64", "c128", "c128df"])
 @pytest.mark.parametrize("dims,radix", SHAPES, ids=[f"{'x'.join(map(str, d))}-r{r}" for d, r in SHAPES])
 def test_shapes_separable(dims, radix, dtype):
     fs, h, x = separable_case(dims, dtype, seed=hash((dims, radix)) % 1000)
@@ -955,6 +956,89 @@ def test_tune_file_narrow_flag(tmp_path):
     subprocess.run([sys.executable, "-c", code1], env=env2, check=True, cwd=root)
     line = path2.read_text().split()
     assert len(line) == 9 and line[1] == "64" and int(line[7]) & ~0xF7 == 0
+
+
+DF_SHAPES = [((4096,), 2), ((3125,), 5), ((2187,), 3), ((25, 125), 5), ((81, 81), 3), ((64, 64, 64), 4),
+             ((2, 1024), 2), ((27, 9, 3), 3), ((16384, 2), 2)]
+
+
+@pytest.mark.parametrize("dims,radix", DF_SHAPES, ids=[f"{'x'.join(map(str, d))}-r{r}" for d, r in DF_SHAPES])
+def test_double_float_plans_match_the_oracle_and_fp64(dims, radix):
+    """PAC_C128_DF: complex FP64 arrays in and out, double-float arithmetic
+    inside; against the oracle within the FP64 bound, and against the plain
+    FP64 plan on the same inputs; the device and host-buffer calls agree."""
+    pac = pac_mod()
+    fs, h, x = separable_case(dims, "c128", seed=31 + dims[0])
+    ref = oracle.conv_separable(fs, x)
+    n = int(np.prod(dims))
+    y = gpu_conv(dims, radix, "c128df", h, x)
+    check(y, ref, "c128df", n, f"df {dims}")
+    y64 = gpu_conv(dims, radix, "c128", h, x)
+    assert oracle.rel_l2(y, y64) <= tol("c128df", n)
+    plan = pac.Plan(dims, radix, "c128df")
+    try:
+        assert plan.query(pac.Q_PLANE) == 0
+        plan.filter_spectrum(dev(h))
+        xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        pac.pac_convolve_host(plan.handle, xh, yh)
+        assert np.array_equal(yh.numpy(), y)
+    finally:
+        plan.close()
+
+
+def test_double_float_large_host_buffers_in_column_blocks():
+    """3125^2 in double-float, device call and the host-buffer call (column
+    blocks: the first pass reads complex FP64 blocks in place, the last writes
+    them): both against the oracle, equal bit for bit."""
+    pac = pac_mod()
+    dims = (3125, 3125)
+    fs, h, x = separable_case(dims, "c128", seed=5)
+    ref = oracle.conv_separable(fs, x)
+    y = gpu_conv(dims, 5, "c128df", h, x)
+    check(y, ref, "c128df", 3125 * 3125, "df 3125^2")
+    plan = pac.Plan(dims, 5, "c128df")
+    try:
+        plan.filter_spectrum(dev(h))
+        xh = torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        pac.pac_convolve_host(plan.handle, xh, yh)
+        assert np.array_equal(yh.numpy(), y)
+    finally:
+        plan.close()
+
+
+def test_double_float_entry_points_and_queue():
+    """Entry points that do not take double-float plans say so (PAC_ERR_ARG);
+    the request queue runs them (same result as pac_convolve)."""
+    pac = pac_mod()
+    dims = (243, 27)
+    fs, h, x = separable_case(dims, "c128", seed=9)
+    plan = pac.Plan(dims, 3, "c128df")
+    try:
+        plan.filter_spectrum(dev(h))
+        xd = dev(x)
+        y = plan.convolve(xd)
+        torch.cuda.synchronize()
+        check(y.cpu().numpy(), oracle.conv_separable(fs, x), "c128df", 243 * 27, "df queue case")
+        yp = torch.empty_like(xd)
+        for call in (lambda: plan.convolve_permuted(xd),
+                     lambda: pac.pac_convolve_many([plan.handle], [xd], [yp]),
+                     lambda: pac.pac_forward_unordered(plan.handle, xd, yp)):
+            with pytest.raises(pac.PacError) as ei:
+                call()
+            assert ei.value.status == pac.Status.ERR_ARG
+        q = pac.pac_queue_create(1 << 30, 2)
+        try:
+            yq = torch.empty_like(xd)
+            t = pac.pac_submit(q, plan.handle, xd, yq)
+            pac.pac_queue_drain(q)
+            assert pac.pac_poll(q, t)[0] == pac.Status.OK
+            assert torch.equal(yq, y)
+        finally:
+            pac.pac_queue_destroy(q)
+    finally:
+        plan.close()
 
 
 def test_tune_search_at_plan_creation_and_plan_log():

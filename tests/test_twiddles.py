@@ -270,6 +270,44 @@ def test_bfly_table_is_exact_and_rounded_once():
     assert np.array_equal(b32, b64.astype(np.float32).astype(np.float64))
 
 
+# ---- the double-float constant tables (c_taudf, c_bflydf): {hi, lo} FP32 pairs of the same values
+
+
+def parse_df_pairs(text, name):
+    body = text.split(name)[1].split("= {")[1].split("};")[0]
+    pairs = re.findall(r"\{(\S+)f, (\S+)f\}", body)
+    return [(float.fromhex(a), float.fromhex(b)) for a, b in pairs]
+
+
+def test_double_float_tables_are_the_exact_values_split_once():
+    """hi is the exact value rounded to FP32 (within half an FP32 ulp) and
+    hi + lo is within 2^-48 of it relative (lo = the remainder rounded to
+    FP32); the two tables have one pair per FP64 entry."""
+    with open(os.path.join(CSRC, "roots.h")) as f:
+        text = f.read()
+    toff, t64, _, boff, b64, _ = parse_roots_h(text)
+    tdf = parse_df_pairs(text, "c_taudf[PAC_TAU_COUNT]")
+    bdf = parse_df_pairs(text, "c_bflydf[PAC_BFLY_COUNT]")
+    assert len(tdf) == len(t64) and len(bdf) == len(b64)
+    exact = [None] * len(t64)
+    for R, off in toff.items():
+        for e in range(R):
+            exact[off + e] = exact_factored(e, R, False)[1]
+    for R, off in boff.items():
+        B, A = bfly_layout(R)
+        for d, inv in enumerate((False, True)):
+            for k1 in range(A):
+                sig = [exact_factored(b * k1, R, inv)[0] for b in range(B)]
+                for i, w in enumerate(exact_bfly(B, sig, inv)):
+                    hi, lo = bdf[off + (d * A + k1) * NC[B] + i]
+                    assert abs(mpmath.mpf(hi) - w) <= 0.5 * float(np.spacing(np.float32(abs(float(w))))) + 1e-50
+                    assert abs(mpmath.mpf(hi) + mpmath.mpf(lo) - w) <= 2.0 ** -48 * abs(w) + 1e-50, (R, inv, k1, i)
+    for (hi, lo), w in zip(tdf, exact):
+        assert abs(mpmath.mpf(hi) - w) <= 0.5 * float(np.spacing(np.float32(abs(float(w))))) + 1e-50
+        assert abs(mpmath.mpf(hi) + mpmath.mpf(lo) - w) <= 2.0 ** -48 * abs(w) + 1e-50
+        assert np.float32(hi) == hi and np.float32(lo) == lo
+
+
 # ---- a numpy model of the kernels' in-register DFT (fft_device.cuh: dft, dft_sc, tw_factored,
 # and the plain-twiddle split of complex FP32 powers of two)
 
