@@ -309,8 +309,9 @@ def launch_table(pac, plan, c):
 
 
 def tolerance(c) -> float:
-    """Relative L2 tolerance: 1e-12 for complex FP64, 1e-5 log2 N for complex FP32."""
-    return 1e-12 if c.dtype == "c128" else 1e-5 * math.log2(max(2, c.n_total))
+    """Relative L2 tolerance: 1e-12 for complex FP64 arrays (computed in FP64
+    or in double-float arithmetic), 1e-5 log2 N for complex FP32."""
+    return 1e-12 if c.dtype in ("c128", "c128df") else 1e-5 * math.log2(max(2, c.n_total))
 
 
 def oracle_run(c, x, h, fs, points=None):
@@ -340,7 +341,8 @@ def oracle_check(c, x, h, fs, y, whole_macs=7e10, point_macs=1e10, cache=None):
     sample, timed on one core and on all cores.  GB/s = 3 N S per whole
     convolution over the time, scaled by the computed fraction of outputs."""
     import oracle
-    key = (c.dims, c.dtype, c.x_kind, c.h_kind, c.seed, c.h_seed, c.h_param)
+    # the same inputs (and oracle) for FP64 and double-float plans of one workload
+    key = (c.dims, "c128" if c.dtype == "c128df" else c.dtype, c.x_kind, c.h_kind, c.seed, c.h_seed, c.h_param)
     if cache is not None and key in cache:  # same inputs (e.g. one shape at several radices)
         ref, pts, base = cache[key]
         yv = np.asarray(y, dtype=np.complex128).reshape(-1)
@@ -598,6 +600,12 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
         for r in (3, 5):
             c = pin.c3(r, dt)
             cases.append((c, f"2-D {c.dims[0]}^2, radix {r}, complex {'FP32' if dt == 'c64' else 'FP64'}"))
+    # complex FP64 arrays computed in double-float arithmetic (PAC_C128_DF), the same inputs as the FP64 rows
+    for r in (2, 4, 8):
+        cases.append((pin.c2(r, "c128df"), f"3-D 128^3, radix {r}, complex FP64 arrays, double-float arithmetic"))
+    for r in (3, 5):
+        c = pin.c3(r, "c128df")
+        cases.append((c, f"2-D {c.dims[0]}^2, radix {r}, complex FP64 arrays, double-float arithmetic"))
     # mixed radix (Section 7.1): 1000 = 2^3 5^3, 6000 = 2^4 3 5^3, 120 = 2^3 3 5
     cases.append((pin.mixed((1000, 1000)), "2-D 1000^2, mixed radix 2^3 5^3, complex FP32"))
     cases.append((pin.mixed((6000, 6000)), "2-D 6000^2, mixed radix 2^4 3 5^3, complex FP32"))
@@ -621,6 +629,10 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
         plan.filter_spectrum(h)
         steps = 30 if N * S < (64 << 20) else 10
         ms = time_steps(torch, lambda: pac.pac_convolve(plan.handle, x, y, sh), steps, 3, flush, stream)
+        if c.dtype == "c128df":
+            out.append(double_float_entry(a, torch, pac, c, name, plan, x, h, y, ms, steps, flush, stream, peak,
+                                          x_np, h_np, fs, oracle_cache, tuned_us))
+            continue
         msp = time_steps(torch, lambda: pac.pac_convolve_permuted(plan.handle, x, y, sh), steps, 3, flush, stream)
         Hn = torch.fft.fftn(h)
         yc = torch.empty_like(x)
@@ -666,6 +678,50 @@ def configs_leg(a, torch, pac, pin, dev, stream, flush, peak):
         out.append(ent)
     out.append(prime_factor_entry(a, torch, pac, pin, dev, stream, flush, peak))
     return out
+
+
+def double_float_entry(a, torch, pac, c, name, plan, x, h, y, ms, steps, flush, stream, peak, x_np, h_np, fs,
+                       oracle_cache, tuned_us):
+    """A configs row of a double-float plan (PAC_C128_DF): complex FP64 arrays,
+    butterflies in pairs of FP32 values.  Against the FP64 plan and cuFFT
+    (FP64) on the same GPU and inputs; the algorithmic flops per second as a
+    fraction of the FP64 pipe's peak (above 1: faster than FP64 arithmetic can
+    be); the relative L2 error against the FP64 oracle (same inputs as the
+    FP64 row, whose oracle result is reused)."""
+    sh = stream.cuda_stream
+    N, S = c.n_total, c.elem_bytes
+    B = 3 * N * S
+    p64 = pac.Plan(c.dims, c.radix, "c128")
+    p64.filter_spectrum(h)
+    y64 = torch.empty_like(x)
+    ms64 = time_steps(torch, lambda: pac.pac_convolve(p64.handle, x, y64, sh), steps, 3, flush, stream)
+    Hn = torch.fft.fftn(h)
+    yc = torch.empty_like(x)
+    msc = time_steps(torch, lambda: torch.fft.ifftn(torch.fft.fftn(x) * Hn, out=yc), steps, 3, flush, stream)
+    pac.pac_convolve(plan.handle, x, y, sh)
+    stream.synchronize()
+    t, t64, tc = (statistics.median(v) for v in (ms, ms64, msc))
+    flops = alg_flops(c.dims)
+    ent = {"workload": name, "dims": list(c.dims), "radix": c.radix, "dtype": c.dtype,
+           "ms": t, "GBps": B / (t * 1e-3) / 1e9, "pct_hbm_roofline": B / (t * 1e-3) / 1e9 / peak,
+           "fp64_plan_ms": t64, "speedup_vs_fp64_plan": t64 / t,
+           "cufft_GBps": B / (tc * 1e-3) / 1e9, "speedup_vs_cufft": tc / t,
+           "launches": plan.query(pac.Q_LAUNCHES_CONVOLVE), "groups": plan.query(pac.Q_GROUPS),
+           "group_cap": plan.query(pac.Q_GROUP_CAP), "tuned_us": tuned_us,
+           "rel_l2_vs_fp64_plan": float(torch.linalg.vector_norm(y - y64) / torch.linalg.vector_norm(y64)),
+           "rel_l2_vs_cufft": float(torch.linalg.vector_norm(y - yc) / torch.linalg.vector_norm(yc)),
+           "alu": {"flops_per_conv": flops, "c_r": c_r_of(c.dims), "achieved_gflops": flops / (t * 1e-3) / 1e9,
+                   "frac_of_fp64_peak": flops / (t * 1e-3) / 1e9 / ALU_PEAK_GFLOPS["c128"],
+                   "note": "algorithmic flops of the convolution over the FP64 pipe's peak; the kernels run "
+                           "about 15 FP32 instructions per FP64 operation on the FP32 pipes"}}
+    y_host = y.cpu().numpy()
+    p64.close()
+    plan.close()
+    del x, y, y64, h, yc, Hn
+    torch.cuda.empty_cache()
+    if not a.no_cpu:
+        ent.update(oracle_check(c, x_np, h_np, fs, y_host, cache=oracle_cache))
+    return ent
 
 
 def prime_factor_entry(a, torch, pac, pin, dev, stream, flush, peak):
@@ -1077,6 +1133,30 @@ def main(argv=None):
         line["e2e"] = {"value": world * ke * B / (te * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": N * S,
                        "d2h_bytes_per_step": N * S, "ms_per_step": te / ke,
                        "call": "pac_convolve_host (pinned host x -> device -> convolve -> host y)"}
+        # the same workload and inputs as complex FP64 arrays computed in double-float arithmetic
+        # (PAC_C128_DF: pairs of FP32 values on the FP32 pipes), device and host buffers
+        ydf = None
+        if c.dtype == "c128":
+            pdf = pac.Plan(c.dims, c.radix, "c128df")
+            pdf.filter_spectrum(h)
+            ydf = torch.empty_like(x)
+            msd = time_steps(torch, lambda: pac.pac_convolve(pdf.handle, x, ydf, sh), a.steps, a.warmup, flush,
+                             stream)
+            td, _ = aggregate(sum(msd), 0, world, dev)
+            msde = time_steps(torch, lambda: pac.pac_convolve_host(pdf.handle, xh, yh, sh), ke, a.warmup, flush,
+                              stream)
+            tde, _ = aggregate(sum(msde), 0, world, dev)
+            pac.pac_convolve(pdf.handle, x, ydf, sh)
+            stream.synchronize()
+            line["double_float"] = {
+                "value": world * a.steps * B / (td * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": td / a.steps,
+                "speedup_vs_fp64": ms_per_step / (td / a.steps), "launches_per_step": pdf.query(pac.Q_LAUNCHES_CONVOLVE),
+                "alu_frac_of_fp64_peak": alg_flops(c.dims) / (td / a.steps * 1e-3) / 1e9 / ALU_PEAK_GFLOPS["c128"],
+                "e2e": {"value": world * ke * B / (tde * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": tde / ke,
+                        "h2d_bytes_per_step": N * S, "d2h_bytes_per_step": N * S},
+                "note": "dtype c128df: complex FP64 arrays in and out, butterflies, twiddles and product in "
+                        "double-float arithmetic; rel_l2 against the FP64 oracle in the configs leg"}
+            pdf.close()
         y_main = None
         if rank == 0:
             pac.pac_convolve(plan.handle, x, y, sh)  # y was reused by the comparison legs
@@ -1084,6 +1164,12 @@ def main(argv=None):
             y_main = y.cpu().numpy()
             ref = yc.cpu().numpy()
             line["check_vs_cufft_rel_l2"] = float(np.linalg.norm(y_main - ref) / np.linalg.norm(ref))
+            if ydf is not None:
+                ydf_h = ydf.cpu().numpy()
+                line["double_float"]["rel_l2_vs_fp64_path"] = float(np.linalg.norm(ydf_h - y_main) /
+                                                                    np.linalg.norm(y_main))
+                line["double_float"]["rel_l2_vs_cufft"] = float(np.linalg.norm(ydf_h - ref) / np.linalg.norm(ref))
+        del ydf
 
     if sampler:
         sampler.stop()

@@ -197,9 +197,14 @@ constexpr int min_blocks(int m, int esize, int nv = 0) {
 }
 // The double-float kernels (16-byte elements like complex FP64, so the same
 // tiles and rounds): a double-float value takes two registers like an FP64
-// one, but each operation keeps a few FP32 temporaries live.
+// one, and each operation keeps a few FP32 temporaries live.  Measured
+// (complex FP64 arrays, median of 20, L2 flushed; budgets for rounds of
+// >= 25 / >= 16 / smaller): 3125^2 255: 2.56 ms, 168: 2.03 ms, 128: 2.19 ms;
+// 128^3 (radix 2) 168/128: 316 us, 128/96: 272 us; 4096^2 1662 -> 1598 us;
+// 2^20 277 -> 194 us.  Groups below 3125 points with 25-point rounds keep
+// the FP64 budget (at 255 registers their 625-point kernel already spills).
 constexpr int reg_target_df(int m) {
-    return max_round_radix(m, 16) >= 25 ? 255 : (max_round_radix(m, 16) >= 16 ? 168 : 128);
+    return max_round_radix(m, 16) >= 25 ? (m >= 3125 ? 168 : 255) : (max_round_radix(m, 16) >= 16 ? 128 : 96);
 }
 constexpr int min_blocks_df(int m) { return clampi(65536 / (pass_threads(m, 16) * reg_target_df(m)), 1, 8); }
 
