@@ -16,7 +16,7 @@ bound by GB300's FP64 pipe, so the line's roofline is the ALU one (flops
 2 c_r N log2 N + 6 N over the FP64 peak), with the HBM fraction beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pac|reference]
-                    [--workload conv2d-r5|conv2d-r3|conv3d|conv1d] [--dtype c128|c64]
+                    [--workload conv2d-r5|conv2d-r3|conv3d|conv1d] [--dtype c128|c64|c128df]
 
 With N > 1 (launched by torch.distributed.run) every rank runs an
 independent replica on its own GPU; value = all ranks' bytes / max time.
@@ -58,7 +58,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["pac", "reference"], default="pac")
     ap.add_argument("--radix", type=int, default=4, help="radix of the conv3d workload")
-    ap.add_argument("--dtype", choices=["c64", "c128"], default="c128")
+    ap.add_argument("--dtype", choices=["c64", "c128", "c128df"], default="c128",
+                    help="c128df (complex FP64 arrays in double-float arithmetic) runs with --quick only")
     ap.add_argument("--n", type=int, default=128, help="edge of the 3-D cube")
     ap.add_argument("--workload", choices=["conv3d", "conv2d-r3", "conv2d-r5", "conv1d"], default="conv2d-r5",
                     help="the main leg's problem (default: the 2-D 3125^2 radix-5 workload)")
@@ -81,7 +82,10 @@ def parse_args(argv=None):
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (default pass schedules)")
     ap.add_argument("--flush-mb", type=int, default=FLUSH_BYTES >> 20,
                     help="L2 flush buffer written before each step (0: none, for profiler runs only)")
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    if args.dtype == "c128df" and not args.quick:
+        ap.error("--dtype c128df runs with --quick (the full line compares entry points that take FP64 plans)")
+    return args
 
 
 # ------------------------------------------------------------------ ranks
@@ -485,7 +489,8 @@ def workload_conv(a, pin):
 
 
 def workload_name(a, c=None):
-    prec = f"complex {'FP32' if a.dtype == 'c64' else 'FP64'}"
+    prec = {"c64": "complex FP32", "c128": "complex FP64",
+            "c128df": "complex FP64 arrays in double-float arithmetic"}[a.dtype]
     if a.workload == "conv2d-r3":
         return f"2-D periodic convolution 2187^2, {prec}, radix 3, periodised exponential filter spectrum resident"
     if a.workload == "conv2d-r5":
@@ -1087,7 +1092,7 @@ def main(argv=None):
     peak, peak_kind = measured_peak_hbm()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if c.dtype == "c64" else "f64", "data": "synthetic",
+            "dtype": {"c64": "f32", "c128": "f64", "c128df": "f32x2 (double-float)"}[c.dtype], "data": "synthetic",
             "config": {"workload": workload_name(a), "dims": list(c.dims), "radix": c.radix,
                        "stages_per_axis": plan.stages(0), "bytes_per_step": B,
                        "schedule": {"passes": launches, "groups": plan.query(pac.Q_GROUPS),
