@@ -12,9 +12,19 @@ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 constexpr int base_of(int m) { return m % 2 == 0 ? 2 : (m % 3 == 0 ? 3 : (m % 5 == 0 ? 5 : 1)); }
 constexpr int ilog(int m, int b) { return m <= 1 ? 0 : 1 + ilog(m / b, b); }
 
-// Largest in-register DFT size of one round.  esize = bytes per complex element.
+// The tiling rules below take a key `esize`: the bytes of a complex element
+// (8: complex FP32, 16: complex FP64), or kEsDf for the double-float kernels
+// (16-byte elements, computed on the FP32 pipes: their own round and register
+// rules).  ebytes(esize) is the element size in bytes.
+constexpr int kEsDf = 17;
+constexpr int ebytes(int esize) { return esize & ~1; }
+
+// Largest in-register DFT size of one round.  Double-float base-5 groups
+// take rounds of 5: a 25-point round held 100 FP32 values a thread and left
+// 3 warps per scheduler to hide the double-float operations' dependent
+// chains (issue active 31 %).
 constexpr int round_rmax(int base, int esize) {
-    return base == 2 ? 16 : base == 3 ? (esize == 8 ? 27 : 9) : 25;
+    return base == 2 ? 16 : base == 3 ? (esize == 8 ? 27 : 9) : (esize == kEsDf ? 5 : 25);
 }
 
 // Largest group (column length M) one CTA transforms in shared memory.
@@ -102,17 +112,17 @@ constexpr int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi 
 // pipe, not by HBM: one column per tile (a 16-byte row segment) halves the
 // CTA so that two CTAs share an SM and one computes while the other waits on
 // its loads.
-constexpr int tile_wmin(int m, int esize) { return esize == 16 && m >= 2187 ? 1 : 32 / esize; }
+constexpr int tile_wmin(int m, int esize) { return ebytes(esize) == 16 && m >= 2187 ? 1 : 32 / ebytes(esize); }
 constexpr int tile_w0(int m, int esize) {
-    return clampi(floor_pow2(kTileBytes / (m * esize)), tile_wmin(m, esize),
-                  (round_count(m, esize) == 1 ? 1024 : 256) / esize);
+    return clampi(floor_pow2(kTileBytes / (m * ebytes(esize))), tile_wmin(m, esize),
+                  (round_count(m, esize) == 1 ? 1024 : 256) / ebytes(esize));
 }
 // The narrow tile variant (nv = 1), one of the autotuner's candidates: half
 // the columns, for one-base groups whose half-width rows still span at least
 // 128 bytes (one 32-byte sector per 8-byte lane of a quarter warp, and the
 // bank model finds every round of these shapes conflict-free with the pads
 // below).
-constexpr bool has_narrow(int m, int esize) { return !is_mixed(m) && (tile_w0(m, esize) / 2) * esize >= 128; }
+constexpr bool has_narrow(int m, int esize) { return !is_mixed(m) && (tile_w0(m, esize) / 2) * ebytes(esize) >= 128; }
 constexpr int tile_w(int m, int esize, int nv = 0) {
     return nv && has_narrow(m, esize) ? tile_w0(m, esize) / 2 : tile_w0(m, esize);
 }
@@ -154,7 +164,7 @@ constexpr int tile_pad(int m, int esize, bool lines, int nv = 0) {
 // bank groups and keeps every other round's accesses within aligned groups of
 // four rows.  Returns log2 R, or 0 for no swizzle.
 constexpr int tile_row_swizzle(int m, int esize) {
-    return (!is_mixed(m) && base_of(m) == 2 && round_count(m, esize) >= 2 && tile_w(m, esize) * esize <= 32 &&
+    return (!is_mixed(m) && base_of(m) == 2 && round_count(m, esize) >= 2 && tile_w(m, esize) * ebytes(esize) <= 32 &&
             round_radix(m, esize, round_count(m, esize) - 1) >= 4)
                ? ilog(round_radix(m, esize, round_count(m, esize) - 1), 2)
                : 0;
@@ -204,9 +214,10 @@ constexpr int min_blocks(int m, int esize, int nv = 0) {
 // 2^20 277 -> 194 us.  Groups below 3125 points with 25-point rounds keep
 // the FP64 budget (at 255 registers their 625-point kernel already spills).
 constexpr int reg_target_df(int m) {
-    return max_round_radix(m, 16) >= 25 ? (m >= 3125 ? 168 : 255) : (max_round_radix(m, 16) >= 16 ? 128 : 96);
+    return base_of(m) == 5 ? 64
+                           : (max_round_radix(m, kEsDf) >= 25 ? 255 : (max_round_radix(m, kEsDf) >= 16 ? 128 : 96));
 }
-constexpr int min_blocks_df(int m) { return clampi(65536 / (pass_threads(m, 16) * reg_target_df(m)), 1, 8); }
+constexpr int min_blocks_df(int m) { return clampi(65536 / (pass_threads(m, kEsDf) * reg_target_df(m)), 1, 8); }
 
 // ------------------------------------------------- the runtime-radix kernel
 // Mixed groups without a compiled kernel run in the runtime-radix kernel

@@ -28,6 +28,9 @@ namespace pac {
 
 // ------------------------------------------------------------------ complex
 
+// key of the tiling rules of element type V (config.h)
+template <typename V> constexpr int cfg_es() { return std::is_same<V, dfloat2>::value ? kEsDf : (int)sizeof(V); }
+
 template <typename V> struct Real;
 template <> struct Real<float2> { using T = float; };
 template <> struct Real<double2> { using T = double; };
@@ -337,7 +340,7 @@ template <int M, int ES> struct RoundGeom<M, ES, -1> {
 
 // NV = 1: the narrow tile variant (has_narrow in config.h)
 template <typename V, int M, bool LINES = false, int NV = 0> struct Shape {
-    static constexpr int ES = sizeof(V);
+    static constexpr int ES = cfg_es<V>();
     static constexpr int W = tile_w(M, ES, NV);
     static constexpr int P = tile_pitch(M, ES, LINES, NV);
     static constexpr int NR = round_count(M, ES);
@@ -364,7 +367,7 @@ template <typename V_, int M_, int W_, int NT_, int RS_, int WS_, bool PF_, int 
           int RSW_ = 0>
 struct Geo {
     using V = V_;
-    static constexpr int M = M_, W = W_, NT = NT_, RS = RS_, WS = WS_, ES = (int)sizeof(V_), KS = KS_;
+    static constexpr int M = M_, W = W_, NT = NT_, RS = RS_, WS = WS_, ES = cfg_es<V_>(), KS = KS_;
     static constexpr int NR = round_count(M_, ES);
     static constexpr bool PF = PF_;
     static constexpr bool SPLIT = SPLIT_;
@@ -376,7 +379,7 @@ struct Geo {
 // P; several CTAs per SM hide latency, so registers are not spent on prefetch
 template <typename V, int M, bool LINES, int NV = 0>
 using PassGeo = Geo<V, M, Shape<V, M, LINES, NV>::W, Shape<V, M, LINES, NV>::NT, Shape<V, M, LINES, NV>::P, 1, false,
-                    1, false, tile_row_swizzle(M, sizeof(V))>;
+                    1, false, tile_row_swizzle(M, cfg_es<V>())>;
 
 // Task tau of round RI: column w of the tile, offset jp inside its block of
 // S rows, first row row0 = block * S + jp; the task transforms rows
@@ -491,7 +494,7 @@ __device__ __forceinline__ uint32_t dsmem_addr(const TileCtx<typename GEO::V>& c
     uint32_t b = c.sk[0];
 #pragma unroll
     for (int k = 1; k < GEO::KS; ++k) b = part == k ? c.sk[k] : b;
-    return b + (uint32_t)(((row - part * H) * GEO::RS + (w + c.wofs) * GEO::WS) * GEO::ES);
+    return b + (uint32_t)(((row - part * H) * GEO::RS + (w + c.wofs) * GEO::WS) * (int)sizeof(typename GEO::V));
 }
 
 // buffer row of tile row `row` (the row swizzle of tile_row_swizzle)
@@ -676,7 +679,7 @@ __device__ __forceinline__ void round_exec(const TileCtx<typename GEO::V>& c) {
     static_assert(!MUL || SP == 1, "the product is taken after the last forward round");
     constexpr bool GSRC = SRC != kFromSmem;
     constexpr int ITER = (T::TASKS + GEO::NT - 1) / GEO::NT;
-    constexpr bool PREFETCH = GEO::PF && ITER > 1 && ITER * R * GEO::ES <= 256 && (GSRC || MUL);
+    constexpr bool PREFETCH = GEO::PF && ITER > 1 && ITER * R * ebytes(GEO::ES) <= 256 && (GSRC || MUL);
     if constexpr (PREFETCH) {
         V pre[ITER][R];
 #pragma unroll
@@ -868,7 +871,7 @@ template <typename V, int M, int NV> constexpr int pass_min_blocks() {
 
 // Generic pass kernel: one pass of a convolution (see run_phase).
 template <typename V, int M, bool LINES, int NV = 0>
-__global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), (pass_min_blocks<V, M, NV>()))
+__global__ void __launch_bounds__(pass_threads(M, cfg_es<V>(), NV), (pass_min_blocks<V, M, NV>()))
     pass_kernel(const __grid_constant__ PassArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     pdl_launch_dependents();
@@ -880,7 +883,7 @@ __global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), (pass_min_bloc
 // tiles of passes list[0..n) are numbered consecutively, pass i owning global
 // tiles [tile_start[i], tile_start[i+1]); CTAs walk the global tiles.
 template <typename V, int M, bool LINES, int NV = 0>
-__global__ void __launch_bounds__(pass_threads(M, sizeof(V), NV), (pass_min_blocks<V, M, NV>()))
+__global__ void __launch_bounds__(pass_threads(M, cfg_es<V>(), NV), (pass_min_blocks<V, M, NV>()))
     pass_multi_kernel(const PassArgs* __restrict__ list, const uint32_t* __restrict__ tile_start, int n) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     V* s = reinterpret_cast<V*>(smem_raw);

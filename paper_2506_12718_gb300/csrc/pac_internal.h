@@ -134,6 +134,7 @@ struct pac_plan_s {
     pac_dtype dtype = PAC_C64;
     int esize = 8;
     bool df = false;  // PAC_C128_DF: double-float passes (kDf* bits in PassArgs::df)
+    int ces = 8;      // key of the tiling rules (config.h): esize, or kEsDf for double-float plans
     int64_t N = 1;
     int uniform_m = 0;  // group size shared by every pass (0: sizes differ)
     bool plane = false;  // the last two axes run as one plane pass (groups plane_g1, plane_g1 + 1)

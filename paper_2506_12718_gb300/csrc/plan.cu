@@ -683,6 +683,7 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     pl->dtype = dtype;
     pl->esize = dtype == PAC_C64 ? 8 : 16;
     pl->df = dtype == PAC_C128_DF;
+    pl->ces = pl->df ? kEsDf : pl->esize;
     pl->N = n_total;
     for (int a = 0; a < ndim; ++a) pl->dims[a] = dims[a];
     pl->stages = stages;
@@ -706,7 +707,7 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
         gs.mixed = 0;
         gs.mix_runtime = false;
     }
-    if (int rc = form_groups(ndim, dims, pl->stages, pl->esize, gs, pl->groups)) {
+    if (int rc = form_groups(ndim, dims, pl->stages, pl->ces, gs, pl->groups)) {
         delete pl;
         return rc;
     }
@@ -789,9 +790,9 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
         reverse_table(pl->stages[g.axis].data() + g.first_stage, g.nstages, f.data());
         // shared-memory row of frequency k after the in-place rounds: digit
         // reversal over the round radices (larger rounds first)
-        const int nr = g.mix_nr > 0 ? g.mix_nr : round_count(g.M, pl->esize);
+        const int nr = g.mix_nr > 0 ? g.mix_nr : round_count(g.M, pl->ces);
         std::vector<int> rr(nr);
-        for (int i = 0; i < nr; ++i) rr[i] = g.mix_nr > 0 ? g.mix_r[i] : round_radix(g.M, pl->esize, i);
+        for (int i = 0; i < nr; ++i) rr[i] = g.mix_nr > 0 ? g.mix_r[i] : round_radix(g.M, pl->ces, i);
         std::vector<int64_t> row_freq(g.M);
         reverse_table(rr.data(), nr, row_freq.data());
         std::vector<int> f2r(g.M);
@@ -828,7 +829,7 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     pl->spec_elems = pl->N;
     if (!pl->groups.empty() && !pl->plane) {  // whole tiles of the fused pass (see SpecOrder)
         const GroupPlan& f = pl->groups.back();
-        const int64_t W = group_w(f, pl->esize);
+        const int64_t W = group_w(f, pl->ces);
         pl->spec_elems = (f.Q + W - 1) / W * W * f.M;
     }
     e = cudaMalloc(&pl->d_spec, (size_t)pl->spec_elems * pl->esize);
@@ -908,13 +909,13 @@ SpecOrder spec_order_of(pac_plan p) {
     }
     o.K = 1;
     o.M = (uint32_t)f.M;
-    o.W = (uint32_t)group_w(f, p->esize);
+    o.W = (uint32_t)group_w(f, p->ces);
     o.C = (uint32_t)f.C;
     if (f.mix_nr > 0) {
         o.R = (uint32_t)f.mix_r[f.mix_nr - 1];
     } else {
-        const int nr = round_count(f.M, p->esize);
-        o.R = (uint32_t)round_radix(f.M, p->esize, nr - 1);
+        const int nr = round_count(f.M, p->ces);
+        o.R = (uint32_t)round_radix(f.M, p->ces, nr - 1);
     }
     o.tasks = o.W * o.M / o.R;
     o.rowmap = reinterpret_cast<const int*>(static_cast<const unsigned char*>(p->d_tables) + f.off_rowmap);
@@ -937,7 +938,7 @@ PassArgs make_pass(pac_plan p, const GroupPlan& g, int mode, const void* src, vo
     a.Q = g.Q;
     a.C = g.C;
     a.I = g.I;
-    const int W = group_w(g, p->esize);
+    const int W = group_w(g, p->ces);
     a.tiles = (g.Q + W - 1) / W;
     a.tile0 = 0;
     a.tw_T = g.tw_T;
@@ -1214,7 +1215,7 @@ static bool host_pipelined(pac_plan p) {
     if (p->groups.size() < 2 || p->single_launch || p->bytes() < kHostBlockMinBytes) return false;
     const GroupPlan& g = p->groups[0];
     if (g.axis != 0 || g.C <= 1 || g.mix_nr > 0 || (p->plane && p->plane_g1 == 0)) return false;
-    const int W = group_w(g, p->esize);
+    const int W = group_w(g, p->ces);
     return (g.Q + W - 1) / W >= 2 * kHostBlocks;
 }
 
@@ -1242,7 +1243,7 @@ static int run_pass_tiles(pac_plan p, const GroupPlan& g, const Step& st, int64_
 static int convolve_host_pipelined(pac_plan p, const void* x_host, void* y_host, cudaStream_t s) {
     if (int rc = ensure_host_pipeline(p)) return rc;
     const GroupPlan& g = p->groups[0];
-    const int W = group_w(g, p->esize);
+    const int W = group_w(g, p->ces);
     const int64_t tiles = (g.Q + W - 1) / W, per = (tiles + kHostBlocks - 1) / kHostBlocks;
     const size_t S = (size_t)p->esize, pitch = (size_t)g.C * S;
     unsigned char* d = static_cast<unsigned char*>(p->d_stage);
