@@ -19,12 +19,16 @@ constexpr int ilog(int m, int b) { return m <= 1 ? 0 : 1 + ilog(m / b, b); }
 constexpr int kEsDf = 17;
 constexpr int ebytes(int esize) { return esize & ~1; }
 
-// Largest in-register DFT size of one round.  Double-float base-5 groups
-// take rounds of 5: a 25-point round held 100 FP32 values a thread and left
-// 3 warps per scheduler to hide the double-float operations' dependent
-// chains (issue active 31 %).
+// Largest in-register DFT size of one round.  The double-float kernels take
+// rounds of 4, 3 and 5 points: a 25-point round held 100 FP32 values a
+// thread, so only 3 warps per scheduler hid the double-float operations'
+// chains of dependent instructions (issue active 31 %); small rounds at 64
+// registers give several times the warps.  Measured (complex FP64 arrays,
+// median of 20, L2 flushed): 3125^2 2.06 -> 1.05 ms (rounds of 25 -> 5),
+// 2187^2 672 -> 535 us (9 -> 3), 128^3 267 -> 169 us, 4096^2 1591 -> 1383 us,
+// 2^20 189 -> 116 us (16 -> 4; rounds of 8 at 96 registers: 220, 1588, 160).
 constexpr int round_rmax(int base, int esize) {
-    return base == 2 ? 16 : base == 3 ? (esize == 8 ? 27 : 9) : (esize == kEsDf ? 5 : 25);
+    return esize == kEsDf ? (base == 2 ? 4 : base) : (base == 2 ? 16 : base == 3 ? (esize == 8 ? 27 : 9) : 25);
 }
 
 // Largest group (column length M) one CTA transforms in shared memory.
@@ -205,18 +209,10 @@ constexpr int reg_target(int m, int esize) {
 constexpr int min_blocks(int m, int esize, int nv = 0) {
     return clampi(65536 / (pass_threads(m, esize, nv) * reg_target(m, esize)), 1, 8);
 }
-// The double-float kernels (16-byte elements like complex FP64, so the same
-// tiles and rounds): a double-float value takes two registers like an FP64
-// one, and each operation keeps a few FP32 temporaries live.  Measured
-// (complex FP64 arrays, median of 20, L2 flushed; budgets for rounds of
-// >= 25 / >= 16 / smaller): 3125^2 255: 2.56 ms, 168: 2.03 ms, 128: 2.19 ms;
-// 128^3 (radix 2) 168/128: 316 us, 128/96: 272 us; 4096^2 1662 -> 1598 us;
-// 2^20 277 -> 194 us.  Groups below 3125 points with 25-point rounds keep
-// the FP64 budget (at 255 registers their 625-point kernel already spills).
-constexpr int reg_target_df(int m) {
-    return base_of(m) == 5 ? 64
-                           : (max_round_radix(m, kEsDf) >= 25 ? 255 : (max_round_radix(m, kEsDf) >= 16 ? 128 : 96));
-}
+// The double-float kernels: rounds of at most 5 points (round_rmax) keep
+// about 20 FP32 values a thread live, which fits 64 registers without
+// spills.
+constexpr int reg_target_df(int) { return 64; }
 constexpr int min_blocks_df(int m) { return clampi(65536 / (pass_threads(m, kEsDf) * reg_target_df(m)), 1, 8); }
 
 // ------------------------------------------------- the runtime-radix kernel
