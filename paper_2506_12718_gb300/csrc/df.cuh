@@ -89,7 +89,19 @@ __device__ __forceinline__ dfloat df_from_double(double d) {
     return dfloat(hi, sign ? -lo : lo);
 }
 
-__device__ __forceinline__ double df_to_double(dfloat a) { return (double)a.hi + (double)a.lo; }
+// FP32 -> FP64 exactly, by integer operations on the bit pattern (no FP64
+// instruction): zero and subnormals give a signed zero, infinities and NaNs
+// keep their kind.
+__device__ __forceinline__ double df_widen(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t sign = b & 0x80000000u, ex = (b >> 23) & 0xffu, man = b & 0x7fffffu;
+    if (ex == 0u) return __hiloint2double((int)sign, 0);
+    const uint32_t dex = ex == 0xffu ? 0x7ffu : ex + 896u;  // rebias 127 -> 1023
+    return __hiloint2double((int)(sign | (dex << 20) | (man >> 3)), (int)(man << 29));
+}
+
+// double-float -> FP64: both parts widened exactly, one FP64 addition
+__device__ __forceinline__ double df_to_double(dfloat a) { return df_widen(a.hi) + df_widen(a.lo); }
 
 __device__ __forceinline__ dfloat2 df2_from_double2(double2 d) { return dfloat2{df_from_double(d.x), df_from_double(d.y)}; }
 __device__ __forceinline__ double2 df2_to_double2(dfloat2 a) { return double2{df_to_double(a.x), df_to_double(a.y)}; }
