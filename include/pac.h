@@ -432,7 +432,9 @@ int pac_measure_fma_peak(int dtype, double* gflops);
  * group-exponent cap (0: none).  For group g: axis[g], size[g] (its M) and
  * rounds[8 g .. 8 g + 7] (its in-CTA round radices, 0-padded).  *count: in,
  * the room of the arrays (groups; ignored when all three are NULL); out, the
- * number of groups.  Errors as pac_plan_create, before any device call.
+ * number of groups.  PAC_C128_DF: one-base groups only (flags ignored) and
+ * the double-float kernels' rounds (at most 4, 3 or 5 points).  Errors as
+ * pac_plan_create, before any device call.
  */
 int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int flags, int cap, int* axis,
                     int* size, int* rounds, int* count);
@@ -447,7 +449,9 @@ int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dtype dtype, i
  * u < M; 1: the external factor's low table w_L^u, u < T; 2: its high table
  * w_L^{T v}, v < ceil(L/T) (tables 1 and 2 are empty when the group has no
  * external factor).  out (may be NULL): *count interleaved complex values of
- * the dtype; *count in: room (entries), out: the table's length.  L, T (may
+ * the dtype (PAC_C128_DF: 16 bytes an entry, each FP64 part split into the
+ * FP32 pair {hi, lo}, hi = the FP64 value rounded to FP32, lo = the rest
+ * rounded to FP32); *count in: room (entries), out: the table's length.  L, T (may
  * be NULL): the table's root order and the two-level split.  PAC_ERR_ARG for
  * a bad group or table or too little room; size errors as pac_plan_create.
  */

@@ -185,14 +185,18 @@ def pac_plan_groups(dims, radix: int, dtype: int = 0, mixed=False, cap: int = 0)
 def pac_plan_twiddles(dims, radix: int, dtype: int, group: int, which: int, mixed=False, cap: int = 0):
     """Host only: twiddle table `which` (0 round, 1 external low, 2 external high) of group `group`
     of the schedule pac_plan_groups gives, as uploaded by a plan; returns (values, L, T) with values a
-    numpy complex64 / complex128 array."""
+    numpy complex64 / complex128 array (C128_DF: a float32 array of shape (n, 4), the pairs
+    re.hi, re.lo, im.hi, im.lo)."""
     import numpy as np
     vals = [int(v) for v in dims]
     d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
     cnt, L, T = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
     args = (len(vals), d, int(radix), int(dtype), _mixed_flags(mixed), int(cap), int(group), int(which))
     _check(load().pac_plan_twiddles(*args, None, ctypes.byref(cnt), ctypes.byref(L), ctypes.byref(T)))
-    out = np.zeros(max(1, cnt.value), np.complex64 if int(dtype) == C64 else np.complex128)
+    if int(dtype) == C128_DF:
+        out = np.zeros((max(1, cnt.value), 4), np.float32)
+    else:
+        out = np.zeros(max(1, cnt.value), np.complex64 if int(dtype) == C64 else np.complex128)
     _check(load().pac_plan_twiddles(*args, out.ctypes.data, ctypes.byref(cnt), None, None))
     return out[: cnt.value], L.value, T.value
 

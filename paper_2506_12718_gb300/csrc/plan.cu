@@ -482,7 +482,8 @@ static int form_groups(int ndim, const int64_t* dims, const std::vector<std::vec
 extern "C" int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int flags, int cap,
                                int* axis, int* size, int* rounds, int* count) {
     if (ndim < 1 || ndim > 3 || !dims || !count) return fail(PAC_ERR_ARG, "bad arguments");
-    if (dtype != PAC_C64 && dtype != PAC_C128) return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
+    if (dtype != PAC_C64 && dtype != PAC_C128 && dtype != PAC_C128_DF)
+        return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
     if (radix != 0 && prime_of(radix) == 0) return fail(PAC_ERR_ARG, "radix %d not in {0,2,3,4,5,8}", radix);
     std::vector<std::vector<int>> st(ndim);
     for (int a = 0; a < ndim; ++a) {
@@ -493,14 +494,16 @@ extern "C" int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dty
     Schedule sch;
     sch.cap = cap;
     sch.mixed = (flags & 2) ? -1 : (flags & 1) ? 1 : 0;
+    if (dtype == PAC_C128_DF) sch.mixed = 0;  // one-base groups only, as plan_build_stages
+    // the tiling rules' key (config.h)
+    const int esize = dtype == PAC_C64 ? 8 : (dtype == PAC_C128_DF ? kEsDf : 16);
     std::vector<GroupPlan> gr;
-    if (int rc = form_groups(ndim, dims, st, dtype == PAC_C64 ? 8 : 16, sch, gr)) return rc;
+    if (int rc = form_groups(ndim, dims, st, esize, sch, gr)) return rc;
     const int n = (int)gr.size();
     if (axis || size || rounds) {
         if (*count < n) return fail(PAC_ERR_ARG, "room for %d groups, %d needed", *count, n);
         for (int g = 0; g < n; ++g) {
             const GroupPlan& p = gr[g];
-            const int esize = dtype == PAC_C64 ? 8 : 16;
             if (axis) axis[g] = p.axis;
             if (size) size[g] = p.M;
             if (rounds) {
@@ -517,7 +520,8 @@ extern "C" int pac_plan_groups(int ndim, const int64_t* dims, int radix, pac_dty
 extern "C" int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int flags, int cap,
                                  int group, int which, void* out, int64_t* count, int64_t* L, int64_t* T) {
     if (ndim < 1 || ndim > 3 || !dims || !count) return fail(PAC_ERR_ARG, "bad arguments");
-    if (dtype != PAC_C64 && dtype != PAC_C128) return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
+    if (dtype != PAC_C64 && dtype != PAC_C128 && dtype != PAC_C128_DF)
+        return fail(PAC_ERR_ARG, "bad dtype %d", (int)dtype);
     if (radix != 0 && prime_of(radix) == 0) return fail(PAC_ERR_ARG, "radix %d not in {0,2,3,4,5,8}", radix);
     if (which < 0 || which > 2) return fail(PAC_ERR_ARG, "table %d not in {0,1,2}", which);
     std::vector<std::vector<int>> st(ndim);
@@ -529,9 +533,10 @@ extern "C" int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_d
     Schedule sch;
     sch.cap = cap;
     sch.mixed = (flags & 2) ? -1 : (flags & 1) ? 1 : 0;
+    if (dtype == PAC_C128_DF) sch.mixed = 0;
     std::vector<GroupPlan> gr;
-    const int esize = dtype == PAC_C64 ? 8 : 16;
-    if (int rc = form_groups(ndim, dims, st, esize, sch, gr)) return rc;
+    const int esize = dtype == PAC_C64 ? 8 : 16;  // bytes of an entry (double-float: two FP32 pairs)
+    if (int rc = form_groups(ndim, dims, st, dtype == PAC_C128_DF ? kEsDf : esize, sch, gr)) return rc;
     if (group < 0 || group >= (int)gr.size()) return fail(PAC_ERR_ARG, "group %d of %d", group, (int)gr.size());
     const GroupPlan& g = gr[group];
     const int64_t n = twiddle_count(g, which);
@@ -541,6 +546,7 @@ extern "C" int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_d
         if (*count < n) return fail(PAC_ERR_ARG, "room for %lld entries, %lld needed", (long long)*count, (long long)n);
         std::vector<unsigned char> blob((size_t)std::max<int64_t>(n, 1) * esize);
         fill_twiddles(g, esize, which, blob, 0);
+        if (dtype == PAC_C128_DF) df_split(blob, 0, (size_t)n);  // the pairs a double-float plan uploads
         std::memcpy(out, blob.data(), (size_t)n * esize);
     }
     *count = n;

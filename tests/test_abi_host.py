@@ -216,6 +216,25 @@ def test_plan_groups_invariants(dims, dtype, mixed):
     assert len(groups) <= len(pac.pac_plan_groups(dims, 0, dtype, False))
 
 
+@pytest.mark.parametrize("dims,radix", [((3125, 3125), 5), ((2187, 2187), 3), ((128, 128, 128), 2), ((4096, 4096), 4),
+                                        ((1 << 20,), 4), ((1000, 1000), 0), ((60, 90, 30), 0), ((6000,), 0)])
+def test_double_float_plan_groups(dims, radix):
+    """Double-float plans (PAC_C128_DF) get the FP64 plans' one-base groups
+    (the same sizes, axes and order; groups spanning bases are never formed,
+    whatever the flags) and their own rounds: at most 4 points for base 2,
+    3 for base 3, 5 for base 5, larger rounds first, multiplying to the group."""
+    df = pac.pac_plan_groups(dims, radix, pac.C128_DF, None)
+    assert [(a, m) for a, m, _ in df] == [(a, m) for a, m, _ in pac.pac_plan_groups(dims, radix, pac.C128, False)]
+    assert df == pac.pac_plan_groups(dims, radix, pac.C128_DF, True)
+    for _, m, rounds in df:
+        base = 2 if m % 2 == 0 else (3 if m % 3 == 0 else 5)
+        assert int(np.prod(rounds)) == m
+        assert all(r <= {2: 4, 3: 3, 5: 5}[base] and r % base == 0 for r in rounds)
+        assert rounds == sorted(rounds, reverse=True)
+    if dims == (3125, 3125):
+        assert df == [(0, 3125, [5] * 5), (1, 3125, [5] * 5)]
+
+
 def test_plan_groups_rejects_bad_problems():
     for dims, radix, status in [((7,), 0, pac.Status.ERR_SIZE), ((100,), 2, pac.Status.ERR_SIZE),
                                 ((64,), 6, pac.Status.ERR_ARG), ((2, 2, 2, 2), 2, pac.Status.ERR_ARG)]:

@@ -270,6 +270,32 @@ def test_bfly_table_is_exact_and_rounded_once():
     assert np.array_equal(b32, b64.astype(np.float32).astype(np.float64))
 
 
+@pytest.mark.parametrize("dims,radix", [((3125,), 5), ((2187, 9), 3), ((4096, 64), 4), ((1 << 16,), 2)])
+def test_double_float_plan_twiddles_are_the_fp64_tables_split_once(dims, radix):
+    """The twiddle tables a double-float plan uploads: every FP64 entry of the
+    FP64 plan's table (same group, same root) as hi = the FP64 value rounded
+    to FP32 and lo = the remainder rounded to FP32, so hi + lo is within
+    2^-48 of it (relative to the root's modulus 1) and the pair is exact
+    where the FP64 value has at most 24 significant bits."""
+    groups = pac.pac_plan_groups(dims, radix, pac.C128_DF, None)
+    seen = 0
+    for g in range(len(groups)):
+        for which in (0, 1, 2):
+            pairs, L, T = pac.pac_plan_twiddles(dims, radix, pac.C128_DF, g, which)
+            if len(pairs) == 0:
+                continue
+            # the FP64 table of the same group (the double-float schedule's group at the same index)
+            ref, L64, T64 = pac.pac_plan_twiddles(dims, radix, pac.C128, g, which)
+            assert (L, T) == (L64, T64) and len(ref) == len(pairs)
+            for part, want in ((pairs[:, 0:2], ref.real), (pairs[:, 2:4], ref.imag)):
+                hi, lo = part[:, 0].astype(np.float64), part[:, 1].astype(np.float64)
+                assert np.array_equal(part[:, 0], want.astype(np.float32))
+                assert np.array_equal(part[:, 1], (want - hi).astype(np.float32))
+                assert np.max(np.abs(hi + lo - want)) <= 2.0 ** -48
+            seen += 1
+    assert seen >= 1
+
+
 # ---- the double-float constant tables (c_taudf, c_bflydf): {hi, lo} FP32 pairs of the same values
 
 
