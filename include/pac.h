@@ -97,8 +97,9 @@ typedef enum {
  * numbers, about 48 significant bits) on the FP32 pipes, which GB300 runs at
  * 64 times its FP64 rate; the twiddles are the FP64 tables split once into
  * two FP32 parts.  The relative L2 error stays within the FP64 tolerance
- * (1e-12) for magnitudes within FP32's range (about 1e-38 to 3e38; smaller
- * values flush to 0).  One-base stage groups only (no plane pass, no groups
+ * (1e-12) for magnitudes within FP32's range (about 1e-38 to 3e38; 48-bit
+ * precision down to about 2e-31, gradually less below; smaller than 1e-38
+ * flushes to 0).  One-base stage groups only (no plane pass, no groups
  * spanning prime bases); pac_convolve, pac_convolve_host, pac_submit and
  * pac_tune take such plans, the other entry points return PAC_ERR_ARG.
  */

@@ -22,9 +22,10 @@
 //          every operation here accepts such operands, and the next sum
 //          renormalises.
 //
-// Range: that of FP32 (normal numbers from about 1.2e-38 to 3.4e38).  The
-// conversions from and to FP64 (df_from_double, df_to_double) are exact
-// within that range up to the 48-bit precision.
+// Range: that of FP32 (normal numbers from about 1.2e-38 to 3.4e38), with
+// the full 48 bits down to about 2^-102 (2e-31); below that the low part is
+// subnormal and the precision falls gradually to FP32's.  The conversions
+// from and to FP64 (df_from_double, df_to_double) keep that precision.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -90,12 +91,13 @@ __device__ __forceinline__ dfloat df_from_double(double d) {
 }
 
 // FP32 -> FP64 exactly, by integer operations on the bit pattern (no FP64
-// instruction): zero and subnormals give a signed zero, infinities and NaNs
-// keep their kind.
+// instruction) for normal numbers, infinities and NaNs; zero and subnormals
+// (a low part below 2^-126, for values below about 2^-102) take the plain
+// conversion.
 __device__ __forceinline__ double df_widen(float f) {
     const uint32_t b = __float_as_uint(f);
     const uint32_t sign = b & 0x80000000u, ex = (b >> 23) & 0xffu, man = b & 0x7fffffu;
-    if (ex == 0u) return __hiloint2double((int)sign, 0);
+    if (ex == 0u) return (double)f;
     const uint32_t dex = ex == 0xffu ? 0x7ffu : ex + 896u;  // rebias 127 -> 1023
     return __hiloint2double((int)(sign | (dex << 20) | (man >> 3)), (int)(man << 29));
 }

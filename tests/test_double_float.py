@@ -15,6 +15,11 @@ which is exact, plus the addend, rounded once to FP32):
   random data, where plain FP32 misses by 1e-7 — and a model with one term of
   the product dropped fails the same test (the bound has teeth).
 
+The header itself (csrc/df.cuh) is also built for the host (tests/c/df_host.cpp,
+with host definitions of the device intrinsics it calls) and checked against the
+model: the FP64 split and the widening back bit for bit (subnormal low parts
+within their spacing), the sum bit for bit, the product within its bound.
+
 Exact references are Python fractions.
 """
 from fractions import Fraction
@@ -144,3 +149,78 @@ def test_model_fft_reaches_fp64_accuracy(n):
     # a plausible mistake (one cross term of the product dropped) fails the bound
     bad = _model_fft(x, drop_cross=True)
     assert np.linalg.norm(bad - want) / np.linalg.norm(want) > 1e-13
+
+
+# ---- the header itself (csrc/df.cuh), built for the host with host definitions of the intrinsics
+
+
+def _df_host():
+    import os
+    import shutil
+    import subprocess
+    import tempfile
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cuda_inc = next((p for p in ("/usr/local/cuda/include",) if os.path.exists(os.path.join(p, "cuda_runtime.h"))), None)
+    if not shutil.which("g++") or cuda_inc is None:
+        pytest.skip("needs g++ and the CUDA headers")
+    exe = os.path.join(tempfile.mkdtemp(), "df_host")
+    subprocess.run(["g++", "-O2", "-ffp-contract=off", "-std=c++17", "-I", cuda_inc, "-I",
+                    os.path.join(root, "paper_2506_12718_gb300", "csrc"), os.path.join(root, "tests", "c", "df_host.cpp"),
+                    "-o", exe], check=True, capture_output=True)
+
+    def run(lines):
+        out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True, check=True).stdout
+        return [[float.fromhex(t) for t in ln.split()] for ln in out.strip().splitlines()]
+    return run
+
+
+def test_header_split_and_widen_match_the_model_bit_for_bit():
+    """df_from_double is the model's split (hi truncated to 24 bits, lo the
+    rest rounded) bit for bit, and df_to_double is hi + lo rounded once to
+    FP64 (subnormal low parts included); the round trip keeps 48 bits down to
+    about 2^-102; out-of-range inputs flush to zero or saturate to infinity,
+    NaN stays NaN."""
+    run = _df_host()
+    rng = np.random.default_rng(7)
+    ds = list(rng.standard_normal(2000) * 10.0 ** rng.integers(-35, 35, 2000)) + [1.0, -1.0, 0.5, 3.0, -7.25]
+    res = run([f"widen {float(d).hex()}" for d in ds])
+    for d, (hi, lo, back) in zip(ds, res):
+        mhi, mlo = df_from_double(float(d))
+        assert hi == float(mhi), d
+        if abs(float(mlo)) >= 2.0 ** -126:
+            assert lo == float(mlo), d
+        else:  # a subnormal low part: rounded twice (to 24 bits, then to the subnormal grid)
+            assert abs(lo - float(mlo)) <= 2.0 ** -149, d
+        assert back == float(np.float64(hi) + np.float64(lo))
+        # 48 bits down to about 2^-102, where lo becomes subnormal (then within its spacing, 2^-149)
+        assert abs(Fraction(back) - Fraction(float(d))) <= max(Fraction(2) ** -47 * abs(Fraction(float(d))),
+                                                                Fraction(2) ** -149)
+    special = run([f"split {v.hex()}" for v in (0.0, -0.0, 1e-40, -1e-45, 1e39, -1e300, float("inf"))] + ["split nan"])
+    assert special[0] == [0.0, 0.0] and math_copysign(special[1][0]) < 0
+    assert special[2] == [0.0, 0.0] and special[3][0] == 0.0
+    assert special[4][0] == float("inf") and special[5][0] == -float("inf") and special[6][0] == float("inf")
+    assert np.isnan(special[7][0])
+
+
+def math_copysign(x):
+    import math
+    return math.copysign(1.0, x)
+
+
+def test_header_sum_and_product_meet_the_bounds():
+    """operator+ is the model's sum bit for bit (no fused operation in it);
+    operator* is within 2^-44 of the exact product; both on operands of many
+    magnitudes, cancellation included."""
+    run = _df_host()
+    rng = np.random.default_rng(8)
+    xs = rand_df(rng, 300, 1.0) + rand_df(rng, 100, 1e-6) + rand_df(rng, 100, 1e6)
+    pairs = [(xs[i], xs[i + 1]) for i in range(len(xs) - 1)] + [(xs[0], (-xs[0][0], -xs[0][1]))]
+    fmt = lambda a, b: f"{float(a[0]).hex()} {float(a[1]).hex()} {float(b[0]).hex()} {float(b[1]).hex()}"
+    sums = run([f"add {fmt(a, b)}" for a, b in pairs])
+    prods = run([f"mul {fmt(a, b)}" for a, b in pairs])
+    for (a, b), s, p in zip(pairs, sums, prods):
+        ms = df_add(a, b)
+        assert (s[0], s[1]) == (float(ms[0]), float(ms[1]))
+        exact = val(a) * val(b)
+        assert abs(Fraction(p[0]) + Fraction(p[1]) - exact) <= Fraction(2) ** -44 * abs(exact)
+    assert sums[-1] == [0.0, 0.0]
