@@ -67,6 +67,22 @@ struct SpecOrder {
     uint32_t K;         // plane: CTAs per plane (columns of axis d-1 split K ways)
 };
 
+// One step of a convolution as pac_test_host_steps lists it for the CPU
+// emulation of the kernels: a pass (kind 0, the pass kernel of group size M,
+// lines layout when lines != 0, the arguments a) or the spectrum reorder
+// (kind 1: dst[slot(e)] = src[e] * scale for e < n, the order o).
+struct HostStep {
+    int kind;
+    int M;
+    int lines;
+    int64_t n;
+    double scale;
+    const void* src;
+    void* dst;
+    PassArgs a;
+    SpecOrder o;
+};
+
 constexpr int kMaxPasses = 12;
 
 // A whole convolution (or forward transform) as one cooperative launch:

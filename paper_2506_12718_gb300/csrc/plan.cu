@@ -649,8 +649,20 @@ int plan_build(int ndim, const int64_t* dims, int radix, pac_dtype dtype, const 
     return plan_build_stages(ndim, dims, st, radix, dtype, sch, out);
 }
 
+// host_blob != NULL: build the groups and the table blob on the host only (no
+// device call: no plane pass, tables and spectrum left to the caller)
+static int plan_build_impl(int ndim, const int64_t* dims, const std::vector<std::vector<int>>& stages, int radix,
+                           pac_dtype dtype, const Schedule& sch, pac_plan* out,
+                           std::vector<unsigned char>* host_blob);
+
 int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vector<int>>& stages, int radix,
                       pac_dtype dtype, const Schedule& sch, pac_plan* out) {
+    return plan_build_impl(ndim, dims, stages, radix, dtype, sch, out, nullptr);
+}
+
+static int plan_build_impl(int ndim, const int64_t* dims, const std::vector<std::vector<int>>& stages, int radix,
+                           pac_dtype dtype, const Schedule& sch, pac_plan* out,
+                           std::vector<unsigned char>* host_blob) {
     if (!out) return fail(PAC_ERR_ARG, "null out");
     *out = nullptr;
     if (ndim < 1 || ndim > 3 || !dims || (int)stages.size() != ndim) return fail(PAC_ERR_ARG, "ndim must be 1, 2 or 3");
@@ -744,7 +756,7 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
     // plane pass: axis d-1 one group, a supported shape of (last group of axis d-2) x (axis d-1);
     // PAC_PLANE=0 in the environment keeps per-axis passes instead
     const char* pe = std::getenv("PAC_PLANE");
-    if (ndim >= 2 && sch.plane && !pl->df && !(pe && pe[0] == '0')) {
+    if (ndim >= 2 && sch.plane && !pl->df && !host_blob && !(pe && pe[0] == '0')) {
         int g_last = 0, g_prev = 0;
         for (const GroupPlan& g : pl->groups) {
             if (g.axis == ndim - 1) ++g_last;
@@ -822,6 +834,19 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
         }
     }
 
+    if (host_blob) {
+        pl->tables_bytes = blob.size();
+        pl->spec_elems = pl->N;
+        if (!pl->groups.empty()) {
+            const GroupPlan& f = pl->groups.back();
+            const int64_t W = group_w(f, pl->ces);
+            pl->spec_elems = (f.Q + W - 1) / W * W * f.M;
+        }
+        pl->schedule = sch;
+        *host_blob = std::move(blob);
+        *out = pl;
+        return PAC_OK;
+    }
     cudaError_t e = cudaGetDevice(&pl->device);
     if (e != cudaSuccess) {
         delete pl;
@@ -851,6 +876,77 @@ int plan_build_stages(int ndim, const int64_t* dims, const std::vector<std::vect
 }
 
 }  // namespace pac
+
+// Test hook (host only): the steps of a plan of this problem with one-base
+// groups and per-axis passes, their tables and arrays in host memory, for the
+// CPU emulation of the kernels (see pac.h).
+extern "C" int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int cap, const void* h,
+                                   const void* x, void* y, void* spec, void* scratch, void* tables,
+                                   int64_t* table_bytes, int64_t* spec_elems, void* steps, int* nsteps) {
+    if (ndim < 1 || ndim > 3 || !dims || !table_bytes || !spec_elems || !nsteps) return fail(PAC_ERR_ARG, "bad arguments");
+    if (radix != 0 && prime_of(radix) == 0) return fail(PAC_ERR_ARG, "radix %d not in {0,2,3,4,5,8}", radix);
+    std::vector<std::vector<int>> st(ndim);
+    for (int a = 0; a < ndim; ++a) {
+        if (dims[a] < 1 || dims[a] > (int64_t(1) << 30))
+            return fail(PAC_ERR_SIZE, "dimension %lld out of range", (long long)dims[a]);
+        if (int rc = stage_list(dims[a], radix, st[a])) return rc;
+    }
+    Schedule sch;
+    sch.cap = cap;
+    sch.plane = false;
+    sch.mixed = 0;
+    pac_plan p = nullptr;
+    std::vector<unsigned char> blob;
+    if (int rc = pac::plan_build_impl(ndim, dims, st, radix, dtype, sch, &p, &blob)) return rc;
+    p->d_tables = tables;  // host memory: the step records point into the caller's buffers
+    p->d_spec = spec;
+    std::vector<HostStep> out;
+    auto pass_step = [&](const Step& s) {
+        HostStep r = {};
+        r.kind = 0;
+        r.M = p->groups[s.group].M;
+        r.lines = p->groups[s.group].C == 1 ? 1 : 0;
+        r.src = s.src;
+        r.dst = s.dst;
+        r.a = make_pass(p, p->groups[s.group], s.mode, s.src, s.dst, s.io);
+        out.push_back(r);
+    };
+    const int G = (int)p->groups.size();
+    if (G > 0) {
+        // the spectrum: forward passes on h, then the reorder with 1/N
+        for (int i = 0; i < G; ++i) {
+            Step s = {i, kFwd, i == 0 ? h : scratch, scratch};
+            if (i == 0) s.io |= kDfSrc64;
+            pass_step(s);
+        }
+        HostStep r = {};
+        r.kind = 1;
+        r.n = p->N;
+        r.scale = 1.0 / (double)p->N;
+        r.src = scratch;
+        r.dst = spec;
+        r.o = spec_order_of(p);
+        out.push_back(r);
+        std::vector<Step> cs;
+        convolve_steps(p, x, y, cs);
+        for (const Step& s : cs) pass_step(s);
+    }
+    *table_bytes = (int64_t)blob.size();
+    *spec_elems = p->spec_elems;
+    int rc = PAC_OK;
+    if (steps) {
+        if (*nsteps < (int)out.size())
+            rc = fail(PAC_ERR_ARG, "room for %d steps, %d needed", *nsteps, (int)out.size());
+        else
+            std::memcpy(steps, out.data(), out.size() * sizeof(HostStep));
+    }
+    if (rc == PAC_OK && tables) std::memcpy(tables, blob.data(), blob.size());
+    if (rc == PAC_OK) *nsteps = (int)out.size();
+    p->d_tables = nullptr;
+    p->d_spec = nullptr;
+    delete p;
+    return rc;
+}
 
 extern "C" int pac_plan_destroy(pac_plan p) {
     if (!p) return fail(PAC_ERR_ARG, "null plan");

@@ -1,0 +1,80 @@
+"""CPU emulation of the pass kernels against the FP64 oracle (no GPU).
+
+tests/c/emulate.cpp builds the kernels' own device code (csrc/fft_device.cuh:
+run_phase, the rounds, the placement tables' use, the spectrum order and the
+double-float loads and stores) for the host and runs each pass as one CTA of
+NT host threads (__syncthreads a barrier of those threads, the exchange
+buffer in host memory), driven by the library's step records
+(pac_test_host_steps: the plan builder's groups, tables and pass arguments).
+So the whole convolution path, apart from the launch and the hardware, is
+checked on the CPU: complex FP32, FP64 and double-float, 1-D to 3-D, rows
+and lines passes, fused single-group plans, and external twiddles (a group
+cap that splits an axis).  Results against the oracle (O2, separable
+filters) within the GPU tests' tolerances.
+"""
+import math
+import os
+import shutil
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import pac_inputs as pin
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CUDA_INC = "/usr/local/cuda/include"
+PKG = os.path.join(ROOT, "paper_2506_12718_gb300")
+CODES = {"c64": 0, "c128": 1, "c128df": 2}
+
+CASES = [((25, 125), 5, 0), ((64, 32), 4, 0), ((27, 81), 3, 0), ((2048,), 2, 0), ((3, 9, 27), 3, 0),
+         ((3125,), 5, 2), ((4096,), 4, 3), ((5, 25, 5), 5, 0), ((2, 8, 16), 2, 0)]
+
+
+@pytest.fixture(scope="module")
+def emulate():
+    if not shutil.which("g++") or not os.path.exists(os.path.join(CUDA_INC, "cuda_runtime.h")):
+        pytest.skip("needs g++ and the CUDA headers")
+    from paper_2506_12718_gb300 import _build
+    _build.build()
+    exe = os.path.join(tempfile.mkdtemp(), "emulate")
+    r = subprocess.run(["g++", "-O1", "-std=c++20", "-ffp-contract=off", "-pthread", "-I", CUDA_INC, "-I",
+                        os.path.join(ROOT, "include"), "-I", os.path.join(PKG, "csrc"),
+                        os.path.join(ROOT, "tests", "c", "emulate.cpp"), "-L", PKG, "-lpac", "-Wl,-rpath," + PKG,
+                        "-o", exe], capture_output=True, text=True)
+    if r.returncode:
+        pytest.fail("emulator build failed:\n" + r.stderr[-2000:])
+
+    def run(dims, radix, dtype, cap, h, x):
+        d = tempfile.mkdtemp()
+        hf, xf, yf = (os.path.join(d, n) for n in ("h", "x", "y"))
+        h.tofile(hf)
+        x.tofile(xf)
+        args = [exe, str(CODES[dtype]), str(radix), str(cap), str(len(dims))] + [str(v) for v in dims] + [hf, xf, yf]
+        r = subprocess.run(args, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr
+        return np.fromfile(yf, dtype=x.dtype).reshape(dims)
+    return run
+
+
+def tol(dtype, n):
+    return 1e-12 if dtype in ("c128", "c128df") else 1e-5 * max(1.0, math.log2(n))
+
+
+@pytest.mark.parametrize("dtype", list(CODES))
+@pytest.mark.parametrize("dims,radix,cap", CASES, ids=[f"{'x'.join(map(str, d))}-r{r}-cap{c}" for d, r, c in CASES])
+def test_emulated_kernels_match_the_oracle(emulate, dims, radix, cap, dtype):
+    seed = 17 + dims[0]
+    fs = [pin.complex_uniform((n,), seed + 100 + a) for a, n in enumerate(dims)]
+    store = "c64" if dtype == "c64" else "c128"
+    h = pin.as_dtype(pin.outer(fs), store)
+    x = pin.as_dtype(pin.complex_uniform(dims, seed), store)
+    y = emulate(dims, radix, dtype, cap, h, x)
+    ref = oracle.conv_separable(fs, x)
+    n = int(np.prod(dims))
+    err = oracle.rel_l2(y, ref)
+    assert err <= tol(dtype, n), f"{dims} r{radix} cap {cap} {dtype}: rel_l2 {err:.3e}"
+    if dtype == "c128df":  # a different arithmetic from FP64, within the same bound
+        assert err > 0
