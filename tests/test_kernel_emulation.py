@@ -11,6 +11,11 @@ checked on the CPU: complex FP32, FP64 and double-float, 1-D to 3-D, rows
 and lines passes, fused single-group plans, and external twiddles (a group
 cap that splits an axis).  Results against the oracle (O2, separable
 filters) within the GPU tests' tolerances.
+
+PAC_EMULATE_SANITIZE=1 in the environment builds the emulator with
+AddressSanitizer and UndefinedBehaviorSanitizer (about ten minutes of
+compilation): every access of the kernels' code to the arrays, tables and
+exchange buffer is then checked on the CPU.
 """
 import math
 import os
@@ -40,7 +45,10 @@ def emulate():
     from paper_2506_12718_gb300 import _build
     _build.build()
     exe = os.path.join(tempfile.mkdtemp(), "emulate")
-    r = subprocess.run(["g++", "-O1", "-std=c++20", "-ffp-contract=off", "-pthread", "-I", CUDA_INC, "-I",
+    sanitize = os.environ.get("PAC_EMULATE_SANITIZE") == "1"
+    san = ["-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined"] if sanitize else []
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=0") if sanitize else None
+    r = subprocess.run(["g++", "-O1"] + san + ["-std=c++20", "-ffp-contract=off", "-pthread", "-I", CUDA_INC, "-I",
                         os.path.join(ROOT, "include"), "-I", os.path.join(PKG, "csrc"),
                         os.path.join(ROOT, "tests", "c", "emulate.cpp"), "-L", PKG, "-lpac", "-Wl,-rpath," + PKG,
                         "-o", exe], capture_output=True, text=True)
@@ -53,7 +61,7 @@ def emulate():
         h.tofile(hf)
         x.tofile(xf)
         args = [exe, str(CODES[dtype]), str(radix), str(cap), str(len(dims))] + [str(v) for v in dims] + [hf, xf, yf]
-        r = subprocess.run(args, capture_output=True, text=True, timeout=600)
+        r = subprocess.run(args, capture_output=True, text=True, timeout=600, env=env)
         assert r.returncode == 0, r.stderr
         return np.fromfile(yf, dtype=x.dtype).reshape(dims)
     return run
