@@ -472,8 +472,9 @@ int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_dtype dtype,
  * the forward passes of the spectrum (h -> scratch), its reorder with 1/N
  * (scratch -> spec), then the convolution's passes (x -> y).  Call first
  * with tables and steps NULL for the sizes (*nsteps = the step count).
- * Errors: PAC_ERR_ARG (bad arguments, too little room), size errors as
- * pac_plan_create.
+ * Errors: PAC_ERR_ARG (bad arguments, too little room, PAC_NARROW or
+ * PAC_MIXED in the environment giving narrow tiles or groups spanning
+ * bases), size errors as pac_plan_create.
  */
 int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int cap, const void* h,
                         const void* x, void* y, void* spec, void* scratch, void* tables, int64_t* table_bytes,

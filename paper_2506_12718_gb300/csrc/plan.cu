@@ -898,6 +898,12 @@ extern "C" int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac
     pac_plan p = nullptr;
     std::vector<unsigned char> blob;
     if (int rc = pac::plan_build_impl(ndim, dims, st, radix, dtype, sch, &p, &blob)) return rc;
+    for (const GroupPlan& g : p->groups) {
+        if (g.nv || g.mix_nr > 0 || is_mixed(g.M)) {  // PAC_NARROW / PAC_MIXED set in the environment
+            delete p;
+            return fail(PAC_ERR_ARG, "pac_test_host_steps: default-tile one-base groups only (PAC_NARROW, PAC_MIXED)");
+        }
+    }
     p->d_tables = tables;  // host memory: the step records point into the caller's buffers
     p->d_spec = spec;
     std::vector<HostStep> out;
