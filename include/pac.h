@@ -463,22 +463,23 @@ int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_dtype dtype,
  * Test hook (host only, no device; no counterpart in the paper): the steps of
  * a convolution plan of this problem, for the CPU tests that run the pass
  * kernels' own code on the host.  The plan is built with one-base groups,
- * per-axis passes (no plane pass) and the group-exponent cap `cap` (0: none);
+ * the group-exponent cap `cap` (0: none) and per-axis passes, or with flags
+ * bit 0 the plane pass where the shape has one of one CTA per plane;
  * its tables are written to `tables` (host memory, *table_bytes bytes) and
  * every step record points into the caller's host buffers: h, x (inputs,
  * N elements of the dtype's 16 or 8 bytes), y (output), scratch (N
  * elements), spec (*spec_elems elements).  `steps` (may be NULL) receives
  * *nsteps records of the library's internal HostStep layout (pass_args.h):
  * the forward passes of the spectrum (h -> scratch), its reorder with 1/N
- * (scratch -> spec), then the convolution's passes (x -> y).  Call first
+ * (scratch -> spec), then the convolution's passes and plane pass (x -> y).  Call first
  * with tables and steps NULL for the sizes (*nsteps = the step count).
  * Errors: PAC_ERR_ARG (bad arguments, too little room, PAC_NARROW or
  * PAC_MIXED in the environment giving narrow tiles or groups spanning
  * bases), size errors as pac_plan_create.
  */
-int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int cap, const void* h,
-                        const void* x, void* y, void* spec, void* scratch, void* tables, int64_t* table_bytes,
-                        int64_t* spec_elems, void* steps, int* nsteps);
+int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int cap, int flags,
+                        const void* h, const void* x, void* y, void* spec, void* scratch, void* tables,
+                        int64_t* table_bytes, int64_t* spec_elems, void* steps, int* nsteps);
 
 /* Host-only helpers (no device needed): the stage list of pac_plan_create
  * (radix 0 included) and the reversal table of a stage list. */

@@ -87,7 +87,7 @@ _SIGS = {
     "pac_test_batch_timeout": (_i32, [_i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp, _i32]),
     "pac_plan_twiddles": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _i32, _i32, _i32, _vp,
                                  ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
-    "pac_test_host_steps": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
+    "pac_test_host_steps": (_i32, [_i32, ctypes.POINTER(_i64), _i32, _i32, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                                    ctypes.POINTER(_i64), ctypes.POINTER(_i64), _vp, ctypes.POINTER(_i32)]),
     "pac_version": (ctypes.c_char_p, []),
     "pac_pfa_create": (_i32, [_i64, _i32, ctypes.POINTER(_vp)]),
@@ -203,16 +203,16 @@ def pac_plan_twiddles(dims, radix: int, dtype: int, group: int, which: int, mixe
     return out[: cnt.value], L.value, T.value
 
 
-def pac_test_host_steps(dims, radix: int, dtype: int, cap: int = 0, h=None, x=None, y=None, spec=None, scratch=None,
-                        tables=None, steps=None, room: int = 0):
+def pac_test_host_steps(dims, radix: int, dtype: int, cap: int = 0, flags: int = 0, h=None, x=None, y=None, spec=None,
+                        scratch=None, tables=None, steps=None, room: int = 0):
     """Host-only test hook: the step records of a plan of this problem for the CPU emulation of the
     kernels (pointer arguments: host addresses as ints, or None).  Returns (table_bytes, spec_elems,
     number of steps)."""
     vals = [int(v) for v in dims]
     d = (ctypes.c_int64 * max(3, len(vals)))(*(vals + [1] * (3 - len(vals))))
     tb, se, ns = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int(int(room))
-    _check(load().pac_test_host_steps(len(vals), d, int(radix), int(dtype), int(cap), h, x, y, spec, scratch, tables,
-                                      ctypes.byref(tb), ctypes.byref(se), steps, ctypes.byref(ns)))
+    _check(load().pac_test_host_steps(len(vals), d, int(radix), int(dtype), int(cap), int(flags), h, x, y, spec, scratch,
+                                      tables, ctypes.byref(tb), ctypes.byref(se), steps, ctypes.byref(ns)))
     return tb.value, se.value, ns.value
 
 

@@ -69,8 +69,10 @@ struct SpecOrder {
 
 // One step of a convolution as pac_test_host_steps lists it for the CPU
 // emulation of the kernels: a pass (kind 0, the pass kernel of group size M,
-// lines layout when lines != 0, the arguments a) or the spectrum reorder
-// (kind 1: dst[slot(e)] = src[e] * scale for e < n, the order o).
+// lines layout when lines != 0, the arguments a), the spectrum reorder
+// (kind 1: dst[slot(e)] = src[e] * scale for e < n, the order o), or a plane
+// pass with one CTA per plane (kind 2: planes of M x lines points, the
+// arguments pa).
 struct HostStep {
     int kind;
     int M;
@@ -81,6 +83,7 @@ struct HostStep {
     void* dst;
     PassArgs a;
     SpecOrder o;
+    PlaneArgs pa;
 };
 
 constexpr int kMaxPasses = 12;

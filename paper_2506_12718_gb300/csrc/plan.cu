@@ -756,7 +756,7 @@ static int plan_build_impl(int ndim, const int64_t* dims, const std::vector<std:
     // plane pass: axis d-1 one group, a supported shape of (last group of axis d-2) x (axis d-1);
     // PAC_PLANE=0 in the environment keeps per-axis passes instead
     const char* pe = std::getenv("PAC_PLANE");
-    if (ndim >= 2 && sch.plane && !pl->df && !host_blob && !(pe && pe[0] == '0')) {
+    if (ndim >= 2 && sch.plane && !pl->df && !(pe && pe[0] == '0')) {
         int g_last = 0, g_prev = 0;
         for (const GroupPlan& g : pl->groups) {
             if (g.axis == ndim - 1) ++g_last;
@@ -764,8 +764,15 @@ static int plan_build_impl(int ndim, const int64_t* dims, const std::vector<std:
         }
         const int G = (int)pl->groups.size();
         // groups[G-2] is the last group of axis d-2 (no external twiddle), groups[G-1] all of axis d-1
-        if (g_last == 1 && g_prev >= 1 && G >= 2 &&
-            plane_supported(pl->groups[G - 2].M, pl->groups[G - 1].M, pl->esize)) {
+        if (host_blob) {  // host only (the CPU emulation): whole planes in one CTA, where the shape has them
+            if (g_last == 1 && g_prev >= 1 && G >= 2 &&
+                plane_supported_k(pl->groups[G - 2].M, pl->groups[G - 1].M, pl->esize, 1)) {
+                pl->plane = true;
+                pl->plane_g1 = G - 2;
+                pl->plane_k = 1;
+            }
+        } else if (g_last == 1 && g_prev >= 1 && G >= 2 &&
+                   plane_supported(pl->groups[G - 2].M, pl->groups[G - 1].M, pl->esize)) {
             pl->plane = true;
             pl->plane_g1 = G - 2;
             int dev = 0;
@@ -837,7 +844,7 @@ static int plan_build_impl(int ndim, const int64_t* dims, const std::vector<std:
     if (host_blob) {
         pl->tables_bytes = blob.size();
         pl->spec_elems = pl->N;
-        if (!pl->groups.empty()) {
+        if (!pl->groups.empty() && !pl->plane) {
             const GroupPlan& f = pl->groups.back();
             const int64_t W = group_w(f, pl->ces);
             pl->spec_elems = (f.Q + W - 1) / W * W * f.M;
@@ -880,8 +887,8 @@ static int plan_build_impl(int ndim, const int64_t* dims, const std::vector<std:
 // Test hook (host only): the steps of a plan of this problem with one-base
 // groups and per-axis passes, their tables and arrays in host memory, for the
 // CPU emulation of the kernels (see pac.h).
-extern "C" int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int cap, const void* h,
-                                   const void* x, void* y, void* spec, void* scratch, void* tables,
+extern "C" int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int cap, int flags,
+                                   const void* h, const void* x, void* y, void* spec, void* scratch, void* tables,
                                    int64_t* table_bytes, int64_t* spec_elems, void* steps, int* nsteps) {
     if (ndim < 1 || ndim > 3 || !dims || !table_bytes || !spec_elems || !nsteps) return fail(PAC_ERR_ARG, "bad arguments");
     if (radix != 0 && prime_of(radix) == 0) return fail(PAC_ERR_ARG, "radix %d not in {0,2,3,4,5,8}", radix);
@@ -893,7 +900,7 @@ extern "C" int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac
     }
     Schedule sch;
     sch.cap = cap;
-    sch.plane = false;
+    sch.plane = (flags & 1) != 0;
     sch.mixed = 0;
     pac_plan p = nullptr;
     std::vector<unsigned char> blob;
@@ -935,7 +942,20 @@ extern "C" int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac
         out.push_back(r);
         std::vector<Step> cs;
         convolve_steps(p, x, y, cs);
-        for (const Step& s : cs) pass_step(s);
+        for (const Step& s : cs) {
+            if (s.mode != kPlane) {
+                pass_step(s);
+                continue;
+            }
+            HostStep r2 = {};
+            r2.kind = 2;
+            r2.M = p->groups[p->plane_g1].M;
+            r2.lines = p->groups[p->plane_g1 + 1].M;
+            r2.src = s.src;
+            r2.dst = s.dst;
+            r2.pa = make_plane(p, s.src, s.dst);
+            out.push_back(r2);
+        }
     }
     *table_bytes = (int64_t)blob.size();
     *spec_elems = p->spec_elems;

@@ -4,7 +4,8 @@
 // (thread-local threadIdx, __syncthreads as a barrier of the CTA's threads,
 // the exchange buffer in host memory), driven by the step records of
 // pac_test_host_steps (libpac: the plan's groups and tables).
-//   emulate <dtype 0|1|2> <radix> <cap> <ndim> <d0> [d1] [d2] <h file> <x file> <y file>
+//   emulate <dtype 0|1|2> <radix> <cap> <flags> <ndim> <d0> [d1] [d2] <h file> <x file> <y file>
+// (flags bit 0: the plane pass, one CTA per plane, where the shape has one)
 // h and x: N complex elements (complex64 for dtype 0, complex128 otherwise);
 // y is written in the same format.
 #include <barrier>
@@ -94,9 +95,52 @@ template <typename V> static bool dispatch(const HostStep& st) {
         case 64: return pass_m<V, 64>(st);
         case 81: return pass_m<V, 81>(st);
         case 125: return pass_m<V, 125>(st);
+        case 128: return pass_m<V, 128>(st);
         case 2048: return pass_m<V, 2048>(st);
         default: return false;
     }
+}
+
+// a plane pass: one CTA of NT host threads walks every plane (plane_kernel's
+// loop with a grid of one, K = 1)
+template <typename V, int M1, int M2> static bool run_plane(const PlaneArgs& pa) {
+    using PS = PlaneShape<V, M1, M2, 1>;
+    const int nt = PS::NT;
+    std::vector<unsigned char> smem(PS::SMEM + 16);
+    V* s = reinterpret_cast<V*>((reinterpret_cast<uintptr_t>(smem.data()) + 15) & ~uintptr_t(15));
+    std::barrier<> bar(nt);
+    std::vector<std::thread> th;
+    for (int i = 0; i < nt; ++i)
+        th.emplace_back([&, i] {
+            threadIdx = uint3{(unsigned)i, 0u, 0u};
+            blockIdx = uint3{0u, 0u, 0u};
+            blockDim = dim3((unsigned)nt);
+            gridDim = dim3(1u);
+            g_cta_barrier = &bar;
+            for (uint32_t p = 0; p < (uint32_t)pa.planes; ++p) {
+                plane_run<V, M1, M2, 1>(pa, p, 0u, s);
+                __syncthreads();
+            }
+        });
+    for (auto& t : th) t.join();
+    return true;
+}
+
+template <typename V> static bool dispatch_plane(const HostStep& st);
+template <> bool dispatch_plane<float2>(const HostStep& st) {
+    if (st.M == 64 && st.lines == 64) return run_plane<float2, 64, 64>(st.pa);
+    if (st.M == 128 && st.lines == 128) return run_plane<float2, 128, 128>(st.pa);
+    if (st.M == 27 && st.lines == 27) return run_plane<float2, 27, 27>(st.pa);
+    if (st.M == 25 && st.lines == 25) return run_plane<float2, 25, 25>(st.pa);
+    if (st.M == 128 && st.lines == 2) return run_plane<float2, 128, 2>(st.pa);
+    return false;
+}
+template <> bool dispatch_plane<double2>(const HostStep& st) {
+    if (st.M == 64 && st.lines == 64) return run_plane<double2, 64, 64>(st.pa);
+    if (st.M == 27 && st.lines == 27) return run_plane<double2, 27, 27>(st.pa);
+    if (st.M == 25 && st.lines == 25) return run_plane<double2, 25, 25>(st.pa);
+    if (st.M == 128 && st.lines == 2) return run_plane<double2, 128, 2>(st.pa);
+    return false;
 }
 
 template <typename V, typename T> static void reorder(const HostStep& st, T scale) {
@@ -112,34 +156,34 @@ static void* aligned(size_t bytes) {
 }
 
 int main(int argc, char** argv) {
-    if (argc < 9) return 2;
+    if (argc < 10) return 2;
     const int dtype = std::atoi(argv[1]), radix = std::atoi(argv[2]), cap = std::atoi(argv[3]);
-    const int ndim = std::atoi(argv[4]);
-    if (ndim < 1 || ndim > 3 || argc != 5 + ndim + 3) return 2;
+    const int flags = std::atoi(argv[4]), ndim = std::atoi(argv[5]);
+    if (ndim < 1 || ndim > 3 || argc != 6 + ndim + 3) return 2;
     int64_t dims[3] = {1, 1, 1};
     int64_t n = 1;
-    for (int a = 0; a < ndim; ++a) n *= (dims[a] = std::atoll(argv[5 + a]));
+    for (int a = 0; a < ndim; ++a) n *= (dims[a] = std::atoll(argv[6 + a]));
     const size_t es = dtype == 0 ? 8 : 16;
     void* h = aligned(n * es);
     void* x = aligned(n * es);
     void* y = aligned(n * es);
     void* scratch = aligned(n * es);
     for (int k = 0; k < 2; ++k) {
-        FILE* f = std::fopen(argv[5 + ndim + k], "rb");
+        FILE* f = std::fopen(argv[6 + ndim + k], "rb");
         if (!f || std::fread(k == 0 ? h : x, es, (size_t)n, f) != (size_t)n) return 3;
         std::fclose(f);
     }
     int64_t tb = 0, se = 0;
     int ns = 0;
-    if (pac_test_host_steps(ndim, dims, radix, (pac_dtype)dtype, cap, h, x, y, nullptr, scratch, nullptr, &tb, &se,
-                            nullptr, &ns) != 0) {
+    if (pac_test_host_steps(ndim, dims, radix, (pac_dtype)dtype, cap, flags, h, x, y, nullptr, scratch, nullptr, &tb,
+                            &se, nullptr, &ns) != 0) {
         std::fprintf(stderr, "%s\n", pac_last_error());
         return 4;
     }
     void* tables = aligned((size_t)tb);
     void* spec = aligned((size_t)se * es);
     std::vector<HostStep> steps(ns);
-    if (pac_test_host_steps(ndim, dims, radix, (pac_dtype)dtype, cap, h, x, y, spec, scratch, tables, &tb, &se,
+    if (pac_test_host_steps(ndim, dims, radix, (pac_dtype)dtype, cap, flags, h, x, y, spec, scratch, tables, &tb, &se,
                             steps.data(), &ns) != 0) {
         std::fprintf(stderr, "%s\n", pac_last_error());
         return 4;
@@ -154,13 +198,17 @@ int main(int argc, char** argv) {
                 reorder<dfloat2>(st, dfloat((float)st.scale, (float)(st.scale - (double)(float)st.scale)));
             continue;
         }
-        const bool ok = dtype == 0 ? dispatch<float2>(st) : dtype == 1 ? dispatch<double2>(st) : dispatch<dfloat2>(st);
+        bool ok;
+        if (st.kind == 2)
+            ok = dtype == 0 ? dispatch_plane<float2>(st) : dtype == 1 ? dispatch_plane<double2>(st) : false;
+        else
+            ok = dtype == 0 ? dispatch<float2>(st) : dtype == 1 ? dispatch<double2>(st) : dispatch<dfloat2>(st);
         if (!ok) {
-            std::fprintf(stderr, "no emulated kernel for group size %d\n", st.M);
+            std::fprintf(stderr, "no emulated kernel for group size %d (%d)\n", st.M, st.lines);
             return 5;
         }
     }
-    FILE* f = std::fopen(argv[5 + ndim + 2], "wb");
+    FILE* f = std::fopen(argv[6 + ndim + 2], "wb");
     if (!f || std::fwrite(y, es, (size_t)n, f) != (size_t)n) return 6;
     std::fclose(f);
     return 0;

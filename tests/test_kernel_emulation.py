@@ -8,8 +8,9 @@ buffer in host memory), driven by the library's step records
 (pac_test_host_steps: the plan builder's groups, tables and pass arguments).
 So the whole convolution path, apart from the launch and the hardware, is
 checked on the CPU: complex FP32, FP64 and double-float, 1-D to 3-D, rows
-and lines passes, fused single-group plans, and external twiddles (a group
-cap that splits an axis).  Results against the oracle (O2, separable
+and lines passes, fused single-group plans, external twiddles (a group cap
+that splits an axis), and the plane pass with one CTA per plane (complex
+FP32 and FP64).  Results against the oracle (O2, separable
 filters) within the GPU tests' tolerances.
 
 PAC_EMULATE_SANITIZE=1 in the environment builds the emulator with
@@ -36,6 +37,10 @@ CODES = {"c64": 0, "c128": 1, "c128df": 2}
 
 CASES = [((25, 125), 5, 0), ((64, 32), 4, 0), ((27, 81), 3, 0), ((2048,), 2, 0), ((3, 9, 27), 3, 0),
          ((3125,), 5, 2), ((4096,), 4, 3), ((5, 25, 5), 5, 0), ((2, 8, 16), 2, 0)]
+# plane passes (one CTA per plane): 3-D with the two innermost axes as planes, and an n x 2 shape
+PLANE_CASES = [((4, 64, 64), 4, "c64"), ((2, 128, 128), 2, "c64"), ((3, 27, 27), 3, "c64"), ((5, 25, 25), 5, "c64"),
+               ((128, 2), 2, "c64"), ((4, 64, 64), 2, "c128"), ((3, 27, 27), 3, "c128"), ((25, 25), 5, "c128"),
+               ((128, 2), 2, "c128")]
 
 
 @pytest.fixture(scope="module")
@@ -55,12 +60,13 @@ def emulate():
     if r.returncode:
         pytest.fail("emulator build failed:\n" + r.stderr[-2000:])
 
-    def run(dims, radix, dtype, cap, h, x):
+    def run(dims, radix, dtype, cap, h, x, flags=0):
         d = tempfile.mkdtemp()
         hf, xf, yf = (os.path.join(d, n) for n in ("h", "x", "y"))
         h.tofile(hf)
         x.tofile(xf)
-        args = [exe, str(CODES[dtype]), str(radix), str(cap), str(len(dims))] + [str(v) for v in dims] + [hf, xf, yf]
+        args = ([exe, str(CODES[dtype]), str(radix), str(cap), str(flags), str(len(dims))] + [str(v) for v in dims] +
+                [hf, xf, yf])
         r = subprocess.run(args, capture_output=True, text=True, timeout=600, env=env)
         assert r.returncode == 0, r.stderr
         return np.fromfile(yf, dtype=x.dtype).reshape(dims)
@@ -86,3 +92,16 @@ def test_emulated_kernels_match_the_oracle(emulate, dims, radix, cap, dtype):
     assert err <= tol(dtype, n), f"{dims} r{radix} cap {cap} {dtype}: rel_l2 {err:.3e}"
     if dtype == "c128df":  # a different arithmetic from FP64, within the same bound
         assert err > 0
+
+
+@pytest.mark.parametrize("dims,radix,dtype", PLANE_CASES, ids=[f"{'x'.join(map(str, d))}-r{r}-{t}" for d, r, t in PLANE_CASES])
+def test_emulated_plane_pass_matches_the_oracle(emulate, dims, radix, dtype):
+    seed = 29 + dims[-1]
+    fs = [pin.complex_uniform((n,), seed + 100 + a) for a, n in enumerate(dims)]
+    h = pin.as_dtype(pin.outer(fs), dtype)
+    x = pin.as_dtype(pin.complex_uniform(dims, seed), dtype)
+    y = emulate(dims, radix, dtype, 0, h, x, flags=1)
+    ref = oracle.conv_separable(fs, x)
+    n = int(np.prod(dims))
+    err = oracle.rel_l2(y, ref)
+    assert err <= tol(dtype, n), f"plane {dims} r{radix} {dtype}: rel_l2 {err:.3e}"
