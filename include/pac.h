@@ -462,9 +462,11 @@ int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_dtype dtype,
 /*
  * Test hook (host only, no device; no counterpart in the paper): the steps of
  * a convolution plan of this problem, for the CPU tests that run the pass
- * kernels' own code on the host.  The plan is built with one-base groups,
- * the group-exponent cap `cap` (0: none) and per-axis passes, or with flags
- * bit 0 the plane pass where the shape has one of one CTA per plane;
+ * kernels' own code on the host.  The plan is built with one-base groups
+ * (flags bit 1: also groups spanning prime bases where they have compiled
+ * kernels, pac_plan_create's default rule), the group-exponent cap `cap`
+ * (0: none) and per-axis passes, or with flags bit 0 the plane pass where
+ * the shape has one of one CTA per plane;
  * its tables are written to `tables` (host memory, *table_bytes bytes) and
  * every step record points into the caller's host buffers: h, x (inputs,
  * N elements of the dtype's 16 or 8 bytes), y (output), scratch (N
@@ -474,8 +476,8 @@ int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_dtype dtype,
  * (scratch -> spec), then the convolution's passes and plane pass (x -> y).  Call first
  * with tables and steps NULL for the sizes (*nsteps = the step count).
  * Errors: PAC_ERR_ARG (bad arguments, too little room, PAC_NARROW or
- * PAC_MIXED in the environment giving narrow tiles or groups spanning
- * bases), size errors as pac_plan_create.
+ * PAC_MIXED in the environment giving narrow tiles or runtime-radix
+ * groups), size errors as pac_plan_create.
  */
 int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac_dtype dtype, int cap, int flags,
                         const void* h, const void* x, void* y, void* spec, void* scratch, void* tables,

@@ -901,14 +901,14 @@ extern "C" int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac
     Schedule sch;
     sch.cap = cap;
     sch.plane = (flags & 1) != 0;
-    sch.mixed = 0;
+    sch.mixed = (flags & 2) ? -1 : 0;  // bit 1: groups spanning bases where they have compiled kernels
     pac_plan p = nullptr;
     std::vector<unsigned char> blob;
     if (int rc = pac::plan_build_impl(ndim, dims, st, radix, dtype, sch, &p, &blob)) return rc;
     for (const GroupPlan& g : p->groups) {
-        if (g.nv || g.mix_nr > 0 || is_mixed(g.M)) {  // PAC_NARROW / PAC_MIXED set in the environment
+        if (g.nv || g.mix_nr > 0) {  // PAC_NARROW / PAC_MIXED set in the environment
             delete p;
-            return fail(PAC_ERR_ARG, "pac_test_host_steps: default-tile one-base groups only (PAC_NARROW, PAC_MIXED)");
+            return fail(PAC_ERR_ARG, "pac_test_host_steps: default tiles and compiled groups only (PAC_NARROW, PAC_MIXED)");
         }
     }
     p->d_tables = tables;  // host memory: the step records point into the caller's buffers

@@ -5,7 +5,8 @@
 // the exchange buffer in host memory), driven by the step records of
 // pac_test_host_steps (libpac: the plan's groups and tables).
 //   emulate <dtype 0|1|2> <radix> <cap> <flags> <ndim> <d0> [d1] [d2] <h file> <x file> <y file>
-// (flags bit 0: the plane pass, one CTA per plane, where the shape has one)
+// (flags bit 0: the plane pass, one CTA per plane, where the shape has one;
+// bit 1: groups spanning prime bases with compiled kernels)
 // h and x: N complex elements (complex64 for dtype 0, complex128 otherwise);
 // y is written in the same format.
 #include <barrier>
@@ -96,6 +97,9 @@ template <typename V> static bool dispatch(const HostStep& st) {
         case 81: return pass_m<V, 81>(st);
         case 125: return pass_m<V, 125>(st);
         case 128: return pass_m<V, 128>(st);
+        case 48: return pass_m<V, 48>(st);
+        case 120: return pass_m<V, 120>(st);
+        case 1000: return pass_m<V, 1000>(st);
         case 2048: return pass_m<V, 2048>(st);
         default: return false;
     }

@@ -9,8 +9,8 @@ buffer in host memory), driven by the library's step records
 So the whole convolution path, apart from the launch and the hardware, is
 checked on the CPU: complex FP32, FP64 and double-float, 1-D to 3-D, rows
 and lines passes, fused single-group plans, external twiddles (a group cap
-that splits an axis), and the plane pass with one CTA per plane (complex
-FP32 and FP64).  Results against the oracle (O2, separable
+that splits an axis), the plane pass with one CTA per plane (complex FP32
+and FP64), and the compiled groups spanning prime bases (48, 120, 1000).  Results against the oracle (O2, separable
 filters) within the GPU tests' tolerances.
 
 PAC_EMULATE_SANITIZE=1 in the environment builds the emulator with
@@ -92,6 +92,22 @@ def test_emulated_kernels_match_the_oracle(emulate, dims, radix, cap, dtype):
     assert err <= tol(dtype, n), f"{dims} r{radix} cap {cap} {dtype}: rel_l2 {err:.3e}"
     if dtype == "c128df":  # a different arithmetic from FP64, within the same bound
         assert err > 0
+
+
+MIXED_CASES = [((120, 120), "c64"), ((1000,), "c128"), ((48, 125), "c64"), ((120, 8), "c128"), ((1000, 3), "c64")]
+
+
+@pytest.mark.parametrize("dims,dtype", MIXED_CASES, ids=[f"{'x'.join(map(str, d))}-{t}" for d, t in MIXED_CASES])
+def test_emulated_compiled_mixed_groups_match_the_oracle(emulate, dims, dtype):
+    """Groups spanning prime bases with compiled kernels (48, 120, 1000 points;
+    mixed radix, radix 0), against the oracle."""
+    seed = 41 + dims[0]
+    fs = [pin.complex_uniform((n,), seed + 100 + a) for a, n in enumerate(dims)]
+    h = pin.as_dtype(pin.outer(fs), dtype)
+    x = pin.as_dtype(pin.complex_uniform(dims, seed), dtype)
+    y = emulate(dims, 0, dtype, 0, h, x, flags=2)
+    err = oracle.rel_l2(y, oracle.conv_separable(fs, x))
+    assert err <= tol(dtype, int(np.prod(dims))), f"mixed {dims} {dtype}: rel_l2 {err:.3e}"
 
 
 @pytest.mark.parametrize("dims,radix,dtype", PLANE_CASES, ids=[f"{'x'.join(map(str, d))}-r{r}-{t}" for d, r, t in PLANE_CASES])
