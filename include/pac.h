@@ -464,7 +464,8 @@ int pac_plan_twiddles(int ndim, const int64_t* dims, int radix, pac_dtype dtype,
  * a convolution plan of this problem, for the CPU tests that run the pass
  * kernels' own code on the host.  The plan is built with one-base groups
  * (flags bit 1: also groups spanning prime bases where they have compiled
- * kernels, pac_plan_create's default rule), the group-exponent cap `cap`
+ * kernels, pac_plan_create's default rule; bit 2: groups spanning bases in
+ * the runtime-radix kernel, as PAC_MIXED=rt), the group-exponent cap `cap`
  * (0: none) and per-axis passes, or with flags bit 0 the plane pass where
  * the shape has one of one CTA per plane;
  * its tables are written to `tables` (host memory, *table_bytes bytes) and

@@ -901,12 +901,13 @@ extern "C" int pac_test_host_steps(int ndim, const int64_t* dims, int radix, pac
     Schedule sch;
     sch.cap = cap;
     sch.plane = (flags & 1) != 0;
-    sch.mixed = (flags & 2) ? -1 : 0;  // bit 1: groups spanning bases where they have compiled kernels
+    sch.mixed = (flags & 4) ? 1 : (flags & 2) ? -1 : 0;  // bit 1: spanning groups with compiled kernels
+    sch.mix_runtime = (flags & 4) != 0;                   // bit 2: every spanning group in the runtime-radix kernel
     pac_plan p = nullptr;
     std::vector<unsigned char> blob;
     if (int rc = pac::plan_build_impl(ndim, dims, st, radix, dtype, sch, &p, &blob)) return rc;
     for (const GroupPlan& g : p->groups) {
-        if (g.nv || g.mix_nr > 0) {  // PAC_NARROW / PAC_MIXED set in the environment
+        if (g.nv || (g.mix_nr > 0 && !(flags & 4))) {  // PAC_NARROW / PAC_MIXED set in the environment
             delete p;
             return fail(PAC_ERR_ARG, "pac_test_host_steps: default tiles and compiled groups only (PAC_NARROW, PAC_MIXED)");
         }

@@ -6,7 +6,8 @@
 // pac_test_host_steps (libpac: the plan's groups and tables).
 //   emulate <dtype 0|1|2> <radix> <cap> <flags> <ndim> <d0> [d1] [d2] <h file> <x file> <y file>
 // (flags bit 0: the plane pass, one CTA per plane, where the shape has one;
-// bit 1: groups spanning prime bases with compiled kernels)
+// bit 1: groups spanning prime bases with compiled kernels; bit 2: groups
+// spanning bases in the runtime-radix kernel)
 // h and x: N complex elements (complex64 for dtype 0, complex128 otherwise);
 // y is written in the same format.
 #include <barrier>
@@ -48,6 +49,7 @@ static inline void __nanosleep(unsigned) {}
 #define __launch_bounds__(...)
 
 #include "fft_device.cuh"
+#include "mix.cuh"
 #include "pac.h"
 
 using namespace pac;
@@ -81,7 +83,40 @@ template <typename V, int M> static bool pass_m(const HostStep& st) {
     return true;
 }
 
+// a pass of the runtime-radix kernel: one CTA of kMixThreads host threads walks every tile
+template <typename V, bool LINES> static void run_mix(const PassArgs& a) {
+    const int nt = kMixThreads;
+    std::vector<unsigned char> smem(mix_smem_bytes(a.mix_m, (int)sizeof(V)) + 16);
+    V* s = reinterpret_cast<V*>((reinterpret_cast<uintptr_t>(smem.data()) + 15) & ~uintptr_t(15));
+    std::barrier<> bar(nt);
+    std::vector<std::thread> th;
+    for (int i = 0; i < nt; ++i)
+        th.emplace_back([&, i] {
+            threadIdx = uint3{(unsigned)i, 0u, 0u};
+            blockIdx = uint3{0u, 0u, 0u};
+            blockDim = dim3((unsigned)nt);
+            gridDim = dim3(1u);
+            g_cta_barrier = &bar;
+            for (uint32_t t = 0; t < (uint32_t)a.tiles; ++t) {
+                mix_tile<V, LINES>(a, s, t);
+                __syncthreads();
+            }
+        });
+    for (auto& t : th) t.join();
+}
+
 template <typename V> static bool dispatch(const HostStep& st) {
+    if (st.a.mix_nr > 0) {
+        if constexpr (std::is_same<V, dfloat2>::value) {
+            return false;
+        } else {
+            if (st.lines)
+                run_mix<V, true>(st.a);
+            else
+                run_mix<V, false>(st.a);
+            return true;
+        }
+    }
     switch (st.M) {
         case 2: return pass_m<V, 2>(st);
         case 3: return pass_m<V, 3>(st);

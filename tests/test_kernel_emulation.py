@@ -10,7 +10,8 @@ So the whole convolution path, apart from the launch and the hardware, is
 checked on the CPU: complex FP32, FP64 and double-float, 1-D to 3-D, rows
 and lines passes, fused single-group plans, external twiddles (a group cap
 that splits an axis), the plane pass with one CTA per plane (complex FP32
-and FP64), and the compiled groups spanning prime bases (48, 120, 1000).  Results against the oracle (O2, separable
+and FP64), the compiled groups spanning prime bases (48, 120, 1000) and the
+runtime-radix kernel of the other groups spanning bases.  Results against the oracle (O2, separable
 filters) within the GPU tests' tolerances.
 
 PAC_EMULATE_SANITIZE=1 in the environment builds the emulator with
@@ -108,6 +109,22 @@ def test_emulated_compiled_mixed_groups_match_the_oracle(emulate, dims, dtype):
     y = emulate(dims, 0, dtype, 0, h, x, flags=2)
     err = oracle.rel_l2(y, oracle.conv_separable(fs, x))
     assert err <= tol(dtype, int(np.prod(dims))), f"mixed {dims} {dtype}: rel_l2 {err:.3e}"
+
+
+RUNTIME_CASES = [((60, 90), "c64"), ((360,), "c128"), ((12, 20, 30), "c64"), ((2000,), "c64"), ((240, 6), "c128")]
+
+
+@pytest.mark.parametrize("dims,dtype", RUNTIME_CASES, ids=[f"{'x'.join(map(str, d))}-{t}" for d, t in RUNTIME_CASES])
+def test_emulated_runtime_radix_kernel_matches_the_oracle(emulate, dims, dtype):
+    """Every group spanning prime bases in the runtime-radix kernel (as
+    PAC_MIXED=rt), against the oracle."""
+    seed = 53 + dims[0]
+    fs = [pin.complex_uniform((n,), seed + 100 + a) for a, n in enumerate(dims)]
+    h = pin.as_dtype(pin.outer(fs), dtype)
+    x = pin.as_dtype(pin.complex_uniform(dims, seed), dtype)
+    y = emulate(dims, 0, dtype, 0, h, x, flags=4)
+    err = oracle.rel_l2(y, oracle.conv_separable(fs, x))
+    assert err <= tol(dtype, int(np.prod(dims))), f"runtime radix {dims} {dtype}: rel_l2 {err:.3e}"
 
 
 @pytest.mark.parametrize("dims,radix,dtype", PLANE_CASES, ids=[f"{'x'.join(map(str, d))}-r{r}-{t}" for d, r, t in PLANE_CASES])
