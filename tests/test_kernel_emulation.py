@@ -19,6 +19,8 @@ AddressSanitizer and UndefinedBehaviorSanitizer (about ten minutes of
 compilation): every access of the kernels' code to the arrays, tables and
 exchange buffer is then checked on the CPU.
 """
+import glob
+import hashlib
 import math
 import os
 import shutil
@@ -50,16 +52,26 @@ def emulate():
         pytest.skip("needs g++ and the CUDA headers")
     from paper_2506_12718_gb300 import _build
     _build.build()
-    exe = os.path.join(tempfile.mkdtemp(), "emulate")
     sanitize = os.environ.get("PAC_EMULATE_SANITIZE") == "1"
     san = ["-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=undefined"] if sanitize else []
     env = dict(os.environ, ASAN_OPTIONS="detect_leaks=0") if sanitize else None
-    r = subprocess.run(["g++", "-O1"] + san + ["-std=c++20", "-ffp-contract=off", "-pthread", "-I", CUDA_INC, "-I",
-                        os.path.join(ROOT, "include"), "-I", os.path.join(PKG, "csrc"),
-                        os.path.join(ROOT, "tests", "c", "emulate.cpp"), "-L", PKG, "-lpac", "-Wl,-rpath," + PKG,
-                        "-o", exe], capture_output=True, text=True)
-    if r.returncode:
-        pytest.fail("emulator build failed:\n" + r.stderr[-2000:])
+    # the emulator is rebuilt only when its sources change (it links libpac.so at run time)
+    h = hashlib.sha256(" ".join(san).encode())
+    srcs = [os.path.join(ROOT, "tests", "c", "emulate.cpp"), os.path.join(ROOT, "include", "pac.h")]
+    srcs += sorted(glob.glob(os.path.join(PKG, "csrc", "*.cuh")) + glob.glob(os.path.join(PKG, "csrc", "*.h")))
+    for f in srcs:
+        h.update(open(f, "rb").read())
+    cache = os.path.join(PKG, "_build")
+    os.makedirs(cache, exist_ok=True)
+    exe = os.path.join(cache, "emulate_" + h.hexdigest()[:16])
+    if not os.path.exists(exe):
+        tmp = exe + ".tmp%d" % os.getpid()
+        r = subprocess.run(["g++", "-O1"] + san + ["-std=c++20", "-ffp-contract=off", "-pthread", "-I", CUDA_INC, "-I",
+                            os.path.join(ROOT, "include"), "-I", os.path.join(PKG, "csrc"), srcs[0], "-L", PKG,
+                            "-lpac", "-Wl,-rpath," + PKG, "-o", tmp], capture_output=True, text=True)
+        if r.returncode:
+            pytest.fail("emulator build failed:\n" + r.stderr[-2000:])
+        os.replace(tmp, exe)
 
     def run(dims, radix, dtype, cap, h, x, flags=0):
         d = tempfile.mkdtemp()
